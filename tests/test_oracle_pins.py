@@ -1,0 +1,397 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against brute force on tiny inputs, a closed form,
+an invariant, a library routine computing the same textbook operation by a
+different formulation, or a value the paper prints (tests/golden/).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+import synth
+from oracle import omniseg_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_params.json")
+F64 = torch.float64
+
+
+def rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- padding, pyramid
+
+
+def test_pad_colour_is_rounded_2x2_mean():
+    img = np.zeros((4, 4, 3), np.uint8)
+    img[0, 0] = (10, 0, 255)
+    img[0, 1] = (11, 1, 255)
+    img[1, 0] = (12, 2, 254)
+    img[1, 1] = (13, 2, 254)
+    # sums 46, 5, 1018 -> means 11.5, 1.25, 254.5 -> round half up 12, 1, 255
+    assert O.pad_colour(img).tolist() == [12, 1, 255]
+
+
+def test_padded_dims_cover_every_scale_grid():
+    for w in (synth.TINY, synth.NEEDLE, synth.DIFF, synth.LARGE):
+        Hp, Wp, lead = O.padded_dims(w)
+        for f in w.factors:
+            for d in (Hp, Wp):
+                assert d % f == 0 and (d // f - w.P) % w.S == 0 and d // f >= w.P
+        assert Hp % synth.THUMB == 0 and Wp % synth.THUMB == 0
+    # needle / large need no padding (their sizes already sit on the grid)
+    assert O.padded_dims(synth.NEEDLE)[:2] == (16384, 49152)
+    assert O.padded_dims(synth.LARGE)[:2] == (32768, 98304)
+    # a ragged size is extended, and the paper's 4096 border adds to both sides
+    w = synth.NEEDLE.with_(H=5000, W=9000)
+    assert O.padded_dims(w)[:2] == (6144, 10240)
+    w2 = w.with_(pad_lead=4096)
+    Hp, Wp, lead = O.padded_dims(w2)
+    assert lead == 4096 and Hp >= 5000 + 8192 and Wp >= 9000 + 8192
+
+
+def test_pad_slide_places_image_and_colour():
+    w = synth.NEEDLE.with_(H=300, W=700, pad_lead=64, S=64, P=128)
+    img = rng().integers(0, 256, (300, 700, 3)).astype(np.uint8)
+    c = O.pad_slide(img, w)
+    assert np.array_equal(c[64:364, 64:764], img)
+    col = O.pad_colour(img)
+    assert (c[:64] == col).all() and (c[364:] == col).all() and (c[:, 764:] == col).all()
+
+
+def test_half_brute_force_and_constant():
+    img = rng(1).integers(0, 256, (6, 8, 3)).astype(np.uint8)
+    h = O.half(img)
+    for i in range(3):
+        for j in range(4):
+            for c in range(3):
+                s = sum(int(img[2 * i + a, 2 * j + b, c]) for a in (0, 1) for b in (0, 1))
+                assert h[i, j, c] == (s + 2) // 4
+    const = np.full((64, 64, 3), 201, np.uint8)
+    for p in O.pyramid(const, (1, 2, 4, 8)):
+        assert (p == 201).all()
+    assert [p.shape[0] for p in O.pyramid(const, (1, 4, 8))] == [64, 16, 8]
+
+
+# ---------------------------------------------------------------- tissue detection
+
+
+def test_thumbnail_and_grey_closed_forms():
+    canvas = rng(2).integers(0, 256, (64, 96, 3)).astype(np.uint8)
+    t = O.thumbnail(canvas)
+    assert t.shape == (2, 3, 3)
+    blk = canvas[32:64, 64:96, 1].astype(np.int64).sum()
+    assert t[1, 2, 1] == (blk + 512) // 1024
+    assert O.grey(np.array([[[255, 255, 255]]], np.uint8))[0, 0] == 255
+    assert O.grey(np.array([[[0, 0, 0]]], np.uint8))[0, 0] == 0
+    assert O.grey(np.array([[[100, 50, 200]]], np.uint8))[0, 0] == (7700 + 7500 + 5800 + 128) >> 8
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 7])
+def test_median_blur_brute_force_and_scipy(k):
+    scipy_nd = pytest.importorskip("scipy.ndimage")
+    img = rng(k).integers(0, 256, (9, 11)).astype(np.uint8)
+    m = O.median_blur(img, k)
+    r = k // 2
+    pad = np.pad(img, r, mode="edge")
+    for i in range(9):
+        for j in range(11):
+            assert m[i, j] == int(np.median(pad[i:i + k, j:j + k]))
+    assert np.array_equal(m, scipy_nd.median_filter(img, size=k, mode="nearest"))
+
+
+def _otsu_float(hist):
+    """Textbook Otsu: maximise w0 w1 (mu0 - mu1)^2 over t, first max wins."""
+    h = np.asarray(hist, np.float64)
+    N = h.sum()
+    lev = np.arange(256)
+    best, bt = -1.0, -1
+    for t in range(256):
+        w0 = h[:t + 1].sum() / N
+        w1 = 1.0 - w0
+        if h[:t + 1].sum() == 0 or h[:t + 1].sum() == N:
+            continue
+        mu0 = (lev[:t + 1] * h[:t + 1]).sum() / h[:t + 1].sum()
+        mu1 = (lev[t + 1:] * h[t + 1:]).sum() / h[t + 1:].sum()
+        v = w0 * w1 * (mu0 - mu1) ** 2
+        if v > best * (1 + 1e-12):
+            best, bt = v, t
+    return bt
+
+
+def test_otsu_two_levels_and_textbook():
+    h = np.zeros(256, np.int64)
+    h[60] = 700
+    h[230] = 300
+    t = O.otsu(h)
+    assert 60 <= t < 230
+    assert t == 60            # every t in [60, 229] gives the same split; smallest wins
+    for s in range(20):
+        hh = rng(100 + s).integers(0, 50, 256)
+        hh[rng(200 + s).integers(0, 256, 100)] = 0
+        assert O.otsu(hh) == _otsu_float(hh)
+    assert O.otsu(np.eye(256, dtype=np.int64)[17] * 1000) == -1     # one level: no split
+
+
+def test_tissue_mask_finds_dark_blobs():
+    img = np.full((256, 256, 3), 235, np.uint8)
+    img[64:192, 32:128] = (150, 90, 170)
+    mask, t, _, _ = O.tissue_mask(img, 3)
+    assert mask.shape == (8, 8)
+    # a 3x3 median removes the block's corners (4 of 9 window pixels) only
+    assert mask[3:5, 1:4].all() and mask[2:6, 2].all() and not mask[:, 5:].any()
+    assert not mask[2, 1] and not mask[5, 3]
+
+
+# ---------------------------------------------------------------- tiling
+
+
+def test_tile_counts_closed_form():
+    for w, expect in ((synth.TINY, [49]), (synth.NEEDLE, [63 * 191, 15 * 47, 7 * 23]),
+                      (synth.DIFF, [225, 9, 1]), (synth.LARGE, [63 * 191, 15 * 47, 7 * 23])):
+        Hp, Wp, _ = O.padded_dims(w)
+        got = [int(np.prod(O.grid(w, Hp, Wp, s))) for s in range(w.n_scales)]
+        assert got == expect, (w.name, got)
+    assert sum([63 * 191, 15 * 47, 7 * 23]) == 12899
+
+
+def test_tile_list_foreground_brute_force():
+    w = synth.NEEDLE.with_(H=2048, W=4096, P=512, S=256, tissue_filter=True)
+    Hp, Wp, _ = O.padded_dims(w)
+    mask = np.zeros((Hp // 32, Wp // 32), bool)
+    mask[10, 70] = True          # 40x pixel rows 320..351, cols 2240..2271
+    tiles, flags = O.tile_list(w, mask, Hp, Wp)
+    for s, f in enumerate(w.factors):
+        ny, nx = O.grid(w, Hp, Wp, s)
+        for i in range(ny):
+            for j in range(nx):
+                y0, x0 = i * w.S * f, j * w.S * f         # 40x footprint
+                y1, x1 = y0 + w.P * f, x0 + w.P * f
+                hit = y0 <= 320 < y1 and x0 <= 2240 < x1
+                assert flags[s][i, j] == hit
+    assert tiles == sorted(tiles)
+    assert all(flags[s][y // w.S, x // w.S] for (s, y, x) in tiles)
+
+
+# ---------------------------------------------------------------- network pieces
+
+
+def test_conv3x3_brute_force():
+    x = torch.from_numpy(rng(3).standard_normal((2, 3, 5, 6)))
+    w = torch.from_numpy(rng(4).standard_normal((4, 3, 3, 3)))
+    y = O.conv3x3(x, w)
+    for b in range(2):
+        for o in range(4):
+            for i in range(5):
+                for j in range(6):
+                    s = 0.0
+                    for c in range(3):
+                        for dy in range(3):
+                            for dx in range(3):
+                                ii, jj = i + dy - 1, j + dx - 1
+                                if 0 <= ii < 5 and 0 <= jj < 6:
+                                    s += float(w[o, c, dy, dx]) * float(x[b, c, ii, jj])
+                    assert abs(float(y[b, o, i, j]) - s) < 1e-12
+
+
+def test_conv_matches_library_conv2d():
+    x = torch.from_numpy(rng(5).standard_normal((2, 16, 12, 10)))
+    w = torch.from_numpy(rng(6).standard_normal((8, 16, 3, 3)))
+    torch.testing.assert_close(O.conv3x3(x, w), F.conv2d(x, w, padding=1), rtol=0, atol=1e-12)
+    wp = torch.from_numpy(rng(7).standard_normal((8, 16)))
+    torch.testing.assert_close(O.conv1x1(x, wp), F.conv2d(x, wp[:, :, None, None]),
+                               rtol=0, atol=1e-12)
+
+
+def test_upsample_bilinear_library_and_constant():
+    x = torch.from_numpy(rng(8).standard_normal((2, 3, 4, 5)))
+    ref = F.interpolate(x, scale_factor=2, mode="bilinear", align_corners=False)
+    torch.testing.assert_close(O.upsample2(x), ref, rtol=0, atol=1e-14)
+    c = torch.full((1, 2, 6, 6), 3.25, dtype=F64)
+    assert torch.equal(O.upsample2(c), torch.full((1, 2, 12, 12), 3.25, dtype=F64))
+    # interior weights 0.25 / 0.75
+    v = torch.arange(4, dtype=F64).reshape(1, 1, 1, 4).expand(1, 1, 2, 4).contiguous()
+    u = O.upsample2(v)[0, 0, 0]
+    assert u.tolist() == [0.0, 0.25, 0.75, 1.25, 1.75, 2.25, 2.75, 3.0]
+
+
+def test_maxpool_library():
+    x = torch.from_numpy(rng(9).standard_normal((2, 3, 8, 6)))
+    torch.testing.assert_close(O.maxpool2(x), F.max_pool2d(x, 2), rtol=0, atol=0)
+
+
+def _torch_unet(v, p, levels):
+    """Independent model from standard torch layers (conv2d / interpolate / max_pool2d)."""
+    def block(x, pre):
+        a = F.relu(F.conv2d(x, p[pre + ".w1"], padding=1) * p[pre + ".g1"].view(1, -1, 1, 1)
+                   + p[pre + ".b1"].view(1, -1, 1, 1))
+        z = (F.conv2d(a, p[pre + ".w2"], padding=1) * p[pre + ".g2"].view(1, -1, 1, 1)
+             + p[pre + ".b2"].view(1, -1, 1, 1))
+        return F.relu(z + F.conv2d(x, p[pre + ".wp"][:, :, None, None]))
+    skips, x = [], v
+    for l in range(levels):
+        y = block(x, f"enc{l}")
+        skips.append(y)
+        x = F.max_pool2d(y, 2)
+    y = skips[-1]
+    for l in range(levels - 2, -1, -1):
+        y = block(torch.cat([F.interpolate(y, scale_factor=2, mode="bilinear",
+                                           align_corners=False), skips[l]], 1), f"dec{l}")
+    return y, skips[-1]
+
+
+def test_unet_matches_independent_torch_model():
+    w = synth.TINY
+    p = O.weights_f64(w, synth.gen_weights(w))
+    patch = rng(10).integers(0, 256, (2, 32, 32, 3)).astype(np.uint8)
+    v = O.normalise(patch)
+    y0, bott, _ = O.unet(v, p, w.levels)
+    r0, rb = _torch_unet(v, p, w.levels)
+    torch.testing.assert_close(y0, r0, rtol=0, atol=1e-10)
+    torch.testing.assert_close(bott, rb, rtol=0, atol=1e-10)
+    assert float(v.min()) >= -1.0 and float(v.max()) <= 1.0
+    assert torch.equal(O.normalise(np.array([[[0, 255, 51]]], np.uint8))[:, 0, 0],
+                       torch.tensor([-1.0, 1.0, -0.6], dtype=F64))
+
+
+def test_one_hot_controller_reproduces_explicit_head():
+    """With the GAP columns of Wc zeroed, theta is the sum of the class column,
+    the scale column and the bias; the dynamic head must equal three explicit
+    1x1 convolutions built from those numbers."""
+    w = synth.NEEDLE
+    p = O.weights_f64(w, synth.gen_weights(w))
+    Cb = w.widths[-1]
+    p = dict(p)
+    wc = p["ctrl.w"].clone()
+    wc[:, :Cb] = 0.0
+    p["ctrl.w"] = wc
+    p["ctrl.b"] = torch.from_numpy(rng(11).standard_normal(153))
+    g = torch.from_numpy(rng(12).standard_normal((3, Cb)))
+    h0 = torch.from_numpy(rng(13).standard_normal((3, 8, 7, 9)))
+    for cls, scl in ((0, 0), (3, 1), (5, 2)):
+        theta = O.controller(g, cls, scl, p, w.n_classes, w.n_scales)
+        col = wc[:, Cb + cls] + wc[:, Cb + w.n_classes + scl] + p["ctrl.b"]
+        torch.testing.assert_close(theta, col[None].expand(3, -1), rtol=0, atol=0)
+        W1 = col[0:64].reshape(8, 8)
+        W2 = col[64:128].reshape(8, 8)
+        W3 = col[128:136].reshape(1, 8)
+        b1, b2, b3 = col[136:144], col[144:152], col[152:153]
+        ref = F.conv2d(h0, W1[:, :, None, None], b1).relu()
+        ref = F.conv2d(ref, W2[:, :, None, None], b2).relu()
+        ref = F.conv2d(ref, W3[:, :, None, None], b3)[:, 0]
+        torch.testing.assert_close(O.dynamic_head(h0, theta), ref, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- stitching, labels
+
+
+def test_stitch_reconstructs_known_canvas_exactly():
+    hs, ws, P, S = 96, 128, 32, 16
+    canvas = rng(14).integers(-512, 512, (hs, ws)) / 64.0       # dyadic: sums are exact
+    tiles = {(y, x): canvas[y:y + P, x:x + P].copy()
+             for y in range(0, hs - P + 1, S) for x in range(0, ws - P + 1, S)}
+    L, cov, votes = O.stitch(tiles, hs, ws, P)
+    assert np.array_equal(L, canvas)
+    # interior coverage is (P/S)^2; corners 1
+    assert cov[40, 40] == 4 and cov[0, 0] == 1 and cov[0, 40] == 2
+    # votes brute force
+    for (yy, xx) in ((5, 5), (40, 60), (95, 127)):
+        v = sum(1 for (y, x), t in tiles.items()
+                if y <= yy < y + P and x <= xx < x + P and t[yy - y, xx - x] > 0)
+        assert votes[yy, xx] == v
+
+
+def test_stitch_constant_field_and_missing_tiles():
+    tiles = {(0, 0): np.full((8, 8), 2.5), (0, 4): np.full((8, 8), 2.5)}
+    L, cov, _ = O.stitch(tiles, 12, 12, 8)
+    assert (L[:8, :12] == 2.5).all() and (L[8:] == 0).all() and (cov[8:] == 0).all()
+
+
+def test_overlap_counts_match_paper():
+    g = json.load(open(GOLDEN))
+    P = g["tile_size"]["value"]
+    for stride, overlaps, thr in ((g["stride_40x"]["value"], g["overlaps_40x"]["value"],
+                                   g["vote_threshold_40x"]["value"]),
+                                  (g["stride_10x_5x"]["value"], g["overlaps_10x_5x"]["value"],
+                                   g["vote_threshold_10x_5x"]["value"])):
+        n = 8 * P // stride
+        tiles = {(0, x): np.ones((P, P)) for x in range(0, n * stride - P + 1, stride)}
+        _, cov, _ = O.stitch(tiles, P, n * stride, P)
+        assert cov[0, n * stride // 2] == overlaps          # one axis: P / S tiles
+        # the vote reading "at least half" gives the paper's thresholds
+        assert (overlaps + 1) // 2 == thr
+
+
+def test_labels_modes_and_argmax():
+    L = np.array([[0.0, 1e-9, -1.0, 2.0]])
+    cov = np.array([[1, 1, 0, 3]])
+    votes = np.array([[0, 1, 0, 1]])
+    assert O.labels(L, cov, votes, synth.STITCH_AVG).tolist() == [[0, 1, 0, 1]]
+    assert O.labels(L, cov, votes, synth.STITCH_VOTE).tolist() == [[0, 1, 0, 0]]
+    tis = np.array([[True, False, True, True]])
+    assert O.labels(L, cov, votes, synth.STITCH_AVG, tis).tolist() == [[0, 0, 0, 1]]
+    a = O.argmax_map([np.array([[1.0, -1.0, 2.0]]), np.array([[1.0, -2.0, 3.0]])], [4, 5])
+    assert a.tolist() == [[5, 0, 6]]
+
+
+# ---------------------------------------------------------------- loss, gradient
+
+
+def test_dice_bce_closed_form():
+    n = 10
+    L = torch.zeros(n, dtype=F64)
+    g = torch.ones(n, dtype=F64)
+    v = O.dice_bce(L, g)
+    dice = 1 - (2 * 0.5 * n + 1) / (0.5 * n + n + 1)
+    assert abs(float(v) - (dice + math.log(2))) < 1e-14
+    L = torch.tensor([-3.0, 0.5, 2.0, 7.0], dtype=F64)
+    g = torch.tensor([0.0, 1.0, 0.0, 1.0], dtype=F64)
+    s = torch.sigmoid(L)
+    naive = (-(g * torch.log(s) + (1 - g) * torch.log(1 - s))).mean()
+    dice = 1 - (2 * (s * g).sum() + 1) / (s.sum() + g.sum() + 1)
+    assert abs(float(O.dice_bce(L, g)) - float(naive + dice)) < 1e-14
+
+
+@pytest.mark.slow
+def test_gradient_matches_central_differences():
+    w = synth.small_variant(synth.DIFF, H=256, W=256, P=64, S=32, base=4, levels=3,
+                            max_batch=16)
+    rgb = synth.gen_slide(synth.spec_for(w))
+    gts = synth.gen_gt_masks(w.H, w.W, w.factors, w.class_scale, seed=7)
+    prob = O.DiffProblem(rgb, w, synth.gen_weights(w), gts)
+    loss, grads = prob.loss_and_grads()
+    base = prob.params()
+    r = rng(8)
+    eps = 1e-6
+    names = list(base)
+    checked = 0
+    for trial in range(48):
+        name = names[trial % len(names)]
+        idx = tuple(int(r.integers(0, s)) for s in base[name].shape)
+        qp = {k: v.clone() for k, v in base.items()}
+        qm = {k: v.clone() for k, v in base.items()}
+        qp[name][idx] += eps
+        qm[name][idx] -= eps
+        with torch.no_grad():
+            fd = (float(prob.loss(qp)) - float(prob.loss(qm))) / (2 * eps)
+        an = float(grads[name][idx])
+        scale = max(abs(fd), 1e-6 * float(grads[name].abs().max()), 1e-9)
+        assert abs(an - fd) / scale < 1e-4, (name, idx, an, fd)
+        checked += 1
+    assert checked == 48
+
+
+# ---------------------------------------------------------------- input generator
+
+
+def test_generator_windows_are_consistent():
+    spec = synth.make_spec(300, 500, 5, 0.4, "cores", 3)
+    full = synth.gen_slide(spec)
+    assert np.array_equal(synth.gen_window(spec, 37, 111, 50, 70), full[37:87, 111:181])
+    bg = full[full.min(axis=2) > 225]
+    assert abs(bg.mean() - 235) < 2 and bg.std() > 3
