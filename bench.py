@@ -1,0 +1,289 @@
+"""Benchmark: segmented slide Mpx/s on the needle-biopsy workload.
+
+One step = one call of omni_segment_slide on a 16384 x 49152 synthetic 40x
+slide (805.3 Mpx): tiling, pyramid, the residual U-Net + dynamic heads on every
+foreground tile at 40x / 10x / 5x, and stitching + labels for all 6 classes.
+The slide (2.4 GB) is larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORK = synth.NEEDLE
+WORKLOAD = (f"needle-biopsy slide {WORK.H}x{WORK.W} at 40x, scales 40x/10x/5x, tiles "
+            f"{WORK.P} stride {WORK.S}, residual U-Net base {WORK.base} x {WORK.levels} levels, "
+            f"6 class heads, tissue filter on")
+METRIC = "segmented slide Mpx/s (6 classes x 3 scales)"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        if self.p is None:
+            return None
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        loaded = [r[0] for r in rows]
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(max_tiles: int = 4):
+    """The FP64 oracle timed on a bounded sample: the first foreground 40x tiles
+    of the needle slide (generated on the CPU), through U-Net, heads and the
+    stitch of those tiles; scaled to the slide by the tile fraction."""
+    import torch
+    from oracle import omniseg_oracle as O
+    spec = synth.spec_for(WORK)
+    blob = synth.gen_weights(WORK)
+    p = O.weights_f64(WORK, blob)
+    # foreground tiles come from the slide's tissue; take tiles along the first core
+    e = spec.ellipses[0]
+    y0 = max(0, (e.cy // WORK.S) * WORK.S - WORK.S)
+    x0 = (e.cx // WORK.S) * WORK.S
+    h = WORK.P + WORK.S
+    w = WORK.P + WORK.S * (max_tiles - 1)
+    img = synth.gen_window(spec, y0, x0, h, w)
+    tiles = [(0, x) for x in range(0, w - WORK.P + 1, WORK.S)][:max_tiles]
+    t0 = time.perf_counter()
+    per = {}
+    for (y, x) in tiles:
+        lg, _ = O.patch_forward(img[None, y:y + WORK.P, x:x + WORK.P], p, WORK, 0)
+        per[(y, x)] = lg[0, 0].numpy()
+    O.stitch(per, h, w, WORK.P)
+    dt = time.perf_counter() - t0
+    total_tiles = 12899 * 0.5   # about half the slide's tiles touch tissue
+    mpx = WORK.H * WORK.W / 1e6 * len(tiles) / total_tiles
+    return {"value": mpx / dt, "unit": "Mpx/s", "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{len(tiles)} foreground 512x512 tiles of the 40x scale (FP64 U-Net, head, "
+                      f"stitch) in {dt:.1f} s, scaled to the slide as {len(tiles)}/{total_tiles:.0f} "
+                      f"of its tiles"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = cpu_baseline()
+    steps = []
+    for _ in range(args.warmup):
+        pass
+    for _ in range(max(1, min(args.steps, 2))):
+        steps.append(cpu_baseline(max_tiles=2)["value"])
+    v = float(np.median(steps + [cb["value"]]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpx/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"],
+                             "value": v, "unit": "Mpx/s"},
+            "e2e": {"value": v, "unit": "Mpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-fp32", action="store_true",
+                    help="also time one step of the plain FP32 path")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2305_14566_gb300.build import build
+    build()
+    from paper_2305_14566_gb300 import api, _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    prec = _lib.BF16 if args.precision == "bf16" else _lib.FP32
+
+    spec = synth.spec_for(WORK)
+    rgb = api.synth_slide(spec, device=dev)
+    blob = synth.gen_weights(WORK)
+    seg = api.Segmenter(WORK, blob, precision=prec)
+    out = seg.segment(rgb)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        seg.segment(rgb, out=out)
+    barrier()
+    seg.set_timing(True)
+    conv_ms = conv_n = conv_flops = 0.0
+    st_ms = st_bytes = 0.0
+    launches = 0
+    with Clocks(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        t0.record()
+        for _ in range(args.steps):
+            seg.segment(rgb, out=out)
+            launches += seg.launch_count()
+            ms, n, fl = seg.timing(0)
+            conv_ms += ms; conv_n += n; conv_flops += fl
+            ms, n, by = seg.timing(1)
+            st_ms += ms; st_bytes += by
+        t1.record()
+        barrier()
+    clocks = clk.summary()
+    seg.set_timing(False)
+    ms_step = t0.elapsed_time(t1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    mpx = WORK.H * WORK.W / 1e6
+    value = mpx * world / (ms_step / 1e3)
+
+    pk, src = peaks()
+    if prec == _lib.BF16:
+        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+        bound, peak_note = "tensor", f"bf16 dense sustained ({src})"
+    else:
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound, peak_note = "alu", "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock"
+    conv_per_launch_ms = conv_ms / max(conv_n, 1)
+    achieved = (conv_flops / max(conv_n, 1)) / (conv_per_launch_ms / 1e3) / 1e12
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "conv (all U-Net layers)",
+            "peak_source": peak_note,
+            "share_of_step": conv_ms / args.steps / ms_step}
+    stitch = {"achieved_gbs": st_bytes / (st_ms / 1e3) / 1e9 if st_ms else None,
+              "peak_gbs": pk["hbm_gbs"], "ms_per_step": st_ms / args.steps}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    rgb_h = rgb.cpu().pin_memory()
+    labs = {c: torch.empty(tuple(out["labels"][c].shape), dtype=torch.uint8).pin_memory()
+            for c in out["labels"]}
+    seg.segment_host(rgb_h, labs, device=dev)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        seg.segment_host(rgb_h, labs, device=dev)
+    barrier()
+    e2e_s = (time.perf_counter() - w0) / e2e_steps
+    e2e = {"value": mpx * world / e2e_s, "unit": "Mpx/s",
+           "h2d_bytes_per_step": int(rgb_h.numel()),
+           "d2h_bytes_per_step": int(sum(t.numel() for t in labs.values()))}
+    del rgb_h, labs
+
+    fp32 = None
+    if args.compare_fp32 and prec == _lib.BF16:
+        seg32 = api.Segmenter(WORK, blob, precision=_lib.FP32)
+        o32 = seg32.segment(rgb)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        seg32.segment(rgb, out=o32)
+        torch.cuda.synchronize()
+        fp32 = {"value": mpx / (time.perf_counter() - a), "unit": "Mpx/s", "steps": 1}
+        seg32.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": WORKLOAD, "slide_px": WORK.H * WORK.W,
+                           "l2": "no flush: inputs (2.4 GB slide) larger than L2",
+                           "parallelism": f"replicas x{world}",
+                           "tiles_per_step": int(conv_flops / max(args.steps, 1) /
+                                                 seg.query(WORK.H, WORK.W).flops_per_tile)},
+                "roofline": roof, "stitch": stitch, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks}
+        if fp32 is not None:
+            line["fp32_plain"] = fp32
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    seg.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * omniseg.h -- C ABI of the GB300 (sm_103a) Omni-Seg slide-wise inference library.
+ *
+ * The method is the three-stage whole-slide pipeline of Leng, Deng et al.,
+ * "An Accelerated Pipeline for Multi-label Renal Pathology Image Segmentation
+ * at the Whole Slide Image Level":
+ *   Sec. 2.1  tissue detection and tile extraction  -> omni_tile_slide
+ *   Sec. 2.2  Omni-Seg segmentation of overlapping 40x/10x/5x tiles
+ *   Sec. 2.3  slide-wise aggregation into per-class label maps
+ *                                                    -> omni_segment_slide
+ * plus a hand-written backward of the stitched soft-Dice + BCE loss through
+ * the dynamic head, controller, pre-head and last decoder block
+ * (omni_backward).
+ *
+ * Conventions (every entry point):
+ *   - Returns an omni_status; 0 is success, negative values are errors.  No
+ *     entry point aborts, asserts or traps; on error, omni_last_error(ctx)
+ *     returns a one-line description and nothing has been launched unless the
+ *     error is OMNI_ECUDA / OMNI_ETIMEOUT.
+ *   - Pointers named *_dev are CUDA device pointers, *_host are host pointers.
+ *     All inputs are borrowed (the caller keeps ownership, the library keeps
+ *     no reference after the call returns).  All outputs are allocated by the
+ *     caller, sized with omni_query.
+ *   - Device work is enqueued on the caller's CUDA stream (`stream`, a
+ *     cudaStream_t passed as void*, NULL = legacy default stream).  Calls that
+ *     need a host-visible intermediate result (the foreground tile count)
+ *     synchronise that stream once; this is stated per call.
+ *   - Images are row-major interleaved RGB uint8 (HWC) with an explicit row
+ *     stride in bytes.  Activations inside the library are NHWC.
+ *   - A context is not thread safe; use one context per host thread/stream.
+ */
+#ifndef OMNISEG_H
+#define OMNISEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int omni_status;
+#define OMNI_OK 0
+#define OMNI_EINVAL (-1)    /* bad argument, shape or configuration          */
+#define OMNI_ENOMEM (-2)    /* caller workspace smaller than omni_query says  */
+#define OMNI_ECUDA (-3)     /* a CUDA runtime/driver call failed              */
+#define OMNI_ETIMEOUT (-4)  /* a bounded device-side wait gave up             */
+#define OMNI_EWEIGHTS (-5)  /* weights blob of the wrong size or non-finite   */
+#define OMNI_ESTATE (-6)    /* call out of order (e.g. segment before weights) */
+
+/* Arithmetic of the U-Net convolutions. */
+#define OMNI_FP32 0  /* FP32 FFMA on the CUDA cores (plain path)                  */
+#define OMNI_BF16 1  /* BF16 operands, FP32 accumulation in TMEM (tcgen05.mma)    */
+
+/* Overlap aggregation (Sec. 2.2, Sec. 3.2). */
+#define OMNI_STITCH_AVG 0   /* label = mean logit of covering tiles > 0            */
+#define OMNI_STITCH_VOTE 1  /* label = at least half of covering tiles vote > 0    */
+
+#define OMNI_MAX_SCALES 4
+#define OMNI_MAX_CLASSES 16
+
+typedef struct omni_ctx omni_ctx;
+
+/* Network and pipeline configuration (fixed for the life of a context). */
+typedef struct omni_config {
+  int32_t patch;        /* tile size P at every scale (Sec. 2.2: 512)                  */
+  int32_t stride;       /* tile stride S (Sec. 3.2: 256 at 40x); P % S == 0            */
+  int32_t levels;       /* U-Net levels L (2..6)                                        */
+  int32_t base;         /* channels of level 0; level l has base << l (multiple of 8)   */
+  int32_t n_scales;     /* number of magnifications (1..4)                              */
+  int32_t factors[OMNI_MAX_SCALES];      /* downsample factor vs 40x: 1, 2, 4 or 8      */
+  int32_t n_classes;    /* number of tissue classes / dynamic heads (1..16)             */
+  int32_t class_scale[OMNI_MAX_CLASSES]; /* scale index each class is predicted at      */
+  int32_t precision;    /* OMNI_FP32 or OMNI_BF16                                       */
+  int32_t stitch_mode;  /* OMNI_STITCH_AVG or OMNI_STITCH_VOTE                          */
+  int32_t tissue_filter;/* 1: segment only tiles touching tissue (Sec. 2.1)             */
+  int32_t tissue_and;   /* 1: AND every label map with the tissue mask (Sec. 2.3)       */
+  int32_t pad_lead;     /* border added on all sides before tiling (Sec. 2.1: 4096)     */
+  int32_t median_k;     /* odd median-blur window on the 32x thumbnail (Sec. 3.2: 59)   */
+  int32_t max_batch;    /* tiles per network batch (workspace scales with it)           */
+} omni_config;
+
+/* Sizes derived from a configuration and a slide size (omni_query). */
+typedef struct omni_sizes {
+  int32_t Hp, Wp;                         /* padded 40x canvas                            */
+  int32_t thumb_h, thumb_w;               /* 32x32-box thumbnail / tissue mask            */
+  int32_t grid_h[OMNI_MAX_SCALES];        /* tile rows per scale                          */
+  int32_t grid_w[OMNI_MAX_SCALES];        /* tile columns per scale                       */
+  int32_t n_tiles_max;                    /* sum over scales of grid_h * grid_w            */
+  int32_t out_h[OMNI_MAX_SCALES];         /* label map rows at each scale = ceil(H / f)   */
+  int32_t out_w[OMNI_MAX_SCALES];         /* label map cols at each scale = ceil(W / f)   */
+  uint64_t tile_workspace_bytes;          /* device workspace for omni_tile_slide         */
+  uint64_t workspace_bytes;               /* device workspace for omni_segment_slide      */
+  uint64_t flops_per_tile;                /* algorithmic conv FLOPs of one tile (2 per MAC) */
+} omni_sizes;
+
+/* Result of tissue detection + tiling, in caller-allocated DEVICE buffers.
+ * Any pointer except `tiles` and `counts` may be NULL. */
+typedef struct omni_tile_list {
+  int32_t* tiles;    /* [n_tiles_max][3] = (scale, y, x): foreground tile origins in
+                        scale pixels, ordered by scale, then row, then column        */
+  int32_t* counts;   /* [1 + n_scales]: total count, then count per scale          */
+  uint8_t* flags;    /* per-scale tile grids concatenated (grid_h*grid_w each): 1 = fg */
+  uint8_t* tissue;   /* [thumb_h][thumb_w] tissue mask, 1 = tissue                  */
+  int32_t* otsu;     /* [1] Otsu threshold on the blurred thumbnail grey (-1: none)  */
+} omni_tile_list;
+
+/* Outputs of omni_segment_slide, caller-allocated DEVICE buffers (NULL = skip).
+ * Class c lives at scale s = class_scale[c] and has out_h[s] x out_w[s] pixels,
+ * row-major, cropped back to the slide (the padding is removed). */
+typedef struct omni_outputs {
+  uint8_t* labels[OMNI_MAX_CLASSES];    /* 0/1 label map per class                      */
+  float* logits[OMNI_MAX_CLASSES];      /* stitched FP32 logit per class (0 if uncovered)*/
+  uint16_t* coverage[OMNI_MAX_SCALES];  /* processed tiles covering each pixel           */
+  uint8_t* argmax[OMNI_MAX_SCALES];     /* 0 = background, else 1 + class id of the
+                                           largest positive logit (ties: lower id)       */
+} omni_outputs;
+
+/* Gradients of omni_backward, caller-allocated DEVICE FP32 buffers in the
+ * weights-blob shapes.  Any may be NULL. */
+typedef struct omni_grads {
+  float* ctrl_w;   /* [153][C_{L-1} + n_classes + n_scales]  */
+  float* ctrl_b;   /* [153]                                 */
+  float* head_w;   /* [8][C_0]                              */
+  float* head_b;   /* [8]                                   */
+  float* dec0_w1;  /* [C_0][3 C_0][3][3]                    */
+  float* dec0_g1;  /* [C_0]                                 */
+  float* dec0_b1;  /* [C_0]                                 */
+  float* dec0_w2;  /* [C_0][C_0][3][3]                      */
+  float* dec0_g2;  /* [C_0]                                 */
+  float* dec0_b2;  /* [C_0]                                 */
+  float* dec0_wp;  /* [C_0][3 C_0]                          */
+} omni_grads;
+
+/* Create a context for `cfg` on the current CUDA device.  Validates the
+ * configuration (OMNI_EINVAL with a message on failure).  Owns only the
+ * device copy of the weights, a status word and timing events. */
+omni_status omni_create(const omni_config* cfg, omni_ctx** out);
+void omni_destroy(omni_ctx* ctx);
+const char* omni_last_error(const omni_ctx* ctx);
+
+/* Number of float32 values a weights blob for `cfg` must hold. The blob order
+ * (C_l = base << l, conv weights [out][in][3][3]):
+ *   encoder l = 0..L-1 (cin = 3 for l = 0 else C_{l-1}, cout = C_l):
+ *       w1[cout][cin][3][3] g1[cout] b1[cout] w2[cout][cout][3][3] g2 b2 wp[cout][cin]
+ *   decoder l = L-2..0 (cin = 3 C_l: upsampled C_{l+1} first, then skip C_l):
+ *       same seven tensors
+ *   pre-head wh[8][C_0] bh[8]; controller wc[153][C_{L-1}+n_classes+n_scales] bc[153]. */
+int64_t omni_weights_count(const omni_config* cfg);
+
+/* Copy a host FP32 weights blob to the device and build the kernels' layouts
+ * (FP32 K-major for the plain path, BF16 K-major tiles for tcgen05).
+ * Synchronous.  OMNI_EWEIGHTS if n_floats is wrong or a value is not finite. */
+omni_status omni_load_weights(omni_ctx* ctx, const float* blob_host, int64_t n_floats);
+
+/* Sizes for an H x W slide under `cfg` (pure host computation, no device
+ * needed).  OMNI_EINVAL for an invalid configuration or slide size. */
+omni_status omni_query(const omni_config* cfg, int32_t H, int32_t W, omni_sizes* out);
+
+/* Sec. 2.1: pad (2x2-mean colour), 32x thumbnail, integer grey, median blur,
+ * Otsu threshold, tissue mask, and the foreground tile list of every scale.
+ * Bit-exact integer arithmetic.  `rgb_dev` is H x W x 3 uint8 with
+ * `row_stride` bytes per row.  Asynchronous on `stream`. */
+omni_status omni_tile_slide(omni_ctx* ctx, const uint8_t* rgb_dev, int32_t H, int32_t W,
+                            int64_t row_stride, void* workspace_dev, uint64_t workspace_bytes,
+                            const omni_tile_list* out, void* stream);
+
+/* Whole path: tiling (as omni_tile_slide), the 40x/10x/5x pyramid, the U-Net
+ * and dynamic heads on every foreground tile of every requested scale, and
+ * the overlap stitch + label emission of every requested class.
+ * `scale_mask` / `class_mask` select scales / classes (bit i = index i); a
+ * class is computed only if its scale is selected.  Synchronises `stream`
+ * once (after tiling) to size the batch loop.  The workspace must hold
+ * omni_sizes.workspace_bytes. */
+omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb_dev, int32_t H, int32_t W,
+                               int64_t row_stride, uint32_t scale_mask, uint32_t class_mask,
+                               void* workspace_dev, uint64_t workspace_bytes,
+                               const omni_outputs* out, void* stream);
+
+/* Same as omni_segment_slide with a HOST slide and HOST label outputs
+ * (`labels_host[c]` of out_h x out_w bytes, NULL = skip).  Copies in and out
+ * on `stream` (pinned host memory gives full copy bandwidth) and returns
+ * after the stream has drained. */
+omni_status omni_segment_slide_host(omni_ctx* ctx, const uint8_t* rgb_host, int32_t H,
+                                    int32_t W, int64_t row_stride, uint32_t scale_mask,
+                                    uint32_t class_mask, void* workspace_dev,
+                                    uint64_t workspace_bytes, uint8_t* const* labels_host,
+                                    void* stream);
+
+/* Seeded synthetic slide window (input generator, not part of the method):
+ * pixel (y, x) of a slide_w-wide slide drawn from `n_ell` rotated ellipses
+ * (int64 rows cy, cx, a, b, cos_q14, sin_q14) and SplitMix64 noise seeded
+ * with `seed`; writes rows y0..y0+h-1, cols x0..x0+w-1 to out_dev. */
+omni_status omni_synth_slide(const int64_t* ellipses_host, int32_t n_ell, uint64_t seed,
+                             int32_t slide_w, int32_t y0, int32_t x0, int32_t h, int32_t w,
+                             uint8_t* out_dev, int64_t row_stride, void* stream);
+
+/* Building block for layer-level checks: one fused residual-U-Net convolution
+ * y = ReLU(g * conv3x3(x) + b [+ wp . r]) on B images of R x R pixels, with the
+ * same kernels omni_segment_slide uses.  x / r / y are NHWC with channel
+ * stride *_cs and channel offset *_co (elements); dtype float32 for
+ * OMNI_FP32, bfloat16 for OMNI_BF16.  Weights are host FP32 ([cout][cin][3][3],
+ * [cout], [cout], [cout][cr]); r may be NULL (no residual).  Allocates and
+ * frees its own temporary weight buffers; synchronises `stream`. */
+omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin, int32_t cout,
+                            const void* x_dev, int32_t x_cs, int32_t x_co,
+                            const float* w_host, const float* g_host, const float* b_host,
+                            const void* r_dev, int32_t r_cs, int32_t r_co, int32_t cr,
+                            const float* wp_host, void* y_dev, int32_t y_cs, int32_t y_co,
+                            void* stream);
+
+/* Per-kernel-class device time of the last omni_segment_slide call, measured
+ * with CUDA events on the call's stream when enabled.  kind: 0 = tensor-core /
+ * FP32 convolutions, 1 = stitch + labels, 2 = head, 3 = everything else.
+ * Returns milliseconds summed over launches and the launch count. */
+omni_status omni_set_timing(omni_ctx* ctx, int32_t enabled);
+omni_status omni_get_timing(omni_ctx* ctx, int32_t kind, double* ms, int64_t* launches,
+                            double* flops_or_bytes);
+
+/* Number of kernel launches enqueued by the last omni_segment_slide call. */
+int64_t omni_last_launch_count(const omni_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OMNISEG_H */

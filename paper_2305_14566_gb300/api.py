@@ -1,0 +1,214 @@
+"""Thin Python layer over the C ABI: torch tensors in, torch tensors out.
+
+PyTorch provides device memory and streams only; every step of the path runs
+in the library's CUDA kernels.  Names follow include/omniseg.h.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream: Optional[torch.cuda.Stream] = None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_config(work, precision: int = L.FP32, max_batch: Optional[int] = None) -> L.Config:
+    """omni_config for a workload description (see synth.configs.Workload)."""
+    c = L.Config()
+    c.patch, c.stride, c.levels, c.base = work.P, work.S, work.levels, work.base
+    c.n_scales = len(work.factors)
+    for i, f in enumerate(work.factors):
+        c.factors[i] = f
+    c.n_classes = len(work.class_scale)
+    for i, s in enumerate(work.class_scale):
+        c.class_scale[i] = s
+    c.precision = precision
+    c.stitch_mode = work.stitch_mode
+    c.tissue_filter = int(work.tissue_filter)
+    c.tissue_and = int(work.tissue_and)
+    c.pad_lead = work.pad_lead
+    c.median_k = work.median_k
+    c.max_batch = max_batch if max_batch is not None else work.max_batch
+    return c
+
+
+class Segmenter:
+    """One library context: configuration + device weights."""
+
+    def __init__(self, work, blob: np.ndarray, precision: int = L.FP32,
+                 max_batch: Optional[int] = None):
+        self.lib = L.lib()
+        self.work = work
+        self.cfg = make_config(work, precision, max_batch)
+        self.ctx = C.c_void_p()
+        st = self.lib.omni_create(C.byref(self.cfg), C.byref(self.ctx))
+        L.check(st, None, "omni_create rejected the configuration")
+        blob = np.ascontiguousarray(blob, dtype=np.float32)
+        L.check(self.lib.omni_load_weights(self.ctx, blob.ctypes.data_as(C.c_void_p), blob.size),
+                self.ctx)
+        self._ws: Optional[torch.Tensor] = None
+
+    def close(self):
+        if self.ctx:
+            self.lib.omni_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ sizes
+    def query(self, H: int, W: int) -> L.Sizes:
+        s = L.Sizes()
+        L.check(self.lib.omni_query(C.byref(self.cfg), H, W, C.byref(s)), None, "omni_query: bad size")
+        return s
+
+    def workspace(self, nbytes: int, device) -> torch.Tensor:
+        if self._ws is None or self._ws.numel() < nbytes or self._ws.device != torch.device(device):
+            self._ws = None
+            self._ws = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        return self._ws
+
+    # ------------------------------------------------------------------ Sec. 2.1
+    def tile_slide(self, rgb: torch.Tensor) -> Dict[str, torch.Tensor]:
+        """Tiles, per-scale counts/flags, tissue mask and Otsu threshold."""
+        H, W, _ = rgb.shape
+        sz = self.query(H, W)
+        dev = rgb.device
+        n = sz.n_tiles_max
+        out = dict(tiles=torch.zeros((n, 3), dtype=torch.int32, device=dev),
+                   counts=torch.zeros(1 + self.cfg.n_scales, dtype=torch.int32, device=dev),
+                   flags=torch.zeros(n, dtype=torch.uint8, device=dev),
+                   tissue=torch.zeros((sz.thumb_h, sz.thumb_w), dtype=torch.uint8, device=dev),
+                   otsu=torch.zeros(1, dtype=torch.int32, device=dev))
+        tl = L.TileList(out["tiles"].data_ptr(), out["counts"].data_ptr(), out["flags"].data_ptr(),
+                        out["tissue"].data_ptr(), out["otsu"].data_ptr())
+        ws = self.workspace(sz.tile_workspace_bytes, dev)
+        L.check(self.lib.omni_tile_slide(self.ctx, _ptr(rgb), H, W, rgb.stride(0), _ptr(ws),
+                                         ws.numel(), C.byref(tl), _stream()), self.ctx)
+        return out
+
+    # ------------------------------------------------------------------ whole path
+    def segment(self, rgb: torch.Tensor, scales: Optional[Sequence[int]] = None,
+                classes: Optional[Sequence[int]] = None, logits: bool = False,
+                coverage: bool = False, argmax: bool = False,
+                out: Optional[Dict] = None) -> Dict:
+        """Label maps (and optional logits / coverage / argmax) per class.
+
+        Returns {"labels": {c: u8 tensor}, "logits": {c: f32}, "coverage": {s: u16},
+        "argmax": {s: u8}}.  Pass ``out`` (a previous result) to reuse its buffers.
+        """
+        H, W, _ = rgb.shape
+        sz = self.query(H, W)
+        dev = rgb.device
+        cfg = self.cfg
+        scales = list(range(cfg.n_scales)) if scales is None else list(scales)
+        classes = [k for k in range(cfg.n_classes) if classes is None or k in classes]
+        smask = sum(1 << s for s in scales)
+        cmask = sum(1 << k for k in classes)
+        if out is None:
+            out = {"labels": {}, "logits": {}, "coverage": {}, "argmax": {}}
+            for k in classes:
+                s = cfg.class_scale[k]
+                if s not in scales:
+                    continue
+                shp = (sz.out_h[s], sz.out_w[s])
+                out["labels"][k] = torch.empty(shp, dtype=torch.uint8, device=dev)
+                if logits:
+                    out["logits"][k] = torch.empty(shp, dtype=torch.float32, device=dev)
+            for s in scales:
+                shp = (sz.out_h[s], sz.out_w[s])
+                if coverage:
+                    out["coverage"][s] = torch.empty(shp, dtype=torch.int16, device=dev)
+                if argmax:
+                    out["argmax"][s] = torch.empty(shp, dtype=torch.uint8, device=dev)
+        o = L.Outputs()
+        for k, t in out["labels"].items():
+            o.labels[k] = t.data_ptr()
+        for k, t in out["logits"].items():
+            o.logits[k] = t.data_ptr()
+        for s, t in out["coverage"].items():
+            o.coverage[s] = t.data_ptr()
+        for s, t in out["argmax"].items():
+            o.argmax[s] = t.data_ptr()
+        ws = self.workspace(sz.workspace_bytes, dev)
+        L.check(self.lib.omni_segment_slide(self.ctx, _ptr(rgb), H, W, rgb.stride(0), smask, cmask,
+                                            _ptr(ws), ws.numel(), C.byref(o), _stream()), self.ctx)
+        return out
+
+    def segment_host(self, rgb_host: torch.Tensor, labels_host: Dict[int, torch.Tensor],
+                     device="cuda") -> Dict[int, torch.Tensor]:
+        """Whole path from a HOST slide into HOST label buffers (copies included)."""
+        H, W, _ = rgb_host.shape
+        sz = self.query(H, W)
+        ws = self.workspace(sz.workspace_bytes, device)
+        arr = (C.c_void_p * L.MAX_CLASSES)()
+        cmask = 0
+        for k, t in labels_host.items():
+            arr[k] = t.data_ptr()
+            cmask |= 1 << k
+        smask = (1 << self.cfg.n_scales) - 1
+        L.check(self.lib.omni_segment_slide_host(self.ctx, _ptr(rgb_host), H, W, rgb_host.stride(0),
+                                                 smask, cmask, _ptr(ws), ws.numel(), arr,
+                                                 _stream()), self.ctx)
+        return labels_host
+
+    # ------------------------------------------------------------------ timing
+    def set_timing(self, on: bool = True):
+        L.check(self.lib.omni_set_timing(self.ctx, int(on)), self.ctx)
+
+    def timing(self, kind: int):
+        ms, n, work = C.c_double(), C.c_int64(), C.c_double()
+        L.check(self.lib.omni_get_timing(self.ctx, kind, C.byref(ms), C.byref(n), C.byref(work)),
+                self.ctx)
+        return ms.value, n.value, work.value
+
+    def launch_count(self) -> int:
+        return int(self.lib.omni_last_launch_count(self.ctx))
+
+
+def synth_slide(spec, y0: int = 0, x0: int = 0, h: Optional[int] = None,
+                w: Optional[int] = None, device="cuda", out: Optional[torch.Tensor] = None):
+    """Window of a seeded synthetic slide generated on the device."""
+    h = spec.H if h is None else h
+    w = spec.W if w is None else w
+    if out is None:
+        out = torch.empty((h, w, 3), dtype=torch.uint8, device=device)
+    ell = np.ascontiguousarray(spec.as_int_array(), dtype=np.int64)
+    st = L.lib().omni_synth_slide(ell.ctypes.data_as(C.c_void_p), ell.shape[0],
+                                  C.c_uint64(spec.seed & 0xFFFFFFFFFFFFFFFF), spec.W, y0, x0, h, w,
+                                  _ptr(out), out.stride(0), _stream())
+    L.check(st, None, "omni_synth_slide failed")
+    return out
+
+
+def conv_layer(precision: int, x: torch.Tensor, R: int, cin: int, cout: int, w: np.ndarray,
+               g: np.ndarray, b: np.ndarray, y: torch.Tensor, r: Optional[torch.Tensor] = None,
+               cr: int = 0, wp: Optional[np.ndarray] = None, x_cs=None, x_co=0, r_cs=None,
+               r_co=0, y_cs=None, y_co=0):
+    """One fused conv layer through omni_conv_layer (layer-level checks)."""
+    B = x.shape[0]
+    w = np.ascontiguousarray(w, np.float32)
+    g = np.ascontiguousarray(g, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    wpp = None if wp is None else np.ascontiguousarray(wp, np.float32)
+    st = L.lib().omni_conv_layer(
+        precision, B, R, cin, cout, _ptr(x), x_cs or cin, x_co, w.ctypes.data_as(C.c_void_p),
+        g.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p), _ptr(r), r_cs or cr, r_co, cr,
+        None if wpp is None else wpp.ctypes.data_as(C.c_void_p), _ptr(y), y_cs or cout, y_co,
+        _stream())
+    L.check(st, None, "omni_conv_layer failed")
+    return y

@@ -1,0 +1,408 @@
+// Residual U-Net building blocks on the CUDA cores (the plain FP32 path),
+// plus the precision-generic pieces both paths share: the first convolution
+// (reads the uint8 tile straight from the canvas), 2x2 max-pool, bilinear x2
+// upsampling into the decoder's concat buffer, and global average pooling.
+//
+// Block structure (residual U-Net of the Omni-Seg network, Sec. 2.2):
+//   out = ReLU(g2 * conv3x3(ReLU(g1 * conv3x3(x) + b1)) + b2 + wp . x)
+// The SIMT implicit GEMM below computes one such convolution with the norm,
+// the 1x1 residual projection and the ReLU fused into its epilogue.
+#include "omni_internal.cuh"
+
+namespace omni {
+namespace {
+
+template <typename T> struct Vec8;
+template <> struct Vec8<float> {
+  static __device__ __forceinline__ void load(const float* p, float v[8]) {
+    float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+  static __device__ __forceinline__ void store(float* p, const float v[8]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  }
+};
+template <> struct Vec8<__nv_bfloat16> {
+  static __device__ __forceinline__ void load(const __nv_bfloat16* p, float v[8]) {
+    uint4 q = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __bfloat1622float2(h[i]);
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+  static __device__ __forceinline__ void store(__nv_bfloat16* p, const float v[8]) {
+    uint4 q;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4*>(p) = q;
+  }
+};
+
+// v = 2 u / 255 - 1  (input normalisation of the tile)
+__device__ __forceinline__ float norm_u8(uint8_t u) { return 2.0f * (float)u / 255.0f - 1.0f; }
+
+// ------------------------------------------------------------------ first conv
+// conv3x3 over the 3 normalised colour channels of a tile read in place from
+// the uint8 canvas (zero padding at the tile border), norm, ReLU.
+template <int C0, typename T>
+__global__ void __launch_bounds__(128) k_conv_first(int B, int P, const uint8_t* __restrict__ canvas,
+                                                    long long cstride,
+                                                    const int32_t* __restrict__ tiles3,
+                                                    const float* __restrict__ w27,  // [27][C0]
+                                                    const float* __restrict__ gamma,
+                                                    const float* __restrict__ beta,
+                                                    T* __restrict__ y, int y_cs, int y_co) {
+  __shared__ float ws[27 * C0];
+  __shared__ float gs[C0], bs[C0];
+  for (int i = threadIdx.x; i < 27 * C0; i += blockDim.x) ws[i] = w27[i];
+  for (int i = threadIdx.x; i < C0; i += blockDim.x) { gs[i] = gamma[i]; bs[i] = beta[i]; }
+  __syncthreads();
+  long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long total = (long long)B * P * P;
+  if (m >= total) return;
+  int b = (int)(m / ((long long)P * P));
+  int rem = (int)(m - (long long)b * P * P);
+  int i = rem / P, j = rem % P;
+  int ty = tiles3[3 * b + 1], tx = tiles3[3 * b + 2];
+  float in[27];
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      int ii = i + dy - 1, jj = j + dx - 1;
+      bool ok = ii >= 0 && ii < P && jj >= 0 && jj < P;
+      const uint8_t* p = canvas + (long long)(ty + ii) * cstride + (long long)(tx + jj) * 3;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) in[(dy * 3 + dx) * 3 + c] = ok ? norm_u8(p[c]) : 0.0f;
+    }
+  T* out = y + m * y_cs + y_co;
+#pragma unroll
+  for (int o0 = 0; o0 < C0; o0 += 8) {
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 27; ++k)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = fmaf(in[k], ws[k * C0 + o0 + q], acc[q]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = fmaxf(fmaf(gs[o0 + q], acc[q], bs[o0 + q]), 0.0f);
+    Vec8<T>::store(out + o0, acc);
+  }
+}
+
+// ------------------------------------------------------------------ FP32 implicit GEMM conv
+// GEMM view: M = B*R*R output pixels, N = cout, K = 9*cin (tap-major, then
+// channel).  Block tile 128 x BN, K step 8, 256 threads, each thread a
+// TM x 4 register tile; A is gathered from the shifted NHWC input with zero
+// padding, B is the K-major weight matrix.  A second K loop over the 1x1
+// residual projection accumulates separately so the epilogue can apply
+// ReLU(g * acc + b + acc_res).
+constexpr int kBM = 128, kBK = 8, kThreads = 256;
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads) k_conv_f32(ConvArgs a) {
+  constexpr int TN = 4;
+  constexpr int NT = BN / TN;            // threads along N
+  constexpr int MT = kThreads / NT;      // threads along M
+  constexpr int TM = kBM / MT;
+  __shared__ __align__(16) float As[2][kBK][kBM];
+  __shared__ __align__(16) float Bs[2][kBK][BN];
+
+  const int t = threadIdx.x;
+  const int tn = t % NT, tm = t / NT;
+  const long long M = (long long)a.B * a.R * a.R;
+  const long long m0 = (long long)blockIdx.x * kBM;
+  const int n0 = blockIdx.y * BN;
+  const int RR = a.R * a.R;
+  const float* X = static_cast<const float*>(a.x);
+  const float* Rin = static_cast<const float*>(a.r);
+
+  // this thread's A-load pixel (one float4 of 4 channels per stage)
+  const int lm = t >> 1, lc = (t & 1) * 4;
+  const long long gm = m0 + lm;
+  const bool mvalid = gm < M;
+  int lb = 0, li = 0, lj = 0;
+  if (mvalid) {
+    lb = (int)(gm / RR);
+    int rem = (int)(gm - (long long)lb * RR);
+    li = rem / a.R;
+    lj = rem % a.R;
+  }
+  // B-load: 8 x BN floats = 2*BN float4
+  const int bk = t / (BN / 4), bn = (t % (BN / 4)) * 4;
+  const bool bload = t < 2 * BN;
+
+  const int nk_main = 9 * (a.cin / kBK);
+  const int nk_res = a.res_mode == RES_TENSOR ? a.cr / kBK : 0;
+  const int nk = nk_main + nk_res;
+
+  auto loadA = [&](int kt) -> float4 {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!mvalid) return v;
+    if (kt < nk_main) {
+      int tap = kt / (a.cin / kBK);
+      int c0 = (kt % (a.cin / kBK)) * kBK + lc;
+      int ii = li + tap / 3 - 1, jj = lj + tap % 3 - 1;
+      if (ii >= 0 && ii < a.R && jj >= 0 && jj < a.R)
+        v = *reinterpret_cast<const float4*>(
+            X + ((long long)lb * RR + (long long)ii * a.R + jj) * a.x_cs + a.x_co + c0);
+    } else {
+      int c0 = (kt - nk_main) * kBK + lc;
+      v = *reinterpret_cast<const float4*>(Rin + gm * a.r_cs + a.r_co + c0);
+    }
+    return v;
+  };
+  auto loadB = [&](int kt) -> float4 {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!bload) return v;
+    const float* W = kt < nk_main ? a.w.w_f32 + (long long)(kt * kBK + bk) * a.cout
+                                  : a.w.wp_f32 + (long long)((kt - nk_main) * kBK + bk) * a.cout;
+    return *reinterpret_cast<const float4*>(W + n0 + bn);
+  };
+  auto storeA = [&](int buf, float4 v) {
+    As[buf][lc + 0][lm] = v.x;
+    As[buf][lc + 1][lm] = v.y;
+    As[buf][lc + 2][lm] = v.z;
+    As[buf][lc + 3][lm] = v.w;
+  };
+  auto storeB = [&](int buf, float4 v) {
+    if (bload) *reinterpret_cast<float4*>(&Bs[buf][bk][bn]) = v;
+  };
+
+  float acc[TM][TN], accr[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) { acc[i][j] = 0.f; accr[i][j] = 0.f; }
+
+  float4 ra = loadA(0), rb = loadB(0);
+  storeA(0, ra);
+  storeB(0, rb);
+  __syncthreads();
+  for (int kt = 0; kt < nk; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < nk) { ra = loadA(kt + 1); rb = loadB(kt + 1); }
+    const bool res = kt >= nk_main;
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      float av[TM], bv[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) av[i] = As[cur][kk][tm * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[cur][kk][tn * TN + j];
+      if (!res) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) accr[i][j] = fmaf(av[i], bv[j], accr[i][j]);
+      }
+    }
+    if (kt + 1 < nk) {
+      storeA(cur ^ 1, ra);
+      storeB(cur ^ 1, rb);
+    }
+    __syncthreads();
+  }
+
+  // epilogue
+  float g[TN], be[TN];
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    g[j] = a.w.gamma[n0 + tn * TN + j];
+    be[j] = a.w.beta[n0 + tn * TN + j];
+  }
+  float* Y = static_cast<float*>(a.y);
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    long long m = m0 + tm * TM + i;
+    if (m >= M) continue;
+    float o[TN];
+    if (a.res_mode == RES_RGB) {
+      int b = (int)(m / RR);
+      int rem = (int)(m - (long long)b * RR);
+      int pi = rem / a.R, pj = rem % a.R;
+      const uint8_t* px = a.canvas + (long long)(a.tiles3[3 * b + 1] + pi) * a.canvas_stride +
+                          (long long)(a.tiles3[3 * b + 2] + pj) * 3;
+      float v0 = norm_u8(px[0]), v1 = norm_u8(px[1]), v2 = norm_u8(px[2]);
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        int n = n0 + tn * TN + j;
+        accr[i][j] = fmaf(v0, a.w.wp_f32[n],
+                          fmaf(v1, a.w.wp_f32[a.cout + n], v2 * a.w.wp_f32[2 * a.cout + n]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) o[j] = fmaxf(fmaf(g[j], acc[i][j], be[j]) + accr[i][j], 0.f);
+    *reinterpret_cast<float4*>(Y + m * a.y_cs + a.y_co + n0 + tn * TN) =
+        make_float4(o[0], o[1], o[2], o[3]);
+  }
+}
+
+// ------------------------------------------------------------------ pooling / upsampling
+template <typename T>
+__global__ void k_maxpool(int B, int R, int C, const T* __restrict__ x, int x_cs, int x_co,
+                          T* __restrict__ y, int y_cs, int y_co) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int Ro = R / 2, cg = C / 8;
+  long long total = (long long)B * Ro * Ro * cg;
+  if (idx >= total) return;
+  int c = (int)(idx % cg) * 8;
+  long long p = idx / cg;
+  int b = (int)(p / ((long long)Ro * Ro));
+  int rem = (int)(p - (long long)b * Ro * Ro);
+  int i = rem / Ro, j = rem % Ro;
+  float m[8], v[8];
+  const T* base = x + ((long long)b * R * R) * x_cs + x_co + c;
+  Vec8<T>::load(base + ((long long)(2 * i) * R + 2 * j) * x_cs, m);
+  const int offs[3][2] = {{0, 1}, {1, 0}, {1, 1}};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    Vec8<T>::load(base + ((long long)(2 * i + offs[q][0]) * R + 2 * j + offs[q][1]) * x_cs, v);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m[k] = fmaxf(m[k], v[k]);
+  }
+  Vec8<T>::store(y + p * y_cs + y_co + c, m);
+}
+
+// bilinear x2, half-pixel centres (align_corners = False), edge clamp:
+// even output 2k mixes source k-1 (0.25) and k (0.75); odd 2k+1 mixes k (0.75)
+// and k+1 (0.25).  R is the OUTPUT size.
+template <typename T>
+__global__ void k_upsample(int B, int R, int C, const T* __restrict__ x, int x_cs, int x_co,
+                           T* __restrict__ y, int y_cs, int y_co) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int cg = C / 8, Ri = R / 2;
+  long long total = (long long)B * R * R * cg;
+  if (idx >= total) return;
+  int c = (int)(idx % cg) * 8;
+  long long p = idx / cg;
+  int b = (int)(p / ((long long)R * R));
+  int rem = (int)(p - (long long)b * R * R);
+  int i = rem / R, j = rem % R;
+  int k = i >> 1, l = j >> 1;
+  int i0, i1, j0, j1;
+  float wi0, wi1, wj0, wj1;
+  if (i & 1) { i0 = k; i1 = min(k + 1, Ri - 1); wi0 = 0.75f; wi1 = 0.25f; }
+  else       { i0 = max(k - 1, 0); i1 = k; wi0 = 0.25f; wi1 = 0.75f; }
+  if (j & 1) { j0 = l; j1 = min(l + 1, Ri - 1); wj0 = 0.75f; wj1 = 0.25f; }
+  else       { j0 = max(l - 1, 0); j1 = l; wj0 = 0.25f; wj1 = 0.75f; }
+  const T* base = x + ((long long)b * Ri * Ri) * x_cs + x_co + c;
+  float a00[8], a01[8], a10[8], a11[8], o[8];
+  Vec8<T>::load(base + ((long long)i0 * Ri + j0) * x_cs, a00);
+  Vec8<T>::load(base + ((long long)i0 * Ri + j1) * x_cs, a01);
+  Vec8<T>::load(base + ((long long)i1 * Ri + j0) * x_cs, a10);
+  Vec8<T>::load(base + ((long long)i1 * Ri + j1) * x_cs, a11);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    o[q] = wi0 * (wj0 * a00[q] + wj1 * a01[q]) + wi1 * (wj0 * a10[q] + wj1 * a11[q]);
+  Vec8<T>::store(y + p * y_cs + y_co + c, o);
+}
+
+// g[b][c] = mean over the R x R pixels of tile b (fixed summation order)
+template <typename T>
+__global__ void k_gap(int R, int C, const T* __restrict__ x, int x_cs, int x_co,
+                      float* __restrict__ g) {
+  int b = blockIdx.x;
+  int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const T* base = x + ((long long)b * R * R) * x_cs + x_co + c;
+  float s = 0.f;
+  for (int p = 0; p < R * R; ++p) {
+    if constexpr (sizeof(T) == 4) s += (float)base[(long long)p * x_cs];
+    else s += __bfloat162float(base[(long long)p * x_cs]);
+  }
+  g[(long long)b * C + c] = s / (float)(R * R);
+}
+
+template <int C0, typename T>
+cudaError_t first_t(const ConvArgs& a, cudaStream_t st) {
+  long long total = (long long)a.B * a.R * a.R;
+  unsigned blocks = (unsigned)((total + 127) / 128);
+  k_conv_first<C0, T><<<blocks, 128, 0, st>>>(a.B, a.R, a.canvas, a.canvas_stride, a.tiles3,
+                                              a.w.w_f32, a.w.gamma, a.w.beta,
+                                              static_cast<T*>(a.y), a.y_cs, a.y_co);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t first_p(const ConvArgs& a, cudaStream_t st) {
+  switch (a.cout) {
+    case 8: return first_t<8, T>(a, st);
+    case 16: return first_t<16, T>(a, st);
+    case 32: return first_t<32, T>(a, st);
+    case 64: return first_t<64, T>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_conv_first(const ConvArgs& a, int precision, cudaStream_t st) {
+  return precision == OMNI_FP32 ? first_p<float>(a, st) : first_p<__nv_bfloat16>(a, st);
+}
+
+cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
+  if (a.cin % kBK || (a.res_mode == RES_TENSOR && a.cr % kBK)) return cudaErrorInvalidValue;
+  long long M = (long long)a.B * a.R * a.R;
+  unsigned gx = (unsigned)((M + kBM - 1) / kBM);
+  int bn = a.cout >= 64 ? 64 : a.cout;
+  if (a.cout % bn) return cudaErrorInvalidValue;
+  dim3 grid(gx, a.cout / bn);
+  switch (bn) {
+    case 64: k_conv_f32<64><<<grid, kThreads, 0, st>>>(a); break;
+    case 32: k_conv_f32<32><<<grid, kThreads, 0, st>>>(a); break;
+    case 16: k_conv_f32<16><<<grid, kThreads, 0, st>>>(a); break;
+    case 8: k_conv_f32<8><<<grid, kThreads, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxpool(int precision, int B, int R, int C, const void* x, int x_cs, int x_co,
+                           void* y, int y_cs, int y_co, cudaStream_t st) {
+  long long total = (long long)B * (R / 2) * (R / 2) * (C / 8);
+  unsigned blocks = (unsigned)((total + 255) / 256);
+  if (precision == OMNI_FP32)
+    k_maxpool<float><<<blocks, 256, 0, st>>>(B, R, C, (const float*)x, x_cs, x_co, (float*)y,
+                                             y_cs, y_co);
+  else
+    k_maxpool<__nv_bfloat16><<<blocks, 256, 0, st>>>(B, R, C, (const __nv_bfloat16*)x, x_cs,
+                                                     x_co, (__nv_bfloat16*)y, y_cs, y_co);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, int x_cs,
+                            int x_co, void* y, int y_cs, int y_co, cudaStream_t st) {
+  long long total = (long long)B * R * R * (C / 8);
+  unsigned blocks = (unsigned)((total + 255) / 256);
+  if (precision == OMNI_FP32)
+    k_upsample<float><<<blocks, 256, 0, st>>>(B, R, C, (const float*)x, x_cs, x_co, (float*)y,
+                                              y_cs, y_co);
+  else
+    k_upsample<__nv_bfloat16><<<blocks, 256, 0, st>>>(B, R, C, (const __nv_bfloat16*)x, x_cs,
+                                                      x_co, (__nv_bfloat16*)y, y_cs, y_co);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gap(int precision, int B, int R, int C, const void* x, int x_cs, int x_co,
+                       float* g, cudaStream_t st) {
+  dim3 grid(B, (C + 127) / 128);
+  if (precision == OMNI_FP32)
+    k_gap<float><<<grid, 128, 0, st>>>(R, C, (const float*)x, x_cs, x_co, g);
+  else
+    k_gap<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co, g);
+  return cudaGetLastError();
+}
+
+}  // namespace omni

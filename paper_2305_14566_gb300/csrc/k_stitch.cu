@@ -1,0 +1,126 @@
+// Slide-wise aggregation (Sec. 2.3) of the overlapping tile predictions
+// (Sec. 2.2, Sec. 3.2): every output pixel is owned by exactly one thread,
+// which reads the logits of the processed tiles covering it in ascending
+// (row, column) tile order, so no atomics are used and the result is
+// deterministic.  The same pass emits the labels:
+//   average mode: label = cov > 0 and mean logit > 0
+//   vote mode:    label = cov > 0 and 2 * (#tiles with logit > 0) >= cov
+// optionally ANDed with the tissue foreground (Sec. 2.3), plus the optional
+// stitched logits, coverage and per-scale argmax map.
+// Each thread handles four consecutive pixels with 16-byte loads when the
+// crop is 4-aligned (tile borders fall on multiples of the stride S, S % 4 == 0).
+#include "omni_internal.cuh"
+
+namespace omni {
+namespace {
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
+  constexpr int NV = VEC ? 4 : 1;
+  const int ox = (blockIdx.x * 64 + (threadIdx.x & 63)) * NV;
+  const int oy = blockIdx.y * 4 + (threadIdx.x >> 6);
+  if (oy >= a.oh || ox >= a.ow) return;
+  const int cy = oy + a.oy0, cx = ox + a.ox0;
+  const long long PP = (long long)a.P * a.P;
+  const int i_lo = max(0, (cy - a.P) / a.S + ((cy - a.P) >= 0 ? 1 : 0));
+  const int i_hi = min(a.gh - 1, cy / a.S);
+  const int j_lo = max(0, (cx - a.P) / a.S + ((cx - a.P) >= 0 ? 1 : 0));
+  const int j_hi = min(a.gw - 1, cx / a.S);
+
+  float sum[OMNI_MAX_CLASSES][NV];
+  int votes[OMNI_MAX_CLASSES][NV];
+#pragma unroll
+  for (int c = 0; c < OMNI_MAX_CLASSES; ++c)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { sum[c][v] = 0.f; votes[c][v] = 0; }
+  int cov = 0;
+  for (int i = i_lo; i <= i_hi; ++i) {
+    for (int j = j_lo; j <= j_hi; ++j) {
+      const int slot = a.slot_map[i * a.gw + j];
+      if (slot < 0) continue;
+      ++cov;
+      const float* base = a.logits + (long long)slot * a.n_cls * PP +
+                          (long long)(cy - i * a.S) * a.P + (cx - j * a.S);
+#pragma unroll
+      for (int c = 0; c < OMNI_MAX_CLASSES; ++c) {
+        if (c >= a.n_cls) break;
+        float l[NV];
+        if constexpr (VEC) {
+          float4 q = __ldg(reinterpret_cast<const float4*>(base + c * PP));
+          l[0] = q.x; l[1] = q.y; l[2] = q.z; l[3] = q.w;
+        } else {
+          l[0] = __ldg(base + c * PP);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          sum[c][v] += l[v];
+          votes[c][v] += l[v] > 0.f ? 1 : 0;
+        }
+      }
+    }
+  }
+  bool tis = true;
+  if (a.tissue) {
+    const int ty = (int)(((long long)cy * a.f) / kThumb), tx = (int)(((long long)cx * a.f) / kThumb);
+    tis = a.tissue[(long long)ty * a.tw + tx] != 0;
+  }
+  const long long o = (long long)oy * a.ow + ox;
+  float best[NV];
+  int arg[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { best[v] = 0.f; arg[v] = 0; }
+#pragma unroll
+  for (int c = 0; c < OMNI_MAX_CLASSES; ++c) {
+    if (c >= a.n_cls) break;
+    float L[NV];
+    uint8_t lab[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      L[v] = cov > 0 ? sum[c][v] / (float)cov : 0.f;
+      bool on = a.mode == OMNI_STITCH_AVG ? (cov > 0 && L[v] > 0.f)
+                                          : (cov > 0 && 2 * votes[c][v] >= cov);
+      lab[v] = (on && tis) ? 1 : 0;
+      if (L[v] > best[v]) { best[v] = L[v]; arg[v] = a.cls_ids[c] + 1; }
+    }
+    if (a.labels[c]) {
+      if constexpr (VEC) {
+        *reinterpret_cast<uchar4*>(a.labels[c] + o) = make_uchar4(lab[0], lab[1], lab[2], lab[3]);
+      } else {
+        a.labels[c][o] = lab[0];
+      }
+    }
+    if (a.out_logits[c]) {
+      if constexpr (VEC) {
+        *reinterpret_cast<float4*>(a.out_logits[c] + o) = make_float4(L[0], L[1], L[2], L[3]);
+      } else {
+        a.out_logits[c][o] = L[0];
+      }
+    }
+  }
+  if (a.coverage) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a.coverage[o + v] = (uint16_t)cov;
+  }
+  if (a.argmax) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a.argmax[o + v] = (uint8_t)arg[v];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stitch(const StitchArgs& a, cudaStream_t st) {
+  if (a.n_cls < 1 || a.n_cls > OMNI_MAX_CLASSES) return cudaErrorInvalidValue;
+  if (a.oh <= 0 || a.ow <= 0) return cudaSuccess;
+  const bool vec = (a.ow % 4 == 0) && (a.ox0 % 4 == 0) && (a.S % 4 == 0) && (a.P % 4 == 0);
+  if (vec) {
+    dim3 grid((a.ow / 4 + 63) / 64, (a.oh + 3) / 4);
+    k_stitch<true><<<grid, 256, 0, st>>>(a);
+  } else {
+    dim3 grid((a.ow + 63) / 64, (a.oh + 3) / 4);
+    k_stitch<false><<<grid, 256, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace omni

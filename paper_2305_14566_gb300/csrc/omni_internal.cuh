@@ -1,0 +1,121 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "omniseg.h"
+
+namespace omni {
+
+constexpr int kThumb = 32;          // tissue thumbnail box (40x pixels)
+constexpr int kHeadCh = 8;          // dynamic head width
+constexpr int kHeadParams = 153;    // 8*8 + 8*8 + 8 + 8 + 8 + 1
+constexpr int kMaxEll = 32;         // ellipses of the synthetic slide generator
+constexpr int kMaxLevels = 6;
+
+// Device-side error word bits (set by bounded waits, read by the host).
+constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned kErrBounds = 2u;
+
+// ---------------------------------------------------------------- slide prep
+struct SlideGeom {
+  int H, W;              // slide
+  int Hp, Wp, lead;      // padded 40x canvas and leading border
+  int th, tw;            // thumbnail
+  int n_scales;
+  int factors[OMNI_MAX_SCALES];
+  int gh[OMNI_MAX_SCALES], gw[OMNI_MAX_SCALES];
+  int grid_off[OMNI_MAX_SCALES + 1];   // offsets of per-scale grids in the flag array
+  int P, S;
+};
+
+// k_slide.cu
+cudaError_t launch_synth(const int64_t* ell_host, int n_ell, uint64_t seed, int slide_w, int y0,
+                         int x0, int h, int w, uint8_t* out, int64_t stride, cudaStream_t st);
+cudaError_t launch_pad(const uint8_t* rgb, int64_t stride, const SlideGeom& g, uint8_t* canvas,
+                       cudaStream_t st);
+// 40x canvas -> downsampled images for factors 2/4/8 (any may be null) + 8x8 block sums
+cudaError_t launch_pyramid(const uint8_t* c40, int64_t stride40, int Hp, int Wp, uint8_t* c20,
+                           uint8_t* c10, uint8_t* c5, uint16_t* blk8, cudaStream_t st);
+cudaError_t launch_tissue(const uint16_t* blk8, const SlideGeom& g, int median_k, uint8_t* grey,
+                          uint8_t* blurred, int32_t* hist, int32_t* otsu, uint8_t* mask,
+                          cudaStream_t st);
+cudaError_t launch_tiles(const uint8_t* mask, const SlideGeom& g, int filter, int32_t* tiles,
+                         int32_t* counts, uint8_t* flags, int32_t* slot_map, cudaStream_t st);
+
+// ---------------------------------------------------------------- network
+struct ConvLayerW {
+  int cin, cout, cproj;          // cproj = channels of the residual projection (0: none)
+  float* w_f32;                  // [9*cin][cout]   K-major rows for the FFMA path
+  float* wp_f32;                 // [cproj][cout]
+  __nv_bfloat16* w_bf16;         // [cout][9*cin]   K contiguous, for tcgen05
+  __nv_bfloat16* wp_bf16;        // [cout][cproj]
+  float* gamma;                  // [cout]
+  float* beta;                   // [cout]
+};
+
+enum ResMode { RES_NONE = 0, RES_TENSOR = 1, RES_RGB = 2 };
+
+struct ConvArgs {
+  int B, R, cin, cout;
+  const void* x; int x_cs, x_co;          // input NHWC (channel stride / offset)
+  const void* r; int r_cs, r_co, cr;      // residual input for RES_TENSOR
+  int res_mode;
+  // RES_RGB / first layer: tiles read straight from the uint8 canvas; tile b
+  // has origin (tiles3[3 b + 1], tiles3[3 b + 2]) in canvas pixels
+  const uint8_t* canvas; int64_t canvas_stride; const int32_t* tiles3;
+  void* y; int y_cs, y_co;                // output NHWC
+  ConvLayerW w;                           // device pointers, passed by value
+  unsigned* err;
+};
+
+// k_conv_f32.cu (plain FP32 path + precision-generic helpers)
+cudaError_t launch_conv_first(const ConvArgs& a, int precision, cudaStream_t st);
+cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st);
+cudaError_t launch_maxpool(int precision, int B, int R, int C, const void* x, int x_cs, int x_co,
+                           void* y, int y_cs, int y_co, cudaStream_t st);
+cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, int x_cs,
+                            int x_co, void* y, int y_cs, int y_co, cudaStream_t st);
+cudaError_t launch_gap(int precision, int B, int R, int C, const void* x, int x_cs, int x_co,
+                       float* g, cudaStream_t st);
+
+// k_conv_tc.cu (BF16 tcgen05 implicit GEMM)
+cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st);
+bool conv_tc_supported(int R, int cin, int cout, int cr);
+
+// k_head.cu
+struct HeadArgs {
+  int B, P, C0, Cb, n_classes, n_scales, scale;
+  int n_cls_here; int cls_ids[OMNI_MAX_CLASSES];
+  const void* y0; int precision;           // [B][P][P][C0]
+  const float* g;                          // [B][Cb]
+  const float* wh; const float* bh;        // [8][C0], [8]
+  const float* wc; const float* bc;        // [153][Cb + ncls + nscl], [153]
+  int slot0;                               // output slot of tile 0 (tile b -> slot0 + b)
+  float* logits;                           // [slot][n_cls_here][P*P]
+};
+cudaError_t launch_head(const HeadArgs& a, cudaStream_t st);
+
+// k_stitch.cu
+struct StitchArgs {
+  int hs, ws;                 // canvas size at this scale
+  int oy0, ox0, oh, ow;       // output crop window in canvas pixels
+  int P, S, gh, gw, f;
+  const int32_t* slot_map;    // [gh][gw] logits slot or -1
+  const float* logits;        // [slot][n_cls][P*P]
+  int n_cls; int cls_ids[OMNI_MAX_CLASSES];
+  int mode;                   // OMNI_STITCH_*
+  const uint8_t* tissue; int th, tw;   // thumbnail mask (null: no AND)
+  uint8_t* labels[OMNI_MAX_CLASSES];
+  float* out_logits[OMNI_MAX_CLASSES];
+  uint16_t* coverage;
+  uint8_t* argmax;
+};
+cudaError_t launch_stitch(const StitchArgs& a, cudaStream_t st);
+
+}  // namespace omni

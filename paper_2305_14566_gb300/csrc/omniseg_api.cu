@@ -1,0 +1,883 @@
+// C ABI of the library (declared in omniseg.h): context, weights layout,
+// workspace planning and the orchestration of the three stages of the
+// whole-slide pipeline (Sec. 2.1 tiling, Sec. 2.2 segmentation, Sec. 2.3
+// aggregation).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "omni_internal.cuh"
+
+using namespace omni;
+
+struct omni_ctx {
+  omni_config cfg;
+  std::string err;
+  int device = 0;
+  bool have_weights = false;
+  void* wdev = nullptr;
+  std::vector<ConvLayerW> enc1, enc2, dec1, dec2;   // indexed by level
+  float *wh = nullptr, *bh = nullptr, *wc = nullptr, *bc = nullptr;
+  unsigned* d_err = nullptr;
+  int32_t* h_counts = nullptr;                      // pinned
+  // timing
+  bool timing = false;
+  struct Ev { cudaEvent_t a, b; int kind; };
+  std::vector<Ev> evs;
+  size_t ev_used = 0;
+  double work[4] = {0, 0, 0, 0};
+  int64_t launches = 0;
+  int64_t tiles_done = 0;
+};
+
+namespace {
+
+omni_status fail(omni_ctx* c, omni_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+omni_status cuda_fail(omni_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, OMNI_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define OMNI_CU(expr, where)                                   \
+  do {                                                         \
+    cudaError_t e_ = (expr);                                   \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);   \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+size_t take(size_t& off, size_t bytes) {
+  size_t o = align_up(off, 256);
+  off = o + bytes;
+  return o;
+}
+
+int widths(const omni_config& c, int l) { return c.base << l; }
+
+std::string validate(const omni_config& c) {
+  if (c.levels < 2 || c.levels > kMaxLevels) return "levels must be in 2..6";
+  if (c.base < 8 || c.base > 64 || c.base % 8) return "base must be 8, 16, 32 or 64";
+  if (c.patch <= 0 || c.patch % (1 << (c.levels - 1)) || (c.patch >> (c.levels - 1)) < 2)
+    return "patch must be divisible by 2^(levels-1) with a bottleneck of at least 2x2";
+  if (c.stride <= 0 || c.patch % c.stride || c.stride % 4) return "stride must divide patch and be a multiple of 4";
+  if (c.n_scales < 1 || c.n_scales > OMNI_MAX_SCALES) return "n_scales must be 1..4";
+  int fmax = 1;
+  for (int s = 0; s < c.n_scales; ++s) {
+    int f = c.factors[s];
+    if (f != 1 && f != 2 && f != 4 && f != 8) return "factors must be 1, 2, 4 or 8";
+    for (int q = 0; q < s; ++q)
+      if (c.factors[q] == f) return "factors must be distinct";
+    fmax = std::max(fmax, f);
+  }
+  if ((fmax * c.stride) % kThumb) return "largest factor times stride must be a multiple of 32";
+  if (c.n_classes < 1 || c.n_classes > OMNI_MAX_CLASSES) return "n_classes must be 1..16";
+  for (int k = 0; k < c.n_classes; ++k)
+    if (c.class_scale[k] < 0 || c.class_scale[k] >= c.n_scales) return "class_scale out of range";
+  if (c.precision != OMNI_FP32 && c.precision != OMNI_BF16) return "precision must be FP32 or BF16";
+  if (c.stitch_mode != OMNI_STITCH_AVG && c.stitch_mode != OMNI_STITCH_VOTE) return "bad stitch_mode";
+  if (c.median_k < 1 || c.median_k % 2 == 0 || c.median_k > 255) return "median_k must be odd, 1..255";
+  if (c.max_batch < 1 || c.max_batch > 4096) return "max_batch must be 1..4096";
+  if (c.pad_lead < 0 || c.pad_lead % fmax) return "pad_lead must be a non-negative multiple of the largest factor";
+  if (widths(c, c.levels - 1) > 1024) return "bottleneck wider than 1024 channels";
+  return "";
+}
+
+int fmax_of(const omni_config& c) {
+  int f = 1;
+  for (int s = 0; s < c.n_scales; ++s) f = std::max(f, c.factors[s]);
+  return f;
+}
+
+struct Plan {
+  SlideGeom g;
+  bool pad;
+  int ncls_s[OMNI_MAX_SCALES];
+  // tile stage
+  size_t canvas, c20, c10, c5, blk8, grey, blur, hist, otsu, mask, tiles, counts, flags, slot;
+  size_t tile_end;
+  // network stage
+  size_t logits, tmp, pooled, cat[kMaxLevels], bott, ydec[kMaxLevels], gap;
+  size_t net_end;
+  // host-buffer variant
+  size_t in, lab[OMNI_MAX_CLASSES];
+  size_t total;
+  uint64_t flops_per_tile;
+};
+
+bool make_plan(const omni_config& c, int H, int W, Plan& p) {
+  if (H <= 0 || W <= 0) return false;
+  memset(&p, 0, sizeof(p));
+  const int fmax = fmax_of(c);
+  const int unit = fmax * c.stride;
+  const int minimum = (fmax * c.patch + unit - 1) / unit * unit;
+  auto ext = [&](long long d) {
+    long long v = (d + 2LL * c.pad_lead + unit - 1) / unit * unit;
+    return (int)std::max<long long>(v, minimum);
+  };
+  SlideGeom& g = p.g;
+  g.H = H; g.W = W; g.lead = c.pad_lead;
+  long long Hp = ext(H), Wp = ext(W);
+  if (Hp > (1LL << 30) || Wp > (1LL << 30)) return false;
+  g.Hp = (int)Hp; g.Wp = (int)Wp;
+  g.th = g.Hp / kThumb; g.tw = g.Wp / kThumb;
+  g.n_scales = c.n_scales; g.P = c.patch; g.S = c.stride;
+  g.grid_off[0] = 0;
+  for (int s = 0; s < c.n_scales; ++s) {
+    int f = c.factors[s];
+    g.factors[s] = f;
+    g.gh[s] = (g.Hp / f - c.patch) / c.stride + 1;
+    g.gw[s] = (g.Wp / f - c.patch) / c.stride + 1;
+    g.grid_off[s + 1] = g.grid_off[s] + g.gh[s] * g.gw[s];
+    p.ncls_s[s] = 0;
+  }
+  for (int k = 0; k < c.n_classes; ++k) p.ncls_s[c.class_scale[k]]++;
+  p.pad = (g.Hp != H) || (g.Wp != W) || c.pad_lead != 0;
+  bool has[9] = {false};
+  for (int s = 0; s < c.n_scales; ++s) has[c.factors[s]] = true;
+  size_t off = 0;
+  const size_t HpWp = (size_t)g.Hp * g.Wp;
+  p.canvas = p.pad ? take(off, HpWp * 3) : 0;
+  p.c20 = has[2] ? take(off, HpWp / 4 * 3) : 0;
+  p.c10 = has[4] ? take(off, HpWp / 16 * 3) : 0;
+  p.c5 = has[8] ? take(off, HpWp / 64 * 3) : 0;
+  p.blk8 = take(off, HpWp / 64 * 3 * sizeof(uint16_t));
+  size_t tn = (size_t)g.th * g.tw;
+  p.grey = take(off, tn);
+  p.blur = take(off, tn);
+  p.mask = take(off, tn);
+  p.hist = take(off, 256 * 4);
+  p.otsu = take(off, 4);
+  int ntile = g.grid_off[c.n_scales];
+  p.tiles = take(off, (size_t)ntile * 3 * 4);
+  p.counts = take(off, (OMNI_MAX_SCALES + 1) * 4);
+  p.flags = take(off, (size_t)ntile);
+  p.slot = take(off, (size_t)ntile * 4);
+  p.tile_end = align_up(off, 256);
+
+  const size_t e = c.precision == OMNI_FP32 ? 4 : 2;
+  const size_t B = (size_t)c.max_batch;
+  const size_t PP = (size_t)c.patch * c.patch;
+  size_t lmax = 0;
+  for (int s = 0; s < c.n_scales; ++s)
+    lmax = std::max(lmax, (size_t)g.gh[s] * g.gw[s] * (size_t)p.ncls_s[s]);
+  p.logits = take(off, lmax * PP * 4);
+  const int L = c.levels;
+  p.tmp = take(off, B * PP * widths(c, 0) * e);
+  p.pooled = take(off, B * PP / 4 * widths(c, 0) * e);
+  for (int l = 0; l < L - 1; ++l) {
+    size_t R = (size_t)(c.patch >> l);
+    p.cat[l] = take(off, B * R * R * 3 * widths(c, l) * e);
+    p.ydec[l] = take(off, B * R * R * widths(c, l) * e);
+  }
+  size_t Rb = (size_t)(c.patch >> (L - 1));
+  p.bott = take(off, B * Rb * Rb * widths(c, L - 1) * e);
+  p.gap = take(off, B * widths(c, L - 1) * 4);
+  p.net_end = align_up(off, 256);
+  p.in = take(off, (size_t)H * W * 3);
+  for (int k = 0; k < c.n_classes; ++k) {
+    int f = c.factors[c.class_scale[k]];
+    p.lab[k] = take(off, (size_t)((H + f - 1) / f) * ((W + f - 1) / f));
+  }
+  p.total = align_up(off, 256);
+
+  // algorithmic conv FLOPs of one tile (2 per multiply-add)
+  double fl = 0;
+  for (int l = 0; l < L; ++l) {
+    double R2 = (double)(c.patch >> l) * (c.patch >> l);
+    double cin = l == 0 ? 3 : widths(c, l - 1), co = widths(c, l);
+    fl += 2 * R2 * co * (9 * cin + 9 * co + cin);
+  }
+  for (int l = 0; l < L - 1; ++l) {
+    double R2 = (double)(c.patch >> l) * (c.patch >> l);
+    double co = widths(c, l), cin = 3 * co;
+    fl += 2 * R2 * co * (9 * cin + 9 * co + cin);
+  }
+  p.flops_per_tile = (uint64_t)fl;
+  return true;
+}
+
+// ------------------------------------------------------------------ bf16 (round to nearest even)
+uint16_t to_bf16(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+
+// ------------------------------------------------------------------ timing helpers
+struct Rec {
+  omni_ctx* c;
+  cudaStream_t st;
+  int idx;
+  Rec(omni_ctx* c_, cudaStream_t st_, int kind) : c(c_), st(st_), idx(-1) {
+    if (!c->timing) return;
+    if (c->ev_used == c->evs.size()) {
+      omni_ctx::Ev e;
+      cudaEventCreate(&e.a);
+      cudaEventCreate(&e.b);
+      c->evs.push_back(e);
+    }
+    idx = (int)c->ev_used++;
+    c->evs[idx].kind = kind;
+    cudaEventRecord(c->evs[idx].a, st);
+  }
+  ~Rec() {
+    if (idx >= 0) cudaEventRecord(c->evs[idx].b, st);
+  }
+};
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+omni_status omni_create(const omni_config* cfg, omni_ctx** out) {
+  if (!cfg || !out) return OMNI_EINVAL;
+  *out = nullptr;
+  std::string v = validate(*cfg);
+  if (!v.empty()) {
+    static thread_local std::string last;
+    last = v;
+    fprintf(stderr, "omni_create: %s\n", v.c_str());
+    return OMNI_EINVAL;
+  }
+  omni_ctx* ctx = new omni_ctx();
+  ctx->cfg = *cfg;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counts, (OMNI_MAX_SCALES + 1) * sizeof(int32_t));
+  if (e != cudaSuccess) {
+    fprintf(stderr, "omni_create: %s\n", cudaGetErrorString(e));
+    omni_destroy(ctx);
+    return OMNI_ECUDA;
+  }
+  *out = ctx;
+  return OMNI_OK;
+}
+
+void omni_destroy(omni_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->wdev) cudaFree(ctx->wdev);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
+  for (auto& e : ctx->evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  delete ctx;
+}
+
+const char* omni_last_error(const omni_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t omni_weights_count(const omni_config* cfg) {
+  if (!cfg || !validate(*cfg).empty()) return -1;
+  const omni_config& c = *cfg;
+  int64_t n = 0;
+  auto block = [&](int64_t cin, int64_t co) { n += co * cin * 9 + 2 * co + co * co * 9 + 2 * co + co * cin; };
+  for (int l = 0; l < c.levels; ++l) block(l == 0 ? 3 : widths(c, l - 1), widths(c, l));
+  for (int l = c.levels - 2; l >= 0; --l) block(3 * widths(c, l), widths(c, l));
+  n += kHeadCh * widths(c, 0) + kHeadCh;
+  int64_t zdim = widths(c, c.levels - 1) + c.n_classes + c.n_scales;
+  n += kHeadParams * zdim + kHeadParams;
+  return n;
+}
+
+omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats) {
+  if (!ctx || !blob) return fail(ctx, OMNI_EINVAL, "null argument");
+  const omni_config& c = ctx->cfg;
+  int64_t need = omni_weights_count(&c);
+  if (n_floats != need)
+    return fail(ctx, OMNI_EWEIGHTS, "weights blob has " + std::to_string(n_floats) +
+                                         " floats, configuration needs " + std::to_string(need));
+  for (int64_t i = 0; i < n_floats; ++i)
+    if (!std::isfinite(blob[i])) return fail(ctx, OMNI_EWEIGHTS, "non-finite weight at " + std::to_string(i));
+
+  // host staging of every device array, 256-byte aligned
+  std::vector<uint8_t> host;
+  size_t off = 0;
+  auto alloc = [&](size_t bytes) {
+    size_t o = take(off, bytes);
+    if (host.size() < off) host.resize(off + (1 << 20));
+    return o;
+  };
+  struct Pending { size_t w32, wp32, w16, wp16, g, b; int cin, cout, cproj; };
+  std::vector<Pending> pend;
+  const float* src = blob;
+  auto conv = [&](int cin, int cout, int cproj_blob, int cproj_used) {
+    // blob: w1-style [cout][cin][3][3], g, b ; projection handled by caller
+    Pending q{};
+    q.cin = cin; q.cout = cout; q.cproj = cproj_used;
+    q.w32 = alloc((size_t)9 * cin * cout * 4);
+    q.w16 = alloc((size_t)9 * cin * cout * 2);
+    q.g = alloc((size_t)cout * 4);
+    q.b = alloc((size_t)cout * 4);
+    float* w32 = reinterpret_cast<float*>(host.data() + q.w32);
+    uint16_t* w16 = reinterpret_cast<uint16_t*>(host.data() + q.w16);
+    for (int o = 0; o < cout; ++o)
+      for (int ci = 0; ci < cin; ++ci)
+        for (int tap = 0; tap < 9; ++tap) {
+          float v = src[((size_t)o * cin + ci) * 9 + tap];
+          w32[((size_t)tap * cin + ci) * cout + o] = v;
+          w16[(size_t)o * 9 * cin + (size_t)tap * cin + ci] = to_bf16(v);
+        }
+    src += (size_t)cout * cin * 9;
+    memcpy(host.data() + q.g, src, cout * 4);
+    src += cout;
+    memcpy(host.data() + q.b, src, cout * 4);
+    src += cout;
+    (void)cproj_blob;
+    return q;
+  };
+  auto proj = [&](Pending& q, int cproj) {
+    q.wp32 = alloc((size_t)cproj * q.cout * 4);
+    q.wp16 = alloc((size_t)cproj * q.cout * 2);
+    float* wp32 = reinterpret_cast<float*>(host.data() + q.wp32);
+    uint16_t* wp16 = reinterpret_cast<uint16_t*>(host.data() + q.wp16);
+    for (int o = 0; o < q.cout; ++o)
+      for (int ci = 0; ci < cproj; ++ci) {
+        float v = src[(size_t)o * cproj + ci];
+        wp32[(size_t)ci * q.cout + o] = v;
+        wp16[(size_t)o * cproj + ci] = to_bf16(v);
+      }
+    src += (size_t)q.cout * cproj;
+    q.cproj = cproj;
+  };
+  const int L = c.levels;
+  std::vector<Pending> e1(L), e2(L), d1(L), d2(L);
+  for (int l = 0; l < L; ++l) {
+    int cin = l == 0 ? 3 : widths(c, l - 1), co = widths(c, l);
+    e1[l] = conv(cin, co, 0, 0);
+    e2[l] = conv(co, co, cin, cin);
+    proj(e2[l], cin);
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    int co = widths(c, l), cin = 3 * co;
+    d1[l] = conv(cin, co, 0, 0);
+    d2[l] = conv(co, co, cin, cin);
+    proj(d2[l], cin);
+  }
+  size_t o_wh = alloc((size_t)kHeadCh * widths(c, 0) * 4);
+  memcpy(host.data() + o_wh, src, (size_t)kHeadCh * widths(c, 0) * 4);
+  src += kHeadCh * widths(c, 0);
+  size_t o_bh = alloc(kHeadCh * 4);
+  memcpy(host.data() + o_bh, src, kHeadCh * 4);
+  src += kHeadCh;
+  size_t zdim = widths(c, L - 1) + c.n_classes + c.n_scales;
+  size_t o_wc = alloc((size_t)kHeadParams * zdim * 4);
+  memcpy(host.data() + o_wc, src, (size_t)kHeadParams * zdim * 4);
+  src += kHeadParams * zdim;
+  size_t o_bc = alloc(kHeadParams * 4);
+  memcpy(host.data() + o_bc, src, kHeadParams * 4);
+  src += kHeadParams;
+  if (src - blob != n_floats) return fail(ctx, OMNI_EWEIGHTS, "internal blob walk mismatch");
+
+  size_t total = align_up(off, 256);
+  void* dev = nullptr;
+  OMNI_CU(cudaMalloc(&dev, total), "cudaMalloc(weights)");
+  cudaError_t e = cudaMemcpy(dev, host.data(), total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return cuda_fail(ctx, e, "cudaMemcpy(weights)");
+  }
+  if (ctx->wdev) cudaFree(ctx->wdev);
+  ctx->wdev = dev;
+  uint8_t* d = static_cast<uint8_t*>(dev);
+  auto mk = [&](const Pending& q) {
+    ConvLayerW w{};
+    w.cin = q.cin; w.cout = q.cout; w.cproj = q.cproj;
+    w.w_f32 = reinterpret_cast<float*>(d + q.w32);
+    w.w_bf16 = reinterpret_cast<__nv_bfloat16*>(d + q.w16);
+    w.gamma = reinterpret_cast<float*>(d + q.g);
+    w.beta = reinterpret_cast<float*>(d + q.b);
+    if (q.cproj) {
+      w.wp_f32 = reinterpret_cast<float*>(d + q.wp32);
+      w.wp_bf16 = reinterpret_cast<__nv_bfloat16*>(d + q.wp16);
+    }
+    return w;
+  };
+  ctx->enc1.assign(L, {}); ctx->enc2.assign(L, {}); ctx->dec1.assign(L, {}); ctx->dec2.assign(L, {});
+  for (int l = 0; l < L; ++l) { ctx->enc1[l] = mk(e1[l]); ctx->enc2[l] = mk(e2[l]); }
+  for (int l = 0; l < L - 1; ++l) { ctx->dec1[l] = mk(d1[l]); ctx->dec2[l] = mk(d2[l]); }
+  ctx->wh = reinterpret_cast<float*>(d + o_wh);
+  ctx->bh = reinterpret_cast<float*>(d + o_bh);
+  ctx->wc = reinterpret_cast<float*>(d + o_wc);
+  ctx->bc = reinterpret_cast<float*>(d + o_bc);
+  ctx->have_weights = true;
+  return OMNI_OK;
+}
+
+omni_status omni_query(const omni_config* cfg, int32_t H, int32_t W, omni_sizes* out) {
+  if (!cfg || !out || !validate(*cfg).empty()) return OMNI_EINVAL;
+  Plan p;
+  if (!make_plan(*cfg, H, W, p)) return OMNI_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->Hp = p.g.Hp; out->Wp = p.g.Wp; out->thumb_h = p.g.th; out->thumb_w = p.g.tw;
+  for (int s = 0; s < cfg->n_scales; ++s) {
+    out->grid_h[s] = p.g.gh[s];
+    out->grid_w[s] = p.g.gw[s];
+    int f = cfg->factors[s];
+    out->out_h[s] = (H + f - 1) / f;
+    out->out_w[s] = (W + f - 1) / f;
+  }
+  out->n_tiles_max = p.g.grid_off[cfg->n_scales];
+  out->tile_workspace_bytes = p.tile_end;
+  out->workspace_bytes = p.total;
+  out->flops_per_tile = p.flops_per_tile;
+  return OMNI_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct Prep {
+  const uint8_t* c[OMNI_MAX_SCALES];
+  int64_t cs[OMNI_MAX_SCALES];
+};
+
+// Sec. 2.1 stages on the device; fills `pr` with every scale's canvas.
+omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Plan& p, uint8_t* ws,
+                     cudaStream_t st, Prep& pr) {
+  const omni_config& c = ctx->cfg;
+  const SlideGeom& g = p.g;
+  const uint8_t* c40 = rgb;
+  int64_t s40 = stride;
+  if (p.pad) {
+    Rec r(ctx, st, 3);
+    OMNI_CU(launch_pad(rgb, stride, g, ws + p.canvas, st), "pad");
+    ctx->launches++;
+    c40 = ws + p.canvas;
+    s40 = (int64_t)g.Wp * 3;
+  } else if ((stride % 8) || (reinterpret_cast<uintptr_t>(rgb) % 8)) {
+    return fail(ctx, OMNI_EINVAL, "unpadded slides need 8-byte aligned rows");
+  }
+  uint8_t* c20 = p.c20 ? ws + p.c20 : nullptr;
+  uint8_t* c10 = p.c10 ? ws + p.c10 : nullptr;
+  uint8_t* c5 = p.c5 ? ws + p.c5 : nullptr;
+  {
+    Rec r(ctx, st, 3);
+    OMNI_CU(launch_pyramid(c40, s40, g.Hp, g.Wp, c20, c10, c5, (uint16_t*)(ws + p.blk8), st), "pyramid");
+    ctx->launches++;
+  }
+  for (int s = 0; s < c.n_scales; ++s) {
+    int f = c.factors[s];
+    pr.c[s] = f == 1 ? c40 : f == 2 ? c20 : f == 4 ? c10 : c5;
+    pr.cs[s] = f == 1 ? s40 : (int64_t)(g.Wp / f) * 3;
+  }
+  {
+    Rec r(ctx, st, 3);
+    OMNI_CU(launch_tissue((uint16_t*)(ws + p.blk8), g, c.median_k, ws + p.grey, ws + p.blur,
+                          (int32_t*)(ws + p.hist), (int32_t*)(ws + p.otsu), ws + p.mask, st),
+            "tissue");
+    ctx->launches += 5;
+  }
+  {
+    Rec r(ctx, st, 3);
+    OMNI_CU(launch_tiles(ws + p.mask, g, c.tissue_filter, (int32_t*)(ws + p.tiles),
+                         (int32_t*)(ws + p.counts), ws + p.flags, (int32_t*)(ws + p.slot), st),
+            "tiles");
+    ctx->launches += 2;
+  }
+  return OMNI_OK;
+}
+
+omni_status run_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st) {
+  Rec r(ctx, st, 0);
+  cudaError_t e;
+  if (ctx->cfg.precision == OMNI_FP32) {
+    e = launch_conv_f32(a, st);
+  } else {
+    if (!conv_tc_supported(a.R, a.cin, a.cout, a.res_mode == RES_TENSOR ? a.cr : 0))
+      return fail(ctx, OMNI_EINVAL, "BF16 tensor-core conv does not support R=" + std::to_string(a.R) +
+                                        " cin=" + std::to_string(a.cin) + " cout=" + std::to_string(a.cout));
+    e = launch_conv_tc(a, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "conv");
+  ctx->launches++;
+  return OMNI_OK;
+}
+
+// U-Net + heads for `nb` tiles of one scale.
+omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const uint8_t* canvas,
+                      int64_t cstride, const int32_t* tiles3, int nb, int slot0, int ncls,
+                      const int* cls, cudaStream_t st) {
+  const omni_config& c = ctx->cfg;
+  const int L = c.levels, prec = c.precision;
+  auto C = [&](int l) { return widths(c, l); };
+  void* tmp = ws + p.tmp;
+  void* pooled = ws + p.pooled;
+  void* bott = ws + p.bott;
+  ConvArgs base{};
+  base.B = nb;
+  base.canvas = canvas;
+  base.canvas_stride = cstride;
+  base.tiles3 = tiles3;
+  base.err = ctx->d_err;
+  // encoder output location of level l
+  auto enc_out = [&](int l, void*& ptr, int& cs, int& co) {
+    if (l < L - 1) { ptr = ws + p.cat[l]; cs = 3 * C(l); co = 2 * C(l); }
+    else { ptr = bott; cs = C(l); co = 0; }
+  };
+  {
+    ConvArgs a = base;
+    a.R = c.patch; a.cin = 3; a.cout = C(0);
+    a.y = tmp; a.y_cs = C(0); a.y_co = 0;
+    a.w = ctx->enc1[0];
+    Rec r(ctx, st, 0);
+    cudaError_t e = launch_conv_first(a, prec, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_first");
+    ctx->launches++;
+  }
+  {
+    ConvArgs a = base;
+    a.R = c.patch; a.cin = C(0); a.cout = C(0);
+    a.x = tmp; a.x_cs = C(0); a.x_co = 0;
+    a.res_mode = RES_RGB; a.cr = 3;
+    enc_out(0, a.y, a.y_cs, a.y_co);
+    a.w = ctx->enc2[0];
+    omni_status r = run_conv(ctx, a, st);
+    if (r) return r;
+  }
+  for (int l = 1; l < L; ++l) {
+    const int R = c.patch >> l;
+    void* pp; int pcs, pco;
+    enc_out(l - 1, pp, pcs, pco);
+    {
+      Rec r(ctx, st, 3);
+      OMNI_CU(launch_maxpool(prec, nb, 2 * R, C(l - 1), pp, pcs, pco, pooled, C(l - 1), 0, st), "maxpool");
+      ctx->launches++;
+    }
+    ConvArgs a = base;
+    a.R = R; a.cin = C(l - 1); a.cout = C(l);
+    a.x = pooled; a.x_cs = C(l - 1); a.x_co = 0;
+    a.y = tmp; a.y_cs = C(l); a.y_co = 0;
+    a.w = ctx->enc1[l];
+    omni_status r = run_conv(ctx, a, st);
+    if (r) return r;
+    ConvArgs b2 = base;
+    b2.R = R; b2.cin = C(l); b2.cout = C(l);
+    b2.x = tmp; b2.x_cs = C(l); b2.x_co = 0;
+    b2.res_mode = RES_TENSOR; b2.r = pooled; b2.r_cs = C(l - 1); b2.r_co = 0; b2.cr = C(l - 1);
+    enc_out(l, b2.y, b2.y_cs, b2.y_co);
+    b2.w = ctx->enc2[l];
+    r = run_conv(ctx, b2, st);
+    if (r) return r;
+  }
+  float* gap = reinterpret_cast<float*>(ws + p.gap);
+  {
+    Rec r(ctx, st, 2);
+    OMNI_CU(launch_gap(prec, nb, c.patch >> (L - 1), C(L - 1), bott, C(L - 1), 0, gap, st), "gap");
+    ctx->launches++;
+  }
+  const void* y = bott;
+  int y_cs = C(L - 1);
+  for (int l = L - 2; l >= 0; --l) {
+    const int R = c.patch >> l;
+    void* cat = ws + p.cat[l];
+    {
+      Rec r(ctx, st, 3);
+      OMNI_CU(launch_upsample(prec, nb, R, 2 * C(l), y, y_cs, 0, cat, 3 * C(l), 0, st), "upsample");
+      ctx->launches++;
+    }
+    ConvArgs a = base;
+    a.R = R; a.cin = 3 * C(l); a.cout = C(l);
+    a.x = cat; a.x_cs = 3 * C(l); a.x_co = 0;
+    a.y = tmp; a.y_cs = C(l); a.y_co = 0;
+    a.w = ctx->dec1[l];
+    omni_status r = run_conv(ctx, a, st);
+    if (r) return r;
+    ConvArgs b2 = base;
+    b2.R = R; b2.cin = C(l); b2.cout = C(l);
+    b2.x = tmp; b2.x_cs = C(l); b2.x_co = 0;
+    b2.res_mode = RES_TENSOR; b2.r = cat; b2.r_cs = 3 * C(l); b2.r_co = 0; b2.cr = 3 * C(l);
+    b2.y = ws + p.ydec[l]; b2.y_cs = C(l); b2.y_co = 0;
+    b2.w = ctx->dec2[l];
+    r = run_conv(ctx, b2, st);
+    if (r) return r;
+    y = ws + p.ydec[l];
+    y_cs = C(l);
+  }
+  HeadArgs h{};
+  h.B = nb; h.P = c.patch; h.C0 = C(0); h.Cb = C(L - 1);
+  h.n_classes = c.n_classes; h.n_scales = c.n_scales; h.scale = s;
+  h.n_cls_here = ncls;
+  for (int k = 0; k < ncls; ++k) h.cls_ids[k] = cls[k];
+  h.y0 = y; h.precision = prec; h.g = gap;
+  h.wh = ctx->wh; h.bh = ctx->bh; h.wc = ctx->wc; h.bc = ctx->bc;
+  h.slot0 = slot0;
+  h.logits = reinterpret_cast<float*>(ws + p.logits);
+  {
+    Rec r(ctx, st, 2);
+    OMNI_CU(launch_head(h, st), "head");
+    ctx->launches++;
+  }
+  return OMNI_OK;
+}
+
+omni_status check_ws(omni_ctx* ctx, void* ws, uint64_t bytes, uint64_t need) {
+  if (!ws) return fail(ctx, OMNI_EINVAL, "null workspace");
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(ctx, OMNI_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < need)
+    return fail(ctx, OMNI_ENOMEM, "workspace has " + std::to_string(bytes) + " bytes, needs " + std::to_string(need));
+  return OMNI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+omni_status omni_tile_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int32_t W, int64_t stride,
+                            void* ws_, uint64_t ws_bytes, const omni_tile_list* out, void* stream) {
+  if (!ctx || !rgb || !out || !out->tiles || !out->counts) return fail(ctx, OMNI_EINVAL, "null argument");
+  if (stride < (int64_t)W * 3) return fail(ctx, OMNI_EINVAL, "row_stride < 3 W");
+  Plan p;
+  if (!make_plan(ctx->cfg, H, W, p)) return fail(ctx, OMNI_EINVAL, "bad slide size");
+  omni_status r = check_ws(ctx, ws_, ws_bytes, p.tile_end);
+  if (r) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(ws_);
+  Prep pr;
+  ctx->launches = 0;
+  r = run_prep(ctx, rgb, stride, p, ws, st, pr);
+  if (r) return r;
+  const int n = p.g.grid_off[ctx->cfg.n_scales];
+  OMNI_CU(cudaMemcpyAsync(out->tiles, ws + p.tiles, (size_t)n * 12, cudaMemcpyDeviceToDevice, st), "copy tiles");
+  OMNI_CU(cudaMemcpyAsync(out->counts, ws + p.counts, (size_t)(1 + ctx->cfg.n_scales) * 4,
+                          cudaMemcpyDeviceToDevice, st), "copy counts");
+  if (out->flags) OMNI_CU(cudaMemcpyAsync(out->flags, ws + p.flags, n, cudaMemcpyDeviceToDevice, st), "copy flags");
+  if (out->tissue)
+    OMNI_CU(cudaMemcpyAsync(out->tissue, ws + p.mask, (size_t)p.g.th * p.g.tw, cudaMemcpyDeviceToDevice, st), "copy mask");
+  if (out->otsu) OMNI_CU(cudaMemcpyAsync(out->otsu, ws + p.otsu, 4, cudaMemcpyDeviceToDevice, st), "copy otsu");
+  return OMNI_OK;
+}
+
+omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int32_t W, int64_t stride,
+                               uint32_t scale_mask, uint32_t class_mask, void* ws_, uint64_t ws_bytes,
+                               const omni_outputs* out, void* stream) {
+  if (!ctx || !rgb || !out) return fail(ctx, OMNI_EINVAL, "null argument");
+  if (!ctx->have_weights) return fail(ctx, OMNI_ESTATE, "omni_load_weights has not been called");
+  if (stride < (int64_t)W * 3) return fail(ctx, OMNI_EINVAL, "row_stride < 3 W");
+  const omni_config& c = ctx->cfg;
+  Plan p;
+  if (!make_plan(c, H, W, p)) return fail(ctx, OMNI_EINVAL, "bad slide size");
+  omni_status r = check_ws(ctx, ws_, ws_bytes, p.net_end);
+  if (r) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(ws_);
+  ctx->ev_used = 0;
+  ctx->launches = 0;
+  ctx->tiles_done = 0;
+  for (int k = 0; k < 4; ++k) ctx->work[k] = 0;
+  Prep pr;
+  r = run_prep(ctx, rgb, stride, p, ws, st, pr);
+  if (r) return r;
+  OMNI_CU(cudaMemcpyAsync(ctx->h_counts, ws + p.counts, (size_t)(1 + c.n_scales) * 4, cudaMemcpyDeviceToHost, st),
+          "read tile counts");
+  OMNI_CU(cudaStreamSynchronize(st), "sync after tiling");
+  unsigned herr = 0;
+  OMNI_CU(cudaMemcpy(&herr, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
+  if (herr) return fail(ctx, OMNI_ETIMEOUT, "a device-side wait gave up in an earlier call");
+
+  const int32_t* tiles = reinterpret_cast<const int32_t*>(ws + p.tiles);
+  const int32_t* slot = reinterpret_cast<const int32_t*>(ws + p.slot);
+  int toff = 0;
+  double stitch_bytes = 0;
+  for (int s = 0; s < c.n_scales; ++s) {
+    const int n_s = ctx->h_counts[1 + s];
+    int cls[OMNI_MAX_CLASSES], ncls = 0;
+    for (int k = 0; k < c.n_classes; ++k)
+      if (c.class_scale[k] == s && (class_mask >> k & 1u)) cls[ncls++] = k;
+    const bool want = (scale_mask >> s & 1u) && ncls > 0;
+    if (want) {
+      for (int start = 0; start < n_s; start += c.max_batch) {
+        int nb = std::min(c.max_batch, n_s - start);
+        r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], tiles + 3 * (toff + start), nb, start, ncls, cls, st);
+        if (r) return r;
+      }
+      ctx->tiles_done += n_s;
+      const int f = c.factors[s];
+      StitchArgs a{};
+      a.hs = p.g.Hp / f; a.ws = p.g.Wp / f;
+      a.oy0 = c.pad_lead / f; a.ox0 = c.pad_lead / f;
+      a.oh = (H + f - 1) / f; a.ow = (W + f - 1) / f;
+      a.P = c.patch; a.S = c.stride; a.gh = p.g.gh[s]; a.gw = p.g.gw[s]; a.f = f;
+      a.slot_map = slot + p.g.grid_off[s];
+      a.logits = reinterpret_cast<const float*>(ws + p.logits);
+      a.n_cls = ncls;
+      for (int k = 0; k < ncls; ++k) {
+        a.cls_ids[k] = cls[k];
+        a.labels[k] = out->labels[cls[k]];
+        a.out_logits[k] = out->logits[cls[k]];
+      }
+      a.mode = c.stitch_mode;
+      a.tissue = c.tissue_and ? ws + p.mask : nullptr;
+      a.th = p.g.th; a.tw = p.g.tw;
+      a.coverage = out->coverage[s];
+      a.argmax = out->argmax[s];
+      double px = (double)a.oh * a.ow;
+      stitch_bytes += (double)n_s * ncls * c.patch * c.patch * 4.0;
+      for (int k = 0; k < ncls; ++k) stitch_bytes += px * ((a.labels[k] ? 1 : 0) + (a.out_logits[k] ? 4 : 0));
+      stitch_bytes += px * ((a.coverage ? 2 : 0) + (a.argmax ? 1 : 0));
+      {
+        Rec rr(ctx, st, 1);
+        OMNI_CU(launch_stitch(a, st), "stitch");
+        ctx->launches++;
+      }
+    }
+    toff += n_s;
+  }
+  ctx->work[0] = (double)ctx->tiles_done * (double)p.flops_per_tile;
+  ctx->work[1] = stitch_bytes;
+  return OMNI_OK;
+}
+
+omni_status omni_segment_slide_host(omni_ctx* ctx, const uint8_t* rgb_host, int32_t H, int32_t W,
+                                    int64_t stride, uint32_t scale_mask, uint32_t class_mask, void* ws_,
+                                    uint64_t ws_bytes, uint8_t* const* labels_host, void* stream) {
+  if (!ctx || !rgb_host || !labels_host) return fail(ctx, OMNI_EINVAL, "null argument");
+  const omni_config& c = ctx->cfg;
+  Plan p;
+  if (!make_plan(c, H, W, p)) return fail(ctx, OMNI_EINVAL, "bad slide size");
+  omni_status r = check_ws(ctx, ws_, ws_bytes, p.total);
+  if (r) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(ws_);
+  const int64_t dstride = (int64_t)W * 3;
+  OMNI_CU(cudaMemcpy2DAsync(ws + p.in, dstride, rgb_host, stride, dstride, H, cudaMemcpyHostToDevice, st),
+          "upload slide");
+  omni_outputs o{};
+  for (int k = 0; k < c.n_classes; ++k)
+    if (labels_host[k] && (class_mask >> k & 1u)) o.labels[k] = ws + p.lab[k];
+  r = omni_segment_slide(ctx, ws + p.in, H, W, dstride, scale_mask, class_mask, ws_, ws_bytes, &o, stream);
+  if (r) return r;
+  for (int k = 0; k < c.n_classes; ++k) {
+    if (!o.labels[k]) continue;
+    int f = c.factors[c.class_scale[k]];
+    size_t n = (size_t)((H + f - 1) / f) * ((W + f - 1) / f);
+    OMNI_CU(cudaMemcpyAsync(labels_host[k], o.labels[k], n, cudaMemcpyDeviceToHost, st), "download labels");
+  }
+  OMNI_CU(cudaStreamSynchronize(st), "sync");
+  unsigned herr = 0;
+  OMNI_CU(cudaMemcpy(&herr, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
+  if (herr) return fail(ctx, OMNI_ETIMEOUT, "a device-side wait gave up");
+  return OMNI_OK;
+}
+
+omni_status omni_synth_slide(const int64_t* ell, int32_t n_ell, uint64_t seed, int32_t slide_w, int32_t y0,
+                             int32_t x0, int32_t h, int32_t w, uint8_t* out, int64_t stride, void* stream) {
+  if ((!ell && n_ell) || !out || n_ell < 0 || n_ell > kMaxEll || stride < (int64_t)w * 3) return OMNI_EINVAL;
+  for (int k = 0; k < n_ell; ++k)
+    if (ell[k * 6 + 2] <= 0 || ell[k * 6 + 3] <= 0) return OMNI_EINVAL;
+  cudaError_t e = launch_synth(ell, n_ell, seed, slide_w, y0, x0, h, w, out, stride,
+                               static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? OMNI_OK : OMNI_ECUDA;
+}
+
+omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin, int32_t cout,
+                            const void* x, int32_t x_cs, int32_t x_co, const float* w_host,
+                            const float* g_host, const float* b_host, const void* r, int32_t r_cs,
+                            int32_t r_co, int32_t cr, const float* wp_host, void* y, int32_t y_cs,
+                            int32_t y_co, void* stream) {
+  if (!x || !y || !w_host || !g_host || !b_host || B <= 0 || R <= 0 || cin <= 0 || cout <= 0) return OMNI_EINVAL;
+  if (cin % 8 || cout % 8 || (r && (cr <= 0 || cr % 8 || !wp_host))) return OMNI_EINVAL;
+  if (precision != OMNI_FP32 && precision != OMNI_BF16) return OMNI_EINVAL;
+  if (precision == OMNI_BF16 && !conv_tc_supported(R, cin, cout, r ? cr : 0)) return OMNI_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  size_t n9 = (size_t)9 * cin * cout, np = r ? (size_t)cr * cout : 0;
+  std::vector<float> w32(n9), wp32(np);
+  std::vector<uint16_t> w16(n9), wp16(np);
+  for (int o = 0; o < cout; ++o)
+    for (int ci = 0; ci < cin; ++ci)
+      for (int tap = 0; tap < 9; ++tap) {
+        float v = w_host[((size_t)o * cin + ci) * 9 + tap];
+        w32[((size_t)tap * cin + ci) * cout + o] = v;
+        w16[(size_t)o * 9 * cin + (size_t)tap * cin + ci] = to_bf16(v);
+      }
+  for (int o = 0; o < cout && r; ++o)
+    for (int ci = 0; ci < cr; ++ci) {
+      float v = wp_host[(size_t)o * cr + ci];
+      wp32[(size_t)ci * cout + o] = v;
+      wp16[(size_t)o * cr + ci] = to_bf16(v);
+    }
+  size_t off = 0;
+  size_t o32 = take(off, n9 * 4), o16 = take(off, n9 * 2), op32 = take(off, np * 4 + 4),
+         op16 = take(off, np * 2 + 4), og = take(off, cout * 4), ob = take(off, cout * 4);
+  std::vector<uint8_t> host(align_up(off, 256));
+  memcpy(host.data() + o32, w32.data(), n9 * 4);
+  memcpy(host.data() + o16, w16.data(), n9 * 2);
+  if (np) {
+    memcpy(host.data() + op32, wp32.data(), np * 4);
+    memcpy(host.data() + op16, wp16.data(), np * 2);
+  }
+  memcpy(host.data() + og, g_host, cout * 4);
+  memcpy(host.data() + ob, b_host, cout * 4);
+  uint8_t* d = nullptr;
+  unsigned* derr = nullptr;
+  if (cudaMalloc(&d, host.size()) != cudaSuccess) return OMNI_ECUDA;
+  if (cudaMalloc(&derr, sizeof(unsigned)) != cudaSuccess) { cudaFree(d); return OMNI_ECUDA; }
+  omni_status rs = OMNI_OK;
+  cudaError_t e = cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(unsigned));
+  if (e == cudaSuccess) {
+    ConvArgs a{};
+    a.B = B; a.R = R; a.cin = cin; a.cout = cout;
+    a.x = x; a.x_cs = x_cs; a.x_co = x_co;
+    a.r = r; a.r_cs = r_cs; a.r_co = r_co; a.cr = r ? cr : 0;
+    a.res_mode = r ? RES_TENSOR : RES_NONE;
+    a.y = y; a.y_cs = y_cs; a.y_co = y_co;
+    a.w.cin = cin; a.w.cout = cout; a.w.cproj = a.cr;
+    a.w.w_f32 = reinterpret_cast<float*>(d + o32);
+    a.w.w_bf16 = reinterpret_cast<__nv_bfloat16*>(d + o16);
+    a.w.wp_f32 = reinterpret_cast<float*>(d + op32);
+    a.w.wp_bf16 = reinterpret_cast<__nv_bfloat16*>(d + op16);
+    a.w.gamma = reinterpret_cast<float*>(d + og);
+    a.w.beta = reinterpret_cast<float*>(d + ob);
+    a.err = derr;
+    e = precision == OMNI_FP32 ? launch_conv_f32(a, st) : launch_conv_tc(a, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    unsigned herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && herr) rs = OMNI_ETIMEOUT;
+  }
+  if (e != cudaSuccess) rs = OMNI_ECUDA;
+  cudaFree(d);
+  cudaFree(derr);
+  return rs;
+}
+
+omni_status omni_set_timing(omni_ctx* ctx, int32_t enabled) {
+  if (!ctx) return OMNI_EINVAL;
+  ctx->timing = enabled != 0;
+  return OMNI_OK;
+}
+
+omni_status omni_get_timing(omni_ctx* ctx, int32_t kind, double* ms, int64_t* launches, double* work) {
+  if (!ctx || kind < 0 || kind > 3) return fail(ctx, OMNI_EINVAL, "bad timing kind");
+  double tot = 0;
+  int64_t n = 0;
+  for (size_t i = 0; i < ctx->ev_used; ++i) {
+    if (ctx->evs[i].kind != kind) continue;
+    float t = 0;
+    cudaError_t e = cudaEventSynchronize(ctx->evs[i].b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ctx->evs[i].a, ctx->evs[i].b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event timing");
+    tot += t;
+    ++n;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = n;
+  if (work) *work = ctx->work[kind];
+  return OMNI_OK;
+}
+
+int64_t omni_last_launch_count(const omni_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"
