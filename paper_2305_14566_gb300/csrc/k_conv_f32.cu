@@ -76,9 +76,14 @@ __global__ void __launch_bounds__(128) k_conv_first(int B, int P, const uint8_t*
     for (int dx = 0; dx < 3; ++dx) {
       int ii = i + dy - 1, jj = j + dx - 1;
       bool ok = ii >= 0 && ii < P && jj >= 0 && jj < P;
-      const uint8_t* p = canvas + (long long)(ty + ii) * cstride + (long long)(tx + jj) * 3;
+      // address of a pixel inside the tile even where the window leaves it
+      const int ic = min(max(ii, 0), P - 1), jc = min(max(jj, 0), P - 1);
+      const uint8_t* p = canvas + (long long)(ty + ic) * cstride + (long long)(tx + jc) * 3;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) in[(dy * 3 + dx) * 3 + c] = ok ? norm_u8(p[c]) : 0.0f;
+      for (int c = 0; c < 3; ++c) {
+        const float v = norm_u8(p[c]);
+        in[(dy * 3 + dx) * 3 + c] = ok ? v : 0.0f;
+      }
     }
   T* out = y + m * y_cs + y_co;
 #pragma unroll

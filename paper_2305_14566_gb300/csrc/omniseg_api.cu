@@ -51,6 +51,7 @@ omni_status cuda_fail(omni_ctx* c, cudaError_t e, const char* where) {
   } while (0)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr size_t kNone = ~size_t(0);   // offset of a workspace region that is absent
 size_t take(size_t& off, size_t bytes) {
   size_t o = align_up(off, 256);
   off = o + bytes;
@@ -141,10 +142,10 @@ bool make_plan(const omni_config& c, int H, int W, Plan& p) {
   for (int s = 0; s < c.n_scales; ++s) has[c.factors[s]] = true;
   size_t off = 0;
   const size_t HpWp = (size_t)g.Hp * g.Wp;
-  p.canvas = p.pad ? take(off, HpWp * 3) : 0;
-  p.c20 = has[2] ? take(off, HpWp / 4 * 3) : 0;
-  p.c10 = has[4] ? take(off, HpWp / 16 * 3) : 0;
-  p.c5 = has[8] ? take(off, HpWp / 64 * 3) : 0;
+  p.canvas = p.pad ? take(off, HpWp * 3) : kNone;
+  p.c20 = has[2] ? take(off, HpWp / 4 * 3) : kNone;
+  p.c10 = has[4] ? take(off, HpWp / 16 * 3) : kNone;
+  p.c5 = has[8] ? take(off, HpWp / 64 * 3) : kNone;
   p.blk8 = take(off, HpWp / 64 * 3 * sizeof(uint16_t));
   size_t tn = (size_t)g.th * g.tw;
   p.grey = take(off, tn);
@@ -380,6 +381,7 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
   if (src - blob != n_floats) return fail(ctx, OMNI_EWEIGHTS, "internal blob walk mismatch");
 
   size_t total = align_up(off, 256);
+  host.resize(total);
   void* dev = nullptr;
   OMNI_CU(cudaMalloc(&dev, total), "cudaMalloc(weights)");
   cudaError_t e = cudaMemcpy(dev, host.data(), total, cudaMemcpyHostToDevice);
@@ -459,9 +461,9 @@ omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Pl
   } else if ((stride % 8) || (reinterpret_cast<uintptr_t>(rgb) % 8)) {
     return fail(ctx, OMNI_EINVAL, "unpadded slides need 8-byte aligned rows");
   }
-  uint8_t* c20 = p.c20 ? ws + p.c20 : nullptr;
-  uint8_t* c10 = p.c10 ? ws + p.c10 : nullptr;
-  uint8_t* c5 = p.c5 ? ws + p.c5 : nullptr;
+  uint8_t* c20 = p.c20 != kNone ? ws + p.c20 : nullptr;
+  uint8_t* c10 = p.c10 != kNone ? ws + p.c10 : nullptr;
+  uint8_t* c5 = p.c5 != kNone ? ws + p.c5 : nullptr;
   {
     Rec r(ctx, st, 3);
     OMNI_CU(launch_pyramid(c40, s40, g.Hp, g.Wp, c20, c10, c5, (uint16_t*)(ws + p.blk8), st), "pyramid");
@@ -471,6 +473,7 @@ omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Pl
     int f = c.factors[s];
     pr.c[s] = f == 1 ? c40 : f == 2 ? c20 : f == 4 ? c10 : c5;
     pr.cs[s] = f == 1 ? s40 : (int64_t)(g.Wp / f) * 3;
+    if (!pr.c[s]) return fail(ctx, OMNI_EINVAL, "internal: no canvas for scale " + std::to_string(s));
   }
   {
     Rec r(ctx, st, 3);

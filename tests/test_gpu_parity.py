@@ -187,7 +187,25 @@ def test_needle_network_small_tiles_fp32_window(api):
     torch.cuda.synchronize()
     orc = O.segment(rgb_np, w, blob, window=(256, 512, 256, 256), batch=8)
     _check_window(out, orc, w, None)
-    assert any(orc["labels"][c].any() for c in orc["labels"])
+    # the window holds tissue and processed tiles at every scale
+    assert orc["prep"]["mask"][8:16, 16:24].any()
+    assert all(orc["cov"][c].max() > 0 for c in orc["cov"])
+    seg.close()
+
+
+def test_needle_network_unpadded_slide_fp32_window(api):
+    """A slide whose size already sits on the tile grid: the 40x canvas is the
+    caller's buffer and the 10x / 5x canvases are the first workspace regions."""
+    w = synth.NEEDLE.with_(H=1024, W=1536, P=128, S=64, median_k=5, max_batch=8)
+    spec = synth.make_spec(1024, 1536, 22, 0.45, "cores", 3)
+    rgb_np = synth.gen_slide(spec)
+    blob = synth.gen_weights(w)
+    seg = api.Segmenter(w, blob)
+    assert seg.query(1024, 1536).Hp == 1024
+    out = seg.segment(torch.from_numpy(rgb_np).cuda(), logits=True, coverage=True)
+    torch.cuda.synchronize()
+    orc = O.segment(rgb_np, w, blob, window=(512, 768, 256, 256), batch=8)
+    _check_window(out, orc, w, None)
     seg.close()
 
 
