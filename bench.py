@@ -92,6 +92,60 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def tag_name(t: int) -> str:
+    if t < 100:
+        return f"conv enc{t // 10}.{t % 10 + 1}"
+    if t < 200:
+        return f"conv dec{(t - 100) // 10}.{t % 10 + 1}"
+    names = {2: "maxpool", 3: "upsample", 4: "gap", 5: "head", 6: "stitch", 7: "prep"}
+    return names.get(t // 100, str(t))
+
+
+def summarize(ms, tags, work, steps):
+    """Per-layer device time per step (ms) and achieved TFLOP/s for convs."""
+    out = {}
+    for t in sorted(set(int(x) for x in tags)):
+        m = tags == t
+        k = tag_name(t)
+        e = out.setdefault(k, {"ms": 0.0, "launches": 0, "flop": 0.0})
+        e["ms"] += float(ms[m].sum()) / steps
+        e["launches"] += int(m.sum()) // steps
+        e["flop"] += float(work[m].sum()) / steps
+    for e in out.values():
+        e["tflops"] = round(e["flop"] / (e["ms"] / 1e3) / 1e12, 1) if e["flop"] and e["ms"] else None
+        e["ms"] = round(e["ms"], 2)
+        del e["flop"]
+    return out
+
+
+def run_layer(args):
+    """One fused conv layer (same kernel as the slide path) launched back to
+    back: the small case used for the tensor-core kernel's ncu capture."""
+    import torch
+    from paper_2305_14566_gb300.build import build
+    build()
+    from paper_2305_14566_gb300 import api, _lib
+    R, cin, cout, cr, B, rep = (int(v) for v in args.layer.split(","))
+    rng = np.random.default_rng(0)
+    prec = _lib.BF16 if args.precision == "bf16" else _lib.FP32
+    dt = torch.bfloat16 if prec == _lib.BF16 else torch.float32
+    x = torch.rand((B, R, R, cin), device="cuda").to(dt)
+    r = torch.rand((B, R, R, cr), device="cuda").to(dt) if cr else None
+    y = torch.empty((B, R, R, cout), device="cuda", dtype=dt)
+    w = (rng.standard_normal((cout, cin, 3, 3)) * np.sqrt(2 / (9 * cin))).astype(np.float32)
+    g = np.ones(cout, np.float32)
+    b = np.zeros(cout, np.float32)
+    wp = (rng.standard_normal((cout, cr)) * np.sqrt(1 / cr)).astype(np.float32) if cr else None
+    api.conv_layer(prec, x, R, cin, cout, w, g, b, y, r, cr, wp, repeat=1)
+    ms = api.conv_layer(prec, x, R, cin, cout, w, g, b, y, r, cr, wp, repeat=rep)
+    fl = 2.0 * B * R * R * cout * (9 * cin + cr)
+    pk, src = peaks()
+    tf = fl / (ms / 1e3) / 1e12
+    print(json.dumps({"layer": {"R": R, "cin": cin, "cout": cout, "cr": cr, "B": B},
+                      "ms_per_launch": ms, "tflops": tf, "frac_of_bf16_burst": tf / pk["bf16_tflops"],
+                      "peak_source": src}))
+
+
 def cpu_baseline(max_tiles: int = 4):
     """The FP64 oracle timed on a bounded sample: the first foreground 40x tiles
     of the needle slide (generated on the CPU), through U-Net, heads and the
@@ -156,7 +210,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-fp32", action="store_true",
                     help="also time one step of the plain FP32 path")
+    ap.add_argument("--layer", default=None,
+                    help="R,cin,cout,cr,B,repeat: time one fused conv layer instead")
     args = ap.parse_args()
+    if args.layer:
+        run_layer(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -192,8 +251,6 @@ def main():
         seg.segment(rgb, out=out)
     barrier()
     seg.set_timing(True)
-    conv_ms = conv_n = conv_flops = 0.0
-    st_ms = st_bytes = 0.0
     launches = 0
     with Clocks(local) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
@@ -203,13 +260,12 @@ def main():
         for _ in range(args.steps):
             seg.segment(rgb, out=out)
             launches += seg.launch_count()
-            ms, n, fl = seg.timing(0)
-            conv_ms += ms; conv_n += n; conv_flops += fl
-            ms, n, by = seg.timing(1)
-            st_ms += ms; st_bytes += by
         t1.record()
         barrier()
     clocks = clk.summary()
+    conv_ms, conv_n, conv_flops = seg.timing(0)
+    st_ms, _, st_bytes = seg.timing(1)
+    ms_l, kinds_l, tags_l, work_l = seg.launch_times()
     seg.set_timing(False)
     ms_step = t0.elapsed_time(t1) / args.steps
     if world > 1:
@@ -218,6 +274,7 @@ def main():
         ms_step = float(tt.item())
     mpx = WORK.H * WORK.W / 1e6
     value = mpx * world / (ms_step / 1e3)
+    breakdown = summarize(ms_l, tags_l, work_l, args.steps)
 
     pk, src = peaks()
     if prec == _lib.BF16:
@@ -274,6 +331,7 @@ def main():
                            "tiles_per_step": int(conv_flops / max(args.steps, 1) /
                                                  seg.query(WORK.H, WORK.W).flops_per_tile)},
                 "roofline": roof, "stitch": stitch, "e2e": e2e, "gpu_launches": int(launches),
+                "breakdown": breakdown,
                 "clocks": clocks}
         if fp32 is not None:
             line["fp32_plain"] = fp32

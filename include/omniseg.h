@@ -200,25 +200,41 @@ omni_status omni_synth_slide(const int64_t* ellipses_host, int32_t n_ell, uint64
  * same kernels omni_segment_slide uses.  x / r / y are NHWC with channel
  * stride *_cs and channel offset *_co (elements); dtype float32 for
  * OMNI_FP32, bfloat16 for OMNI_BF16.  Weights are host FP32 ([cout][cin][3][3],
- * [cout], [cout], [cout][cr]); r may be NULL (no residual).  Allocates and
- * frees its own temporary weight buffers; synchronises `stream`. */
+ * [cout], [cout], [cout][cr]); r may be NULL (no residual).  The layer is
+ * launched `repeat` (>= 1) times back to back; if `ms_per_launch` is not NULL
+ * it receives the mean device time of one launch (CUDA events on `stream`).
+ * Allocates and frees its own temporary weight buffers; synchronises `stream`. */
 omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin, int32_t cout,
                             const void* x_dev, int32_t x_cs, int32_t x_co,
                             const float* w_host, const float* g_host, const float* b_host,
                             const void* r_dev, int32_t r_cs, int32_t r_co, int32_t cr,
                             const float* wp_host, void* y_dev, int32_t y_cs, int32_t y_co,
-                            void* stream);
+                            int32_t repeat, float* ms_per_launch, void* stream);
 
-/* Per-kernel-class device time of the last omni_segment_slide call, measured
- * with CUDA events on the call's stream when enabled.  kind: 0 = tensor-core /
- * FP32 convolutions, 1 = stitch + labels, 2 = head, 3 = everything else.
- * Returns milliseconds summed over launches and the launch count. */
+/* Device timing of omni_segment_slide calls with CUDA events recorded on the
+ * call's stream around every launch.  omni_set_timing(ctx, 1) enables it and
+ * starts a new record (later calls append to it); omni_get_timing sums, for
+ * one kind (0 = U-Net convolutions, 1 = stitch + labels, 2 = GAP + head,
+ * 3 = everything else), the milliseconds and launch count of the record and
+ * returns its algorithmic work (kind 0: conv FLOPs of the processed tiles;
+ * kind 1: bytes the stitch must move).  Synchronises on the recorded events. */
 omni_status omni_set_timing(omni_ctx* ctx, int32_t enabled);
 omni_status omni_get_timing(omni_ctx* ctx, int32_t kind, double* ms, int64_t* launches,
                             double* flops_or_bytes);
 
 /* Number of kernel launches enqueued by the last omni_segment_slide call. */
 int64_t omni_last_launch_count(const omni_ctx* ctx);
+
+/* Per-launch device times (ms) of the current timing record, with each
+ * launch's kind (as above), tag and algorithmic
+ * work (FLOPs for convolutions, else 0).  Tags: conv of encoder level l =
+ * 10 l (first) / 10 l + 1 (second), decoder level l = 100 + 10 l (+1);
+ * max-pool 200 + l, upsample 300 + l, GAP 400, head 500, stitch 600 + scale,
+ * pad 700, pyramid 701, tissue 702, tiles 703.  Writes at most `max`
+ * entries into the caller's host arrays (any may be NULL) and returns the
+ * count, or -1 on error.  Synchronises on the recorded events. */
+int64_t omni_get_launch_times(omni_ctx* ctx, int64_t max, double* ms, int32_t* kinds,
+                              int32_t* tags, double* work);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libomniseg.
 EXPORTS = ("omni_create", "omni_destroy", "omni_last_error", "omni_weights_count",
            "omni_load_weights", "omni_query", "omni_tile_slide", "omni_segment_slide",
            "omni_segment_slide_host", "omni_synth_slide", "omni_conv_layer", "omni_set_timing",
-           "omni_get_timing", "omni_last_launch_count")
+           "omni_get_timing", "omni_last_launch_count", "omni_get_launch_times")
 
 
 class Config(C.Structure):
@@ -80,11 +80,12 @@ def lib() -> C.CDLL:
                                           C.POINTER(vp), vp]),
         "omni_synth_slide": (i32, [vp, i32, u64, i32, i32, i32, i32, i32, vp, i64, vp]),
         "omni_conv_layer": (i32, [i32, i32, i32, i32, i32, vp, i32, i32, vp, vp, vp, vp, i32,
-                                  i32, i32, vp, vp, i32, i32, vp]),
+                                  i32, i32, vp, vp, i32, i32, i32, vp, vp]),
         "omni_set_timing": (i32, [vp, i32]),
         "omni_get_timing": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64),
                                   C.POINTER(C.c_double)]),
         "omni_last_launch_count": (i64, [vp]),
+        "omni_get_launch_times": (i64, [vp, i64, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

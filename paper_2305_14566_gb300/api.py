@@ -179,6 +179,20 @@ class Segmenter:
     def launch_count(self) -> int:
         return int(self.lib.omni_last_launch_count(self.ctx))
 
+    def launch_times(self, max_n: int = 1 << 16):
+        """(ms, kind, tag, work) arrays of every timed launch of the last call."""
+        ms = np.zeros(max_n, np.float64)
+        kinds = np.zeros(max_n, np.int32)
+        tags = np.zeros(max_n, np.int32)
+        work = np.zeros(max_n, np.float64)
+        n = self.lib.omni_get_launch_times(self.ctx, max_n, ms.ctypes.data_as(C.c_void_p),
+                                           kinds.ctypes.data_as(C.c_void_p),
+                                           tags.ctypes.data_as(C.c_void_p),
+                                           work.ctypes.data_as(C.c_void_p))
+        if n < 0:
+            raise L.OmniError(L.ECUDA, "omni_get_launch_times failed")
+        return ms[:n], kinds[:n], tags[:n], work[:n]
+
 
 def synth_slide(spec, y0: int = 0, x0: int = 0, h: Optional[int] = None,
                 w: Optional[int] = None, device="cuda", out: Optional[torch.Tensor] = None):
@@ -198,17 +212,18 @@ def synth_slide(spec, y0: int = 0, x0: int = 0, h: Optional[int] = None,
 def conv_layer(precision: int, x: torch.Tensor, R: int, cin: int, cout: int, w: np.ndarray,
                g: np.ndarray, b: np.ndarray, y: torch.Tensor, r: Optional[torch.Tensor] = None,
                cr: int = 0, wp: Optional[np.ndarray] = None, x_cs=None, x_co=0, r_cs=None,
-               r_co=0, y_cs=None, y_co=0):
-    """One fused conv layer through omni_conv_layer (layer-level checks)."""
+               r_co=0, y_cs=None, y_co=0, repeat: int = 1) -> float:
+    """One fused conv layer through omni_conv_layer; returns ms per launch."""
     B = x.shape[0]
     w = np.ascontiguousarray(w, np.float32)
     g = np.ascontiguousarray(g, np.float32)
     b = np.ascontiguousarray(b, np.float32)
     wpp = None if wp is None else np.ascontiguousarray(wp, np.float32)
+    ms = C.c_float(0.0)
     st = L.lib().omni_conv_layer(
         precision, B, R, cin, cout, _ptr(x), x_cs or cin, x_co, w.ctypes.data_as(C.c_void_p),
         g.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p), _ptr(r), r_cs or cr, r_co, cr,
         None if wpp is None else wpp.ctypes.data_as(C.c_void_p), _ptr(y), y_cs or cout, y_co,
-        _stream())
+        repeat, C.byref(ms), _stream())
     L.check(st, None, "omni_conv_layer failed")
-    return y
+    return ms.value

@@ -25,7 +25,7 @@ struct omni_ctx {
   int32_t* h_counts = nullptr;                      // pinned
   // timing
   bool timing = false;
-  struct Ev { cudaEvent_t a, b; int kind; };
+  struct Ev { cudaEvent_t a, b; int kind, tag; double work; };
   std::vector<Ev> evs;
   size_t ev_used = 0;
   double work[4] = {0, 0, 0, 0};
@@ -217,16 +217,21 @@ struct Rec {
   omni_ctx* c;
   cudaStream_t st;
   int idx;
-  Rec(omni_ctx* c_, cudaStream_t st_, int kind) : c(c_), st(st_), idx(-1) {
+  // kind: 0 conv, 1 stitch, 2 head/GAP, 3 other; tag identifies the layer
+  // (see omni_get_launch_times); work = algorithmic FLOPs (convs) or bytes
+  Rec(omni_ctx* c_, cudaStream_t st_, int kind, int tag = -1, double work = 0)
+      : c(c_), st(st_), idx(-1) {
     if (!c->timing) return;
     if (c->ev_used == c->evs.size()) {
-      omni_ctx::Ev e;
+      omni_ctx::Ev e{};
       cudaEventCreate(&e.a);
       cudaEventCreate(&e.b);
       c->evs.push_back(e);
     }
     idx = (int)c->ev_used++;
     c->evs[idx].kind = kind;
+    c->evs[idx].tag = tag;
+    c->evs[idx].work = work;
     cudaEventRecord(c->evs[idx].a, st);
   }
   ~Rec() {
@@ -453,7 +458,7 @@ omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Pl
   const uint8_t* c40 = rgb;
   int64_t s40 = stride;
   if (p.pad) {
-    Rec r(ctx, st, 3);
+    Rec r(ctx, st, 3, 700);
     OMNI_CU(launch_pad(rgb, stride, g, ws + p.canvas, st), "pad");
     ctx->launches++;
     c40 = ws + p.canvas;
@@ -465,7 +470,7 @@ omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Pl
   uint8_t* c10 = p.c10 != kNone ? ws + p.c10 : nullptr;
   uint8_t* c5 = p.c5 != kNone ? ws + p.c5 : nullptr;
   {
-    Rec r(ctx, st, 3);
+    Rec r(ctx, st, 3, 701);
     OMNI_CU(launch_pyramid(c40, s40, g.Hp, g.Wp, c20, c10, c5, (uint16_t*)(ws + p.blk8), st), "pyramid");
     ctx->launches++;
   }
@@ -476,14 +481,14 @@ omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Pl
     if (!pr.c[s]) return fail(ctx, OMNI_EINVAL, "internal: no canvas for scale " + std::to_string(s));
   }
   {
-    Rec r(ctx, st, 3);
+    Rec r(ctx, st, 3, 702);
     OMNI_CU(launch_tissue((uint16_t*)(ws + p.blk8), g, c.median_k, ws + p.grey, ws + p.blur,
                           (int32_t*)(ws + p.hist), (int32_t*)(ws + p.otsu), ws + p.mask, st),
             "tissue");
     ctx->launches += 5;
   }
   {
-    Rec r(ctx, st, 3);
+    Rec r(ctx, st, 3, 703);
     OMNI_CU(launch_tiles(ws + p.mask, g, c.tissue_filter, (int32_t*)(ws + p.tiles),
                          (int32_t*)(ws + p.counts), ws + p.flags, (int32_t*)(ws + p.slot), st),
             "tiles");
@@ -492,8 +497,13 @@ omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Pl
   return OMNI_OK;
 }
 
-omni_status run_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st) {
-  Rec r(ctx, st, 0);
+double conv_flops(const ConvArgs& a) {
+  const double cr = a.res_mode == RES_TENSOR ? a.cr : (a.res_mode == RES_RGB ? 3 : 0);
+  return 2.0 * a.B * a.R * a.R * a.cout * (9.0 * a.cin + cr);
+}
+
+omni_status run_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, int tag) {
+  Rec r(ctx, st, 0, tag, conv_flops(a));
   cudaError_t e;
   if (ctx->cfg.precision == OMNI_FP32) {
     e = launch_conv_f32(a, st);
@@ -534,7 +544,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     a.R = c.patch; a.cin = 3; a.cout = C(0);
     a.y = tmp; a.y_cs = C(0); a.y_co = 0;
     a.w = ctx->enc1[0];
-    Rec r(ctx, st, 0);
+    Rec r(ctx, st, 0, 0, conv_flops(a));
     cudaError_t e = launch_conv_first(a, prec, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_first");
     ctx->launches++;
@@ -546,7 +556,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     a.res_mode = RES_RGB; a.cr = 3;
     enc_out(0, a.y, a.y_cs, a.y_co);
     a.w = ctx->enc2[0];
-    omni_status r = run_conv(ctx, a, st);
+    omni_status r = run_conv(ctx, a, st, 1);
     if (r) return r;
   }
   for (int l = 1; l < L; ++l) {
@@ -554,7 +564,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     void* pp; int pcs, pco;
     enc_out(l - 1, pp, pcs, pco);
     {
-      Rec r(ctx, st, 3);
+      Rec r(ctx, st, 3, 200 + l);
       OMNI_CU(launch_maxpool(prec, nb, 2 * R, C(l - 1), pp, pcs, pco, pooled, C(l - 1), 0, st), "maxpool");
       ctx->launches++;
     }
@@ -563,7 +573,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     a.x = pooled; a.x_cs = C(l - 1); a.x_co = 0;
     a.y = tmp; a.y_cs = C(l); a.y_co = 0;
     a.w = ctx->enc1[l];
-    omni_status r = run_conv(ctx, a, st);
+    omni_status r = run_conv(ctx, a, st, 10 * l);
     if (r) return r;
     ConvArgs b2 = base;
     b2.R = R; b2.cin = C(l); b2.cout = C(l);
@@ -571,12 +581,12 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     b2.res_mode = RES_TENSOR; b2.r = pooled; b2.r_cs = C(l - 1); b2.r_co = 0; b2.cr = C(l - 1);
     enc_out(l, b2.y, b2.y_cs, b2.y_co);
     b2.w = ctx->enc2[l];
-    r = run_conv(ctx, b2, st);
+    r = run_conv(ctx, b2, st, 10 * l + 1);
     if (r) return r;
   }
   float* gap = reinterpret_cast<float*>(ws + p.gap);
   {
-    Rec r(ctx, st, 2);
+    Rec r(ctx, st, 2, 400);
     OMNI_CU(launch_gap(prec, nb, c.patch >> (L - 1), C(L - 1), bott, C(L - 1), 0, gap, st), "gap");
     ctx->launches++;
   }
@@ -586,7 +596,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     const int R = c.patch >> l;
     void* cat = ws + p.cat[l];
     {
-      Rec r(ctx, st, 3);
+      Rec r(ctx, st, 3, 300 + l);
       OMNI_CU(launch_upsample(prec, nb, R, 2 * C(l), y, y_cs, 0, cat, 3 * C(l), 0, st), "upsample");
       ctx->launches++;
     }
@@ -595,7 +605,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     a.x = cat; a.x_cs = 3 * C(l); a.x_co = 0;
     a.y = tmp; a.y_cs = C(l); a.y_co = 0;
     a.w = ctx->dec1[l];
-    omni_status r = run_conv(ctx, a, st);
+    omni_status r = run_conv(ctx, a, st, 100 + 10 * l);
     if (r) return r;
     ConvArgs b2 = base;
     b2.R = R; b2.cin = C(l); b2.cout = C(l);
@@ -603,7 +613,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     b2.res_mode = RES_TENSOR; b2.r = cat; b2.r_cs = 3 * C(l); b2.r_co = 0; b2.cr = 3 * C(l);
     b2.y = ws + p.ydec[l]; b2.y_cs = C(l); b2.y_co = 0;
     b2.w = ctx->dec2[l];
-    r = run_conv(ctx, b2, st);
+    r = run_conv(ctx, b2, st, 100 + 10 * l + 1);
     if (r) return r;
     y = ws + p.ydec[l];
     y_cs = C(l);
@@ -618,7 +628,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   h.slot0 = slot0;
   h.logits = reinterpret_cast<float*>(ws + p.logits);
   {
-    Rec r(ctx, st, 2);
+    Rec r(ctx, st, 2, 500);
     OMNI_CU(launch_head(h, st), "head");
     ctx->launches++;
   }
@@ -675,10 +685,8 @@ omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int
   if (r) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t* ws = static_cast<uint8_t*>(ws_);
-  ctx->ev_used = 0;
   ctx->launches = 0;
   ctx->tiles_done = 0;
-  for (int k = 0; k < 4; ++k) ctx->work[k] = 0;
   Prep pr;
   r = run_prep(ctx, rgb, stride, p, ws, st, pr);
   if (r) return r;
@@ -730,15 +738,15 @@ omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int
       for (int k = 0; k < ncls; ++k) stitch_bytes += px * ((a.labels[k] ? 1 : 0) + (a.out_logits[k] ? 4 : 0));
       stitch_bytes += px * ((a.coverage ? 2 : 0) + (a.argmax ? 1 : 0));
       {
-        Rec rr(ctx, st, 1);
+        Rec rr(ctx, st, 1, 600 + s);
         OMNI_CU(launch_stitch(a, st), "stitch");
         ctx->launches++;
       }
     }
     toff += n_s;
   }
-  ctx->work[0] = (double)ctx->tiles_done * (double)p.flops_per_tile;
-  ctx->work[1] = stitch_bytes;
+  ctx->work[0] += (double)ctx->tiles_done * (double)p.flops_per_tile;
+  ctx->work[1] += stitch_bytes;
   return OMNI_OK;
 }
 
@@ -788,7 +796,8 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
                             const void* x, int32_t x_cs, int32_t x_co, const float* w_host,
                             const float* g_host, const float* b_host, const void* r, int32_t r_cs,
                             int32_t r_co, int32_t cr, const float* wp_host, void* y, int32_t y_cs,
-                            int32_t y_co, void* stream) {
+                            int32_t y_co, int32_t repeat, float* ms_per_launch, void* stream) {
+  if (repeat < 1) return OMNI_EINVAL;
   if (!x || !y || !w_host || !g_host || !b_host || B <= 0 || R <= 0 || cin <= 0 || cout <= 0) return OMNI_EINVAL;
   if (cin % 8 || cout % 8 || (r && (cr <= 0 || cr % 8 || !wp_host))) return OMNI_EINVAL;
   if (precision != OMNI_FP32 && precision != OMNI_BF16) return OMNI_EINVAL;
@@ -844,8 +853,23 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
     a.w.gamma = reinterpret_cast<float*>(d + og);
     a.w.beta = reinterpret_cast<float*>(d + ob);
     a.err = derr;
-    e = precision == OMNI_FP32 ? launch_conv_f32(a, st) : launch_conv_tc(a, st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms_per_launch) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, st);
+    }
+    for (int i = 0; i < repeat && e == cudaSuccess; ++i)
+      e = precision == OMNI_FP32 ? launch_conv_f32(a, st) : launch_conv_tc(a, st);
+    if (ms_per_launch) cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (ms_per_launch) {
+      float t = 0;
+      if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+      *ms_per_launch = t / repeat;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
     unsigned herr = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && herr) rs = OMNI_ETIMEOUT;
@@ -859,6 +883,8 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
 omni_status omni_set_timing(omni_ctx* ctx, int32_t enabled) {
   if (!ctx) return OMNI_EINVAL;
   ctx->timing = enabled != 0;
+  ctx->ev_used = 0;
+  for (int k = 0; k < 4; ++k) ctx->work[k] = 0;
   return OMNI_OK;
 }
 
@@ -882,5 +908,22 @@ omni_status omni_get_timing(omni_ctx* ctx, int32_t kind, double* ms, int64_t* la
 }
 
 int64_t omni_last_launch_count(const omni_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int64_t omni_get_launch_times(omni_ctx* ctx, int64_t max, double* ms, int32_t* kinds, int32_t* tags,
+                              double* work) {
+  if (!ctx) return -1;
+  int64_t n = 0;
+  for (size_t i = 0; i < ctx->ev_used && n < max; ++i, ++n) {
+    float t = 0;
+    if (cudaEventSynchronize(ctx->evs[i].b) != cudaSuccess ||
+        cudaEventElapsedTime(&t, ctx->evs[i].a, ctx->evs[i].b) != cudaSuccess)
+      return -1;
+    if (ms) ms[n] = t;
+    if (kinds) kinds[n] = ctx->evs[i].kind;
+    if (tags) tags[n] = ctx->evs[i].tag;
+    if (work) work[n] = ctx->evs[i].work;
+  }
+  return n;
+}
 
 }  // extern "C"
