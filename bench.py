@@ -210,6 +210,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-fp32", action="store_true",
                     help="also time one step of the plain FP32 path")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run exactly one slide step after the generator (for ncu launch lists)")
     ap.add_argument("--layer", default=None,
                     help="R,cin,cout,cr,B,repeat: time one fused conv layer instead")
     args = ap.parse_args()
@@ -241,6 +243,10 @@ def main():
     seg = api.Segmenter(WORK, blob, precision=prec)
     out = seg.segment(rgb)
     torch.cuda.synchronize()
+    if args.profile_step:
+        print(json.dumps({"profile_step": True, "launches": seg.launch_count()}))
+        seg.close()
+        return
 
     def barrier():
         if world > 1:
