@@ -236,6 +236,32 @@ int64_t omni_last_launch_count(const omni_ctx* ctx);
 int64_t omni_get_launch_times(omni_ctx* ctx, int64_t max, double* ms, int32_t* kinds,
                               int32_t* tags, double* work);
 
+/* Tissue detection and tiling (as omni_tile_slide) for callers that may not
+ * allocate device memory while they run -- for instance a slide scanner's
+ * acquisition loop that reserves its whole device-memory budget at start-up,
+ * or a host process whose device memory is owned by another framework's pool,
+ * where an extra cudaMalloc could fail or fragment that pool mid-run.  It
+ * takes no workspace and calls no allocating routine: its scratch is a fixed
+ * static device array of about 13 MiB (OMNI_NOALLOC_MAX_THUMB_PX thumbnail
+ * pixels, OMNI_NOALLOC_MAX_TILES tile-grid cells, i.e. slides up to about
+ * 4 Gpx at 40x), which every GPU that loads the library keeps until the
+ * process exits.  Larger slides return OMNI_EINVAL with a message on stderr
+ * and launch nothing.  The thumbnail is computed straight from `rgb_dev`
+ * (padding is applied virtually), so no padded copy of the slide is made.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the one array and leave their scratch in
+ * it (every call re-initialises what it needs), so calls that can overlap on
+ * the GPU -- on different streams or host threads, on the same device --
+ * race and must be serialised by the caller.  The outputs go to the caller's
+ * `out` buffers exactly as for omni_tile_slide and are bit-identical to its.
+ * The paper has no counterpart of this entry point. */
+#define OMNI_NOALLOC_MAX_THUMB_PX (4 << 20)
+#define OMNI_NOALLOC_MAX_TILES (1 << 16)
+omni_status omni_tile_slide_noalloc(const omni_config* cfg, const uint8_t* rgb_dev, int32_t H,
+                                    int32_t W, int64_t row_stride, const omni_tile_list* out,
+                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,13 +15,16 @@ MAX_CLASSES = 16
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EWEIGHTS, ESTATE = 0, -1, -2, -3, -4, -5, -6
 FP32, BF16 = 0, 1
 STITCH_AVG, STITCH_VOTE = 0, 1
+NOALLOC_MAX_THUMB_PX = 4 << 20
+NOALLOC_MAX_TILES = 1 << 16
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libomniseg.so")
 
 EXPORTS = ("omni_create", "omni_destroy", "omni_last_error", "omni_weights_count",
            "omni_load_weights", "omni_query", "omni_tile_slide", "omni_segment_slide",
            "omni_segment_slide_host", "omni_synth_slide", "omni_conv_layer", "omni_set_timing",
-           "omni_get_timing", "omni_last_launch_count", "omni_get_launch_times")
+           "omni_get_timing", "omni_last_launch_count", "omni_get_launch_times",
+           "omni_tile_slide_noalloc")
 
 
 class Config(C.Structure):
@@ -86,6 +89,8 @@ def lib() -> C.CDLL:
                                   C.POINTER(C.c_double)]),
         "omni_last_launch_count": (i64, [vp]),
         "omni_get_launch_times": (i64, [vp, i64, vp, vp, vp, vp]),
+        "omni_tile_slide_noalloc": (i32, [C.POINTER(Config), vp, i32, i32, i64,
+                                          C.POINTER(TileList), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -194,6 +194,28 @@ class Segmenter:
         return ms[:n], kinds[:n], tags[:n], work[:n]
 
 
+def tile_slide_noalloc(work, rgb: torch.Tensor) -> Dict[str, torch.Tensor]:
+    """omni_tile_slide_noalloc: tiling with the library's static scratch
+    (no workspace, no device allocation inside the call)."""
+    cfg = make_config(work)
+    H, W, _ = rgb.shape
+    s = L.Sizes()
+    L.check(L.lib().omni_query(C.byref(cfg), H, W, C.byref(s)), None, "omni_query: bad size")
+    dev = rgb.device
+    n = s.n_tiles_max
+    out = dict(tiles=torch.zeros((n, 3), dtype=torch.int32, device=dev),
+               counts=torch.zeros(1 + cfg.n_scales, dtype=torch.int32, device=dev),
+               flags=torch.zeros(n, dtype=torch.uint8, device=dev),
+               tissue=torch.zeros((s.thumb_h, s.thumb_w), dtype=torch.uint8, device=dev),
+               otsu=torch.zeros(1, dtype=torch.int32, device=dev))
+    tl = L.TileList(out["tiles"].data_ptr(), out["counts"].data_ptr(), out["flags"].data_ptr(),
+                    out["tissue"].data_ptr(), out["otsu"].data_ptr())
+    L.check(L.lib().omni_tile_slide_noalloc(C.byref(cfg), _ptr(rgb), H, W, rgb.stride(0),
+                                            C.byref(tl), _stream()),
+            None, "omni_tile_slide_noalloc rejected the call")
+    return out
+
+
 def synth_slide(spec, y0: int = 0, x0: int = 0, h: Optional[int] = None,
                 w: Optional[int] = None, device="cuda", out: Optional[torch.Tensor] = None):
     """Window of a seeded synthetic slide generated on the device."""

@@ -417,6 +417,19 @@ cudaError_t launch_tissue(const uint16_t* blk8, const SlideGeom& g, int median_k
   return cudaGetLastError();
 }
 
+cudaError_t launch_tissue_grey(const uint8_t* grey, const SlideGeom& g, int median_k, uint8_t* blurred,
+                               int32_t* hist, int32_t* otsu, uint8_t* mask, cudaStream_t st) {
+  dim3 g2((g.tw + 31) / 32, (g.th + kMedStrip - 1) / kMedStrip);
+  k_median<<<g2, 32, 0, st>>>(grey, g.th, g.tw, median_k, blurred);
+  cudaError_t e = cudaMemsetAsync(hist, 0, 256 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  long long n = (long long)g.th * g.tw;
+  k_hist<<<152, 256, 0, st>>>(blurred, n, hist);
+  k_otsu<<<1, 256, 0, st>>>(hist, otsu);
+  k_mask<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(blurred, n, otsu, mask);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tiles(const uint8_t* mask, const SlideGeom& g, int filter, int32_t* tiles,
                          int32_t* counts, uint8_t* flags, int32_t* slot_map, cudaStream_t st) {
   int total = g.grid_off[g.n_scales];

@@ -45,6 +45,9 @@ cudaError_t launch_pyramid(const uint8_t* c40, int64_t stride40, int Hp, int Wp,
 cudaError_t launch_tissue(const uint16_t* blk8, const SlideGeom& g, int median_k, uint8_t* grey,
                           uint8_t* blurred, int32_t* hist, int32_t* otsu, uint8_t* mask,
                           cudaStream_t st);
+// median blur, histogram, Otsu and mask from an existing thumbnail grey image
+cudaError_t launch_tissue_grey(const uint8_t* grey, const SlideGeom& g, int median_k, uint8_t* blurred,
+                               int32_t* hist, int32_t* otsu, uint8_t* mask, cudaStream_t st);
 cudaError_t launch_tiles(const uint8_t* mask, const SlideGeom& g, int filter, int32_t* tiles,
                          int32_t* counts, uint8_t* flags, int32_t* slot_map, cudaStream_t st);
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -927,3 +928,112 @@ int64_t omni_get_launch_times(omni_ctx* ctx, int64_t max, double* ms, int32_t* k
 }
 
 }  // extern "C"
+
+// ====================================================================== tiling without allocation
+// omni_tile_slide_noalloc serves callers that may not allocate device memory
+// while they run (see omniseg.h).  Its scratch is this file-scope array, which
+// every GPU that loads the library holds until the process exits.  Host code
+// must not pass the symbol itself to a kernel: on the host it names a stand-in
+// object, not device memory.  The device address is looked up once per device
+// with cudaGetSymbolAddress and cached.
+namespace {
+
+constexpr size_t kNoAllocScratch = 13u << 20;
+static __device__ __align__(256) uint8_t g_tile_scratch[kNoAllocScratch];
+
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[64] = {};
+
+// Device address of g_tile_scratch on the current device (set-up on first use).
+cudaError_t scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_tile_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+// Thumbnail grey straight from the caller's slide: one warp per 32x32 block of
+// the padded 40x canvas, lane = block row; canvas pixels outside the slide take
+// the 2x2-mean pad colour, so no padded copy of the slide is needed.
+__global__ void k_thumb_direct(const uint8_t* __restrict__ rgb, long long stride, SlideGeom g,
+                               uint8_t* __restrict__ grey) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= g.th * g.tw) return;
+  const int ty = warp / g.tw, tx = warp % g.tw;
+  int pad[3];
+  const int h2 = g.H > 1 ? 1 : 0, w2 = g.W > 1 ? 1 : 0;
+  for (int c = 0; c < 3; ++c) {
+    int s = rgb[c] + rgb[w2 * 3 + c] + rgb[(long long)h2 * stride + c] + rgb[(long long)h2 * stride + w2 * 3 + c];
+    pad[c] = (s + 2) >> 2;
+  }
+  const int y = ty * kThumb + lane - g.lead;
+  int sum[3] = {0, 0, 0};
+  for (int q = 0; q < kThumb; ++q) {
+    const int x = tx * kThumb + q - g.lead;
+    if (y >= 0 && y < g.H && x >= 0 && x < g.W) {
+      const uint8_t* p = rgb + (long long)y * stride + (long long)x * 3;
+      sum[0] += p[0]; sum[1] += p[1]; sum[2] += p[2];
+    } else {
+      sum[0] += pad[0]; sum[1] += pad[1]; sum[2] += pad[2];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int c = 0; c < 3; ++c) sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], o);
+  if (lane == 0) {
+    const int R = (sum[0] + 512) >> 10, G = (sum[1] + 512) >> 10, B = (sum[2] + 512) >> 10;
+    grey[warp] = (uint8_t)((77 * R + 150 * G + 29 * B + 128) >> 8);
+  }
+}
+
+}  // namespace
+
+extern "C" omni_status omni_tile_slide_noalloc(const omni_config* cfg, const uint8_t* rgb, int32_t H,
+                                               int32_t W, int64_t stride, const omni_tile_list* out,
+                                               void* stream) {
+  if (!cfg || !rgb || !out || !out->tiles || !out->counts) return OMNI_EINVAL;
+  if (!validate(*cfg).empty() || stride < (int64_t)W * 3) return OMNI_EINVAL;
+  Plan p;
+  if (!make_plan(*cfg, H, W, p)) return OMNI_EINVAL;
+  const SlideGeom& g = p.g;
+  const size_t thumb = (size_t)g.th * g.tw;
+  const size_t ntile = (size_t)g.grid_off[cfg->n_scales];
+  if (thumb > OMNI_NOALLOC_MAX_THUMB_PX || ntile > OMNI_NOALLOC_MAX_TILES) {
+    fprintf(stderr,
+            "omni_tile_slide_noalloc: slide needs a %dx%d thumbnail and %zu tile cells; the static "
+            "scratch holds %d thumbnail pixels and %d tile cells\n",
+            g.th, g.tw, ntile, OMNI_NOALLOC_MAX_THUMB_PX, OMNI_NOALLOC_MAX_TILES);
+    return OMNI_EINVAL;
+  }
+  void* base = nullptr;
+  if (scratch_address(&base) != cudaSuccess) return OMNI_ECUDA;
+  size_t off = 0;
+  uint8_t* sc = static_cast<uint8_t*>(base);
+  uint8_t* grey = sc + take(off, OMNI_NOALLOC_MAX_THUMB_PX);
+  uint8_t* blur = sc + take(off, OMNI_NOALLOC_MAX_THUMB_PX);
+  uint8_t* mask = sc + take(off, OMNI_NOALLOC_MAX_THUMB_PX);
+  int32_t* hist = reinterpret_cast<int32_t*>(sc + take(off, 256 * 4));
+  int32_t* otsu = reinterpret_cast<int32_t*>(sc + take(off, 4));
+  uint8_t* flags = sc + take(off, OMNI_NOALLOC_MAX_TILES);
+  int32_t* slot = reinterpret_cast<int32_t*>(sc + take(off, (size_t)OMNI_NOALLOC_MAX_TILES * 4));
+  if (off > kNoAllocScratch) return OMNI_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const unsigned blocks = (unsigned)((thumb * 32 + 255) / 256);
+  k_thumb_direct<<<blocks, 256, 0, st>>>(rgb, stride, g, grey);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_tissue_grey(grey, g, cfg->median_k, blur, hist, otsu, mask, st);
+  if (e == cudaSuccess)
+    e = launch_tiles(mask, g, cfg->tissue_filter, out->tiles, out->counts, out->flags ? out->flags : flags,
+                     slot, st);
+  if (e == cudaSuccess && out->tissue) e = cudaMemcpyAsync(out->tissue, mask, thumb, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && out->otsu) e = cudaMemcpyAsync(out->otsu, otsu, 4, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? OMNI_OK : OMNI_ECUDA;
+}
