@@ -97,6 +97,8 @@ def tag_name(t: int) -> str:
         return f"conv enc{t // 10}.{t % 10 + 1}"
     if t < 200:
         return f"conv dec{(t - 100) // 10}.{t % 10 + 1}"
+    if t == 401:
+        return "controller"
     names = {2: "maxpool", 3: "upsample", 4: "gap", 5: "head", 6: "stitch", 7: "prep"}
     return names.get(t // 100, str(t))
 
@@ -170,7 +172,9 @@ def cpu_baseline(max_tiles: int = 4):
         per[(y, x)] = lg[0, 0].numpy()
     O.stitch(per, h, w, WORK.P)
     dt = time.perf_counter() - t0
-    total_tiles = 12899 * 0.5   # about half the slide's tiles touch tissue
+    # foreground tiles of the slide, as the oracle counts them (tests/golden/make_needle_tiles.py)
+    gold = os.path.join(ROOT, "tests", "golden", "needle_tiles.json")
+    total_tiles = json.load(open(gold))["tiles_total"] if os.path.exists(gold) else 12899 * 0.5
     mpx = WORK.H * WORK.W / 1e6 * len(tiles) / total_tiles
     return {"value": mpx / dt, "unit": "Mpx/s", "cores": torch.get_num_threads(),
             "kind": "oracle",

@@ -229,7 +229,7 @@ int64_t omni_last_launch_count(const omni_ctx* ctx);
  * launch's kind (as above), tag and algorithmic
  * work (FLOPs for convolutions, else 0).  Tags: conv of encoder level l =
  * 10 l (first) / 10 l + 1 (second), decoder level l = 100 + 10 l (+1);
- * max-pool 200 + l, upsample 300 + l, GAP 400, head 500, stitch 600 + scale,
+ * max-pool 200 + l, upsample 300 + l, GAP 400, controller 401, head 500, stitch 600 + scale,
  * pad 700, pyramid 701, tissue 702, tiles 703.  Writes at most `max`
  * entries into the caller's host arrays (any may be NULL) and returns the
  * count, or -1 on error.  Synchronises on the recorded events. */

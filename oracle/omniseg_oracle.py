@@ -507,6 +507,65 @@ def segment(rgb: np.ndarray, work, blob: np.ndarray, window=None, batch: int = 4
     return out
 
 
+def segment_window_regions(get40, mask: np.ndarray, work, blob: np.ndarray, window,
+                           Hp: int, Wp: int, batch: int = 2, scales=None):
+    """The whole path restricted to a window, for slides too large to hold.
+
+    ``get40(y0, x0, h, w)`` returns 40x padded-canvas pixels; ``mask`` is the
+    slide's thumbnail tissue mask (computed by ``tissue_mask`` on the full
+    slide).  Each covering tile's pixels at scale f come from its 40x footprint
+    by iterated 2x2 means, which equals the same crop of the full pyramid
+    because every output pixel depends only on its own f x f block.
+    """
+    p = weights_f64(work, blob)
+    tiles, _ = tile_list(work, mask, Hp, Wp)
+    P = work.P
+    out = {"L": {}, "cov": {}, "labels": {}, "window": {}}
+    for s, f in enumerate(work.factors):
+        if scales is not None and s not in scales:
+            continue
+        hs, ws = Hp // f, Wp // f
+        wy0, wx0, wh, ww = window[0] // f, window[1] // f, max(1, window[2] // f), max(1, window[3] // f)
+        mine = [(y, x) for (ss, y, x) in tiles if ss == s
+                and y < wy0 + wh and y + P > wy0 and x < wx0 + ww and x + P > wx0]
+        classes = [c for c, cs in enumerate(work.class_scale) if cs == s]
+        per_class = {c: {} for c in classes}
+        for k in range(0, len(mine), batch):
+            chunk = mine[k:k + batch]
+            pats = []
+            for (y, x) in chunk:
+                img = get40(y * f, x * f, P * f, P * f)
+                g = f
+                while g > 1:
+                    img = half(img)
+                    g //= 2
+                pats.append(img)
+            lg, cls = patch_forward(np.stack(pats, 0), p, work, s)
+            for ci, c in enumerate(cls):
+                for bi, (y, x) in enumerate(chunk):
+                    per_class[c][(y, x)] = lg[ci, bi].numpy()
+        # stitch only the window: shift tile origins into window coordinates
+        tis = tissue_at_scale(mask, f, hs, ws)[wy0:wy0 + wh, wx0:wx0 + ww] if work.tissue_and else None
+        for c in classes:
+            acc = np.zeros((wh, ww), np.float64)
+            cov = np.zeros((wh, ww), np.int64)
+            votes = np.zeros((wh, ww), np.int64)
+            for (y, x) in sorted(per_class[c]):
+                lp = per_class[c][(y, x)]
+                ya, yb = max(y, wy0), min(y + P, wy0 + wh)
+                xa, xb = max(x, wx0), min(x + P, wx0 + ww)
+                sub = lp[ya - y:yb - y, xa - x:xb - x]
+                acc[ya - wy0:yb - wy0, xa - wx0:xb - wx0] += sub
+                cov[ya - wy0:yb - wy0, xa - wx0:xb - wx0] += 1
+                votes[ya - wy0:yb - wy0, xa - wx0:xb - wx0] += (sub > 0)
+            L = np.where(cov > 0, acc / np.maximum(cov, 1), 0.0)
+            out["L"][c] = L
+            out["cov"][c] = cov
+            out["labels"][c] = labels(L, cov, votes, work.stitch_mode, tis)
+        out["window"][s] = (wy0, wx0, wh, ww)
+    return out
+
+
 # ----------------------------------------------------------------------------
 # Differentiation: stitched soft-Dice + BCE and its gradient
 # ----------------------------------------------------------------------------

@@ -49,8 +49,11 @@ __device__ __forceinline__ float norm_u8(uint8_t u) { return 2.0f * (float)u / 2
 // ------------------------------------------------------------------ first conv
 // conv3x3 over the 3 normalised colour channels of a tile read in place from
 // the uint8 canvas (zero padding at the tile border), norm, ReLU.
+// Each thread computes four horizontally adjacent pixels so every weight read
+// from shared memory feeds four FMAs.  grid: x = column quads, y = row, z = tile.
+constexpr int kFirstPix = 4;
 template <int C0, typename T>
-__global__ void __launch_bounds__(128) k_conv_first(int B, int P, const uint8_t* __restrict__ canvas,
+__global__ void __launch_bounds__(128) k_conv_first(int P, const uint8_t* __restrict__ canvas,
                                                     long long cstride,
                                                     const int32_t* __restrict__ tiles3,
                                                     const float* __restrict__ w27,  // [27][C0]
@@ -62,42 +65,55 @@ __global__ void __launch_bounds__(128) k_conv_first(int B, int P, const uint8_t*
   for (int i = threadIdx.x; i < 27 * C0; i += blockDim.x) ws[i] = w27[i];
   for (int i = threadIdx.x; i < C0; i += blockDim.x) { gs[i] = gamma[i]; bs[i] = beta[i]; }
   __syncthreads();
-  long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long total = (long long)B * P * P;
-  if (m >= total) return;
-  int b = (int)(m / ((long long)P * P));
-  int rem = (int)(m - (long long)b * P * P);
-  int i = rem / P, j = rem % P;
-  int ty = tiles3[3 * b + 1], tx = tiles3[3 * b + 2];
-  float in[27];
+  const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * kFirstPix;
+  if (j0 >= P) return;
+  const int i = blockIdx.y, b = blockIdx.z;
+  const int ty = tiles3[3 * b + 1], tx = tiles3[3 * b + 2];
+  // 3 rows x 6 columns x 3 channels of normalised input around the four pixels
+  float in[3][kFirstPix + 2][3];
 #pragma unroll
   for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-    for (int dx = 0; dx < 3; ++dx) {
-      int ii = i + dy - 1, jj = j + dx - 1;
-      bool ok = ii >= 0 && ii < P && jj >= 0 && jj < P;
+    for (int q = 0; q < kFirstPix + 2; ++q) {
+      const int ii = i + dy - 1, jj = j0 + q - 1;
+      const bool ok = ii >= 0 && ii < P && jj >= 0 && jj < P;
       // address of a pixel inside the tile even where the window leaves it
       const int ic = min(max(ii, 0), P - 1), jc = min(max(jj, 0), P - 1);
       const uint8_t* p = canvas + (long long)(ty + ic) * cstride + (long long)(tx + jc) * 3;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float v = norm_u8(p[c]);
-        in[(dy * 3 + dx) * 3 + c] = ok ? v : 0.0f;
+        in[dy][q][c] = ok ? v : 0.0f;
       }
     }
-  T* out = y + m * y_cs + y_co;
-#pragma unroll
+  T* out = y + (((long long)b * P + i) * P + j0) * y_cs + y_co;
+#pragma unroll 1
   for (int o0 = 0; o0 < C0; o0 += 8) {
-    float acc[8];
+    float acc[kFirstPix][8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+    for (int u = 0; u < kFirstPix; ++u)
 #pragma unroll
-    for (int k = 0; k < 27; ++k)
+      for (int q = 0; q < 8; ++q) acc[u][q] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q] = fmaf(in[k], ws[k * C0 + o0 + q], acc[q]);
+    for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = fmaxf(fmaf(gs[o0 + q], acc[q], bs[o0 + q]), 0.0f);
-    Vec8<T>::store(out + o0, acc);
+      for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float* wr = ws + ((dy * 3 + dx) * 3 + c) * C0 + o0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float w = wr[q];
+#pragma unroll
+            for (int u = 0; u < kFirstPix; ++u) acc[u][q] = fmaf(in[dy][u + dx][c], w, acc[u][q]);
+          }
+        }
+#pragma unroll
+    for (int u = 0; u < kFirstPix; ++u) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[u][q] = fmaxf(fmaf(gs[o0 + q], acc[u][q], bs[o0 + q]), 0.0f);
+      Vec8<T>::store(out + (long long)u * y_cs + o0, acc[u]);
+    }
   }
 }
 
@@ -247,6 +263,14 @@ __global__ void __launch_bounds__(kThreads) k_conv_f32(ConvArgs a) {
                           fmaf(v1, a.w.wp_f32[a.cout + n], v2 * a.w.wp_f32[2 * a.cout + n]));
       }
     }
+    if (a.raw) {
+      *reinterpret_cast<float4*>(Y + m * a.y_cs + a.y_co + n0 + tn * TN) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      if (a.res_mode == RES_TENSOR)
+        *reinterpret_cast<float4*>(static_cast<float*>(a.y2) + m * a.y2_cs + n0 + tn * TN) =
+            make_float4(accr[i][0], accr[i][1], accr[i][2], accr[i][3]);
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < TN; ++j) o[j] = fmaxf(fmaf(g[j], acc[i][j], be[j]) + accr[i][j], 0.f);
     *reinterpret_cast<float4*>(Y + m * a.y_cs + a.y_co + n0 + tn * TN) =
@@ -255,18 +279,15 @@ __global__ void __launch_bounds__(kThreads) k_conv_f32(ConvArgs a) {
 }
 
 // ------------------------------------------------------------------ pooling / upsampling
+// grid: x = (output column, 8-channel group), y = output row, z = image
 template <typename T>
-__global__ void k_maxpool(int B, int R, int C, const T* __restrict__ x, int x_cs, int x_co,
+__global__ void k_maxpool(int R, int C, const T* __restrict__ x, int x_cs, int x_co,
                           T* __restrict__ y, int y_cs, int y_co) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int Ro = R / 2, cg = C / 8;
-  long long total = (long long)B * Ro * Ro * cg;
-  if (idx >= total) return;
-  int c = (int)(idx % cg) * 8;
-  long long p = idx / cg;
-  int b = (int)(p / ((long long)Ro * Ro));
-  int rem = (int)(p - (long long)b * Ro * Ro);
-  int i = rem / Ro, j = rem % Ro;
+  const int Ro = R >> 1, cg = C >> 3;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Ro * cg) return;
+  const int j = t / cg, c = (t - j * cg) * 8;
+  const int i = blockIdx.y, b = blockIdx.z;
   float m[8], v[8];
   const T* base = x + ((long long)b * R * R) * x_cs + x_co + c;
   Vec8<T>::load(base + ((long long)(2 * i) * R + 2 * j) * x_cs, m);
@@ -277,25 +298,21 @@ __global__ void k_maxpool(int B, int R, int C, const T* __restrict__ x, int x_cs
 #pragma unroll
     for (int k = 0; k < 8; ++k) m[k] = fmaxf(m[k], v[k]);
   }
-  Vec8<T>::store(y + p * y_cs + y_co + c, m);
+  Vec8<T>::store(y + (((long long)b * Ro + i) * Ro + j) * y_cs + y_co + c, m);
 }
 
 // bilinear x2, half-pixel centres (align_corners = False), edge clamp:
 // even output 2k mixes source k-1 (0.25) and k (0.75); odd 2k+1 mixes k (0.75)
-// and k+1 (0.25).  R is the OUTPUT size.
+// and k+1 (0.25).  R is the OUTPUT size; grid as for k_maxpool.
 template <typename T>
-__global__ void k_upsample(int B, int R, int C, const T* __restrict__ x, int x_cs, int x_co,
+__global__ void k_upsample(int R, int C, const T* __restrict__ x, int x_cs, int x_co,
                            T* __restrict__ y, int y_cs, int y_co) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int cg = C / 8, Ri = R / 2;
-  long long total = (long long)B * R * R * cg;
-  if (idx >= total) return;
-  int c = (int)(idx % cg) * 8;
-  long long p = idx / cg;
-  int b = (int)(p / ((long long)R * R));
-  int rem = (int)(p - (long long)b * R * R);
-  int i = rem / R, j = rem % R;
-  int k = i >> 1, l = j >> 1;
+  const int cg = C >> 3, Ri = R >> 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= R * cg) return;
+  const int j = t / cg, c = (t - j * cg) * 8;
+  const int i = blockIdx.y, b = blockIdx.z;
+  const int k = i >> 1, l = j >> 1;
   int i0, i1, j0, j1;
   float wi0, wi1, wj0, wj1;
   if (i & 1) { i0 = k; i1 = min(k + 1, Ri - 1); wi0 = 0.75f; wi1 = 0.25f; }
@@ -311,7 +328,7 @@ __global__ void k_upsample(int B, int R, int C, const T* __restrict__ x, int x_c
 #pragma unroll
   for (int q = 0; q < 8; ++q)
     o[q] = wi0 * (wj0 * a00[q] + wj1 * a01[q]) + wi1 * (wj0 * a10[q] + wj1 * a11[q]);
-  Vec8<T>::store(y + p * y_cs + y_co + c, o);
+  Vec8<T>::store(y + (((long long)b * R + i) * R + j) * y_cs + y_co + c, o);
 }
 
 // g[b][c] = mean over the R x R pixels of tile b (fixed summation order)
@@ -332,9 +349,9 @@ __global__ void k_gap(int R, int C, const T* __restrict__ x, int x_cs, int x_co,
 
 template <int C0, typename T>
 cudaError_t first_t(const ConvArgs& a, cudaStream_t st) {
-  long long total = (long long)a.B * a.R * a.R;
-  unsigned blocks = (unsigned)((total + 127) / 128);
-  k_conv_first<C0, T><<<blocks, 128, 0, st>>>(a.B, a.R, a.canvas, a.canvas_stride, a.tiles3,
+  if (a.R % kFirstPix) return cudaErrorInvalidValue;
+  dim3 grid((a.R / kFirstPix + 127) / 128, a.R, a.B);
+  k_conv_first<C0, T><<<grid, 128, 0, st>>>(a.R, a.canvas, a.canvas_stride, a.tiles3,
                                               a.w.w_f32, a.w.gamma, a.w.beta,
                                               static_cast<T*>(a.y), a.y_cs, a.y_co);
   return cudaGetLastError();
@@ -376,27 +393,25 @@ cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
 
 cudaError_t launch_maxpool(int precision, int B, int R, int C, const void* x, int x_cs, int x_co,
                            void* y, int y_cs, int y_co, cudaStream_t st) {
-  long long total = (long long)B * (R / 2) * (R / 2) * (C / 8);
-  unsigned blocks = (unsigned)((total + 255) / 256);
+  const int n = (R / 2) * (C / 8);
+  dim3 grid((n + 127) / 128, R / 2, B);
   if (precision == OMNI_FP32)
-    k_maxpool<float><<<blocks, 256, 0, st>>>(B, R, C, (const float*)x, x_cs, x_co, (float*)y,
-                                             y_cs, y_co);
+    k_maxpool<float><<<grid, 128, 0, st>>>(R, C, (const float*)x, x_cs, x_co, (float*)y, y_cs, y_co);
   else
-    k_maxpool<__nv_bfloat16><<<blocks, 256, 0, st>>>(B, R, C, (const __nv_bfloat16*)x, x_cs,
-                                                     x_co, (__nv_bfloat16*)y, y_cs, y_co);
+    k_maxpool<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co,
+                                                   (__nv_bfloat16*)y, y_cs, y_co);
   return cudaGetLastError();
 }
 
 cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, int x_cs,
                             int x_co, void* y, int y_cs, int y_co, cudaStream_t st) {
-  long long total = (long long)B * R * R * (C / 8);
-  unsigned blocks = (unsigned)((total + 255) / 256);
+  const int n = R * (C / 8);
+  dim3 grid((n + 127) / 128, R, B);
   if (precision == OMNI_FP32)
-    k_upsample<float><<<blocks, 256, 0, st>>>(B, R, C, (const float*)x, x_cs, x_co, (float*)y,
-                                              y_cs, y_co);
+    k_upsample<float><<<grid, 128, 0, st>>>(R, C, (const float*)x, x_cs, x_co, (float*)y, y_cs, y_co);
   else
-    k_upsample<__nv_bfloat16><<<blocks, 256, 0, st>>>(B, R, C, (const __nv_bfloat16*)x, x_cs,
-                                                      x_co, (__nv_bfloat16*)y, y_cs, y_co);
+    k_upsample<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co,
+                                                    (__nv_bfloat16*)y, y_cs, y_co);
   return cudaGetLastError();
 }
 

@@ -374,6 +374,251 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                  : "memory");
 }
 
+// ------------------------------------------------------------------ small-N variant
+// For cout <= 64 the A tile of one tap feeds only a few MMA cycles, so the
+// per-tap refetch above starves the tensor pipe.  This variant keeps the whole
+// layer's weights resident in shared memory (loaded once per CTA) and tiles the
+// output as 8 rows x 16 columns.  Per channel chunk it loads three boxes of
+// 10 x 16 input pixels, one per horizontal tap offset dx; the operand of tap
+// (dy, dx) is rows 16*dy .. 16*dy+127 of box dx, an offset of whole swizzle
+// atoms, so nine taps reuse three loads.
+constexpr int kHTH = 8, kHTW = 16;
+constexpr int kHBoxPix = (kHTH + 2) * kHTW;   // 160 input pixels per dx box
+
+template <int BN, int CK, bool RES>
+struct HaloCfg {
+  static constexpr int kBoxBytes = kHBoxPix * CK * 2;
+  static constexpr int kStageBytes = 3 * kBoxBytes;
+  static constexpr int kWTileBytes = BN * CK * 2;
+  static constexpr int kBufCols = RES ? 2 * BN : BN;
+  static constexpr int kTmemCols = 2 * kBufCols;
+  static constexpr int kSW = CK * 2;
+};
+
+struct HaloParams {
+  TCParams t;
+  int stages, n_wtiles, cpt;        // cpt = channel chunks of the main input
+  int tiles_per_img, tiles_w;       // (R/8)*(R/16), R/16
+};
+
+template <int BN, int CK, bool RES>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_conv_tc_halo(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
+                   HaloParams hp) {
+  using Cfg = HaloCfg<BN, CK, RES>;
+  const TCParams& p = hp.t;
+  const int ST = hp.stages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sW = smem;
+  uint8_t* sA = smem + (size_t)hp.n_wtiles * Cfg::kWTileBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * Cfg::kStageBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + ST;
+  uint64_t* tfull = bars + 2 * ST;
+  uint64_t* tempty = bars + 2 * ST + 2;
+  uint64_t* drain = bars + 2 * ST + 4;
+  uint64_t* wbar = bars + 2 * ST + 5;
+  float* sg = reinterpret_cast<float*>(bars + 2 * ST + 6);    // gamma[BN]
+  float* sb = sg + BN;                                          // beta[BN]
+  float* swp = sb + BN;                                         // wp_rgb[3][BN]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(swp + 3 * BN);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < BN; i += blockDim.x) {
+    sg[i] = p.gamma[i];
+    sb[i] = p.beta[i];
+    if (p.res_mode == RES_RGB) {
+      swp[i] = p.wp_rgb[i];
+      swp[BN + i] = p.wp_rgb[p.cout + i];
+      swp[2 * BN + i] = p.wp_rgb[2 * p.cout + i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 4);
+    }
+    mbar_init(smem_u32(drain), 1);
+    mbar_init(smem_u32(wbar), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int k_total = p.k_main + p.k_res;
+  const int RR = p.R * p.R;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- producer
+      const uint32_t wb = smem_u32(wbar);
+      mbar_expect_tx(wb, (uint32_t)(hp.n_wtiles * Cfg::kWTileBytes));
+      for (int t = 0; t < 9 * hp.cpt; ++t) {
+        const int tap = t / hp.cpt, c = t % hp.cpt;
+        tma_load_2d(smem_u32(sW + (size_t)t * Cfg::kWTileBytes), &mapB, wb, tap * p.cin + c * CK, 0);
+      }
+      for (int r = 0; r < p.k_res; ++r)
+        tma_load_2d(smem_u32(sW + (size_t)(9 * hp.cpt + r) * Cfg::kWTileBytes), &mapB2, wb, r * CK, 0);
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+        const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
+        const int h0 = (rem / hp.tiles_w) * kHTH, w0 = (rem % hp.tiles_w) * kHTW;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (it >= ST && !mbar_wait(smem_u32(&empty[s]), ((it / ST) & 1) ^ 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full[s]);
+          uint8_t* st = sA + (size_t)s * Cfg::kStageBytes;
+          if (k < p.k_main) {
+            mbar_expect_tx(fb, Cfg::kStageBytes);
+            const int c0 = k * CK;
+            for (int dx = 0; dx < 3; ++dx)
+              tma_load_4d(smem_u32(st + dx * Cfg::kBoxBytes), &mapA, fb, c0, w0 + dx - 1, h0 - 1, img);
+          } else {
+            mbar_expect_tx(fb, kBM * CK * 2);
+            tma_load_4d(smem_u32(st), &mapA2, fb, (k - p.k_main) * CK, w0, h0, img);
+          }
+        }
+      }
+      const int last = it;
+      for (int q = last - 1; q >= 0 && q >= last - ST; --q) mbar_drain(smem_u32(&full[q % ST]), (q / ST) & 1);
+      mbar_drain(wb, 0);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BN);
+      bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, p.err);
+      int it = 0, tcount = 0;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
+        const int buf = tcount & 1, use = tcount >> 1;
+        if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
+        const uint32_t acc1 = acc0 + BN;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (!mbar_wait(smem_u32(&full[s]), (it / ST) & 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(sA + (size_t)s * Cfg::kStageBytes);
+          if (k < p.k_main) {
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+              const int dy = tap / 3, dx = tap % 3;
+              const uint64_t ad = smem_desc(st + dx * Cfg::kBoxBytes + dy * kHTW * CK * 2, Cfg::kSW);
+              const uint64_t bd =
+                  smem_desc(smem_u32(sW + (size_t)(tap * hp.cpt + k) * Cfg::kWTileBytes), Cfg::kSW);
+#pragma unroll
+              for (int kk = 0; kk < CK / 16; ++kk)
+                mma_bf16(acc0, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                         (k > 0 || tap > 0 || kk > 0) ? 1u : 0u);
+            }
+          } else if (RES) {
+            const uint64_t ad = smem_desc(st, Cfg::kSW);
+            const uint64_t bd = smem_desc(
+                smem_u32(sW + (size_t)(9 * hp.cpt + (k - p.k_main)) * Cfg::kWTileBytes), Cfg::kSW);
+#pragma unroll
+            for (int kk = 0; kk < CK / 16; ++kk)
+              mma_bf16(acc1, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                       (k > p.k_main || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&tfull[buf]));
+      }
+      mma_commit(smem_u32(drain));
+      mbar_drain(smem_u32(drain), 0);
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
+      const int buf = tcount & 1, use = tcount >> 1;
+      const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
+      const int hh = (rem / hp.tiles_w) * kHTH + row / kHTW;
+      const int ww = (rem % hp.tiles_w) * kHTW + row % kHTW;
+      const long long m = (long long)img * RR + (long long)hh * p.R + ww;
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      if (p.res_mode == RES_RGB) {
+        const uint8_t* px = p.canvas + (long long)(p.tiles3[3 * img + 1] + hh) * p.canvas_stride +
+                            (long long)(p.tiles3[3 * img + 2] + ww) * 3;
+        v0 = norm_u8(px[0]);
+        v1 = norm_u8(px[1]);
+        v2 = norm_u8(px[2]);
+      }
+      __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float a[16], r[16];
+        tmem_ld16(tb + c, a);
+        if constexpr (RES) tmem_ld16(tb + BN + c, r);
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float o[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int n = c + j + u;
+            float z = fmaf(sg[n], a[j + u], sb[n]);
+            if constexpr (RES) z += r[j + u];
+            if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[BN + n], v2 * swp[2 * BN + n]));
+            o[u] = fmaxf(z, 0.f);
+          }
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(o[0], o[1]);
+          packed[j / 2] = *reinterpret_cast<uint32_t*>(&h2);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(out + c);
+        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+}
+
 // ------------------------------------------------------------------ host side
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
@@ -404,6 +649,23 @@ bool map_act(CUtensorMap* m, const void* base, int channels, int cs, int co, int
   cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)R * cs * 2, (cuuint64_t)R * R * cs * 2};
   const int bw = R < kBM ? R : kBM;
   cuuint32_t box[4] = {(cuuint32_t)CK, (cuuint32_t)bw, (cuuint32_t)(kBM / bw), 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<char*>(ptr), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// NHWC activation box of bw x bh pixels (small-N variant: 16 x 10 or 16 x 8)
+bool map_act_box(CUtensorMap* m, const void* base, int channels, int cs, int co, int R, int B, int CK,
+                 int bw, int bh) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  const char* ptr = static_cast<const char*>(base) + (size_t)co * 2;
+  cuuint64_t dims[4] = {(cuuint64_t)channels, (cuuint64_t)R, (cuuint64_t)R, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)R * cs * 2, (cuuint64_t)R * R * cs * 2};
+  cuuint32_t box[4] = {(cuuint32_t)CK, (cuuint32_t)bw, (cuuint32_t)bh, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<char*>(ptr), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -481,6 +743,74 @@ cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+constexpr int kHaloSmemMax = 227 * 1024;
+constexpr int kHaloSmemExtra = 3072;   // barriers, gamma/beta, alignment slack
+
+// stages of the small-N variant for a layer and channel chunk (0: does not fit)
+int halo_stages(int cin, int cout, int cr, int ck) {
+  if (cin % ck || cr % ck) return 0;
+  const long long wbytes = (long long)(9 * (cin / ck) + cr / ck) * cout * ck * 2;
+  const long long stage = 3LL * kHBoxPix * ck * 2;
+  long long st = (kHaloSmemMax - wbytes - kHaloSmemExtra) / stage;
+  return st < 2 ? 0 : (int)(st > 8 ? 8 : st);
+}
+
+bool halo_ok(int R, int cout, int cin, int cr) {
+  if (R < 16 || R % 16 || (cout != 32 && cout != 64)) return false;
+  return halo_stages(cin, cout, cr, 32) >= 2;
+}
+
+template <int BN, int CK, bool RES>
+cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
+  using Cfg = HaloCfg<BN, CK, RES>;
+  CUtensorMap mA, mB, mA2, mB2;
+  if (!map_act_box(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, kHTW, kHTH + 2)) return cudaErrorInvalidValue;
+  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, BN, CK)) return cudaErrorInvalidValue;
+  if (RES) {
+    if (!map_act_box(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK, kHTW, kHTH)) return cudaErrorInvalidValue;
+    if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, BN, CK)) return cudaErrorInvalidValue;
+  } else {
+    mA2 = mA;
+    mB2 = mB;
+  }
+  HaloParams hp{};
+  TCParams& p = hp.t;
+  p.B = a.B; p.R = a.R; p.cin = a.cin; p.cout = a.cout; p.cr = RES ? a.cr : 0;
+  p.res_mode = a.res_mode;
+  hp.tiles_w = a.R / kHTW;
+  hp.tiles_per_img = (a.R / kHTH) * hp.tiles_w;
+  p.n_tiles_m = a.B * hp.tiles_per_img;
+  p.n_tiles_n = 1;
+  p.n_tiles = p.n_tiles_m;
+  p.k_main = a.cin / CK;
+  p.k_res = RES ? a.cr / CK : 0;
+  hp.cpt = a.cin / CK;
+  hp.n_wtiles = 9 * hp.cpt + p.k_res;
+  hp.stages = stages;
+  p.gamma = a.w.gamma;
+  p.beta = a.w.beta;
+  p.wp_rgb = a.w.wp_f32;
+  p.canvas = a.canvas;
+  p.canvas_stride = a.canvas_stride;
+  p.tiles3 = a.tiles3;
+  p.y = static_cast<__nv_bfloat16*>(a.y);
+  p.y_cs = a.y_cs;
+  p.y_co = a.y_co;
+  p.err = a.err;
+  const size_t smem = (size_t)hp.n_wtiles * Cfg::kWTileBytes + (size_t)stages * Cfg::kStageBytes + kHaloSmemExtra;
+  if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
+  auto kern = k_conv_tc_halo<BN, CK, RES>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloSmemMax);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
+  kern<<<grid, kThreadsTC, smem, st>>>(mA, mB, mA2, mB2, hp);
+  return cudaGetLastError();
+}
+
 int pick_bn(int cout, bool res) {
   const int cap = res ? 128 : 256;
   return cout < cap ? cout : cap;
@@ -506,6 +836,17 @@ cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st) {
                                                      reinterpret_cast<uintptr_t>(a.w.wp_bf16) : 0)) % 16)
     return cudaErrorInvalidValue;
   const bool res = cr > 0;
+  if (halo_ok(a.R, a.cout, a.cin, cr)) {
+    int ck = 32, stg = halo_stages(a.cin, a.cout, cr, 32);
+    const int stg64 = halo_stages(a.cin, a.cout, cr, 64);
+    if (stg64 >= 3) { ck = 64; stg = stg64; }
+#define OMNI_HALO(BN_, CK_, RES_) \
+    if (a.cout == BN_ && ck == CK_ && res == RES_) return launch_halo<BN_, CK_, RES_>(a, st, stg);
+    OMNI_HALO(32, 32, false) OMNI_HALO(32, 32, true) OMNI_HALO(32, 64, false) OMNI_HALO(32, 64, true)
+    OMNI_HALO(64, 32, false) OMNI_HALO(64, 32, true) OMNI_HALO(64, 64, false) OMNI_HALO(64, 64, true)
+#undef OMNI_HALO
+    return cudaErrorInvalidValue;
+  }
   const int ck = (a.cin % 64 == 0 && (!res || cr % 64 == 0)) ? 64 : 32;
   const int bn = pick_bn(a.cout, res);
 #define OMNI_TC(BN_, CK_, RES_) \

@@ -1,11 +1,12 @@
-// Omni-Seg dynamic head (Sec. 2.2): the controller turns the tile's global
+// Omni-Seg dynamic head (Sec. 2.2): a controller turns the tile's global
 // average-pooled bottleneck feature plus one-hot class and scale codes into the
 // 153 parameters of a per-tile, per-class 1x1 head 8 -> 8 -> 8 -> 1, which is
 // applied at every pixel of the pre-head feature h0 = ReLU(Wh y0 + bh).
 //
-// One fused kernel: each block first evaluates the controller for its tile
-// and every class of the scale (theta kept in shared memory), then runs the
-// pre-head and all heads over 4096 pixels, writing FP32 logits.
+// Two kernels: k_controller evaluates theta for every tile of a batch and every
+// class of the scale (the controller weights are read once per batch, not once
+// per pixel block), and k_head runs the pre-head and all heads of the scale
+// over the tile pixels, writing FP32 logits.
 #include "omni_internal.cuh"
 
 namespace omni {
@@ -13,37 +14,59 @@ namespace {
 
 constexpr int kHeadThreads = 256;
 constexpr int kPixPerBlock = 4096;
+constexpr int kCtrlRows = 32;          // controller rows per block
 
-template <typename T> __device__ __forceinline__ float ld(const T* p);
-template <> __device__ __forceinline__ float ld<float>(const float* p) { return *p; }
-template <> __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(*p);
+// grid.x = ceil(153 / kCtrlRows); block = 8 warps, one (row, tile) dot per warp step
+__global__ void __launch_bounds__(256) k_controller(HeadArgs a) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int zdim = a.Cb + a.n_classes + a.n_scales;
+  const int r0 = blockIdx.x * kCtrlRows;
+  for (int q = warp; q < kCtrlRows * a.B; q += 8) {
+    const int row = r0 + q % kCtrlRows, b = q / kCtrlRows;
+    if (row >= kHeadParams) continue;
+    const float* w = a.wc + (long long)row * zdim;
+    const float* g = a.g + (long long)b * a.Cb;
+    float s = 0.f;
+    for (int k = lane; k < a.Cb; k += 32) s = fmaf(w[k], g[k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane < a.n_cls_here) {
+      const float th = s + w[a.Cb + a.n_classes + a.scale] + a.bc[row] + w[a.Cb + a.cls_ids[lane]];
+      a.theta[((long long)b * a.n_cls_here + lane) * kHeadParams + row] = th;
+    }
+  }
 }
+
+template <typename T> struct Load8;
+template <> struct Load8<float> {
+  static __device__ __forceinline__ void f(const float* p, float v[8]) {
+    const float4 x = *reinterpret_cast<const float4*>(p), y = *reinterpret_cast<const float4*>(p + 4);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w; v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+  }
+};
+template <> struct Load8<__nv_bfloat16> {
+  static __device__ __forceinline__ void f(const __nv_bfloat16* p, float v[8]) {
+    const uint4 q = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(h[i]);
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+};
 
 template <int C0, typename T>
 __global__ void __launch_bounds__(kHeadThreads) k_head(HeadArgs a) {
   __shared__ float theta[OMNI_MAX_CLASSES][kHeadParams];
   __shared__ float wh[kHeadCh * C0], bh[kHeadCh];
-  __shared__ float gs[1024];
   const int b = blockIdx.y;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int zdim = a.Cb + a.n_classes + a.n_scales;
+  const int t = threadIdx.x;
   for (int i = t; i < kHeadCh * C0; i += kHeadThreads) wh[i] = a.wh[i];
   if (t < kHeadCh) bh[t] = a.bh[t];
-  for (int i = t; i < a.Cb; i += kHeadThreads) gs[i] = a.g[(long long)b * a.Cb + i];
-  __syncthreads();
-  // controller: theta_c = Wc [g; onehot(c); onehot(scale)] + bc, one warp per row
-  for (int row = warp; row < kHeadParams; row += kHeadThreads / 32) {
-    const float* w = a.wc + (long long)row * zdim;
-    float s = 0.f;
-    for (int k = lane; k < a.Cb; k += 32) s = fmaf(w[k], gs[k], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      float common = s + w[a.Cb + a.n_classes + a.scale] + a.bc[row];
-      for (int ci = 0; ci < a.n_cls_here; ++ci) theta[ci][row] = common + w[a.Cb + a.cls_ids[ci]];
-    }
-  }
+  for (int i = t; i < a.n_cls_here * kHeadParams; i += kHeadThreads)
+    theta[i / kHeadParams][i % kHeadParams] = a.theta[(long long)b * a.n_cls_here * kHeadParams + i];
   __syncthreads();
 
   const long long PP = (long long)a.P * a.P;
@@ -51,19 +74,22 @@ __global__ void __launch_bounds__(kHeadThreads) k_head(HeadArgs a) {
   float* out = a.logits + (long long)(a.slot0 + b) * a.n_cls_here * PP;
   const long long p0 = (long long)blockIdx.x * kPixPerBlock;
   for (int q = t; q < kPixPerBlock; q += kHeadThreads) {
-    long long p = p0 + q;
+    const long long p = p0 + q;
     if (p >= PP) break;
-    float y[C0];
-#pragma unroll
-    for (int c = 0; c < C0; ++c) y[c] = ld<T>(Y + p * C0 + c);
     float h0[kHeadCh];
 #pragma unroll
-    for (int o = 0; o < kHeadCh; ++o) {
-      float s = bh[o];
+    for (int o = 0; o < kHeadCh; ++o) h0[o] = bh[o];
 #pragma unroll
-      for (int c = 0; c < C0; ++c) s = fmaf(wh[o * C0 + c], y[c], s);
-      h0[o] = fmaxf(s, 0.f);
+    for (int c0 = 0; c0 < C0; c0 += 8) {
+      float y[8];
+      Load8<T>::f(Y + p * C0 + c0, y);
+#pragma unroll
+      for (int o = 0; o < kHeadCh; ++o)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) h0[o] = fmaf(wh[o * C0 + c0 + c], y[c], h0[o]);
     }
+#pragma unroll
+    for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaxf(h0[o], 0.f);
     for (int ci = 0; ci < a.n_cls_here; ++ci) {
       const float* th = theta[ci];
       float h1[kHeadCh], h2[kHeadCh];
@@ -105,8 +131,14 @@ cudaError_t head_t(const HeadArgs& a, cudaStream_t st) {
 
 }  // namespace
 
+cudaError_t launch_controller(const HeadArgs& a, cudaStream_t st) {
+  if (a.n_cls_here < 1 || a.n_cls_here > OMNI_MAX_CLASSES) return cudaErrorInvalidValue;
+  k_controller<<<(kHeadParams + kCtrlRows - 1) / kCtrlRows, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_head(const HeadArgs& a, cudaStream_t st) {
-  if (a.Cb > 1024 || a.n_cls_here < 1 || a.n_cls_here > OMNI_MAX_CLASSES) return cudaErrorInvalidValue;
+  if (a.n_cls_here < 1 || a.n_cls_here > OMNI_MAX_CLASSES) return cudaErrorInvalidValue;
   return a.precision == OMNI_FP32 ? head_t<float>(a, st) : head_t<__nv_bfloat16>(a, st);
 }
 

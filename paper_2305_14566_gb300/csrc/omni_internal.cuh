@@ -75,6 +75,11 @@ struct ConvArgs {
   void* y; int y_cs, y_co;                // output NHWC
   ConvLayerW w;                           // device pointers, passed by value
   unsigned* err;
+  // FP32 path only: raw = 1 writes the bare convolution sum to y (no norm, no
+  // ReLU) and, with RES_TENSOR, the bare projection sum to y2 (channel stride
+  // y2_cs); used by the backward's recomputation
+  int raw;
+  void* y2; int y2_cs;
 };
 
 // k_conv_f32.cu (plain FP32 path + precision-generic helpers)
@@ -101,7 +106,11 @@ struct HeadArgs {
   const float* wc; const float* bc;        // [153][Cb + ncls + nscl], [153]
   int slot0;                               // output slot of tile 0 (tile b -> slot0 + b)
   float* logits;                           // [slot][n_cls_here][P*P]
+  float* theta;                            // [B][n_cls_here][153] controller output
 };
+// controller for a batch of tiles: theta[b][ci] = Wc [g_b; onehot; onehot] + bc
+cudaError_t launch_controller(const HeadArgs& a, cudaStream_t st);
+// pre-head + dynamic heads over every pixel, reading theta
 cudaError_t launch_head(const HeadArgs& a, cudaStream_t st);
 
 // k_stitch.cu

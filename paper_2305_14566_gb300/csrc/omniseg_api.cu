@@ -103,7 +103,7 @@ struct Plan {
   size_t canvas, c20, c10, c5, blk8, grey, blur, hist, otsu, mask, tiles, counts, flags, slot;
   size_t tile_end;
   // network stage
-  size_t logits, tmp, pooled, cat[kMaxLevels], bott, ydec[kMaxLevels], gap;
+  size_t logits, tmp, pooled, cat[kMaxLevels], bott, ydec[kMaxLevels], gap, theta;
   size_t net_end;
   // host-buffer variant
   size_t in, lab[OMNI_MAX_CLASSES];
@@ -179,6 +179,7 @@ bool make_plan(const omni_config& c, int H, int W, Plan& p) {
   size_t Rb = (size_t)(c.patch >> (L - 1));
   p.bott = take(off, B * Rb * Rb * widths(c, L - 1) * e);
   p.gap = take(off, B * widths(c, L - 1) * 4);
+  p.theta = take(off, B * OMNI_MAX_CLASSES * kHeadParams * 4);
   p.net_end = align_up(off, 256);
   p.in = take(off, (size_t)H * W * 3);
   for (int k = 0; k < c.n_classes; ++k) {
@@ -628,6 +629,12 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   h.wh = ctx->wh; h.bh = ctx->bh; h.wc = ctx->wc; h.bc = ctx->bc;
   h.slot0 = slot0;
   h.logits = reinterpret_cast<float*>(ws + p.logits);
+  h.theta = reinterpret_cast<float*>(ws + p.theta);
+  {
+    Rec r(ctx, st, 2, 401);
+    OMNI_CU(launch_controller(h, st), "controller");
+    ctx->launches++;
+  }
   {
     Rec r(ctx, st, 2, 500);
     OMNI_CU(launch_head(h, st), "head");

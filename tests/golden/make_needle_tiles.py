@@ -1,5 +1,6 @@
-"""Write needle_tiles.json: the oracle's tissue threshold and foreground tile
-counts for the 16384 x 49152 needle-biopsy workload.
+"""Write needle_tiles.json (the oracle's tissue threshold and foreground tile
+counts) and needle_tissue_mask.npz (its 512 x 1536 tissue mask, bit-packed)
+for the 16384 x 49152 needle-biopsy workload.
 
 Calls only the input generator and the FP64 oracle.  The slide is generated
 on the CPU in bands of 1024 rows; the oracle's thumbnail is a per-32x32-block
@@ -33,9 +34,11 @@ def main():
            "otsu": int(t), "tissue_fraction": float(mask.mean()),
            "tiles_per_scale": per, "tiles_total": len(tiles),
            "grid_per_scale": [int(f.size) for f in flags]}
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "needle_tiles.json")
-    with open(path, "w") as f:
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "needle_tiles.json"), "w") as f:
         json.dump(out, f, indent=1)
+    np.savez_compressed(os.path.join(here, "needle_tissue_mask.npz"), shape=np.array(mask.shape),
+                        bits=np.packbits(mask.astype(np.uint8).ravel()))
     print(json.dumps(out))
 
 

@@ -8,6 +8,8 @@ output (relative 2^-8).
 Whole path: label agreement and per-class Dice of the BF16 labels against the
 oracle's (FP64) labels, and the logit error statistics.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -16,6 +18,8 @@ import synth
 from oracle import omniseg_oracle as O
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN_MASK = os.path.join(os.path.dirname(__file__), "golden", "needle_tissue_mask.npz")
 
 
 @pytest.fixture(scope="module")
@@ -31,12 +35,14 @@ def bf16_round(a: np.ndarray) -> np.ndarray:
     return torch.from_numpy(np.ascontiguousarray(a, np.float32)).bfloat16().float().numpy()
 
 
-# (R, cin, cout, cr): every kernel variant (N tile 32..256, channel chunk 32 / 64,
-# with and without the projection segment, several N tiles, rows of 16..256)
+# (R, cin, cout, cr): every kernel variant.  cout <= 64 runs the small-N
+# variant (resident weights, 8x16 tiles, three dx boxes per channel chunk) when
+# its weights fit in shared memory, else the per-tap kernel (N tile 32..256,
+# channel chunk 32 / 64, with and without the projection segment).
 SHAPES = [(16, 32, 32, 32), (32, 64, 128, 0), (64, 64, 256, 0), (32, 256, 512, 0),
           (128, 32, 64, 32), (64, 128, 256, 128), (256, 96, 32, 96), (32, 768, 256, 768),
-          (16, 512, 512, 256), (32, 32, 32, 0)]
-
+          (16, 512, 512, 256), (32, 32, 32, 0), (512, 96, 32, 0), (64, 64, 64, 192),
+          (32, 32, 64, 0), (64, 64, 64, 32), (64, 192, 64, 0), (48, 32, 32, 0)]
 
 @pytest.mark.parametrize("R,cin,cout,cr", SHAPES)
 def test_conv_layer_bf16(api, R, cin, cout, cr):
@@ -76,17 +82,36 @@ def _stats(gpu_lab, gpu_L, orc_lab, orc_L):
     return agree, dice, float(d.max()), float(np.percentile(d, 99)), int((orc_lab > 0).sum())
 
 
+def _agree_dice(a, b):
+    a = a > 0
+    b = b > 0
+    den = int(a.sum() + b.sum())
+    return float((a == b).mean()), (1.0 if den == 0 else 2.0 * float((a & b).sum()) / den), int(b.sum())
+
+
 def test_bf16_whole_path_window_against_oracle(api):
     """The needle network (base 32, 5 levels, 3 scales, 6 heads) with 256 px
-    tiles at stride 128 on a 2048 x 2048 slide with tissue filtering."""
+    tiles at stride 128 on a 2048 x 2048 slide with tissue filtering: BF16
+    labels against the oracle on a window, and against the FP32 path (which
+    matches the oracle within 1e-4) on the whole slide."""
     from paper_2305_14566_gb300 import _lib as L
     w = synth.NEEDLE.with_(H=2048, W=2048, P=256, S=128, median_k=5, max_batch=16)
     spec = synth.make_spec(2048, 2048, 41, 0.5, "cores", 3)
     rgb_np = synth.gen_slide(spec)
+    rgb = torch.from_numpy(rgb_np).cuda()
     blob = synth.gen_weights(w)
     seg = api.Segmenter(w, blob, precision=L.BF16)
-    out = seg.segment(torch.from_numpy(rgb_np).cuda(), logits=True, coverage=True)
+    out = seg.segment(rgb, logits=True, coverage=True)
+    seg32 = api.Segmenter(w, blob, precision=L.FP32)
+    o32 = seg32.segment(rgb, logits=True)
     torch.cuda.synchronize()
+    for c in range(w.n_classes):
+        ag, dc, pos = _agree_dice(out["labels"][c].cpu().numpy(), o32["labels"][c].cpu().numpy())
+        d = (out["logits"][c] - o32["logits"][c]).abs()
+        print("slide class %d agree %.5f dice %.5f positives %d max|dL| %.3e" % (c, ag, dc, pos, float(d.max())))
+        assert ag >= 0.999
+        if pos >= 2000:
+            assert dc >= 0.995
     orc = O.segment(rgb_np, w, blob, window=(640, 768, 512, 512), batch=8)
     rows = []
     for c, s in enumerate(w.class_scale):
@@ -97,10 +122,56 @@ def test_bf16_whole_path_window_against_oracle(api):
         cov = out["coverage"][s][wy:wy + wh, wx:wx + ww].cpu().numpy().astype(np.int64)
         assert np.array_equal(cov, orc["cov"][c])
     for row in rows:
-        print("class %d agree %.5f dice %.5f max|dL| %.3e p99|dL| %.3e positives %d" % row)
-    agree_all = np.mean([r[1] for r in rows])
-    assert agree_all >= 0.999, rows
+        print("window class %d agree %.5f dice %.5f max|dL| %.3e p99|dL| %.3e positives %d" % row)
+    assert np.mean([r[1] for r in rows]) >= 0.999, rows
     for r in rows:
         if r[5] >= 2000:
             assert r[2] >= 0.995, r
+    seg.close()
+    seg32.close()
+
+
+def test_needle_full_slide_bf16_against_fp32_and_oracle(api):
+    """The benchmark workload itself (16384 x 49152, 512 px tiles, 6 heads):
+    BF16 labels against the FP32 path over the whole slide, and against the
+    oracle on a 256 x 256 window inside a tissue core at every scale."""
+    from paper_2305_14566_gb300 import _lib as L
+    w = synth.NEEDLE
+    spec = synth.spec_for(w)
+    rgb = api.synth_slide(spec)
+    blob = synth.gen_weights(w)
+    seg = api.Segmenter(w, blob, precision=L.BF16)
+    out = seg.segment(rgb, logits=True)
+    torch.cuda.synchronize()
+    seg32 = api.Segmenter(w, blob, precision=L.FP32)
+    o32 = seg32.segment(rgb, logits=True)
+    torch.cuda.synchronize()
+    seg32.close()
+    worst = 1.0
+    for c in range(w.n_classes):
+        ag, dc, pos = _agree_dice(out["labels"][c].cpu().numpy(), o32["labels"][c].cpu().numpy())
+        print("needle class %d agree %.6f dice %.5f positives %d" % (c, ag, dc, pos))
+        worst = min(worst, ag)
+        assert ag >= 0.999
+        if pos >= 10000:
+            assert dc >= 0.995
+    # the oracle's tissue mask of this slide (written by tests/golden/make_needle_tiles.py)
+    gold = np.load(GOLDEN_MASK)
+    mask = np.unpackbits(gold["bits"])[:int(np.prod(gold["shape"]))].reshape(gold["shape"]).astype(bool)
+    t = seg.tile_slide(rgb)
+    assert np.array_equal(t["tissue"].cpu().numpy().astype(bool), mask)
+    # a 256 x 256 window at 40x inside the first tissue core (4 covering tiles)
+    e = spec.ellipses[0]
+    win = ((e.cy // 256) * 256, (e.cx // 256) * 256, 256, 256)
+    orc = O.segment_window_regions(lambda y, x, h, wd: synth.gen_window(spec, y, x, h, wd), mask,
+                                   w, blob, win, w.H, w.W, scales=(0,))
+    wy, wx, wh, ww = orc["window"][0]
+    for c in (0, 1):
+        o = orc["L"][c]
+        g32 = o32["logits"][c][wy:wy + wh, wx:wx + ww].double().cpu().numpy()
+        assert np.abs(g32 - o).max() <= 1e-4
+        gb = out["labels"][c][wy:wy + wh, wx:wx + ww].cpu().numpy()
+        ag = float((gb == orc["labels"][c]).mean())
+        print("needle window class %d fp32 max|dL| %.2e bf16 agree %.5f" % (c, float(np.abs(g32 - o).max()), ag))
+        assert ag >= 0.999
     seg.close()

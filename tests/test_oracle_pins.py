@@ -386,6 +386,25 @@ def test_gradient_matches_central_differences():
     assert checked == 48
 
 
+def test_window_from_regions_equals_whole_slide():
+    """Evaluating a window from 40x regions (pyramid crops built per tile) gives
+    exactly the whole-slide evaluation restricted to that window."""
+    w = synth.NEEDLE.with_(H=1024, W=1536, P=128, S=64, base=8, levels=3, median_k=5)
+    spec = synth.make_spec(1024, 1536, 3, 0.45, "cores", 3)
+    rgb = synth.gen_slide(spec)
+    blob = synth.gen_weights(w)
+    win = (256, 512, 256, 256)
+    full = O.segment(rgb, w, blob, window=win, batch=8)
+    prep = full["prep"]
+    reg = O.segment_window_regions(lambda y, x, h, ww: prep["canvas"][y:y + h, x:x + ww], prep["mask"],
+                                   w, blob, win, prep["Hp"], prep["Wp"], batch=8)
+    for c in range(w.n_classes):
+        assert np.array_equal(full["L"][c], reg["L"][c])
+        assert np.array_equal(full["cov"][c], reg["cov"][c])
+        assert np.array_equal(full["labels"][c], reg["labels"][c])
+    assert any(full["cov"][c].max() > 0 for c in full["cov"])
+
+
 # ---------------------------------------------------------------- input generator
 
 
