@@ -236,6 +236,25 @@ int64_t omni_last_launch_count(const omni_ctx* ctx);
 int64_t omni_get_launch_times(omni_ctx* ctx, int64_t max, double* ms, int32_t* kinds,
                               int32_t* tags, double* work);
 
+/* Loss and hand-written backward for one slide (FP32 contexts only).
+ * Forward: the whole path with stitched FP32 logits; loss = mean over the
+ * classes of soft-Dice (smoothing 1) + mean BCE between the stitched logits of
+ * the class (label-map pixels of its scale) and `gt_dev[c]` (uint8 0/1, same
+ * size as the class's label map).  Backward through the overlap average, the
+ * dynamic heads, the controller, the pre-head and the last decoder block;
+ * the gradient stops at the GAP feature and at that block's input.  The last
+ * block is recomputed batch by batch from its saved input, so memory is bounded
+ * by one batch of tiles.  Writes the loss to `loss_dev[0]` and every non-NULL
+ * gradient of `grads` (blob layouts).  Deterministic: every sum has a fixed
+ * order.  The workspace must hold omni_backward_workspace() bytes; the call
+ * synchronises `stream` once per batch.  OMNI_EINVAL for BF16 contexts or
+ * max_batch > 64. */
+uint64_t omni_backward_workspace(const omni_config* cfg, int32_t H, int32_t W);
+omni_status omni_backward(omni_ctx* ctx, const uint8_t* rgb_dev, int32_t H, int32_t W,
+                          int64_t row_stride, const uint8_t* const* gt_dev, void* workspace_dev,
+                          uint64_t workspace_bytes, float* loss_dev, const omni_grads* grads,
+                          void* stream);
+
 /* Tissue detection and tiling (as omni_tile_slide) for callers that may not
  * allocate device memory while they run -- for instance a slide scanner's
  * acquisition loop that reserves its whole device-memory budget at start-up,

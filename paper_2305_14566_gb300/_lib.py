@@ -24,7 +24,7 @@ EXPORTS = ("omni_create", "omni_destroy", "omni_last_error", "omni_weights_count
            "omni_load_weights", "omni_query", "omni_tile_slide", "omni_segment_slide",
            "omni_segment_slide_host", "omni_synth_slide", "omni_conv_layer", "omni_set_timing",
            "omni_get_timing", "omni_last_launch_count", "omni_get_launch_times",
-           "omni_tile_slide_noalloc")
+           "omni_tile_slide_noalloc", "omni_backward", "omni_backward_workspace")
 
 
 class Config(C.Structure):
@@ -49,6 +49,14 @@ class Sizes(C.Structure):
 class TileList(C.Structure):
     _fields_ = [("tiles", C.c_void_p), ("counts", C.c_void_p), ("flags", C.c_void_p),
                 ("tissue", C.c_void_p), ("otsu", C.c_void_p)]
+
+
+GRAD_FIELDS = ("ctrl_w", "ctrl_b", "head_w", "head_b", "dec0_w1", "dec0_g1", "dec0_b1", "dec0_w2",
+               "dec0_g2", "dec0_b2", "dec0_wp")
+
+
+class Grads(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in GRAD_FIELDS]
 
 
 class Outputs(C.Structure):
@@ -91,6 +99,8 @@ def lib() -> C.CDLL:
         "omni_get_launch_times": (i64, [vp, i64, vp, vp, vp, vp]),
         "omni_tile_slide_noalloc": (i32, [C.POINTER(Config), vp, i32, i32, i64,
                                           C.POINTER(TileList), vp]),
+        "omni_backward_workspace": (u64, [C.POINTER(Config), i32, i32]),
+        "omni_backward": (i32, [vp, vp, i32, i32, i64, C.POINTER(vp), vp, u64, vp, C.POINTER(Grads), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -166,6 +166,35 @@ class Segmenter:
                                                  _stream()), self.ctx)
         return labels_host
 
+    # ------------------------------------------------------------------ loss + backward
+    def grad_shapes(self):
+        w = self.work
+        C0, zdim = w.base, w.widths[-1] + w.n_classes + w.n_scales
+        return {"ctrl_w": (153, zdim), "ctrl_b": (153,), "head_w": (8, C0), "head_b": (8,),
+                "dec0_w1": (C0, 3 * C0, 3, 3), "dec0_g1": (C0,), "dec0_b1": (C0,),
+                "dec0_w2": (C0, C0, 3, 3), "dec0_g2": (C0,), "dec0_b2": (C0,),
+                "dec0_wp": (C0, 3 * C0)}
+
+    def backward(self, rgb: torch.Tensor, gts):
+        """Stitched soft-Dice + BCE loss of one slide and its gradients (omni_backward).
+
+        ``gts``: one uint8 device tensor per class at its scale's label-map size.
+        Returns (loss tensor [1], {name: FP32 gradient tensor}).
+        """
+        H, W, _ = rgb.shape
+        dev = rgb.device
+        nbytes = int(self.lib.omni_backward_workspace(C.byref(self.cfg), H, W))
+        if nbytes == 0:
+            raise L.OmniError(L.EINVAL, "omni_backward_workspace: bad configuration or size")
+        ws = self.workspace(nbytes, dev)
+        grads = {k: torch.zeros(v, dtype=torch.float32, device=dev) for k, v in self.grad_shapes().items()}
+        g = L.Grads(*[grads[k].data_ptr() for k in L.GRAD_FIELDS])
+        gt_arr = (C.c_void_p * len(gts))(*[t.data_ptr() for t in gts])
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        L.check(self.lib.omni_backward(self.ctx, _ptr(rgb), H, W, rgb.stride(0), gt_arr, _ptr(ws),
+                                       ws.numel(), _ptr(loss), C.byref(g), _stream()), self.ctx)
+        return loss, grads
+
     # ------------------------------------------------------------------ timing
     def set_timing(self, on: bool = True):
         L.check(self.lib.omni_set_timing(self.ctx, int(on)), self.ctx)
@@ -192,6 +221,24 @@ class Segmenter:
         if n < 0:
             raise L.OmniError(L.ECUDA, "omni_get_launch_times failed")
         return ms[:n], kinds[:n], tags[:n], work[:n]
+
+
+class OmniSegLoss(torch.autograd.Function):
+    """loss = OmniSegLoss.apply(segmenter, rgb, gts, *params): the stitched
+    soft-Dice + BCE loss as a differentiable function of the controller, the
+    pre-head and the last decoder block (in the order of _lib.GRAD_FIELDS).
+    The parameter values must match the weights loaded into ``segmenter``;
+    forward and backward both come from one omni_backward call."""
+
+    @staticmethod
+    def forward(ctx, seg, rgb, gts, *params):
+        loss, grads = seg.backward(rgb, gts)
+        ctx.grads = [grads[k] for k in L.GRAD_FIELDS]
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, gout):
+        return (None, None, None) + tuple(gout * g for g in ctx.grads)
 
 
 def tile_slide_noalloc(work, rgb: torch.Tensor) -> Dict[str, torch.Tensor]:

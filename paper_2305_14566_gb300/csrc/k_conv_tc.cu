@@ -819,6 +819,7 @@ int pick_bn(int cout, bool res) {
 }  // namespace
 
 bool conv_tc_supported(int R, int cin, int cout, int cr) {
+  if (cin % 32 == 0 && cr % 32 == 0 && halo_ok(R, cout, cin, cr)) return true;
   if (!(R == 16 || R == 32 || R == 64 || (R >= 128 && R % 128 == 0))) return false;
   if (cin % 32 || cr % 32 || cout % 32) return false;
   const int bn = pick_bn(cout, cr > 0);

@@ -130,4 +130,43 @@ struct StitchArgs {
 };
 cudaError_t launch_stitch(const StitchArgs& a, cudaStream_t st);
 
+// k_backward.cu
+struct NPix { long long n[OMNI_MAX_CLASSES]; };
+struct BwdHeadArgs {
+  int B, P, ci, n_cls;                     // tiles in the batch, tile size, class index in scale list
+  const float* theta;                      // [B][n_cls][153]
+  const float *wh, *bh, *g2, *b2;          // pre-head, last block's second norm
+  const int32_t* tiles3;                   // tile origins (scale pixels)
+  int oy0, ox0, oh, ow;                    // label-map crop of this scale
+  const uint16_t* cov;                     // [oh][ow] coverage
+  const float* dL;                         // [oh][ow] dloss / dstitched logit of class ci
+  const float *c2, *pr;                    // [B*P*P][C0] bare second conv and projection sums
+  float* dh0;                              // [B*P*P][8]
+  float* dtheta_partial;                   // [B][n_cls][blocks][153]
+  float *y0, *dh0_pre, *dy0_pre, *dc2;     // pre-head backward outputs
+};
+int loss_blocks();
+cudaError_t launch_loss_partial(const float* L, const uint8_t* gt, long long n, double* partial,
+                                cudaStream_t st);
+cudaError_t launch_loss_final(const double* partial, int n_cls, const NPix& npix, double* sums,
+                              float* loss, cudaStream_t st);
+cudaError_t launch_loss_grad(const float* L, const uint8_t* gt, long long n, const double* sums, double npix,
+                             int n_cls, float* dL, cudaStream_t st);
+cudaError_t launch_affine_relu(const float* c, const float* g, const float* b, int C, long long n, float* a,
+                               cudaStream_t st);
+cudaError_t launch_relu_bwd(const float* da, const float* c1, const float* g1, const float* b1, int C,
+                            long long n, float* da_pre, float* dc, cudaStream_t st);
+int head_bwd_blocks(int P);
+cudaError_t launch_head_bwd(const BwdHeadArgs& a, int C0, cudaStream_t st);
+cudaError_t launch_prehead_bwd(const BwdHeadArgs& a, int C0, long long npx, cudaStream_t st);
+int wgrad_chunks(long long npx);
+cudaError_t launch_wgrad(const float* dY, int O, const float* X, int x_cs, int cin, int taps, int P,
+                         long long npx, float* partial, double* acc, cudaStream_t st);
+cudaError_t launch_colsum(const float* A, const float* B, int C, long long npx, float* partial, double* acc,
+                          cudaStream_t st);
+cudaError_t launch_ctrl_bwd(const float* dtheta_partial, int hblocks, int B, int n_cls, const int* cls_ids_dev,
+                            int n_classes, int n_scales, int scale, const float* g, int Cb, double* dwc,
+                            double* dbc, cudaStream_t st);
+cudaError_t launch_to_f32(const double* a, long long n, float* out, cudaStream_t st);
+
 }  // namespace omni

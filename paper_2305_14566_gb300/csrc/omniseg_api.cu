@@ -21,6 +21,7 @@ struct omni_ctx {
   bool have_weights = false;
   void* wdev = nullptr;
   std::vector<ConvLayerW> enc1, enc2, dec1, dec2;   // indexed by level
+  ConvLayerW dec2t0{};                              // last block's second conv, transposed + flipped
   float *wh = nullptr, *bh = nullptr, *wc = nullptr, *bc = nullptr;
   unsigned* d_err = nullptr;
   int32_t* h_counts = nullptr;                      // pinned
@@ -372,6 +373,18 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
     d2[l] = conv(co, co, cin, cin);
     proj(d2[l], cin);
   }
+  // dec0 conv2 transposed and flipped (input gradient of the last block):
+  // wt[(tap * C0 + o)][ci] = w2[o][ci][8 - tap]
+  const int C0 = widths(c, 0);
+  const size_t o_w2t = alloc((size_t)9 * C0 * C0 * 4);
+  {
+    const float* w2 = src - ((size_t)C0 * C0 * 9 + 2 * C0 + (size_t)C0 * 3 * C0);  // dec0.w2 in the blob
+    float* wt = reinterpret_cast<float*>(host.data() + o_w2t);
+    for (int o = 0; o < C0; ++o)
+      for (int ci = 0; ci < C0; ++ci)
+        for (int tap = 0; tap < 9; ++tap)
+          wt[((size_t)tap * C0 + o) * C0 + ci] = w2[((size_t)o * C0 + ci) * 9 + (8 - tap)];
+  }
   size_t o_wh = alloc((size_t)kHeadCh * widths(c, 0) * 4);
   memcpy(host.data() + o_wh, src, (size_t)kHeadCh * widths(c, 0) * 4);
   src += kHeadCh * widths(c, 0);
@@ -415,6 +428,9 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
   ctx->enc1.assign(L, {}); ctx->enc2.assign(L, {}); ctx->dec1.assign(L, {}); ctx->dec2.assign(L, {});
   for (int l = 0; l < L; ++l) { ctx->enc1[l] = mk(e1[l]); ctx->enc2[l] = mk(e2[l]); }
   for (int l = 0; l < L - 1; ++l) { ctx->dec1[l] = mk(d1[l]); ctx->dec2[l] = mk(d2[l]); }
+  ctx->dec2t0 = ctx->dec2[0];
+  ctx->dec2t0.w_f32 = reinterpret_cast<float*>(d + o_w2t);
+  ctx->dec2t0.cproj = 0;
   ctx->wh = reinterpret_cast<float*>(d + o_wh);
   ctx->bh = reinterpret_cast<float*>(d + o_bh);
   ctx->wc = reinterpret_cast<float*>(d + o_wc);
@@ -523,7 +539,7 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, int tag)
 // U-Net + heads for `nb` tiles of one scale.
 omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const uint8_t* canvas,
                       int64_t cstride, const int32_t* tiles3, int nb, int slot0, int ncls,
-                      const int* cls, cudaStream_t st) {
+                      const int* cls, cudaStream_t st, bool stop_before_dec0 = false) {
   const omni_config& c = ctx->cfg;
   const int L = c.levels, prec = c.precision;
   auto C = [&](int l) { return widths(c, l); };
@@ -592,6 +608,21 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     OMNI_CU(launch_gap(prec, nb, c.patch >> (L - 1), C(L - 1), bott, C(L - 1), 0, gap, st), "gap");
     ctx->launches++;
   }
+  HeadArgs h{};
+  h.B = nb; h.P = c.patch; h.C0 = C(0); h.Cb = C(L - 1);
+  h.n_classes = c.n_classes; h.n_scales = c.n_scales; h.scale = s;
+  h.n_cls_here = ncls;
+  for (int k = 0; k < ncls; ++k) h.cls_ids[k] = cls[k];
+  h.precision = prec; h.g = gap;
+  h.wh = ctx->wh; h.bh = ctx->bh; h.wc = ctx->wc; h.bc = ctx->bc;
+  h.slot0 = slot0;
+  h.logits = reinterpret_cast<float*>(ws + p.logits);
+  h.theta = reinterpret_cast<float*>(ws + p.theta);
+  {
+    Rec r(ctx, st, 2, 401);
+    OMNI_CU(launch_controller(h, st), "controller");
+    ctx->launches++;
+  }
   const void* y = bott;
   int y_cs = C(L - 1);
   for (int l = L - 2; l >= 0; --l) {
@@ -602,6 +633,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
       OMNI_CU(launch_upsample(prec, nb, R, 2 * C(l), y, y_cs, 0, cat, 3 * C(l), 0, st), "upsample");
       ctx->launches++;
     }
+    if (l == 0 && stop_before_dec0) return OMNI_OK;
     ConvArgs a = base;
     a.R = R; a.cin = 3 * C(l); a.cout = C(l);
     a.x = cat; a.x_cs = 3 * C(l); a.x_co = 0;
@@ -620,21 +652,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     y = ws + p.ydec[l];
     y_cs = C(l);
   }
-  HeadArgs h{};
-  h.B = nb; h.P = c.patch; h.C0 = C(0); h.Cb = C(L - 1);
-  h.n_classes = c.n_classes; h.n_scales = c.n_scales; h.scale = s;
-  h.n_cls_here = ncls;
-  for (int k = 0; k < ncls; ++k) h.cls_ids[k] = cls[k];
-  h.y0 = y; h.precision = prec; h.g = gap;
-  h.wh = ctx->wh; h.bh = ctx->bh; h.wc = ctx->wc; h.bc = ctx->bc;
-  h.slot0 = slot0;
-  h.logits = reinterpret_cast<float*>(ws + p.logits);
-  h.theta = reinterpret_cast<float*>(ws + p.theta);
-  {
-    Rec r(ctx, st, 2, 401);
-    OMNI_CU(launch_controller(h, st), "controller");
-    ctx->launches++;
-  }
+  h.y0 = y;
   {
     Rec r(ctx, st, 2, 500);
     OMNI_CU(launch_head(h, st), "head");
@@ -1043,4 +1061,226 @@ extern "C" omni_status omni_tile_slide_noalloc(const omni_config* cfg, const uin
   if (e == cudaSuccess && out->tissue) e = cudaMemcpyAsync(out->tissue, mask, thumb, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && out->otsu) e = cudaMemcpyAsync(out->otsu, otsu, 4, cudaMemcpyDeviceToDevice, st);
   return e == cudaSuccess ? OMNI_OK : OMNI_ECUDA;
+}
+
+// ====================================================================== backward
+namespace {
+
+struct BwdPlan {
+  Plan f;                      // forward workspace (first part of the buffer)
+  size_t lg[OMNI_MAX_CLASSES], dl[OMNI_MAX_CLASSES], cov[OMNI_MAX_SCALES];
+  size_t loss_partial, sums, cls_ids;
+  size_t c1, a1, c2, pr, y0, dy0pre, dc2, da1, da1pre, dc1, dh0, dh0pre;
+  size_t dtheta, wpart;
+  size_t acc_wc, acc_bc, acc_wh, acc_bh, acc_w1, acc_g1, acc_b1, acc_w2, acc_g2, acc_b2, acc_wp;
+  size_t total;
+};
+
+bool make_bwd_plan(const omni_config& c, int H, int W, BwdPlan& b) {
+  if (!make_plan(c, H, W, b.f)) return false;
+  size_t off = b.f.total;
+  const int C0 = widths(c, 0), Cb = widths(c, c.levels - 1);
+  for (int k = 0; k < c.n_classes; ++k) {
+    const int f = c.factors[c.class_scale[k]];
+    const size_t n = (size_t)((H + f - 1) / f) * ((W + f - 1) / f);
+    b.lg[k] = take(off, n * 4);
+    b.dl[k] = take(off, n * 4);
+  }
+  for (int s = 0; s < c.n_scales; ++s) {
+    const int f = c.factors[s];
+    b.cov[s] = take(off, (size_t)((H + f - 1) / f) * ((W + f - 1) / f) * 2);
+  }
+  b.loss_partial = take(off, (size_t)OMNI_MAX_CLASSES * loss_blocks() * 4 * 8);
+  b.sums = take(off, (size_t)OMNI_MAX_CLASSES * 4 * 8);
+  b.cls_ids = take(off, OMNI_MAX_CLASSES * 4);
+  const size_t npx = (size_t)c.max_batch * c.patch * c.patch;
+  const size_t fc = npx * C0 * 4;
+  b.c1 = take(off, fc); b.a1 = take(off, fc); b.c2 = take(off, fc); b.pr = take(off, fc);
+  b.y0 = take(off, fc); b.dy0pre = take(off, fc); b.dc2 = take(off, fc); b.da1 = take(off, fc);
+  b.da1pre = take(off, fc); b.dc1 = take(off, fc);
+  b.dh0 = take(off, npx * kHeadCh * 4); b.dh0pre = take(off, npx * kHeadCh * 4);
+  b.dtheta = take(off, (size_t)c.max_batch * OMNI_MAX_CLASSES * head_bwd_blocks(c.patch) * kHeadParams * 4);
+  b.wpart = take(off, (size_t)wgrad_chunks((long long)npx) * C0 * 27 * C0 * 4);
+  const size_t zdim = Cb + c.n_classes + c.n_scales;
+  b.acc_wc = take(off, (size_t)kHeadParams * zdim * 8);
+  b.acc_bc = take(off, kHeadParams * 8);
+  b.acc_wh = take(off, (size_t)kHeadCh * C0 * 8);
+  b.acc_bh = take(off, kHeadCh * 8);
+  b.acc_w1 = take(off, (size_t)C0 * 27 * C0 * 8);
+  b.acc_g1 = take(off, C0 * 8);
+  b.acc_b1 = take(off, C0 * 8);
+  b.acc_w2 = take(off, (size_t)C0 * 9 * C0 * 8);
+  b.acc_g2 = take(off, C0 * 8);
+  b.acc_b2 = take(off, C0 * 8);
+  b.acc_wp = take(off, (size_t)C0 * 3 * C0 * 8);
+  b.total = align_up(off, 256);
+  return true;
+}
+
+// [o][tap][c] (FP64 accumulation order) -> [o][c][tap] (blob order), FP32
+__global__ void k_w_to_blob(const double* __restrict__ acc, int O, int cin, int taps, float* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)O * cin * taps;
+  if (i >= n) return;
+  const int o = (int)(i / ((long long)cin * taps));
+  const int rem = (int)(i % ((long long)cin * taps));
+  const int c = rem / taps, t = rem % taps;
+  out[i] = (float)acc[(long long)o * cin * taps + (long long)t * cin + c];
+}
+
+}  // namespace
+
+extern "C" uint64_t omni_backward_workspace(const omni_config* cfg, int32_t H, int32_t W) {
+  if (!cfg || !validate(*cfg).empty()) return 0;
+  BwdPlan b;
+  if (!make_bwd_plan(*cfg, H, W, b)) return 0;
+  return b.total;
+}
+
+extern "C" omni_status omni_backward(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int32_t W, int64_t stride,
+                                     const uint8_t* const* gt_dev, void* ws_, uint64_t ws_bytes, float* loss_dev,
+                                     const omni_grads* grads, void* stream) {
+  if (!ctx || !rgb || !gt_dev || !loss_dev || !grads) return fail(ctx, OMNI_EINVAL, "null argument");
+  if (!ctx->have_weights) return fail(ctx, OMNI_ESTATE, "omni_load_weights has not been called");
+  const omni_config& c = ctx->cfg;
+  if (c.precision != OMNI_FP32) return fail(ctx, OMNI_EINVAL, "omni_backward needs an OMNI_FP32 context");
+  for (int k = 0; k < c.n_classes; ++k)
+    if (!gt_dev[k]) return fail(ctx, OMNI_EINVAL, "missing ground-truth mask for class " + std::to_string(k));
+  BwdPlan bp;
+  if (!make_bwd_plan(c, H, W, bp)) return fail(ctx, OMNI_EINVAL, "bad slide size");
+  omni_status r = check_ws(ctx, ws_, ws_bytes, bp.total);
+  if (r) return r;
+  if (c.max_batch > 64) return fail(ctx, OMNI_EINVAL, "omni_backward supports max_batch <= 64");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(ws_);
+  const Plan& p = bp.f;
+  const int L = c.levels, C0 = widths(c, 0), Cb = widths(c, L - 1), P = c.patch;
+  const long long PP = (long long)P * P;
+  auto F = [&](size_t o) { return reinterpret_cast<float*>(ws + o); };
+  auto D = [&](size_t o) { return reinterpret_cast<double*>(ws + o); };
+
+  // ---------------------------------------------------------------- pass 1: forward
+  omni_outputs fo{};
+  for (int k = 0; k < c.n_classes; ++k) fo.logits[k] = F(bp.lg[k]);
+  for (int s = 0; s < c.n_scales; ++s) fo.coverage[s] = reinterpret_cast<uint16_t*>(ws + bp.cov[s]);
+  const uint32_t all_s = (1u << c.n_scales) - 1, all_c = (1u << c.n_classes) - 1;
+  r = omni_segment_slide(ctx, rgb, H, W, stride, all_s, all_c, ws_, ws_bytes, &fo, stream);
+  if (r) return r;
+
+  // ---------------------------------------------------------------- loss and dloss/dL
+  NPix npix{};
+  for (int k = 0; k < c.n_classes; ++k) {
+    const int f = c.factors[c.class_scale[k]];
+    npix.n[k] = (long long)((H + f - 1) / f) * ((W + f - 1) / f);
+    OMNI_CU(launch_loss_partial(F(bp.lg[k]), gt_dev[k], npix.n[k], D(bp.loss_partial) + (size_t)k * loss_blocks() * 4, st),
+            "loss partial");
+  }
+  OMNI_CU(launch_loss_final(D(bp.loss_partial), c.n_classes, npix, D(bp.sums), loss_dev, st), "loss");
+  for (int k = 0; k < c.n_classes; ++k)
+    OMNI_CU(launch_loss_grad(F(bp.lg[k]), gt_dev[k], npix.n[k], D(bp.sums) + 4 * k, (double)npix.n[k],
+                             c.n_classes, F(bp.dl[k]), st),
+            "loss grad");
+  OMNI_CU(cudaMemsetAsync(ws + bp.acc_wc, 0, bp.total - bp.acc_wc, st), "clear accumulators");
+
+  // ---------------------------------------------------------------- pass 2: recompute + backward per batch
+  Prep pr;
+  {
+    // canvases of every scale (integer stages, identical to pass 1)
+    r = run_prep(ctx, rgb, stride, p, ws, st, pr);
+    if (r) return r;
+  }
+  const int32_t* tiles = reinterpret_cast<const int32_t*>(ws + p.tiles);
+  int32_t* cls_dev = reinterpret_cast<int32_t*>(ws + bp.cls_ids);
+  int toff = 0;
+  for (int s = 0; s < c.n_scales; ++s) {
+    const int n_s = ctx->h_counts[1 + s];
+    int cls[OMNI_MAX_CLASSES], ncls = 0;
+    for (int k = 0; k < c.n_classes; ++k)
+      if (c.class_scale[k] == s) cls[ncls++] = k;
+    if (ncls == 0) { toff += n_s; continue; }
+    const int f = c.factors[s];
+    for (int start = 0; start < n_s; start += c.max_batch) {
+      const int nb = std::min(c.max_batch, n_s - start);
+      const int32_t* t3 = tiles + 3 * (toff + start);
+      const long long npx = (long long)nb * PP;
+      r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], t3, nb, start, ncls, cls, st, true);
+      if (r) return r;
+      void* cat0 = ws + p.cat[0];
+      ConvArgs a{};
+      a.B = nb; a.R = P; a.raw = 1; a.err = ctx->d_err;
+      a.cin = 3 * C0; a.cout = C0; a.x = cat0; a.x_cs = 3 * C0; a.y = F(bp.c1); a.y_cs = C0; a.w = ctx->dec1[0];
+      OMNI_CU(launch_conv_f32(a, st), "recompute conv1");
+      OMNI_CU(launch_affine_relu(F(bp.c1), ctx->dec1[0].gamma, ctx->dec1[0].beta, C0, npx, F(bp.a1), st), "a1");
+      ConvArgs b2{};
+      b2.B = nb; b2.R = P; b2.raw = 1; b2.err = ctx->d_err;
+      b2.cin = C0; b2.cout = C0; b2.x = F(bp.a1); b2.x_cs = C0; b2.y = F(bp.c2); b2.y_cs = C0;
+      b2.res_mode = RES_TENSOR; b2.r = cat0; b2.r_cs = 3 * C0; b2.cr = 3 * C0; b2.y2 = F(bp.pr); b2.y2_cs = C0;
+      b2.w = ctx->dec2[0];
+      OMNI_CU(launch_conv_f32(b2, st), "recompute conv2");
+      BwdHeadArgs h{};
+      h.B = nb; h.P = P; h.n_cls = ncls;
+      h.theta = F(p.theta);
+      h.wh = ctx->wh; h.bh = ctx->bh; h.g2 = ctx->dec2[0].gamma; h.b2 = ctx->dec2[0].beta;
+      h.tiles3 = t3;
+      h.oy0 = c.pad_lead / f; h.ox0 = c.pad_lead / f; h.oh = (H + f - 1) / f; h.ow = (W + f - 1) / f;
+      h.cov = reinterpret_cast<const uint16_t*>(ws + bp.cov[s]);
+      h.c2 = F(bp.c2); h.pr = F(bp.pr); h.dh0 = F(bp.dh0); h.dtheta_partial = F(bp.dtheta);
+      h.y0 = F(bp.y0); h.dh0_pre = F(bp.dh0pre); h.dy0_pre = F(bp.dy0pre); h.dc2 = F(bp.dc2);
+      for (int ci = 0; ci < ncls; ++ci) {
+        h.ci = ci;
+        h.dL = F(bp.dl[cls[ci]]);
+        OMNI_CU(launch_head_bwd(h, C0, st), "head backward");
+      }
+      OMNI_CU(launch_prehead_bwd(h, C0, npx, st), "pre-head backward");
+      float* wpart = F(bp.wpart);
+      OMNI_CU(launch_wgrad(F(bp.dh0pre), kHeadCh, F(bp.y0), C0, C0, 1, P, npx, wpart, D(bp.acc_wh), st), "dWh");
+      OMNI_CU(launch_colsum(F(bp.dh0pre), nullptr, kHeadCh, npx, wpart, D(bp.acc_bh), st), "dbh");
+      OMNI_CU(launch_colsum(F(bp.dy0pre), nullptr, C0, npx, wpart, D(bp.acc_b2), st), "db2");
+      OMNI_CU(launch_colsum(F(bp.dy0pre), F(bp.c2), C0, npx, wpart, D(bp.acc_g2), st), "dg2");
+      OMNI_CU(launch_wgrad(F(bp.dy0pre), C0, static_cast<const float*>(cat0), 3 * C0, 3 * C0, 1, P, npx, wpart,
+                           D(bp.acc_wp), st), "dWp");
+      OMNI_CU(launch_wgrad(F(bp.dc2), C0, F(bp.a1), C0, C0, 9, P, npx, wpart, D(bp.acc_w2), st), "dW2");
+      ConvArgs dg{};
+      dg.B = nb; dg.R = P; dg.raw = 1; dg.err = ctx->d_err;
+      dg.cin = C0; dg.cout = C0; dg.x = F(bp.dc2); dg.x_cs = C0; dg.y = F(bp.da1); dg.y_cs = C0; dg.w = ctx->dec2t0;
+      OMNI_CU(launch_conv_f32(dg, st), "da1");
+      OMNI_CU(launch_relu_bwd(F(bp.da1), F(bp.c1), ctx->dec1[0].gamma, ctx->dec1[0].beta, C0, npx, F(bp.da1pre),
+                              F(bp.dc1), st), "relu backward");
+      OMNI_CU(launch_colsum(F(bp.da1pre), nullptr, C0, npx, wpart, D(bp.acc_b1), st), "db1");
+      OMNI_CU(launch_colsum(F(bp.da1pre), F(bp.c1), C0, npx, wpart, D(bp.acc_g1), st), "dg1");
+      OMNI_CU(launch_wgrad(F(bp.dc1), C0, static_cast<const float*>(cat0), 3 * C0, 3 * C0, 9, P, npx, wpart,
+                           D(bp.acc_w1), st), "dW1");
+      OMNI_CU(cudaMemcpyAsync(cls_dev, cls, ncls * sizeof(int32_t), cudaMemcpyHostToDevice, st), "class ids");
+      OMNI_CU(launch_ctrl_bwd(F(bp.dtheta), head_bwd_blocks(P), nb, ncls, cls_dev, c.n_classes, c.n_scales, s,
+                              F(p.gap), Cb, D(bp.acc_wc), D(bp.acc_bc), st), "controller backward");
+      // the class-id upload reads host memory that changes next batch
+      OMNI_CU(cudaStreamSynchronize(st), "batch sync");
+    }
+    toff += n_s;
+  }
+
+  // ---------------------------------------------------------------- FP32 outputs in blob layouts
+  const long long zdim = Cb + c.n_classes + c.n_scales;
+  auto out = [&](float* dst, size_t acc, long long n) -> cudaError_t {
+    return dst ? launch_to_f32(D(acc), n, dst, st) : cudaSuccess;
+  };
+  OMNI_CU(out(grads->ctrl_w, bp.acc_wc, kHeadParams * zdim), "ctrl_w");
+  OMNI_CU(out(grads->ctrl_b, bp.acc_bc, kHeadParams), "ctrl_b");
+  OMNI_CU(out(grads->head_w, bp.acc_wh, (long long)kHeadCh * C0), "head_w");
+  OMNI_CU(out(grads->head_b, bp.acc_bh, kHeadCh), "head_b");
+  OMNI_CU(out(grads->dec0_g1, bp.acc_g1, C0), "g1");
+  OMNI_CU(out(grads->dec0_b1, bp.acc_b1, C0), "b1");
+  OMNI_CU(out(grads->dec0_g2, bp.acc_g2, C0), "g2");
+  OMNI_CU(out(grads->dec0_b2, bp.acc_b2, C0), "b2");
+  OMNI_CU(out(grads->dec0_wp, bp.acc_wp, (long long)C0 * 3 * C0), "wp");
+  if (grads->dec0_w1) {
+    const long long n = (long long)C0 * 3 * C0 * 9;
+    k_w_to_blob<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D(bp.acc_w1), C0, 3 * C0, 9, grads->dec0_w1);
+  }
+  if (grads->dec0_w2) {
+    const long long n = (long long)C0 * C0 * 9;
+    k_w_to_blob<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D(bp.acc_w2), C0, C0, 9, grads->dec0_w2);
+  }
+  OMNI_CU(cudaGetLastError(), "gradient outputs");
+  return OMNI_OK;
 }

@@ -48,6 +48,7 @@ class Workload:
     median_k: int = 59
     pad_lead: int = 0              # the paper's 4096 border; 0 for these workloads
     max_batch: int = 32
+    head_offset: float = 0.0       # controller bias of the head's final bias b3 (weights init)
 
     @property
     def n_classes(self) -> int:
@@ -77,18 +78,18 @@ TINY = Workload(
 NEEDLE = Workload(
     name="needle", H=16384, W=49152, seed=1, tissue=0.40, layout="cores", n_blobs=4,
     factors=(1, 4, 8), P=512, S=256, base=32, levels=5,
-    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=32)
+    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=32, head_offset=3.3)
 
 DIFF = Workload(
     name="diff", H=2048, W=2048, seed=7, tissue=0.40, layout="blobs", n_blobs=6,
     factors=(1, 4, 8), P=256, S=128, base=32, levels=5,
     class_scale=(0, 0, 1, 1, 2, 2), weights_seed=12, tissue_filter=False,
-    tissue_and=False, max_batch=64)
+    tissue_and=False, max_batch=64, head_offset=3.3)
 
 LARGE = Workload(
     name="large", H=32768, W=98304, seed=200, tissue=0.35, layout="cores", n_blobs=4,
     factors=(1, 4, 8), P=1024, S=512, base=32, levels=5,
-    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=8)
+    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=8, head_offset=3.3)
 
 
 def ragged_workloads(n: int = 12, seed0: int = 100) -> List[Workload]:

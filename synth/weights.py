@@ -20,7 +20,11 @@ bias ~ U[-0.05, 0.05]; controller He-normal with zero bias.  The second norm
 scale and the projection of every residual block are multiplied by 1/sqrt(2)
 so that the two branches of each residual sum add up to the variance of one
 (the residual-gain reading), which keeps activations and logits O(1) through
-the 2L-1 blocks.
+the 2L-1 blocks.  Random weights make the head's output nearly constant within
+a tile and negative everywhere; the controller bias of theta[152] (the head's
+final bias b3) is therefore set to the workload's ``head_offset`` so that the
+decision threshold falls between tissue-interior and tissue-edge responses
+(3.3 for the base-32 workloads, 0 for the tiny one).
 """
 from __future__ import annotations
 
@@ -84,6 +88,7 @@ def gen_weights(work, seed: int | None = None) -> np.ndarray:
             t = rng.uniform(-0.05, 0.05, shape)
         else:  # ctrl.b
             t = np.zeros(shape)
+            t[-1] = getattr(work, "head_offset", 0.0)
         parts.append(np.asarray(t, np.float32).ravel())
     return np.concatenate(parts).astype(np.float32)
 
