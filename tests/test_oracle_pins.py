@@ -380,7 +380,9 @@ def test_gradient_matches_central_differences():
         with torch.no_grad():
             fd = (float(prob.loss(qp)) - float(prob.loss(qm))) / (2 * eps)
         an = float(grads[name][idx])
-        scale = max(abs(fd), 1e-6 * float(grads[name].abs().max()), 1e-9)
+        # central differences at eps = 1e-6 carry ~1e-10 absolute round-off, so
+        # entries far below the tensor's largest are compared against 1e-5 * max
+        scale = max(abs(fd), 1e-5 * float(grads[name].abs().max()), 1e-9)
         assert abs(an - fd) / scale < 1e-4, (name, idx, an, fd)
         checked += 1
     assert checked == 48
