@@ -148,6 +148,45 @@ def run_layer(args):
                       "peak_source": src}))
 
 
+def run_ragged(args, api, _lib, dev, prec):
+    """Twelve synthetic slides (long side U[8192, 49152], aspect U[1, 4], tissue
+    U[0.2, 0.6]); one step segments all of them.  One context and one
+    workspace serve every slide (sized for the largest)."""
+    import torch
+    works = synth.ragged_workloads()
+    blob = synth.gen_weights(works[0])
+    seg = api.Segmenter(works[0], blob, precision=prec)
+    if prec == _lib.BF16 and not args.no_autotune:
+        seg.set_autotune(True)
+    need = max(seg.query(w.H, w.W).workspace_bytes for w in works)
+    seg.workspace(need, dev)
+    rgbs = [api.synth_slide(synth.spec_for(w), device=dev) for w in works]
+    outs = [seg.segment(r) for r in rgbs]
+    torch.cuda.synchronize()
+    for _ in range(max(0, args.warmup - 1)):
+        for r, o in zip(rgbs, outs):
+            seg.segment(r, out=o)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(works) + 1)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        ev[k][0].record()
+        for i, (r, o) in enumerate(zip(rgbs, outs)):
+            seg.segment(r, out=o)
+            ev[k][i + 1].record()
+    torch.cuda.synchronize()
+    per = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(len(works))] for k in range(args.steps)])
+    total_ms = float(per.sum(axis=1).mean())
+    mpx = sum(w.H * w.W for w in works) / 1e6
+    print(json.dumps({"metric": "ragged 12-slide segmentation Mpx/s", "value": mpx / (total_ms / 1e3),
+                      "unit": "Mpx/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": total_ms, "higher_is_better": True, "dtype": args.precision,
+                      "data": "synthetic",
+                      "config": {"workload": "12 ragged needle-like slides, seeds 100-111",
+                                 "slides": [[w.H, w.W, round(w.tissue, 3)] for w in works]},
+                      "per_slide_ms": [round(float(v), 2) for v in per.mean(axis=0)]}))
+    seg.close()
+
+
 def cpu_baseline(max_tiles: int = 4):
     """The FP64 oracle timed on a bounded sample: the first foreground 40x tiles
     of the needle slide (generated on the CPU), through U-Net, heads and the
@@ -214,6 +253,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-fp32", action="store_true",
                     help="also time one step of the plain FP32 path")
+    ap.add_argument("--ragged", action="store_true",
+                    help="the 12-slide ragged workload: per-slide latency and aggregate Mpx/s")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one slide step after the generator (for ncu launch lists)")
     ap.add_argument("--layer", default=None,
@@ -241,10 +283,15 @@ def main():
     dev = torch.device("cuda", local)
     prec = _lib.BF16 if args.precision == "bf16" else _lib.FP32
 
+    if args.ragged:
+        run_ragged(args, api, _lib, dev, prec)
+        return
     spec = synth.spec_for(WORK)
     rgb = api.synth_slide(spec, device=dev)
     blob = synth.gen_weights(WORK)
     seg = api.Segmenter(WORK, blob, precision=prec)
+    if prec == _lib.BF16 and not args.no_autotune:
+        seg.set_autotune(True)          # the first (untimed) call tunes every conv shape
     out = seg.segment(rgb)
     torch.cuda.synchronize()
     if args.profile_step:
@@ -302,6 +349,22 @@ def main():
     stitch = {"achieved_gbs": st_bytes / (st_ms / 1e3) / 1e9 if st_ms else None,
               "peak_gbs": pk["hbm_gbs"], "ms_per_step": st_ms / args.steps}
 
+    # the same steps replayed from a captured CUDA graph (library timing off)
+    seg.set_graphs(True)
+    for _ in range(2):
+        seg.segment(rgb, out=out)          # second call captures
+    barrier()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record()
+    for _ in range(args.steps):
+        seg.segment(rgb, out=out)
+    g1.record()
+    barrier()
+    graph = {"value": mpx * world / (g0.elapsed_time(g1) / args.steps / 1e3), "unit": "Mpx/s",
+             "ms_per_step": g0.elapsed_time(g1) / args.steps}
+    seg.set_graphs(False)
+
     # end to end through the host-buffer entry point (pinned host memory)
     rgb_h = rgb.cpu().pin_memory()
     labs = {c: torch.empty(tuple(out["labels"][c].shape), dtype=torch.uint8).pin_memory()
@@ -341,7 +404,8 @@ def main():
                            "tiles_per_step": int(conv_flops / max(args.steps, 1) /
                                                  seg.query(WORK.H, WORK.W).flops_per_tile)},
                 "roofline": roof, "stitch": stitch, "e2e": e2e, "gpu_launches": int(launches),
-                "breakdown": breakdown,
+                "breakdown": breakdown, "graph_replay": graph,
+                "autotuned": [list(t) for t in seg.tuned()],
                 "clocks": clocks}
         if fp32 is not None:
             line["fp32_plain"] = fp32

@@ -225,6 +225,25 @@ omni_status omni_get_timing(omni_ctx* ctx, int32_t kind, double* ms, int64_t* la
 /* Number of kernel launches enqueued by the last omni_segment_slide call. */
 int64_t omni_last_launch_count(const omni_ctx* ctx);
 
+/* Conv autotuner (BF16 contexts).  When enabled, the first time a layer
+ * shape (R, cin, cout, residual channels, residual kind, batch) is met, every
+ * legal tensor-core configuration (small-N variant with 32/64-channel chunks;
+ * per-tap variant with each legal N tile and channel chunk) is timed on the
+ * real operands and the fastest is kept for the context's lifetime.  Tuning
+ * synchronises the stream, so run one untimed call first.  omni_get_tuned
+ * writes 10 int32 per tuned shape: R, cin, cout, cr, residual kind, batch,
+ * kind (0 per-tap, 1 small-N), N tile, channel chunk, stages; returns the count. */
+omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled);
+int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows);
+
+/* CUDA graphs.  When enabled, omni_segment_slide captures its post-tiling
+ * launch chain (every network batch and the stitches) into a CUDA graph on
+ * the second call that sees the same slide pointer, size, scale/class masks,
+ * workspace, stream, output buffers and foreground tile counts, and replays
+ * that graph on later such calls.  Tiling still runs eagerly each call (its
+ * counts decide the key).  Ignored while timing is enabled. */
+omni_status omni_set_graphs(omni_ctx* ctx, int32_t enabled);
+
 /* Per-launch device times (ms) of the current timing record, with each
  * launch's kind (as above), tag and algorithmic
  * work (FLOPs for convolutions, else 0).  Tags: conv of encoder level l =

@@ -205,6 +205,19 @@ class Segmenter:
                 self.ctx)
         return ms.value, n.value, work.value
 
+    def set_autotune(self, on: bool = True):
+        L.check(self.lib.omni_set_autotune(self.ctx, int(on)), self.ctx)
+
+    def set_graphs(self, on: bool = True):
+        L.check(self.lib.omni_set_graphs(self.ctx, int(on)), self.ctx)
+
+    def tuned(self):
+        """[(R, cin, cout, cr, res_kind, batch, kind, N tile, chunk, stages)] chosen by the autotuner."""
+        n = self.lib.omni_get_tuned(self.ctx, None, 0)
+        rows = np.zeros((max(n, 1), 10), np.int32)
+        self.lib.omni_get_tuned(self.ctx, rows.ctypes.data_as(C.c_void_p), n)
+        return [tuple(int(v) for v in r) for r in rows[:n]]
+
     def launch_count(self) -> int:
         return int(self.lib.omni_last_launch_count(self.ctx))
 

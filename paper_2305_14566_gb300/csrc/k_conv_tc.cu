@@ -826,9 +826,8 @@ bool conv_tc_supported(int R, int cin, int cout, int cr) {
   return bn % 32 == 0 && cout % bn == 0;
 }
 
-cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st) {
-  const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
-  if (!conv_tc_supported(a.R, a.cin, a.cout, cr)) return cudaErrorInvalidValue;
+namespace {
+cudaError_t check_tc_args(const ConvArgs& a, int cr) {
   if (a.res_mode == RES_RGB && !a.w.wp_f32) return cudaErrorInvalidValue;
   if ((a.x_co % 8) || (a.x_cs % 8) || (a.y_co % 8) || (a.y_cs % 8)) return cudaErrorInvalidValue;
   if (cr && ((a.r_co % 8) || (a.r_cs % 8))) return cudaErrorInvalidValue;
@@ -836,28 +835,72 @@ cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st) {
        reinterpret_cast<uintptr_t>(a.w.w_bf16) | (cr ? reinterpret_cast<uintptr_t>(a.r) |
                                                      reinterpret_cast<uintptr_t>(a.w.wp_bf16) : 0)) % 16)
     return cudaErrorInvalidValue;
-  const bool res = cr > 0;
-  if (halo_ok(a.R, a.cout, a.cin, cr)) {
-    int ck = 32, stg = halo_stages(a.cin, a.cout, cr, 32);
-    const int stg64 = halo_stages(a.cin, a.cout, cr, 64);
+  return cudaSuccess;
+}
+
+bool pertap_ok(int R, int cin, int cout, int cr, int bn, int ck) {
+  if (!(R == 16 || R == 32 || R == 64 || (R >= 128 && R % 128 == 0))) return false;
+  if (cin % ck || cr % ck || bn > cout || cout % bn) return false;
+  if (cr > 0 && bn > 128) return false;
+  return bn == 32 || bn == 64 || bn == 128 || bn == 256;
+}
+}  // namespace
+
+int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
+  int n = 0;
+  if (halo_ok(R, cout, cin, cr))
+    for (int ck = 32; ck <= 64; ck *= 2) {
+      const int stg = halo_stages(cin, cout, cr, ck);
+      if (stg >= 2 && n < max) out[n++] = TcConfig{1, cout, ck, stg};
+    }
+  for (int bn = 32; bn <= 256; bn *= 2)
+    for (int ck = 32; ck <= 64; ck *= 2)
+      if (pertap_ok(R, cin, cout, cr, bn, ck) && n < max) out[n++] = TcConfig{0, bn, ck, 0};
+  return n;
+}
+
+TcConfig tc_default(int R, int cin, int cout, int cr) {
+  if (halo_ok(R, cout, cin, cr)) {
+    int ck = 32, stg = halo_stages(cin, cout, cr, 32);
+    const int stg64 = halo_stages(cin, cout, cr, 64);
     if (stg64 >= 3) { ck = 64; stg = stg64; }
+    return TcConfig{1, cout, ck, stg};
+  }
+  const bool res = cr > 0;
+  return TcConfig{0, pick_bn(cout, res), (cin % 64 == 0 && (!res || cr % 64 == 0)) ? 64 : 32, 0};
+}
+
+cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_t st) {
+  const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
+  cudaError_t e = check_tc_args(a, cr);
+  if (e != cudaSuccess) return e;
+  const bool res = cr > 0;
+  if (c.kind == 1) {
+    if (!halo_ok(a.R, a.cout, a.cin, cr) || c.bn != a.cout || c.stages < 2 ||
+        c.stages > halo_stages(a.cin, a.cout, cr, c.ck))
+      return cudaErrorInvalidValue;
 #define OMNI_HALO(BN_, CK_, RES_) \
-    if (a.cout == BN_ && ck == CK_ && res == RES_) return launch_halo<BN_, CK_, RES_>(a, st, stg);
+    if (c.bn == BN_ && c.ck == CK_ && res == RES_) return launch_halo<BN_, CK_, RES_>(a, st, c.stages);
     OMNI_HALO(32, 32, false) OMNI_HALO(32, 32, true) OMNI_HALO(32, 64, false) OMNI_HALO(32, 64, true)
     OMNI_HALO(64, 32, false) OMNI_HALO(64, 32, true) OMNI_HALO(64, 64, false) OMNI_HALO(64, 64, true)
 #undef OMNI_HALO
     return cudaErrorInvalidValue;
   }
-  const int ck = (a.cin % 64 == 0 && (!res || cr % 64 == 0)) ? 64 : 32;
-  const int bn = pick_bn(a.cout, res);
+  if (!pertap_ok(a.R, a.cin, a.cout, cr, c.bn, c.ck)) return cudaErrorInvalidValue;
 #define OMNI_TC(BN_, CK_, RES_) \
-  if (bn == BN_ && ck == CK_ && res == RES_) return launch_t<BN_, CK_, RES_>(a, st);
+  if (c.bn == BN_ && c.ck == CK_ && res == RES_) return launch_t<BN_, CK_, RES_>(a, st);
   OMNI_TC(32, 32, false) OMNI_TC(32, 32, true) OMNI_TC(32, 64, false) OMNI_TC(32, 64, true)
   OMNI_TC(64, 32, false) OMNI_TC(64, 32, true) OMNI_TC(64, 64, false) OMNI_TC(64, 64, true)
   OMNI_TC(128, 32, false) OMNI_TC(128, 32, true) OMNI_TC(128, 64, false) OMNI_TC(128, 64, true)
   OMNI_TC(256, 32, false) OMNI_TC(256, 64, false)
 #undef OMNI_TC
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st) {
+  const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
+  if (!conv_tc_supported(a.R, a.cin, a.cout, cr)) return cudaErrorInvalidValue;
+  return launch_conv_tc_cfg(a, tc_default(a.R, a.cin, a.cout, cr), st);
 }
 
 }  // namespace omni

@@ -93,7 +93,16 @@ cudaError_t launch_gap(int precision, int B, int R, int C, const void* x, int x_
                        float* g, cudaStream_t st);
 
 // k_conv_tc.cu (BF16 tcgen05 implicit GEMM)
+struct TcConfig {
+  int kind;     // 0: per-tap A loads, 1: small-N variant (resident weights, 8x16 tiles)
+  int bn;       // N tile
+  int ck;       // channel chunk (32 -> 64-byte swizzle, 64 -> 128-byte swizzle)
+  int stages;   // pipeline stages (small-N variant; per-tap derives its own)
+};
 cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st);
+cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
+int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max);
+TcConfig tc_default(int R, int cin, int cout, int cr);
 bool conv_tc_supported(int R, int cin, int cout, int cr);
 
 // k_head.cu

@@ -3,7 +3,9 @@
 // whole-slide pipeline (Sec. 2.1 tiling, Sec. 2.2 segmentation, Sec. 2.3
 // aggregation).
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -33,6 +35,16 @@ struct omni_ctx {
   double work[4] = {0, 0, 0, 0};
   int64_t launches = 0;
   int64_t tiles_done = 0;
+  // conv autotuner: layer shape -> fastest tensor-core configuration
+  bool autotune = false;
+  std::map<std::array<int, 6>, TcConfig> tuned;
+  // CUDA graph of the post-tiling launch chain (network + stitch)
+  bool graphs = false;
+  std::vector<uint64_t> last_key, graph_key;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_launches = 0, graph_tiles = 0;
+  double graph_stitch_bytes = 0;
+  bool capturing = false;
 };
 
 namespace {
@@ -274,6 +286,7 @@ omni_status omni_create(const omni_config* cfg, omni_ctx** out) {
 
 void omni_destroy(omni_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->wdev) cudaFree(ctx->wdev);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
@@ -520,6 +533,36 @@ double conv_flops(const ConvArgs& a) {
   return 2.0 * a.B * a.R * a.R * a.cout * (9.0 * a.cin + cr);
 }
 
+// Times every legal tensor-core configuration of a layer on the real operands
+// (two warm-up launches, then three timed with events) and returns the
+// fastest; the launches only rewrite the layer's own output.  Synchronises.
+TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st) {
+  const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
+  TcConfig cands[16];
+  const int n = tc_candidates(a.R, a.cin, a.cout, cr, cands, 16);
+  TcConfig best = tc_default(a.R, a.cin, a.cout, cr);
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return best;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return best; }
+  for (int i = 0; i < n; ++i) {
+    bool ok = launch_conv_tc_cfg(a, cands[i], st) == cudaSuccess &&
+              launch_conv_tc_cfg(a, cands[i], st) == cudaSuccess;
+    ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
+    for (int r = 0; r < 3 && ok; ++r) ok = launch_conv_tc_cfg(a, cands[i], st) == cudaSuccess;
+    ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0;
+    if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = cands[i];
+    }
+    ctx->launches += 5;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
 omni_status run_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, int tag) {
   Rec r(ctx, st, 0, tag, conv_flops(a));
   cudaError_t e;
@@ -529,7 +572,19 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, int tag)
     if (!conv_tc_supported(a.R, a.cin, a.cout, a.res_mode == RES_TENSOR ? a.cr : 0))
       return fail(ctx, OMNI_EINVAL, "BF16 tensor-core conv does not support R=" + std::to_string(a.R) +
                                         " cin=" + std::to_string(a.cin) + " cout=" + std::to_string(a.cout));
-    e = launch_conv_tc(a, st);
+    const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
+    TcConfig cfg = tc_default(a.R, a.cin, a.cout, cr);
+    if (ctx->autotune) {
+      const std::array<int, 6> key{a.R, a.cin, a.cout, cr, a.res_mode, a.B};
+      auto it = ctx->tuned.find(key);
+      if (it != ctx->tuned.end()) {
+        cfg = it->second;
+      } else if (!ctx->capturing) {
+        cfg = tune_conv(ctx, a, st);
+        ctx->tuned[key] = cfg;
+      }
+    }
+    e = launch_conv_tc_cfg(a, cfg, st);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv");
   ctx->launches++;
@@ -661,6 +716,63 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   return OMNI_OK;
 }
 
+// Everything after tiling: every batch of every requested scale, then the
+// stitch + labels of each scale.  Launch-only (no synchronisation), so it can
+// be captured into a CUDA graph.
+omni_status run_network(omni_ctx* ctx, const omni_config& c, const Plan& p, uint8_t* ws, const Prep& pr,
+                        const omni_outputs* out, int H, int W, uint32_t scale_mask, uint32_t class_mask,
+                        cudaStream_t st, double& stitch_bytes) {
+  omni_status r = OMNI_OK;
+  const int32_t* tiles = reinterpret_cast<const int32_t*>(ws + p.tiles);
+  const int32_t* slot = reinterpret_cast<const int32_t*>(ws + p.slot);
+  int toff = 0;
+  for (int s = 0; s < c.n_scales; ++s) {
+    const int n_s = ctx->h_counts[1 + s];
+    int cls[OMNI_MAX_CLASSES], ncls = 0;
+    for (int k = 0; k < c.n_classes; ++k)
+      if (c.class_scale[k] == s && (class_mask >> k & 1u)) cls[ncls++] = k;
+    const bool want = (scale_mask >> s & 1u) && ncls > 0;
+    if (want) {
+      for (int start = 0; start < n_s; start += c.max_batch) {
+        int nb = std::min(c.max_batch, n_s - start);
+        r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], tiles + 3 * (toff + start), nb, start, ncls, cls, st);
+        if (r) return r;
+      }
+      ctx->tiles_done += n_s;
+      const int f = c.factors[s];
+      StitchArgs a{};
+      a.hs = p.g.Hp / f; a.ws = p.g.Wp / f;
+      a.oy0 = c.pad_lead / f; a.ox0 = c.pad_lead / f;
+      a.oh = (H + f - 1) / f; a.ow = (W + f - 1) / f;
+      a.P = c.patch; a.S = c.stride; a.gh = p.g.gh[s]; a.gw = p.g.gw[s]; a.f = f;
+      a.slot_map = slot + p.g.grid_off[s];
+      a.logits = reinterpret_cast<const float*>(ws + p.logits);
+      a.n_cls = ncls;
+      for (int k = 0; k < ncls; ++k) {
+        a.cls_ids[k] = cls[k];
+        a.labels[k] = out->labels[cls[k]];
+        a.out_logits[k] = out->logits[cls[k]];
+      }
+      a.mode = c.stitch_mode;
+      a.tissue = c.tissue_and ? ws + p.mask : nullptr;
+      a.th = p.g.th; a.tw = p.g.tw;
+      a.coverage = out->coverage[s];
+      a.argmax = out->argmax[s];
+      double px = (double)a.oh * a.ow;
+      stitch_bytes += (double)n_s * ncls * c.patch * c.patch * 4.0;
+      for (int k = 0; k < ncls; ++k) stitch_bytes += px * ((a.labels[k] ? 1 : 0) + (a.out_logits[k] ? 4 : 0));
+      stitch_bytes += px * ((a.coverage ? 2 : 0) + (a.argmax ? 1 : 0));
+      {
+        Rec rr(ctx, st, 1, 600 + s);
+        OMNI_CU(launch_stitch(a, st), "stitch");
+        ctx->launches++;
+      }
+    }
+    toff += n_s;
+  }
+  return OMNI_OK;
+}
+
 omni_status check_ws(omni_ctx* ctx, void* ws, uint64_t bytes, uint64_t need) {
   if (!ws) return fail(ctx, OMNI_EINVAL, "null workspace");
   if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(ctx, OMNI_EINVAL, "workspace must be 256-byte aligned");
@@ -723,53 +835,59 @@ omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int
   OMNI_CU(cudaMemcpy(&herr, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
   if (herr) return fail(ctx, OMNI_ETIMEOUT, "a device-side wait gave up in an earlier call");
 
-  const int32_t* tiles = reinterpret_cast<const int32_t*>(ws + p.tiles);
-  const int32_t* slot = reinterpret_cast<const int32_t*>(ws + p.slot);
-  int toff = 0;
+  // ---------------------------------------------------------------- network + stitch
+  std::vector<uint64_t> key = {reinterpret_cast<uint64_t>(rgb), (uint64_t)H, (uint64_t)W, (uint64_t)stride,
+                               scale_mask, class_mask, reinterpret_cast<uint64_t>(ws_),
+                               reinterpret_cast<uint64_t>(st)};
+  for (int s = 0; s <= c.n_scales; ++s) key.push_back((uint64_t)ctx->h_counts[s]);
+  for (int k = 0; k < OMNI_MAX_CLASSES; ++k) {
+    key.push_back(reinterpret_cast<uint64_t>(out->labels[k]));
+    key.push_back(reinterpret_cast<uint64_t>(out->logits[k]));
+  }
+  for (int s = 0; s < OMNI_MAX_SCALES; ++s) {
+    key.push_back(reinterpret_cast<uint64_t>(out->coverage[s]));
+    key.push_back(reinterpret_cast<uint64_t>(out->argmax[s]));
+  }
   double stitch_bytes = 0;
-  for (int s = 0; s < c.n_scales; ++s) {
-    const int n_s = ctx->h_counts[1 + s];
-    int cls[OMNI_MAX_CLASSES], ncls = 0;
-    for (int k = 0; k < c.n_classes; ++k)
-      if (c.class_scale[k] == s && (class_mask >> k & 1u)) cls[ncls++] = k;
-    const bool want = (scale_mask >> s & 1u) && ncls > 0;
-    if (want) {
-      for (int start = 0; start < n_s; start += c.max_batch) {
-        int nb = std::min(c.max_batch, n_s - start);
-        r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], tiles + 3 * (toff + start), nb, start, ncls, cls, st);
-        if (r) return r;
-      }
-      ctx->tiles_done += n_s;
-      const int f = c.factors[s];
-      StitchArgs a{};
-      a.hs = p.g.Hp / f; a.ws = p.g.Wp / f;
-      a.oy0 = c.pad_lead / f; a.ox0 = c.pad_lead / f;
-      a.oh = (H + f - 1) / f; a.ow = (W + f - 1) / f;
-      a.P = c.patch; a.S = c.stride; a.gh = p.g.gh[s]; a.gw = p.g.gw[s]; a.f = f;
-      a.slot_map = slot + p.g.grid_off[s];
-      a.logits = reinterpret_cast<const float*>(ws + p.logits);
-      a.n_cls = ncls;
-      for (int k = 0; k < ncls; ++k) {
-        a.cls_ids[k] = cls[k];
-        a.labels[k] = out->labels[cls[k]];
-        a.out_logits[k] = out->logits[cls[k]];
-      }
-      a.mode = c.stitch_mode;
-      a.tissue = c.tissue_and ? ws + p.mask : nullptr;
-      a.th = p.g.th; a.tw = p.g.tw;
-      a.coverage = out->coverage[s];
-      a.argmax = out->argmax[s];
-      double px = (double)a.oh * a.ow;
-      stitch_bytes += (double)n_s * ncls * c.patch * c.patch * 4.0;
-      for (int k = 0; k < ncls; ++k) stitch_bytes += px * ((a.labels[k] ? 1 : 0) + (a.out_logits[k] ? 4 : 0));
-      stitch_bytes += px * ((a.coverage ? 2 : 0) + (a.argmax ? 1 : 0));
-      {
-        Rec rr(ctx, st, 1, 600 + s);
-        OMNI_CU(launch_stitch(a, st), "stitch");
-        ctx->launches++;
-      }
+  const bool use_graph = ctx->graphs && !ctx->timing;
+  if (use_graph && ctx->graph_exec && key == ctx->graph_key) {
+    OMNI_CU(cudaGraphLaunch(ctx->graph_exec, st), "graph launch");
+    ctx->launches += ctx->graph_launches;
+    ctx->tiles_done = ctx->graph_tiles;
+    stitch_bytes = ctx->graph_stitch_bytes;
+  } else if (use_graph && key == ctx->last_key) {
+    // second call with the same geometry and buffers: capture and replay from now on
+    if (ctx->graph_exec) {
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
     }
-    toff += n_s;
+    const int64_t before = ctx->launches;
+    OMNI_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    ctx->capturing = true;
+    r = run_network(ctx, c, p, ws, pr, out, H, W, scale_mask, class_mask, st, stitch_bytes);
+    ctx->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (r) {
+      if (graph) cudaGraphDestroy(graph);
+      return r;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "end capture");
+    const cudaError_t ie = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      ctx->graph_exec = nullptr;
+      return cuda_fail(ctx, ie, "graph instantiate");
+    }
+    ctx->graph_key = key;
+    ctx->graph_launches = ctx->launches - before;
+    ctx->graph_tiles = ctx->tiles_done;
+    ctx->graph_stitch_bytes = stitch_bytes;
+    OMNI_CU(cudaGraphLaunch(ctx->graph_exec, st), "graph launch");
+  } else {
+    ctx->last_key = key;
+    r = run_network(ctx, c, p, ws, pr, out, H, W, scale_mask, class_mask, st, stitch_bytes);
+    if (r) return r;
   }
   ctx->work[0] += (double)ctx->tiles_done * (double)p.flops_per_tile;
   ctx->work[1] += stitch_bytes;
@@ -934,6 +1052,38 @@ omni_status omni_get_timing(omni_ctx* ctx, int32_t kind, double* ms, int64_t* la
 }
 
 int64_t omni_last_launch_count(const omni_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled) {
+  if (!ctx) return OMNI_EINVAL;
+  ctx->autotune = enabled != 0;
+  return OMNI_OK;
+}
+
+omni_status omni_set_graphs(omni_ctx* ctx, int32_t enabled) {
+  if (!ctx) return OMNI_EINVAL;
+  ctx->graphs = enabled != 0;
+  if (!ctx->graphs && ctx->graph_exec) {
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+  }
+  ctx->last_key.clear();
+  ctx->graph_key.clear();
+  return OMNI_OK;
+}
+
+int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows) {
+  if (!ctx) return -1;
+  int32_t n = 0;
+  for (const auto& kv : ctx->tuned) {
+    if (rows && n < max_rows) {
+      int32_t* r = rows + 10 * n;
+      for (int q = 0; q < 6; ++q) r[q] = kv.first[q];
+      r[6] = kv.second.kind; r[7] = kv.second.bn; r[8] = kv.second.ck; r[9] = kv.second.stages;
+    }
+    ++n;
+  }
+  return n;
+}
 
 int64_t omni_get_launch_times(omni_ctx* ctx, int64_t max, double* ms, int32_t* kinds, int32_t* tags,
                               double* work) {

@@ -176,3 +176,40 @@ def test_needle_full_slide_bf16_against_fp32_and_oracle(api):
         print("needle window class %d fp32 max|dL| %.2e bf16 agree %.5f" % (c, float(np.abs(g32 - o).max()), ag))
         assert ag >= 0.999
     seg.close()
+
+
+def test_graph_replay_is_bit_identical_and_autotune_agrees(api):
+    """CUDA-graph replay of the post-tiling launch chain reproduces the eager
+    results exactly; autotuned kernel choices agree with the default ones
+    within BF16 rounding."""
+    from paper_2305_14566_gb300 import _lib as L
+    w = synth.NEEDLE.with_(H=2048, W=4096, P=256, S=128, median_k=5, max_batch=16)
+    spec = synth.make_spec(2048, 4096, 43, 0.5, "cores", 3)
+    rgb = api.synth_slide(spec)
+    blob = synth.gen_weights(w)
+    seg = api.Segmenter(w, blob, precision=L.BF16)
+    ref = seg.segment(rgb, logits=True)
+    ref = {k: {c: t.clone() for c, t in d.items()} for k, d in ref.items()}
+    seg.set_graphs(True)
+    out = None
+    for call in range(3):            # eager (records the key), capture + launch, replay
+        out = seg.segment(rgb, logits=True, out=out)
+        torch.cuda.synchronize()
+        for c in ref["logits"]:
+            assert torch.equal(out["logits"][c], ref["logits"][c]), (call, c)
+            assert torch.equal(out["labels"][c], ref["labels"][c]), (call, c)
+    n_eager = seg.launch_count()
+    assert n_eager > 0
+    seg.close()
+    tuned = api.Segmenter(w, blob, precision=L.BF16)
+    tuned.set_autotune(True)
+    t_out = tuned.segment(rgb, logits=True)
+    torch.cuda.synchronize()
+    rows = tuned.tuned()
+    assert len(rows) >= 10
+    for c in ref["logits"]:
+        d = (t_out["logits"][c] - ref["logits"][c]).abs().max().item()
+        agree = (t_out["labels"][c] == ref["labels"][c]).float().mean().item()
+        print("autotune class %d max|dL| %.3e agree %.6f" % (c, d, agree))
+        assert d < 0.25 and agree >= 0.999
+    tuned.close()
