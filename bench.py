@@ -351,16 +351,19 @@ def main():
 
     # the same steps replayed from a captured CUDA graph (library timing off)
     seg.set_graphs(True)
-    for _ in range(2):
-        seg.segment(rgb, out=out)          # second call captures
-    barrier()
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    g0.record()
-    for _ in range(args.steps):
-        seg.segment(rgb, out=out)
-    g1.record()
-    barrier()
+    gstream = torch.cuda.Stream()          # the legacy default stream cannot be captured
+    gstream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(gstream):
+        for _ in range(2):
+            seg.segment(rgb, out=out)      # second call captures
+        barrier()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record()
+        for _ in range(args.steps):
+            seg.segment(rgb, out=out)
+        g1.record()
+        barrier()
     graph = {"value": mpx * world / (g0.elapsed_time(g1) / args.steps / 1e3), "unit": "Mpx/s",
              "ms_per_step": g0.elapsed_time(g1) / args.steps}
     seg.set_graphs(False)

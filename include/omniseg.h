@@ -241,7 +241,8 @@ int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows);
  * the second call that sees the same slide pointer, size, scale/class masks,
  * workspace, stream, output buffers and foreground tile counts, and replays
  * that graph on later such calls.  Tiling still runs eagerly each call (its
- * counts decide the key).  Ignored while timing is enabled. */
+ * counts decide the key).  Ignored while timing is enabled and on the legacy
+ * default stream (NULL), which cannot be captured: pass a created stream. */
 omni_status omni_set_graphs(omni_ctx* ctx, int32_t enabled);
 
 /* Per-launch device times (ms) of the current timing record, with each

@@ -179,7 +179,8 @@ struct TCCfg {
   static constexpr int kBufCols = RES ? 2 * BN : BN;     // TMEM columns per accumulator buffer
   static constexpr int kTmemCols = 2 * kBufCols;          // double buffered
   static constexpr int kSW = CK * 2;                      // row bytes = swizzle span
-  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*align*/;
+  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*align*/ +
+                                  2 * 512 * 4 /*gamma, beta*/;
 };
 
 template <int BN, int CK, bool RES>
@@ -201,8 +202,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   uint64_t* drain = bars + 2 * ST + 4;   // [1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * ST + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* sg = reinterpret_cast<float*>(smem + (size_t)ST * Cfg::kStageBytes + 1024);   // gamma[cout]
+  float* sb = sg + 512;                                                                // beta[cout]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < p.cout; i += blockDim.x) {
+    sg[i] = p.gamma[i];
+    sb[i] = p.beta[i];
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
@@ -271,6 +278,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(BN);
+      const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
+      const uint64_t b_desc0 = smem_desc(smem_u32(sB), Cfg::kSW);
       int it = 0, tcount = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
@@ -289,8 +298,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             break;
           }
           tc_fence_after();
-          const uint64_t ad = smem_desc(smem_u32(sA + (size_t)s * Cfg::kABytes), Cfg::kSW);
-          const uint64_t bd = smem_desc(smem_u32(sB + (size_t)s * Cfg::kBBytes), Cfg::kSW);
+          const uint64_t ad = a_desc0 + (uint64_t)(s * (Cfg::kABytes >> 4));
+          const uint64_t bd = b_desc0 + (uint64_t)(s * (Cfg::kBBytes >> 4));
           const bool second = RES && k >= p.k_main;
           const uint32_t d = second ? acc1 : acc0;
           const int kfirst = second ? p.k_main : 0;
@@ -345,7 +354,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             const int n = n0 + c + j + u;
-            float z = fmaf(__ldg(p.gamma + n), a[j + u], __ldg(p.beta + n));
+            float z = fmaf(sg[n], a[j + u], sb[n]);
             if constexpr (RES) z += r[j + u];
             if (p.res_mode == RES_RGB)
               z += fmaf(v0, __ldg(p.wp_rgb + n),
@@ -508,6 +517,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(BN);
+      const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
+      const uint64_t b_desc0 = smem_desc(smem_u32(sW), Cfg::kSW);
+      const uint64_t b_tap_step = (uint64_t)(hp.cpt * (Cfg::kWTileBytes >> 4));
       bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, p.err);
       int it = 0, tcount = 0;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
@@ -526,23 +538,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(sA + (size_t)s * Cfg::kStageBytes);
+          // descriptor start addresses advance in 16-byte units: add (bytes >> 4)
+          const uint64_t ad = a_desc0 + (uint64_t)((s * Cfg::kStageBytes) >> 4);
           if (k < p.k_main) {
-#pragma unroll 1
+            const uint64_t bd = b_desc0 + (uint64_t)(k * (Cfg::kWTileBytes >> 4));
+            const uint32_t acc_first = k > 0 ? 1u : 0u;
+#pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
-              const int dy = tap / 3, dx = tap % 3;
-              const uint64_t ad = smem_desc(st + dx * Cfg::kBoxBytes + dy * kHTW * CK * 2, Cfg::kSW);
-              const uint64_t bd =
-                  smem_desc(smem_u32(sW + (size_t)(tap * hp.cpt + k) * Cfg::kWTileBytes), Cfg::kSW);
+              const uint64_t at = ad + (uint64_t)(((tap % 3) * Cfg::kBoxBytes + (tap / 3) * kHTW * CK * 2) >> 4);
+              const uint64_t bt = bd + (uint64_t)tap * b_tap_step;
 #pragma unroll
               for (int kk = 0; kk < CK / 16; ++kk)
-                mma_bf16(acc0, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                         (k > 0 || tap > 0 || kk > 0) ? 1u : 0u);
+                mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc,
+                         (tap > 0 || kk > 0) ? 1u : acc_first);
             }
           } else if (RES) {
-            const uint64_t ad = smem_desc(st, Cfg::kSW);
-            const uint64_t bd = smem_desc(
-                smem_u32(sW + (size_t)(9 * hp.cpt + (k - p.k_main)) * Cfg::kWTileBytes), Cfg::kSW);
+            const uint64_t bd =
+                b_desc0 + (uint64_t)((9 * hp.cpt + (k - p.k_main)) * (Cfg::kWTileBytes >> 4));
 #pragma unroll
             for (int kk = 0; kk < CK / 16; ++kk)
               mma_bf16(acc1, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
@@ -820,6 +832,7 @@ int pick_bn(int cout, bool res) {
 
 bool conv_tc_supported(int R, int cin, int cout, int cr) {
   if (cin % 32 == 0 && cr % 32 == 0 && halo_ok(R, cout, cin, cr)) return true;
+  if (cout > 512) return false;
   if (!(R == 16 || R == 32 || R == 64 || (R >= 128 && R % 128 == 0))) return false;
   if (cin % 32 || cr % 32 || cout % 32) return false;
   const int bn = pick_bn(cout, cr > 0);
@@ -840,7 +853,7 @@ cudaError_t check_tc_args(const ConvArgs& a, int cr) {
 
 bool pertap_ok(int R, int cin, int cout, int cr, int bn, int ck) {
   if (!(R == 16 || R == 32 || R == 64 || (R >= 128 && R % 128 == 0))) return false;
-  if (cin % ck || cr % ck || bn > cout || cout % bn) return false;
+  if (cin % ck || cr % ck || bn > cout || cout % bn || cout > 512) return false;
   if (cr > 0 && bn > 128) return false;
   return bn == 32 || bn == 64 || bn == 128 || bn == 256;
 }

@@ -787,6 +787,7 @@ extern "C" {
 
 omni_status omni_tile_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int32_t W, int64_t stride,
                             void* ws_, uint64_t ws_bytes, const omni_tile_list* out, void* stream) {
+  (void)cudaGetLastError();   // errors of earlier, unrelated calls are not ours to report
   if (!ctx || !rgb || !out || !out->tiles || !out->counts) return fail(ctx, OMNI_EINVAL, "null argument");
   if (stride < (int64_t)W * 3) return fail(ctx, OMNI_EINVAL, "row_stride < 3 W");
   Plan p;
@@ -813,6 +814,7 @@ omni_status omni_tile_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int32_
 omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int32_t W, int64_t stride,
                                uint32_t scale_mask, uint32_t class_mask, void* ws_, uint64_t ws_bytes,
                                const omni_outputs* out, void* stream) {
+  (void)cudaGetLastError();   // errors of earlier, unrelated calls are not ours to report
   if (!ctx || !rgb || !out) return fail(ctx, OMNI_EINVAL, "null argument");
   if (!ctx->have_weights) return fail(ctx, OMNI_ESTATE, "omni_load_weights has not been called");
   if (stride < (int64_t)W * 3) return fail(ctx, OMNI_EINVAL, "row_stride < 3 W");
@@ -849,7 +851,9 @@ omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int
     key.push_back(reinterpret_cast<uint64_t>(out->argmax[s]));
   }
   double stitch_bytes = 0;
-  const bool use_graph = ctx->graphs && !ctx->timing;
+  // the legacy default stream cannot be captured: such calls run eagerly
+  const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+  const bool use_graph = ctx->graphs && !ctx->timing && capturable;
   if (use_graph && ctx->graph_exec && key == ctx->graph_key) {
     OMNI_CU(cudaGraphLaunch(ctx->graph_exec, st), "graph launch");
     ctx->launches += ctx->graph_launches;
@@ -929,6 +933,7 @@ omni_status omni_segment_slide_host(omni_ctx* ctx, const uint8_t* rgb_host, int3
 omni_status omni_synth_slide(const int64_t* ell, int32_t n_ell, uint64_t seed, int32_t slide_w, int32_t y0,
                              int32_t x0, int32_t h, int32_t w, uint8_t* out, int64_t stride, void* stream) {
   if ((!ell && n_ell) || !out || n_ell < 0 || n_ell > kMaxEll || stride < (int64_t)w * 3) return OMNI_EINVAL;
+  (void)cudaGetLastError();
   for (int k = 0; k < n_ell; ++k)
     if (ell[k * 6 + 2] <= 0 || ell[k * 6 + 3] <= 0) return OMNI_EINVAL;
   cudaError_t e = launch_synth(ell, n_ell, seed, slide_w, y0, x0, h, w, out, stride,
