@@ -10,11 +10,13 @@
 // window does, and TMA's zero fill supplies the convolution's zero padding.
 // B tiles (BN x CK) are TMA loads of the K-major BF16 weights.
 //
-// Persistent, warp-specialised CTA (192 threads):
+// Persistent, warp-specialised CTA (320 threads):
 //   warp 0      TMA producer (one elected lane), owns the TMEM allocation
 //   warp 1      MMA issuer (one lane): tcgen05.mma M=128 x N=BN x K=16,
 //               FP32 accumulators in TMEM, double buffered across tiles
-//   warps 2..5  epilogue: tcgen05.ld -> norm, residual, ReLU -> BF16 stores
+//   warps 2..9  epilogue: tcgen05.ld -> norm, residual, ReLU -> BF16 stores;
+//               warps w and w+4 share TMEM lane quarter w%4 and split the
+//               columns, so each SM sub-partition interleaves two of them
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
 // records kErrTimeout in the caller's status word, drains its own copies and
 // MMAs (again bounded), frees TMEM and returns.
@@ -26,7 +28,8 @@ namespace omni {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kThreadsTC = 192;
+constexpr int kEpiWarps = 8;                         // two epilogue warpgroups
+constexpr int kThreadsTC = 64 + 32 * kEpiWarps;      // producer warp, MMA warp, epilogue
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 constexpr int kSmemBudget = 200 * 1024;
 
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
-      mbar_init(smem_u32(&tempty[b]), 4);
+      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
     }
     mbar_init(smem_u32(drain), 1);
     *abort_flag = 0;
@@ -320,6 +323,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // ------------------------------------------------------------------ epilogue
     const int q = warp & 3;                  // TMEM lane quarter this warp may access
     const int row = q * 32 + lane;
+    const int c_beg = ((warp - 2) >> 2) * (BN / 2), c_end = c_beg + BN / 2;
     int tcount = 0;
     for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
       const int buf = tcount & 1, use = tcount >> 1;
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co + n0;
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 16) {
+      for (int c = c_beg; c < c_end; c += 16) {
         float a[16], r[16];
         tmem_ld16(tb + c, a);
         if constexpr (RES) tmem_ld16(tb + BN + c, r);
@@ -405,7 +409,8 @@ struct HaloCfg {
 };
 
 struct HaloParams {
-  TCParams t;
+  TCParams t;                       // t.k_res = stages of the projection segment (3 chunks each)
+  int res_chunks;                   // channel chunks of the projection input
   int stages, n_wtiles, cpt;        // cpt = channel chunks of the main input
   int tiles_per_img, tiles_w;       // (R/8)*(R/16), R/16
 };
@@ -452,7 +457,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
-      mbar_init(smem_u32(&tempty[b]), 4);
+      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
     }
     mbar_init(smem_u32(drain), 1);
     mbar_init(smem_u32(wbar), 1);
@@ -483,7 +488,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int tap = t / hp.cpt, c = t % hp.cpt;
         tma_load_2d(smem_u32(sW + (size_t)t * Cfg::kWTileBytes), &mapB, wb, tap * p.cin + c * CK, 0);
       }
-      for (int r = 0; r < p.k_res; ++r)
+      for (int r = 0; r < hp.res_chunks; ++r)
         tma_load_2d(smem_u32(sW + (size_t)(9 * hp.cpt + r) * Cfg::kWTileBytes), &mapB2, wb, r * CK, 0);
       int it = 0;
       bool ok = true;
@@ -504,8 +509,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             for (int dx = 0; dx < 3; ++dx)
               tma_load_4d(smem_u32(st + dx * Cfg::kBoxBytes), &mapA, fb, c0, w0 + dx - 1, h0 - 1, img);
           } else {
-            mbar_expect_tx(fb, kBM * CK * 2);
-            tma_load_4d(smem_u32(st), &mapA2, fb, (k - p.k_main) * CK, w0, h0, img);
+            // up to three projection chunks per stage, one per box slot
+            const int c0 = (k - p.k_main) * 3, nbx = min(3, hp.res_chunks - c0);
+            mbar_expect_tx(fb, (uint32_t)(nbx * kBM * CK * 2));
+            for (int j = 0; j < nbx; ++j)
+              tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA2, fb, (c0 + j) * CK, w0, h0, img);
           }
         }
       }
@@ -553,12 +561,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                          (tap > 0 || kk > 0) ? 1u : acc_first);
             }
           } else if (RES) {
-            const uint64_t bd =
-                b_desc0 + (uint64_t)((9 * hp.cpt + (k - p.k_main)) * (Cfg::kWTileBytes >> 4));
+            const int c0 = (k - p.k_main) * 3, nbx = min(3, hp.res_chunks - c0);
+            for (int j = 0; j < nbx; ++j) {
+              const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
+              const uint64_t bd = b_desc0 + (uint64_t)((9 * hp.cpt + c0 + j) * (Cfg::kWTileBytes >> 4));
 #pragma unroll
-            for (int kk = 0; kk < CK / 16; ++kk)
-              mma_bf16(acc1, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                       (k > p.k_main || kk > 0) ? 1u : 0u);
+              for (int kk = 0; kk < CK / 16; ++kk)
+                mma_bf16(acc1, aj + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                         (c0 + j > 0 || kk > 0) ? 1u : 0u);
+            }
           }
           mma_commit(smem_u32(&empty[s]));
         }
@@ -572,6 +583,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // ------------------------------------------------------------------ epilogue
     const int q = warp & 3;
     const int row = q * 32 + lane;
+    const int c_beg = ((warp - 2) >> 2) * (BN / 2), c_end = c_beg + BN / 2;
     int tcount = 0;
     for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
       const int buf = tcount & 1, use = tcount >> 1;
@@ -593,7 +605,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 16) {
+      for (int c = c_beg; c < c_end; c += 16) {
         float a[16], r[16];
         tmem_ld16(tb + c, a);
         if constexpr (RES) tmem_ld16(tb + BN + c, r);
@@ -795,9 +807,10 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
   p.n_tiles_n = 1;
   p.n_tiles = p.n_tiles_m;
   p.k_main = a.cin / CK;
-  p.k_res = RES ? a.cr / CK : 0;
+  hp.res_chunks = RES ? a.cr / CK : 0;
+  p.k_res = (hp.res_chunks + 2) / 3;
   hp.cpt = a.cin / CK;
-  hp.n_wtiles = 9 * hp.cpt + p.k_res;
+  hp.n_wtiles = 9 * hp.cpt + hp.res_chunks;
   hp.stages = stages;
   p.gamma = a.w.gamma;
   p.beta = a.w.beta;
