@@ -92,6 +92,24 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value: float, device="cpu") -> float:
+    """Largest value over all ranks of the current process group (or the value
+    itself without one): the step time of a multi-GPU run is its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(mpx_per_rank: float, ms_step_max: float, world: int) -> float:
+    """Whole-job throughput: every rank segments its own slide (weak scaling),
+    so the job processes world * mpx_per_rank per slowest-rank step."""
+    return mpx_per_rank * world / (ms_step_max / 1e3)
+
+
 def tag_name(t: int) -> str:
     if t < 100:
         return f"conv enc{t // 10}.{t % 10 + 1}"
@@ -324,13 +342,9 @@ def main():
     st_ms, _, st_bytes = seg.timing(1)
     ms_l, kinds_l, tags_l, work_l = seg.launch_times()
     seg.set_timing(False)
-    ms_step = t0.elapsed_time(t1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, device=dev)
     mpx = WORK.H * WORK.W / 1e6
-    value = mpx * world / (ms_step / 1e3)
+    value = whole_job_value(mpx, ms_step, world)
     breakdown = summarize(ms_l, tags_l, work_l, args.steps)
 
     pk, src = peaks()
