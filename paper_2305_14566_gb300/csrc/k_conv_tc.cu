@@ -643,6 +643,268 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                  : "memory");
 }
 
+// ------------------------------------------------------------------ dx-in-N variant
+// Pixels stay on M (128 = 8 rows x 16 columns), but the three horizontal taps
+// move to N: B stacks the weights of dx = 0, 1, 2 (N = 3 * cout), so one MMA of
+// tap row dy computes D[p][(dx, co)] for the unshifted input rows.  A is a
+// single box of 10 x 16 input pixels per channel chunk, whose three dy views
+// are 16-row (whole swizzle atom) offsets.  The output at column c of a tile
+// row is D0[c-1] + D1[c] + D2[c+1]: a horizontal pixel shift is a neighbouring
+// TMEM lane inside a 16-lane row group, so the epilogue sums the three dx
+// blocks with +-1 lane warp shuffles.  Tiles advance by 14 columns and keep
+// one halo column on each side (lanes 0 and 15 of each row group write nothing).
+constexpr int kXTW = 14;                       // valid output columns per tile row
+
+template <int CO, int CK, bool RES>
+struct DxnCfg {
+  static constexpr int kN = 3 * CO;                        // MMA N (dx blocks)
+  static constexpr int kBoxBytes = kHBoxPix * CK * 2;      // 10 x 16 pixels
+  static constexpr int kStageBytes = kBoxBytes;            // one box per stage
+  static constexpr int kWTileBytes = kN * CK * 2;          // 3 dx slices of cout x CK
+  static constexpr int kRTileBytes = CO * CK * 2;          // projection weights
+  static constexpr int kBufCols = RES ? kN + CO : kN;
+  static constexpr int kTmemCols = 2 * kBufCols <= 64 ? 64 : (2 * kBufCols <= 128 ? 128 : (2 * kBufCols <= 256 ? 256 : 512));
+  static constexpr int kSW = CK * 2;
+};
+
+struct DxnParams {
+  TCParams t;
+  int res_chunks, stages, cpt;
+  int tiles_per_img, tiles_w;      // (R/8) * ceil(R/14), ceil(R/14)
+  int wbytes;                      // resident weight bytes (main + projection)
+};
+
+template <int CO, int CK, bool RES>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_conv_tc_dxn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
+                  DxnParams hp) {
+  using Cfg = DxnCfg<CO, CK, RES>;
+  const TCParams& p = hp.t;
+  const int ST = hp.stages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sW = smem;                                              // [3 dy][cpt][3 cout x CK]
+  uint8_t* sR = sW + (size_t)9 * hp.cpt * Cfg::kRTileBytes;        // [res_chunks][cout x CK]
+  uint8_t* sA = smem + hp.wbytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * Cfg::kStageBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + ST;
+  uint64_t* tfull = bars + 2 * ST;
+  uint64_t* tempty = bars + 2 * ST + 2;
+  uint64_t* drain = bars + 2 * ST + 4;
+  uint64_t* wbar = bars + 2 * ST + 5;
+  float* sg = reinterpret_cast<float*>(bars + 2 * ST + 6);
+  float* sb = sg + CO;
+  float* swp = sb + CO;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(swp + 3 * CO);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < CO; i += blockDim.x) {
+    sg[i] = p.gamma[i];
+    sb[i] = p.beta[i];
+    if (p.res_mode == RES_RGB) {
+      swp[i] = p.wp_rgb[i];
+      swp[CO + i] = p.wp_rgb[p.cout + i];
+      swp[2 * CO + i] = p.wp_rgb[2 * p.cout + i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+    }
+    mbar_init(smem_u32(drain), 1);
+    mbar_init(smem_u32(wbar), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int k_total = p.k_main + p.k_res;
+  const int RR = p.R * p.R;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- producer
+      const uint32_t wb = smem_u32(wbar);
+      mbar_expect_tx(wb, (uint32_t)hp.wbytes);
+      for (int dy = 0; dy < 3; ++dy)
+        for (int c = 0; c < hp.cpt; ++c)
+          for (int dx = 0; dx < 3; ++dx)
+            tma_load_2d(smem_u32(sW + (size_t)(dy * hp.cpt + c) * Cfg::kWTileBytes + dx * Cfg::kRTileBytes),
+                        &mapB, wb, (dy * 3 + dx) * p.cin + c * CK, 0);
+      for (int r = 0; r < hp.res_chunks; ++r)
+        tma_load_2d(smem_u32(sR + (size_t)r * Cfg::kRTileBytes), &mapB2, wb, r * CK, 0);
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+        const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
+        const int h0 = (rem / hp.tiles_w) * kHTH, w0 = (rem % hp.tiles_w) * kXTW;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (it >= ST && !mbar_wait(smem_u32(&empty[s]), ((it / ST) & 1) ^ 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full[s]);
+          uint8_t* st = sA + (size_t)s * Cfg::kStageBytes;
+          if (k < p.k_main) {
+            mbar_expect_tx(fb, Cfg::kBoxBytes);
+            tma_load_4d(smem_u32(st), &mapA, fb, k * CK, w0 - 1, h0 - 1, img);
+          } else {
+            mbar_expect_tx(fb, kBM * CK * 2);
+            tma_load_4d(smem_u32(st), &mapA2, fb, (k - p.k_main) * CK, w0 - 1, h0, img);
+          }
+        }
+      }
+      const int last = it;
+      for (int q = last - 1; q >= 0 && q >= last - ST; --q) mbar_drain(smem_u32(&full[q % ST]), (q / ST) & 1);
+      mbar_drain(wb, 0);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc_n = idesc_bf16(Cfg::kN);
+      constexpr uint32_t idesc_r = idesc_bf16(CO);
+      const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
+      const uint64_t w_desc0 = smem_desc(smem_u32(sW), Cfg::kSW);
+      const uint64_t r_desc0 = smem_desc(smem_u32(sR), Cfg::kSW);
+      const uint64_t dy_step = (uint64_t)(hp.cpt * (Cfg::kWTileBytes >> 4));
+      bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, p.err);
+      int it = 0, tcount = 0;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
+        const int buf = tcount & 1, use = tcount >> 1;
+        if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
+        const uint32_t acc1 = acc0 + Cfg::kN;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (!mbar_wait(smem_u32(&full[s]), (it / ST) & 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = a_desc0 + (uint64_t)((s * Cfg::kStageBytes) >> 4);
+          if (k < p.k_main) {
+            const uint64_t bk = w_desc0 + (uint64_t)(k * (Cfg::kWTileBytes >> 4));
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) {
+              const uint64_t at = ad + (uint64_t)((dy * kHTW * CK * 2) >> 4);
+              const uint64_t bt = bk + (uint64_t)dy * dy_step;
+#pragma unroll
+              for (int kk = 0; kk < CK / 16; ++kk)
+                mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc_n,
+                         (k > 0 || dy > 0 || kk > 0) ? 1u : 0u);
+            }
+          } else if (RES) {
+            const uint64_t bd = r_desc0 + (uint64_t)((k - p.k_main) * (Cfg::kRTileBytes >> 4));
+#pragma unroll
+            for (int kk = 0; kk < CK / 16; ++kk)
+              mma_bf16(acc1, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc_r,
+                       (k > p.k_main || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&tfull[buf]));
+      }
+      mma_commit(smem_u32(drain));
+      mbar_drain(smem_u32(drain), 0);
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    // warps w and w+4 share lane quarter w%4 and split the output channels
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int col = row % kHTW;                        // column inside the 16-lane row group
+    const int co_beg = ((warp - 2) >> 2) * (CO / 2), co_end = co_beg + CO / 2;
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
+      const int buf = tcount & 1, use = tcount >> 1;
+      const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
+      const int hh = (rem / hp.tiles_w) * kHTH + row / kHTW;
+      const int ww = (rem % hp.tiles_w) * kXTW + col - 1;           // this lane's pixel column
+      const bool writes = col >= 1 && col <= kXTW && ww < p.R;
+      const long long m = (long long)img * RR + (long long)hh * p.R + (ww < 0 ? 0 : ww);
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      if (p.res_mode == RES_RGB && writes) {
+        const uint8_t* px = p.canvas + (long long)(p.tiles3[3 * img + 1] + hh) * p.canvas_stride +
+                            (long long)(p.tiles3[3 * img + 2] + ww) * 3;
+        v0 = norm_u8(px[0]);
+        v1 = norm_u8(px[1]);
+        v2 = norm_u8(px[2]);
+      }
+      __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
+#pragma unroll 1
+      for (int c = co_beg; c < co_end; c += 16) {
+        float d0[16], d1[16], d2[16], r[16];
+        tmem_ld16(tb + c, d0);                   // dx = 0 block
+        tmem_ld16(tb + CO + c, d1);              // dx = 1 block
+        tmem_ld16(tb + 2 * CO + c, d2);          // dx = 2 block
+        if constexpr (RES) tmem_ld16(tb + Cfg::kN + c, r);
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float o[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int n = c + j + u;
+            // lane-1 holds the left neighbour's dx=0 sum, lane+1 the right's dx=2 sum
+            const float left = __shfl_up_sync(0xffffffffu, d0[j + u], 1);
+            const float right = __shfl_down_sync(0xffffffffu, d2[j + u], 1);
+            float z = fmaf(sg[n], left + d1[j + u] + right, sb[n]);
+            if constexpr (RES) z += r[j + u];
+            if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[CO + n], v2 * swp[2 * CO + n]));
+            o[u] = fmaxf(z, 0.f);
+          }
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(o[0], o[1]);
+          packed[j / 2] = *reinterpret_cast<uint32_t*>(&h2);
+        }
+        if (writes) {
+          uint4* dst = reinterpret_cast<uint4*>(out + c);
+          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+}
+
 // ------------------------------------------------------------------ host side
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
@@ -836,6 +1098,71 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
   return cudaGetLastError();
 }
 
+// dx-in-N variant: resident weights + one 10 x 16 box per stage
+int dxn_wbytes(int cin, int cout, int cr, int ck) { return (9 * (cin / ck) + cr / ck) * cout * ck * 2; }
+int dxn_stages(int cin, int cout, int cr, int ck) {
+  if (cin % ck || cr % ck) return 0;
+  const long long st = (kHaloSmemMax - (long long)dxn_wbytes(cin, cout, cr, ck) - kHaloSmemExtra) /
+                       ((long long)kHBoxPix * ck * 2);
+  return st < 2 ? 0 : (int)(st > 12 ? 12 : st);
+}
+bool dxn_ok(int R, int cout, int cin, int cr) {
+  if (R < 16 || R % kHTH || (cout != 32 && cout != 64)) return false;
+  return dxn_stages(cin, cout, cr, 32) >= 2;
+}
+
+template <int CO, int CK, bool RES>
+cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
+  using Cfg = DxnCfg<CO, CK, RES>;
+  CUtensorMap mA, mB, mA2, mB2;
+  if (!map_act_box(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, kHTW, kHTH + 2)) return cudaErrorInvalidValue;
+  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, CO, CK)) return cudaErrorInvalidValue;
+  if (RES) {
+    if (!map_act_box(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK, kHTW, kHTH)) return cudaErrorInvalidValue;
+    if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, CO, CK)) return cudaErrorInvalidValue;
+  } else {
+    mA2 = mA;
+    mB2 = mB;
+  }
+  DxnParams hp{};
+  TCParams& p = hp.t;
+  p.B = a.B; p.R = a.R; p.cin = a.cin; p.cout = a.cout; p.cr = RES ? a.cr : 0;
+  p.res_mode = a.res_mode;
+  hp.tiles_w = (a.R + kXTW - 1) / kXTW;
+  hp.tiles_per_img = (a.R / kHTH) * hp.tiles_w;
+  p.n_tiles_m = a.B * hp.tiles_per_img;
+  p.n_tiles_n = 1;
+  p.n_tiles = p.n_tiles_m;
+  p.k_main = a.cin / CK;
+  hp.res_chunks = RES ? a.cr / CK : 0;
+  p.k_res = hp.res_chunks;
+  hp.cpt = a.cin / CK;
+  hp.stages = stages;
+  hp.wbytes = dxn_wbytes(a.cin, a.cout, RES ? a.cr : 0, CK);
+  p.gamma = a.w.gamma;
+  p.beta = a.w.beta;
+  p.wp_rgb = a.w.wp_f32;
+  p.canvas = a.canvas;
+  p.canvas_stride = a.canvas_stride;
+  p.tiles3 = a.tiles3;
+  p.y = static_cast<__nv_bfloat16*>(a.y);
+  p.y_cs = a.y_cs;
+  p.y_co = a.y_co;
+  p.err = a.err;
+  const size_t smem = (size_t)hp.wbytes + (size_t)stages * Cfg::kStageBytes + kHaloSmemExtra;
+  if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
+  auto kern = k_conv_tc_dxn<CO, CK, RES>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloSmemMax);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
+  kern<<<grid, kThreadsTC, smem, st>>>(mA, mB, mA2, mB2, hp);
+  return cudaGetLastError();
+}
+
 int pick_bn(int cout, bool res) {
   const int cap = res ? 128 : 256;
   return cout < cap ? cout : cap;
@@ -845,6 +1172,7 @@ int pick_bn(int cout, bool res) {
 
 bool conv_tc_supported(int R, int cin, int cout, int cr) {
   if (cin % 32 == 0 && cr % 32 == 0 && halo_ok(R, cout, cin, cr)) return true;
+  if (cin % 32 == 0 && cr % 32 == 0 && R >= 64 && dxn_ok(R, cout, cin, cr)) return true;
   if (cout > 512) return false;
   if (!(R == 16 || R == 32 || R == 64 || (R >= 128 && R % 128 == 0))) return false;
   if (cin % 32 || cr % 32 || cout % 32) return false;
@@ -874,6 +1202,11 @@ bool pertap_ok(int R, int cin, int cout, int cr, int bn, int ck) {
 
 int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
   int n = 0;
+  if (dxn_ok(R, cout, cin, cr))
+    for (int ck = 32; ck <= 64; ck *= 2) {
+      const int stg = dxn_stages(cin, cout, cr, ck);
+      if (stg >= 2 && n < max) out[n++] = TcConfig{2, cout, ck, stg};
+    }
   if (halo_ok(R, cout, cin, cr))
     for (int ck = 32; ck <= 64; ck *= 2) {
       const int stg = halo_stages(cin, cout, cr, ck);
@@ -886,6 +1219,12 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
 }
 
 TcConfig tc_default(int R, int cin, int cout, int cr) {
+  if (R >= 64 && dxn_ok(R, cout, cin, cr)) {
+    int ck = 32, stg = dxn_stages(cin, cout, cr, 32);
+    const int stg64 = dxn_stages(cin, cout, cr, 64);
+    if (stg64 >= 4) { ck = 64; stg = stg64; }
+    return TcConfig{2, cout, ck, stg};
+  }
   if (halo_ok(R, cout, cin, cr)) {
     int ck = 32, stg = halo_stages(cin, cout, cr, 32);
     const int stg64 = halo_stages(cin, cout, cr, 64);
@@ -901,6 +1240,17 @@ cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_
   cudaError_t e = check_tc_args(a, cr);
   if (e != cudaSuccess) return e;
   const bool res = cr > 0;
+  if (c.kind == 2) {
+    if (!dxn_ok(a.R, a.cout, a.cin, cr) || c.bn != a.cout || c.stages < 2 ||
+        c.stages > dxn_stages(a.cin, a.cout, cr, c.ck))
+      return cudaErrorInvalidValue;
+#define OMNI_DXN(CO_, CK_, RES_) \
+    if (c.bn == CO_ && c.ck == CK_ && res == RES_) return launch_dxn<CO_, CK_, RES_>(a, st, c.stages);
+    OMNI_DXN(32, 32, false) OMNI_DXN(32, 32, true) OMNI_DXN(32, 64, false) OMNI_DXN(32, 64, true)
+    OMNI_DXN(64, 32, false) OMNI_DXN(64, 32, true) OMNI_DXN(64, 64, false) OMNI_DXN(64, 64, true)
+#undef OMNI_DXN
+    return cudaErrorInvalidValue;
+  }
   if (c.kind == 1) {
     if (!halo_ok(a.R, a.cout, a.cin, cr) || c.bn != a.cout || c.stages < 2 ||
         c.stages > halo_stages(a.cin, a.cout, cr, c.ck))
