@@ -147,8 +147,8 @@ def run_layer(args):
     from paper_2305_14566_gb300 import api, _lib
     R, cin, cout, cr, B, rep = (int(v) for v in args.layer.split(","))
     rng = np.random.default_rng(0)
-    prec = _lib.BF16 if args.precision == "bf16" else _lib.FP32
-    dt = torch.bfloat16 if prec == _lib.BF16 else torch.float32
+    prec = {"bf16": _lib.BF16, "fp16": _lib.FP16, "fp32": _lib.FP32}[args.precision]
+    dt = {"bf16": torch.bfloat16, "fp16": torch.float16, "fp32": torch.float32}[args.precision]
     x = torch.rand((B, R, R, cin), device="cuda").to(dt)
     r = torch.rand((B, R, R, cr), device="cuda").to(dt) if cr else None
     y = torch.empty((B, R, R, cout), device="cuda", dtype=dt)
@@ -174,7 +174,7 @@ def run_ragged(args, api, _lib, dev, prec):
     works = synth.ragged_workloads()
     blob = synth.gen_weights(works[0])
     seg = api.Segmenter(works[0], blob, precision=prec)
-    if prec == _lib.BF16 and not args.no_autotune:
+    if prec != _lib.FP32 and not args.no_autotune:
         seg.set_autotune(True)
     need = max(seg.query(w.H, w.W).workspace_bytes for w in works)
     seg.workspace(need, dev)
@@ -267,7 +267,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-fp32", action="store_true",
                     help="also time one step of the plain FP32 path")
@@ -299,7 +299,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    prec = _lib.BF16 if args.precision == "bf16" else _lib.FP32
+    prec = {"bf16": _lib.BF16, "fp16": _lib.FP16, "fp32": _lib.FP32}[args.precision]
 
     if args.ragged:
         run_ragged(args, api, _lib, dev, prec)
@@ -308,7 +308,7 @@ def main():
     rgb = api.synth_slide(spec, device=dev)
     blob = synth.gen_weights(WORK)
     seg = api.Segmenter(WORK, blob, precision=prec)
-    if prec == _lib.BF16 and not args.no_autotune:
+    if prec != _lib.FP32 and not args.no_autotune:
         seg.set_autotune(True)          # the first (untimed) call tunes every conv shape
     out = seg.segment(rgb)
     torch.cuda.synchronize()
@@ -348,9 +348,10 @@ def main():
     breakdown = summarize(ms_l, tags_l, work_l, args.steps)
 
     pk, src = peaks()
-    if prec == _lib.BF16:
+    if prec != _lib.FP32:
+        # FP16 and BF16 share the kind::f16 tensor-core rate
         peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
-        bound, peak_note = "tensor", f"bf16 dense sustained ({src})"
+        bound, peak_note = "tensor", f"bf16 dense sustained ({src}); fp16 runs at the same rate"
     else:
         peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         bound, peak_note = "alu", "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock"
@@ -400,7 +401,7 @@ def main():
     del rgb_h, labs
 
     fp32 = None
-    if args.compare_fp32 and prec == _lib.BF16:
+    if args.compare_fp32 and prec != _lib.FP32:
         seg32 = api.Segmenter(WORK, blob, precision=_lib.FP32)
         o32 = seg32.segment(rgb)
         torch.cuda.synchronize()

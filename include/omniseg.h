@@ -51,6 +51,8 @@ typedef int omni_status;
 /* Arithmetic of the U-Net convolutions. */
 #define OMNI_FP32 0  /* FP32 FFMA on the CUDA cores (plain path)                  */
 #define OMNI_BF16 1  /* BF16 operands, FP32 accumulation in TMEM (tcgen05.mma)    */
+#define OMNI_FP16 2  /* FP16 operands and activations, FP32 accumulation in TMEM;
+                        same tensor-core rate as BF16, 3 more mantissa bits      */
 
 /* Overlap aggregation (Sec. 2.2, Sec. 3.2). */
 #define OMNI_STITCH_AVG 0   /* label = mean logit of covering tiles > 0            */
@@ -71,7 +73,7 @@ typedef struct omni_config {
   int32_t factors[OMNI_MAX_SCALES];      /* downsample factor vs 40x: 1, 2, 4 or 8      */
   int32_t n_classes;    /* number of tissue classes / dynamic heads (1..16)             */
   int32_t class_scale[OMNI_MAX_CLASSES]; /* scale index each class is predicted at      */
-  int32_t precision;    /* OMNI_FP32 or OMNI_BF16                                       */
+  int32_t precision;    /* OMNI_FP32, OMNI_BF16 or OMNI_FP16                            */
   int32_t stitch_mode;  /* OMNI_STITCH_AVG or OMNI_STITCH_VOTE                          */
   int32_t tissue_filter;/* 1: segment only tiles touching tissue (Sec. 2.1)             */
   int32_t tissue_and;   /* 1: AND every label map with the tissue mask (Sec. 2.3)       */
@@ -199,7 +201,7 @@ omni_status omni_synth_slide(const int64_t* ellipses_host, int32_t n_ell, uint64
  * y = ReLU(g * conv3x3(x) + b [+ wp . r]) on B images of R x R pixels, with the
  * same kernels omni_segment_slide uses.  x / r / y are NHWC with channel
  * stride *_cs and channel offset *_co (elements); dtype float32 for
- * OMNI_FP32, bfloat16 for OMNI_BF16.  Weights are host FP32 ([cout][cin][3][3],
+ * OMNI_FP32, bfloat16 for OMNI_BF16, float16 for OMNI_FP16.  Weights are host FP32 ([cout][cin][3][3],
  * [cout], [cout], [cout][cr]); r may be NULL (no residual).  The layer is
  * launched `repeat` (>= 1) times back to back; if `ms_per_launch` is not NULL
  * it receives the mean device time of one launch (CUDA events on `stream`).

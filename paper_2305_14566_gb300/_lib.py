@@ -13,7 +13,7 @@ MAX_SCALES = 4
 MAX_CLASSES = 16
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EWEIGHTS, ESTATE = 0, -1, -2, -3, -4, -5, -6
-FP32, BF16 = 0, 1
+FP32, BF16, FP16 = 0, 1, 2
 STITCH_AVG, STITCH_VOTE = 0, 1
 NOALLOC_MAX_THUMB_PX = 4 << 20
 NOALLOC_MAX_TILES = 1 << 16

@@ -1,0 +1,1319 @@
+// BF16 implicit-GEMM 3x3 convolution of the residual U-Net on the tcgen05
+// tensor cores (sm_103a), with the folded norm, the 1x1 residual projection
+// and the ReLU fused:  y = ReLU(g * conv3x3(x) + b + wp . r).
+//
+// GEMM view: M = B*R*R output pixels (NHWC order), N = cout, K = 9*cin
+// (tap-major, then channel) for the main segment, plus a second K segment of
+// cr channels (the projection, centre tap only) accumulated into its own TMEM
+// columns.  A tiles (128 pixels x CK channels) are TMA loads of the shifted
+// NHWC input box for each tap; the box runs off the image where the 3x3
+// window does, and TMA's zero fill supplies the convolution's zero padding.
+// B tiles (BN x CK) are TMA loads of the K-major BF16 weights.
+//
+// Persistent, warp-specialised CTA (320 threads):
+//   warp 0      TMA producer (one elected lane), owns the TMEM allocation
+//   warp 1      MMA issuer (one lane): tcgen05.mma M=128 x N=BN x K=16,
+//               FP32 accumulators in TMEM, double buffered across tiles
+//   warps 2..9  epilogue: tcgen05.ld -> norm, residual, ReLU -> BF16 stores;
+//               warps w and w+4 share TMEM lane quarter w%4 and split the
+//               columns, so each SM sub-partition interleaves two of them
+// Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
+// records kErrTimeout in the caller's status word, drains its own copies and
+// MMAs (again bounded), frees TMEM and returns.
+// This file is compiled twice: k_conv_tc.cu (OMNI_TC_F16 = 0, BF16 operands)
+// and k_conv_tc_f16.cu (OMNI_TC_F16 = 1, FP16 operands).  The two differ only
+// in the MMA operand format and the epilogue's rounding of the output.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include "omni_internal.cuh"
+
+#ifndef OMNI_TC_F16
+#error "define OMNI_TC_F16 before including conv_tc_impl.cuh"
+#endif
+
+namespace omni {
+namespace {
+
+constexpr bool kF16 = OMNI_TC_F16 != 0;
+
+// two FP32 values rounded to the operand type, packed as one 32-bit word
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if constexpr (kF16) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+constexpr int kBM = 128;
+constexpr int kEpiWarps = 8;                         // two epilogue warpgroups
+constexpr int kThreadsTC = 64 + 32 * kEpiWarps;      // producer warp, MMA warp, epilogue
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+constexpr int kSmemBudget = 200 * 1024;
+
+struct TCParams {
+  int B, R, cin, cout, cr;
+  int res_mode;
+  int n_tiles_m, n_tiles_n, n_tiles;
+  int k_main, k_res;                 // K iterations of the two segments
+  const float* gamma;
+  const float* beta;
+  const float* wp_rgb;               // [3][cout] for RES_RGB
+  const uint8_t* canvas;
+  long long canvas_stride;
+  const int32_t* tiles3;
+  __nv_bfloat16* y;
+  int y_cs, y_co;
+  unsigned* err;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false if the CTA aborted or the limit expired (then sets abort).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned* err) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (now_ns() - t0 > kWaitNs) {
+      *abort_flag = 1;
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+}
+// Drain wait used after an abort: bounded, ignores the abort flag.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = now_ns();
+  while (!mbar_try(bar, parity) && now_ns() - t0 < kWaitNs) {
+  }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major, swizzled operand tile whose
+// rows are SW bytes long (SW = 64 or 128), 8-row groups SW*8 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int sw) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                            // leading offset (unused, K-major swizzled)
+  d |= (uint64_t)((sw * 8) >> 4) << 32;              // stride offset: next 8-row group
+  d |= (uint64_t)1 << 46;                            // descriptor version for tcgen05
+  d |= (uint64_t)(sw == 128 ? 2 : 4) << 61;          // swizzle mode: 128B = 2, 64B = 4
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 (or FP16 x FP16) -> FP32,
+// both operands K-major, M = 128.  Operand format field: 0 = FP16, 1 = BF16.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | ((kF16 ? 0u : 1u) << 7) | ((kF16 ? 0u : 1u) << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane; the
+// load and its completion wait are one asm statement so no use of the
+// registers can be scheduled before the data has arrived.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float norm_u8(uint8_t u) { return 2.0f * (float)u / 255.0f - 1.0f; }
+
+template <int BN, int CK, bool RES>
+struct TCCfg {
+  static constexpr int kABytes = kBM * CK * 2;
+  static constexpr int kBBytes = BN * CK * 2;
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kStages0 = (kSmemBudget - 2048) / kStageBytes;
+  static constexpr int kStages = kStages0 > 16 ? 16 : kStages0;
+  static constexpr int kBufCols = RES ? 2 * BN : BN;     // TMEM columns per accumulator buffer
+  static constexpr int kTmemCols = 2 * kBufCols;          // double buffered
+  static constexpr int kSW = CK * 2;                      // row bytes = swizzle span
+  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*align*/ +
+                                  2 * 512 * 4 /*gamma, beta*/;
+};
+
+template <int BN, int CK, bool RES>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
+              TCParams p) {
+  using Cfg = TCCfg<BN, CK, RES>;
+  constexpr int ST = Cfg::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + (size_t)ST * Cfg::kABytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)ST * Cfg::kStageBytes);
+  uint64_t* full = bars;                 // [ST]
+  uint64_t* empty = bars + ST;           // [ST]
+  uint64_t* tfull = bars + 2 * ST;       // [2]
+  uint64_t* tempty = bars + 2 * ST + 2;  // [2]
+  uint64_t* drain = bars + 2 * ST + 4;   // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * ST + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* sg = reinterpret_cast<float*>(smem + (size_t)ST * Cfg::kStageBytes + 1024);   // gamma[cout]
+  float* sb = sg + 512;                                                                // beta[cout]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < p.cout; i += blockDim.x) {
+    sg[i] = p.gamma[i];
+    sb[i] = p.beta[i];
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+    }
+    mbar_init(smem_u32(drain), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int k_total = p.k_main + p.k_res;
+  const int RR = p.R * p.R;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- producer
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+        const int mt = tile / p.n_tiles_n, nt = tile % p.n_tiles_n;
+        const int m0 = mt * kBM;
+        const int img = m0 / RR, rem = m0 % RR;
+        const int h0 = rem / p.R, w0 = rem % p.R;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (it >= ST && !mbar_wait(smem_u32(&empty[s]), ((it / ST) & 1) ^ 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full[s]);
+          mbar_expect_tx(fb, Cfg::kStageBytes);
+          const uint32_t da = smem_u32(sA + (size_t)s * Cfg::kABytes);
+          const uint32_t db = smem_u32(sB + (size_t)s * Cfg::kBBytes);
+          if (k < p.k_main) {
+            const int cpt = p.cin / CK;
+            const int tap = k / cpt, c0 = (k % cpt) * CK;
+            tma_load_4d(da, &mapA, fb, c0, w0 + tap % 3 - 1, h0 + tap / 3 - 1, img);
+            tma_load_2d(db, &mapB, fb, tap * p.cin + c0, nt * BN);
+          } else {
+            const int c0 = (k - p.k_main) * CK;
+            tma_load_4d(da, &mapA2, fb, c0, w0, h0, img);
+            tma_load_2d(db, &mapB2, fb, c0, nt * BN);
+          }
+        }
+      }
+      // make sure no copy of ours is still landing in shared memory
+      const int last = it;
+      for (int q = last - 1; q >= 0 && q >= last - ST; --q) mbar_drain(smem_u32(&full[q % ST]), (q / ST) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BN);
+      const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
+      const uint64_t b_desc0 = smem_desc(smem_u32(sB), Cfg::kSW);
+      int it = 0, tcount = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
+        const int buf = tcount & 1, use = tcount >> 1;
+        if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
+        const uint32_t acc1 = acc0 + BN;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (!mbar_wait(smem_u32(&full[s]), (it / ST) & 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = a_desc0 + (uint64_t)(s * (Cfg::kABytes >> 4));
+          const uint64_t bd = b_desc0 + (uint64_t)(s * (Cfg::kBBytes >> 4));
+          const bool second = RES && k >= p.k_main;
+          const uint32_t d = second ? acc1 : acc0;
+          const int kfirst = second ? p.k_main : 0;
+#pragma unroll
+          for (int kk = 0; kk < CK / 16; ++kk)
+            mma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                     (k > kfirst || kk > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&tfull[buf]));
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      mma_commit(smem_u32(drain));
+      mbar_drain(smem_u32(drain), 0);
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const int q = warp & 3;                  // TMEM lane quarter this warp may access
+    const int row = q * 32 + lane;
+    const int c_beg = ((warp - 2) >> 2) * (BN / 2), c_end = c_beg + BN / 2;
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
+      const int buf = tcount & 1, use = tcount >> 1;
+      // every lane waits; the vote keeps the warp converged for tcgen05.ld
+      const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int mt = tile / p.n_tiles_n, nt = tile % p.n_tiles_n;
+      const long long m = (long long)mt * kBM + row;
+      const int n0 = nt * BN;
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      if (p.res_mode == RES_RGB) {
+        const int b = (int)(m / RR);
+        const int rem = (int)(m - (long long)b * RR);
+        const uint8_t* px = p.canvas + (long long)(p.tiles3[3 * b + 1] + rem / p.R) * p.canvas_stride +
+                            (long long)(p.tiles3[3 * b + 2] + rem % p.R) * 3;
+        v0 = norm_u8(px[0]);
+        v1 = norm_u8(px[1]);
+        v2 = norm_u8(px[2]);
+      }
+      __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co + n0;
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
+#pragma unroll 1
+      for (int c = c_beg; c < c_end; c += 16) {
+        float a[16], r[16];
+        tmem_ld16(tb + c, a);
+        if constexpr (RES) tmem_ld16(tb + BN + c, r);
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float o[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int n = n0 + c + j + u;
+            float z = fmaf(sg[n], a[j + u], sb[n]);
+            if constexpr (RES) z += r[j + u];
+            if (p.res_mode == RES_RGB)
+              z += fmaf(v0, __ldg(p.wp_rgb + n),
+                        fmaf(v1, __ldg(p.wp_rgb + p.cout + n), v2 * __ldg(p.wp_rgb + 2 * p.cout + n)));
+            o[u] = fmaxf(z, 0.f);
+          }
+          packed[j / 2] = pack2(o[0], o[1]);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(out + c);
+        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ small-N variant
+// For cout <= 64 the A tile of one tap feeds only a few MMA cycles, so the
+// per-tap refetch above starves the tensor pipe.  This variant keeps the whole
+// layer's weights resident in shared memory (loaded once per CTA) and tiles the
+// output as 8 rows x 16 columns.  Per channel chunk it loads three boxes of
+// 10 x 16 input pixels, one per horizontal tap offset dx; the operand of tap
+// (dy, dx) is rows 16*dy .. 16*dy+127 of box dx, an offset of whole swizzle
+// atoms, so nine taps reuse three loads.
+constexpr int kHTH = 8, kHTW = 16;
+constexpr int kHBoxPix = (kHTH + 2) * kHTW;   // 160 input pixels per dx box
+
+template <int BN, int CK, bool RES>
+struct HaloCfg {
+  static constexpr int kBoxBytes = kHBoxPix * CK * 2;
+  static constexpr int kStageBytes = 3 * kBoxBytes;
+  static constexpr int kWTileBytes = BN * CK * 2;
+  static constexpr int kBufCols = RES ? 2 * BN : BN;
+  static constexpr int kTmemCols = 2 * kBufCols;
+  static constexpr int kSW = CK * 2;
+};
+
+struct HaloParams {
+  TCParams t;                       // t.k_res = stages of the projection segment (3 chunks each)
+  int res_chunks;                   // channel chunks of the projection input
+  int stages, n_wtiles, cpt;        // cpt = channel chunks of the main input
+  int tiles_per_img, tiles_w;       // (R/8)*(R/16), R/16
+};
+
+template <int BN, int CK, bool RES>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_conv_tc_halo(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
+                   HaloParams hp) {
+  using Cfg = HaloCfg<BN, CK, RES>;
+  const TCParams& p = hp.t;
+  const int ST = hp.stages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sW = smem;
+  uint8_t* sA = smem + (size_t)hp.n_wtiles * Cfg::kWTileBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * Cfg::kStageBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + ST;
+  uint64_t* tfull = bars + 2 * ST;
+  uint64_t* tempty = bars + 2 * ST + 2;
+  uint64_t* drain = bars + 2 * ST + 4;
+  uint64_t* wbar = bars + 2 * ST + 5;
+  float* sg = reinterpret_cast<float*>(bars + 2 * ST + 6);    // gamma[BN]
+  float* sb = sg + BN;                                          // beta[BN]
+  float* swp = sb + BN;                                         // wp_rgb[3][BN]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(swp + 3 * BN);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < BN; i += blockDim.x) {
+    sg[i] = p.gamma[i];
+    sb[i] = p.beta[i];
+    if (p.res_mode == RES_RGB) {
+      swp[i] = p.wp_rgb[i];
+      swp[BN + i] = p.wp_rgb[p.cout + i];
+      swp[2 * BN + i] = p.wp_rgb[2 * p.cout + i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+    }
+    mbar_init(smem_u32(drain), 1);
+    mbar_init(smem_u32(wbar), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int k_total = p.k_main + p.k_res;
+  const int RR = p.R * p.R;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- producer
+      const uint32_t wb = smem_u32(wbar);
+      mbar_expect_tx(wb, (uint32_t)(hp.n_wtiles * Cfg::kWTileBytes));
+      for (int t = 0; t < 9 * hp.cpt; ++t) {
+        const int tap = t / hp.cpt, c = t % hp.cpt;
+        tma_load_2d(smem_u32(sW + (size_t)t * Cfg::kWTileBytes), &mapB, wb, tap * p.cin + c * CK, 0);
+      }
+      for (int r = 0; r < hp.res_chunks; ++r)
+        tma_load_2d(smem_u32(sW + (size_t)(9 * hp.cpt + r) * Cfg::kWTileBytes), &mapB2, wb, r * CK, 0);
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+        const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
+        const int h0 = (rem / hp.tiles_w) * kHTH, w0 = (rem % hp.tiles_w) * kHTW;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (it >= ST && !mbar_wait(smem_u32(&empty[s]), ((it / ST) & 1) ^ 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full[s]);
+          uint8_t* st = sA + (size_t)s * Cfg::kStageBytes;
+          if (k < p.k_main) {
+            mbar_expect_tx(fb, Cfg::kStageBytes);
+            const int c0 = k * CK;
+            for (int dx = 0; dx < 3; ++dx)
+              tma_load_4d(smem_u32(st + dx * Cfg::kBoxBytes), &mapA, fb, c0, w0 + dx - 1, h0 - 1, img);
+          } else {
+            // up to three projection chunks per stage, one per box slot
+            const int c0 = (k - p.k_main) * 3, nbx = min(3, hp.res_chunks - c0);
+            mbar_expect_tx(fb, (uint32_t)(nbx * kBM * CK * 2));
+            for (int j = 0; j < nbx; ++j)
+              tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA2, fb, (c0 + j) * CK, w0, h0, img);
+          }
+        }
+      }
+      const int last = it;
+      for (int q = last - 1; q >= 0 && q >= last - ST; --q) mbar_drain(smem_u32(&full[q % ST]), (q / ST) & 1);
+      mbar_drain(wb, 0);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BN);
+      const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
+      const uint64_t b_desc0 = smem_desc(smem_u32(sW), Cfg::kSW);
+      const uint64_t b_tap_step = (uint64_t)(hp.cpt * (Cfg::kWTileBytes >> 4));
+      bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, p.err);
+      int it = 0, tcount = 0;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
+        const int buf = tcount & 1, use = tcount >> 1;
+        if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
+        const uint32_t acc1 = acc0 + BN;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (!mbar_wait(smem_u32(&full[s]), (it / ST) & 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          // descriptor start addresses advance in 16-byte units: add (bytes >> 4)
+          const uint64_t ad = a_desc0 + (uint64_t)((s * Cfg::kStageBytes) >> 4);
+          if (k < p.k_main) {
+            const uint64_t bd = b_desc0 + (uint64_t)(k * (Cfg::kWTileBytes >> 4));
+            const uint32_t acc_first = k > 0 ? 1u : 0u;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+              const uint64_t at = ad + (uint64_t)(((tap % 3) * Cfg::kBoxBytes + (tap / 3) * kHTW * CK * 2) >> 4);
+              const uint64_t bt = bd + (uint64_t)tap * b_tap_step;
+#pragma unroll
+              for (int kk = 0; kk < CK / 16; ++kk)
+                mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc,
+                         (tap > 0 || kk > 0) ? 1u : acc_first);
+            }
+          } else if (RES) {
+            const int c0 = (k - p.k_main) * 3, nbx = min(3, hp.res_chunks - c0);
+            for (int j = 0; j < nbx; ++j) {
+              const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
+              const uint64_t bd = b_desc0 + (uint64_t)((9 * hp.cpt + c0 + j) * (Cfg::kWTileBytes >> 4));
+#pragma unroll
+              for (int kk = 0; kk < CK / 16; ++kk)
+                mma_bf16(acc1, aj + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                         (c0 + j > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&tfull[buf]));
+      }
+      mma_commit(smem_u32(drain));
+      mbar_drain(smem_u32(drain), 0);
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int c_beg = ((warp - 2) >> 2) * (BN / 2), c_end = c_beg + BN / 2;
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
+      const int buf = tcount & 1, use = tcount >> 1;
+      const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
+      const int hh = (rem / hp.tiles_w) * kHTH + row / kHTW;
+      const int ww = (rem % hp.tiles_w) * kHTW + row % kHTW;
+      const long long m = (long long)img * RR + (long long)hh * p.R + ww;
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      if (p.res_mode == RES_RGB) {
+        const uint8_t* px = p.canvas + (long long)(p.tiles3[3 * img + 1] + hh) * p.canvas_stride +
+                            (long long)(p.tiles3[3 * img + 2] + ww) * 3;
+        v0 = norm_u8(px[0]);
+        v1 = norm_u8(px[1]);
+        v2 = norm_u8(px[2]);
+      }
+      __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
+#pragma unroll 1
+      for (int c = c_beg; c < c_end; c += 16) {
+        float a[16], r[16];
+        tmem_ld16(tb + c, a);
+        if constexpr (RES) tmem_ld16(tb + BN + c, r);
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float o[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int n = c + j + u;
+            float z = fmaf(sg[n], a[j + u], sb[n]);
+            if constexpr (RES) z += r[j + u];
+            if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[BN + n], v2 * swp[2 * BN + n]));
+            o[u] = fmaxf(z, 0.f);
+          }
+          packed[j / 2] = pack2(o[0], o[1]);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(out + c);
+        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ dx-in-N variant
+// Pixels stay on M (128 = 8 rows x 16 columns), but the three horizontal taps
+// move to N: B stacks the weights of dx = 0, 1, 2 (N = 3 * cout), so one MMA of
+// tap row dy computes D[p][(dx, co)] for the unshifted input rows.  A is a
+// single box of 10 x 16 input pixels per channel chunk, whose three dy views
+// are 16-row (whole swizzle atom) offsets.  The output at column c of a tile
+// row is D0[c-1] + D1[c] + D2[c+1]: a horizontal pixel shift is a neighbouring
+// TMEM lane inside a 16-lane row group, so the epilogue sums the three dx
+// blocks with +-1 lane warp shuffles.  Tiles advance by 14 columns and keep
+// one halo column on each side (lanes 0 and 15 of each row group write nothing).
+constexpr int kXTW = 14;                       // valid output columns per tile row
+
+template <int CO, int CK, bool RES>
+struct DxnCfg {
+  static constexpr int kN = 3 * CO;                        // MMA N (dx blocks)
+  static constexpr int kBoxBytes = kHBoxPix * CK * 2;      // 10 x 16 pixels
+  static constexpr int kStageBytes = kBoxBytes;            // one box per stage
+  static constexpr int kWTileBytes = kN * CK * 2;          // 3 dx slices of cout x CK
+  static constexpr int kRTileBytes = CO * CK * 2;          // projection weights
+  static constexpr int kBufCols = RES ? kN + CO : kN;
+  static constexpr int kTmemCols = 2 * kBufCols <= 64 ? 64 : (2 * kBufCols <= 128 ? 128 : (2 * kBufCols <= 256 ? 256 : 512));
+  static constexpr int kSW = CK * 2;
+};
+
+struct DxnParams {
+  TCParams t;
+  int res_chunks, stages, cpt;
+  int tiles_per_img, tiles_w;      // (R/8) * ceil(R/14), ceil(R/14)
+  int wbytes;                      // resident weight bytes (main + projection)
+};
+
+template <int CO, int CK, bool RES>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_conv_tc_dxn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
+                  DxnParams hp) {
+  using Cfg = DxnCfg<CO, CK, RES>;
+  const TCParams& p = hp.t;
+  const int ST = hp.stages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sW = smem;                                              // [3 dy][cpt][3 cout x CK]
+  uint8_t* sR = sW + (size_t)9 * hp.cpt * Cfg::kRTileBytes;        // [res_chunks][cout x CK]
+  uint8_t* sA = smem + hp.wbytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * Cfg::kStageBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + ST;
+  uint64_t* tfull = bars + 2 * ST;
+  uint64_t* tempty = bars + 2 * ST + 2;
+  uint64_t* drain = bars + 2 * ST + 4;
+  uint64_t* wbar = bars + 2 * ST + 5;
+  float* sg = reinterpret_cast<float*>(bars + 2 * ST + 6);
+  float* sb = sg + CO;
+  float* swp = sb + CO;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(swp + 3 * CO);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < CO; i += blockDim.x) {
+    sg[i] = p.gamma[i];
+    sb[i] = p.beta[i];
+    if (p.res_mode == RES_RGB) {
+      swp[i] = p.wp_rgb[i];
+      swp[CO + i] = p.wp_rgb[p.cout + i];
+      swp[2 * CO + i] = p.wp_rgb[2 * p.cout + i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+    }
+    mbar_init(smem_u32(drain), 1);
+    mbar_init(smem_u32(wbar), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int k_total = p.k_main + p.k_res;
+  const int RR = p.R * p.R;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- producer
+      const uint32_t wb = smem_u32(wbar);
+      mbar_expect_tx(wb, (uint32_t)hp.wbytes);
+      for (int dy = 0; dy < 3; ++dy)
+        for (int c = 0; c < hp.cpt; ++c)
+          for (int dx = 0; dx < 3; ++dx)
+            tma_load_2d(smem_u32(sW + (size_t)(dy * hp.cpt + c) * Cfg::kWTileBytes + dx * Cfg::kRTileBytes),
+                        &mapB, wb, (dy * 3 + dx) * p.cin + c * CK, 0);
+      for (int r = 0; r < hp.res_chunks; ++r)
+        tma_load_2d(smem_u32(sR + (size_t)r * Cfg::kRTileBytes), &mapB2, wb, r * CK, 0);
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+        const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
+        const int h0 = (rem / hp.tiles_w) * kHTH, w0 = (rem % hp.tiles_w) * kXTW;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (it >= ST && !mbar_wait(smem_u32(&empty[s]), ((it / ST) & 1) ^ 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full[s]);
+          uint8_t* st = sA + (size_t)s * Cfg::kStageBytes;
+          if (k < p.k_main) {
+            mbar_expect_tx(fb, Cfg::kBoxBytes);
+            tma_load_4d(smem_u32(st), &mapA, fb, k * CK, w0 - 1, h0 - 1, img);
+          } else {
+            mbar_expect_tx(fb, kBM * CK * 2);
+            tma_load_4d(smem_u32(st), &mapA2, fb, (k - p.k_main) * CK, w0 - 1, h0, img);
+          }
+        }
+      }
+      const int last = it;
+      for (int q = last - 1; q >= 0 && q >= last - ST; --q) mbar_drain(smem_u32(&full[q % ST]), (q / ST) & 1);
+      mbar_drain(wb, 0);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc_n = idesc_bf16(Cfg::kN);
+      constexpr uint32_t idesc_r = idesc_bf16(CO);
+      const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
+      const uint64_t w_desc0 = smem_desc(smem_u32(sW), Cfg::kSW);
+      const uint64_t r_desc0 = smem_desc(smem_u32(sR), Cfg::kSW);
+      const uint64_t dy_step = (uint64_t)(hp.cpt * (Cfg::kWTileBytes >> 4));
+      bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, p.err);
+      int it = 0, tcount = 0;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
+        const int buf = tcount & 1, use = tcount >> 1;
+        if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
+        const uint32_t acc1 = acc0 + Cfg::kN;
+        for (int k = 0; k < k_total; ++k, ++it) {
+          const int s = it % ST;
+          if (!mbar_wait(smem_u32(&full[s]), (it / ST) & 1, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = a_desc0 + (uint64_t)((s * Cfg::kStageBytes) >> 4);
+          if (k < p.k_main) {
+            const uint64_t bk = w_desc0 + (uint64_t)(k * (Cfg::kWTileBytes >> 4));
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) {
+              const uint64_t at = ad + (uint64_t)((dy * kHTW * CK * 2) >> 4);
+              const uint64_t bt = bk + (uint64_t)dy * dy_step;
+#pragma unroll
+              for (int kk = 0; kk < CK / 16; ++kk)
+                mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc_n,
+                         (k > 0 || dy > 0 || kk > 0) ? 1u : 0u);
+            }
+          } else if (RES) {
+            const uint64_t bd = r_desc0 + (uint64_t)((k - p.k_main) * (Cfg::kRTileBytes >> 4));
+#pragma unroll
+            for (int kk = 0; kk < CK / 16; ++kk)
+              mma_bf16(acc1, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc_r,
+                       (k > p.k_main || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&tfull[buf]));
+      }
+      mma_commit(smem_u32(drain));
+      mbar_drain(smem_u32(drain), 0);
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    // warps w and w+4 share lane quarter w%4 and split the output channels
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int col = row % kHTW;                        // column inside the 16-lane row group
+    const int co_beg = ((warp - 2) >> 2) * (CO / 2), co_end = co_beg + CO / 2;
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
+      const int buf = tcount & 1, use = tcount >> 1;
+      const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
+      const int hh = (rem / hp.tiles_w) * kHTH + row / kHTW;
+      const int ww = (rem % hp.tiles_w) * kXTW + col - 1;           // this lane's pixel column
+      const bool writes = col >= 1 && col <= kXTW && ww < p.R;
+      const long long m = (long long)img * RR + (long long)hh * p.R + (ww < 0 ? 0 : ww);
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      if (p.res_mode == RES_RGB && writes) {
+        const uint8_t* px = p.canvas + (long long)(p.tiles3[3 * img + 1] + hh) * p.canvas_stride +
+                            (long long)(p.tiles3[3 * img + 2] + ww) * 3;
+        v0 = norm_u8(px[0]);
+        v1 = norm_u8(px[1]);
+        v2 = norm_u8(px[2]);
+      }
+      __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
+#pragma unroll 1
+      for (int c = co_beg; c < co_end; c += 16) {
+        float d0[16], d1[16], d2[16], r[16];
+        tmem_ld16(tb + c, d0);                   // dx = 0 block
+        tmem_ld16(tb + CO + c, d1);              // dx = 1 block
+        tmem_ld16(tb + 2 * CO + c, d2);          // dx = 2 block
+        if constexpr (RES) tmem_ld16(tb + Cfg::kN + c, r);
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float o[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int n = c + j + u;
+            // lane-1 holds the left neighbour's dx=0 sum, lane+1 the right's dx=2 sum
+            const float left = __shfl_up_sync(0xffffffffu, d0[j + u], 1);
+            const float right = __shfl_down_sync(0xffffffffu, d2[j + u], 1);
+            float z = fmaf(sg[n], left + d1[j + u] + right, sb[n]);
+            if constexpr (RES) z += r[j + u];
+            if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[CO + n], v2 * swp[2 * CO + n]));
+            o[u] = fmaxf(z, 0.f);
+          }
+          packed[j / 2] = pack2(o[0], o[1]);
+        }
+        if (writes) {
+          uint4* dst = reinterpret_cast<uint4*>(out + c);
+          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ host side
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                              CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  }
+  return fn;
+}
+
+// NHWC activation box: {CK channels, bw pixels, bh rows, 1 image}
+bool map_act(CUtensorMap* m, const void* base, int channels, int cs, int co, int R, int B, int CK) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  const char* ptr = static_cast<const char*>(base) + (size_t)co * 2;
+  cuuint64_t dims[4] = {(cuuint64_t)channels, (cuuint64_t)R, (cuuint64_t)R, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)R * cs * 2, (cuuint64_t)R * R * cs * 2};
+  const int bw = R < kBM ? R : kBM;
+  cuuint32_t box[4] = {(cuuint32_t)CK, (cuuint32_t)bw, (cuuint32_t)(kBM / bw), 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<char*>(ptr), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// NHWC activation box of bw x bh pixels (small-N variant: 16 x 10 or 16 x 8)
+bool map_act_box(CUtensorMap* m, const void* base, int channels, int cs, int co, int R, int B, int CK,
+                 int bw, int bh) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  const char* ptr = static_cast<const char*>(base) + (size_t)co * 2;
+  cuuint64_t dims[4] = {(cuuint64_t)channels, (cuuint64_t)R, (cuuint64_t)R, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)R * cs * 2, (cuuint64_t)R * R * cs * 2};
+  cuuint32_t box[4] = {(cuuint32_t)CK, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<char*>(ptr), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// K-major weights [rows = cout][K]: box {CK, BN}
+bool map_w(CUtensorMap* m, const void* base, int K, int cout, int BN, int CK) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cout};
+  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  cuuint32_t box[2] = {(cuuint32_t)CK, (cuuint32_t)BN};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+template <int BN, int CK, bool RES>
+cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
+  using Cfg = TCCfg<BN, CK, RES>;
+  CUtensorMap mA, mB, mA2, mB2;
+  if (!map_act(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK)) return cudaErrorInvalidValue;
+  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, BN, CK)) return cudaErrorInvalidValue;
+  if (RES) {
+    if (!map_act(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK)) return cudaErrorInvalidValue;
+    if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, BN, CK)) return cudaErrorInvalidValue;
+  } else {
+    mA2 = mA;
+    mB2 = mB;
+  }
+  TCParams p{};
+  p.B = a.B; p.R = a.R; p.cin = a.cin; p.cout = a.cout; p.cr = RES ? a.cr : 0;
+  p.res_mode = a.res_mode;
+  p.n_tiles_m = (int)((long long)a.B * a.R * a.R / kBM);
+  p.n_tiles_n = a.cout / BN;
+  p.n_tiles = p.n_tiles_m * p.n_tiles_n;
+  p.k_main = 9 * (a.cin / CK);
+  p.k_res = RES ? a.cr / CK : 0;
+  p.gamma = a.w.gamma;
+  p.beta = a.w.beta;
+  p.wp_rgb = a.w.wp_f32;
+  p.canvas = a.canvas;
+  p.canvas_stride = a.canvas_stride;
+  p.tiles3 = a.tiles3;
+  p.y = static_cast<__nv_bfloat16*>(a.y);
+  p.y_cs = a.y_cs;
+  p.y_co = a.y_co;
+  p.err = a.err;
+  auto kern = k_conv_tc<BN, CK, RES>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
+  kern<<<grid, kThreadsTC, Cfg::kSmem, st>>>(mA, mB, mA2, mB2, p);
+  return cudaGetLastError();
+}
+
+constexpr int kHaloSmemMax = 227 * 1024;
+constexpr int kHaloSmemExtra = 3072;   // barriers, gamma/beta, alignment slack
+
+// stages of the small-N variant for a layer and channel chunk (0: does not fit)
+int halo_stages(int cin, int cout, int cr, int ck) {
+  if (cin % ck || cr % ck) return 0;
+  const long long wbytes = (long long)(9 * (cin / ck) + cr / ck) * cout * ck * 2;
+  const long long stage = 3LL * kHBoxPix * ck * 2;
+  long long st = (kHaloSmemMax - wbytes - kHaloSmemExtra) / stage;
+  return st < 2 ? 0 : (int)(st > 8 ? 8 : st);
+}
+
+bool halo_ok(int R, int cout, int cin, int cr) {
+  if (R < 16 || R % 16 || (cout != 32 && cout != 64)) return false;
+  return halo_stages(cin, cout, cr, 32) >= 2;
+}
+
+template <int BN, int CK, bool RES>
+cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
+  using Cfg = HaloCfg<BN, CK, RES>;
+  CUtensorMap mA, mB, mA2, mB2;
+  if (!map_act_box(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, kHTW, kHTH + 2)) return cudaErrorInvalidValue;
+  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, BN, CK)) return cudaErrorInvalidValue;
+  if (RES) {
+    if (!map_act_box(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK, kHTW, kHTH)) return cudaErrorInvalidValue;
+    if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, BN, CK)) return cudaErrorInvalidValue;
+  } else {
+    mA2 = mA;
+    mB2 = mB;
+  }
+  HaloParams hp{};
+  TCParams& p = hp.t;
+  p.B = a.B; p.R = a.R; p.cin = a.cin; p.cout = a.cout; p.cr = RES ? a.cr : 0;
+  p.res_mode = a.res_mode;
+  hp.tiles_w = a.R / kHTW;
+  hp.tiles_per_img = (a.R / kHTH) * hp.tiles_w;
+  p.n_tiles_m = a.B * hp.tiles_per_img;
+  p.n_tiles_n = 1;
+  p.n_tiles = p.n_tiles_m;
+  p.k_main = a.cin / CK;
+  hp.res_chunks = RES ? a.cr / CK : 0;
+  p.k_res = (hp.res_chunks + 2) / 3;
+  hp.cpt = a.cin / CK;
+  hp.n_wtiles = 9 * hp.cpt + hp.res_chunks;
+  hp.stages = stages;
+  p.gamma = a.w.gamma;
+  p.beta = a.w.beta;
+  p.wp_rgb = a.w.wp_f32;
+  p.canvas = a.canvas;
+  p.canvas_stride = a.canvas_stride;
+  p.tiles3 = a.tiles3;
+  p.y = static_cast<__nv_bfloat16*>(a.y);
+  p.y_cs = a.y_cs;
+  p.y_co = a.y_co;
+  p.err = a.err;
+  const size_t smem = (size_t)hp.n_wtiles * Cfg::kWTileBytes + (size_t)stages * Cfg::kStageBytes + kHaloSmemExtra;
+  if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
+  auto kern = k_conv_tc_halo<BN, CK, RES>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloSmemMax);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
+  kern<<<grid, kThreadsTC, smem, st>>>(mA, mB, mA2, mB2, hp);
+  return cudaGetLastError();
+}
+
+// dx-in-N variant: resident weights + one 10 x 16 box per stage
+int dxn_wbytes(int cin, int cout, int cr, int ck) { return (9 * (cin / ck) + cr / ck) * cout * ck * 2; }
+int dxn_stages(int cin, int cout, int cr, int ck) {
+  if (cin % ck || cr % ck) return 0;
+  const long long st = (kHaloSmemMax - (long long)dxn_wbytes(cin, cout, cr, ck) - kHaloSmemExtra) /
+                       ((long long)kHBoxPix * ck * 2);
+  return st < 2 ? 0 : (int)(st > 12 ? 12 : st);
+}
+bool dxn_ok(int R, int cout, int cin, int cr) {
+  if (R < 16 || R % kHTH || (cout != 32 && cout != 64)) return false;
+  return dxn_stages(cin, cout, cr, 32) >= 2;
+}
+
+template <int CO, int CK, bool RES>
+cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
+  using Cfg = DxnCfg<CO, CK, RES>;
+  CUtensorMap mA, mB, mA2, mB2;
+  if (!map_act_box(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, kHTW, kHTH + 2)) return cudaErrorInvalidValue;
+  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, CO, CK)) return cudaErrorInvalidValue;
+  if (RES) {
+    if (!map_act_box(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK, kHTW, kHTH)) return cudaErrorInvalidValue;
+    if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, CO, CK)) return cudaErrorInvalidValue;
+  } else {
+    mA2 = mA;
+    mB2 = mB;
+  }
+  DxnParams hp{};
+  TCParams& p = hp.t;
+  p.B = a.B; p.R = a.R; p.cin = a.cin; p.cout = a.cout; p.cr = RES ? a.cr : 0;
+  p.res_mode = a.res_mode;
+  hp.tiles_w = (a.R + kXTW - 1) / kXTW;
+  hp.tiles_per_img = (a.R / kHTH) * hp.tiles_w;
+  p.n_tiles_m = a.B * hp.tiles_per_img;
+  p.n_tiles_n = 1;
+  p.n_tiles = p.n_tiles_m;
+  p.k_main = a.cin / CK;
+  hp.res_chunks = RES ? a.cr / CK : 0;
+  p.k_res = hp.res_chunks;
+  hp.cpt = a.cin / CK;
+  hp.stages = stages;
+  hp.wbytes = dxn_wbytes(a.cin, a.cout, RES ? a.cr : 0, CK);
+  p.gamma = a.w.gamma;
+  p.beta = a.w.beta;
+  p.wp_rgb = a.w.wp_f32;
+  p.canvas = a.canvas;
+  p.canvas_stride = a.canvas_stride;
+  p.tiles3 = a.tiles3;
+  p.y = static_cast<__nv_bfloat16*>(a.y);
+  p.y_cs = a.y_cs;
+  p.y_co = a.y_co;
+  p.err = a.err;
+  const size_t smem = (size_t)hp.wbytes + (size_t)stages * Cfg::kStageBytes + kHaloSmemExtra;
+  if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
+  auto kern = k_conv_tc_dxn<CO, CK, RES>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloSmemMax);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
+  kern<<<grid, kThreadsTC, smem, st>>>(mA, mB, mA2, mB2, hp);
+  return cudaGetLastError();
+}
+
+int pick_bn(int cout, bool res) {
+  const int cap = res ? 128 : 256;
+  return cout < cap ? cout : cap;
+}
+
+}  // namespace
+
+#if !OMNI_TC_F16
+bool conv_tc_supported(int R, int cin, int cout, int cr) {
+  if (cin % 32 == 0 && cr % 32 == 0 && halo_ok(R, cout, cin, cr)) return true;
+  if (cin % 32 == 0 && cr % 32 == 0 && R >= 64 && dxn_ok(R, cout, cin, cr)) return true;
+  if (cout > 512) return false;
+  if (!(R == 16 || R == 32 || R == 64 || (R >= 128 && R % 128 == 0))) return false;
+  if (cin % 32 || cr % 32 || cout % 32) return false;
+  const int bn = pick_bn(cout, cr > 0);
+  return bn % 32 == 0 && cout % bn == 0;
+}
+#endif
+
+namespace {
+cudaError_t check_tc_args(const ConvArgs& a, int cr) {
+  if (a.res_mode == RES_RGB && !a.w.wp_f32) return cudaErrorInvalidValue;
+  if ((a.x_co % 8) || (a.x_cs % 8) || (a.y_co % 8) || (a.y_cs % 8)) return cudaErrorInvalidValue;
+  if (cr && ((a.r_co % 8) || (a.r_cs % 8))) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.y) |
+       reinterpret_cast<uintptr_t>(a.w.w_bf16) | (cr ? reinterpret_cast<uintptr_t>(a.r) |
+                                                     reinterpret_cast<uintptr_t>(a.w.wp_bf16) : 0)) % 16)
+    return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+bool pertap_ok(int R, int cin, int cout, int cr, int bn, int ck) {
+  if (!(R == 16 || R == 32 || R == 64 || (R >= 128 && R % 128 == 0))) return false;
+  if (cin % ck || cr % ck || bn > cout || cout % bn || cout > 512) return false;
+  if (cr > 0 && bn > 128) return false;
+  return bn == 32 || bn == 64 || bn == 128 || bn == 256;
+}
+}  // namespace
+
+#if !OMNI_TC_F16
+int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
+  int n = 0;
+  if (dxn_ok(R, cout, cin, cr))
+    for (int ck = 32; ck <= 64; ck *= 2) {
+      const int stg = dxn_stages(cin, cout, cr, ck);
+      if (stg >= 2 && n < max) out[n++] = TcConfig{2, cout, ck, stg};
+    }
+  if (halo_ok(R, cout, cin, cr))
+    for (int ck = 32; ck <= 64; ck *= 2) {
+      const int stg = halo_stages(cin, cout, cr, ck);
+      if (stg >= 2 && n < max) out[n++] = TcConfig{1, cout, ck, stg};
+    }
+  for (int bn = 32; bn <= 256; bn *= 2)
+    for (int ck = 32; ck <= 64; ck *= 2)
+      if (pertap_ok(R, cin, cout, cr, bn, ck) && n < max) out[n++] = TcConfig{0, bn, ck, 0};
+  return n;
+}
+
+TcConfig tc_default(int R, int cin, int cout, int cr) {
+  // measured: the dx-in-N kernel wins when a tile carries at least 64 input
+  // channels of work; with 32 its epilogue dominates and the 3-box kernel wins
+  if (R >= 64 && cin >= 64 && dxn_ok(R, cout, cin, cr)) {
+    int ck = 32, stg = dxn_stages(cin, cout, cr, 32);
+    const int stg64 = dxn_stages(cin, cout, cr, 64);
+    if (stg64 >= 4) { ck = 64; stg = stg64; }
+    return TcConfig{2, cout, ck, stg};
+  }
+  if (halo_ok(R, cout, cin, cr)) {
+    int ck = 32, stg = halo_stages(cin, cout, cr, 32);
+    const int stg64 = halo_stages(cin, cout, cr, 64);
+    if (stg64 >= 3) { ck = 64; stg = stg64; }
+    return TcConfig{1, cout, ck, stg};
+  }
+  const bool res = cr > 0;
+  return TcConfig{0, pick_bn(cout, res), (cin % 64 == 0 && (!res || cr % 64 == 0)) ? 64 : 32, 0};
+}
+
+#endif
+
+#if OMNI_TC_F16
+cudaError_t launch_conv_tc_cfg_f16(const ConvArgs& a, const TcConfig& c, cudaStream_t st) {
+#else
+cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaStream_t st) {
+#endif
+  const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
+  cudaError_t e = check_tc_args(a, cr);
+  if (e != cudaSuccess) return e;
+  const bool res = cr > 0;
+  if (c.kind == 2) {
+    if (!dxn_ok(a.R, a.cout, a.cin, cr) || c.bn != a.cout || c.stages < 2 ||
+        c.stages > dxn_stages(a.cin, a.cout, cr, c.ck))
+      return cudaErrorInvalidValue;
+#define OMNI_DXN(CO_, CK_, RES_) \
+    if (c.bn == CO_ && c.ck == CK_ && res == RES_) return launch_dxn<CO_, CK_, RES_>(a, st, c.stages);
+    OMNI_DXN(32, 32, false) OMNI_DXN(32, 32, true) OMNI_DXN(32, 64, false) OMNI_DXN(32, 64, true)
+    OMNI_DXN(64, 32, false) OMNI_DXN(64, 32, true) OMNI_DXN(64, 64, false) OMNI_DXN(64, 64, true)
+#undef OMNI_DXN
+    return cudaErrorInvalidValue;
+  }
+  if (c.kind == 1) {
+    if (!halo_ok(a.R, a.cout, a.cin, cr) || c.bn != a.cout || c.stages < 2 ||
+        c.stages > halo_stages(a.cin, a.cout, cr, c.ck))
+      return cudaErrorInvalidValue;
+#define OMNI_HALO(BN_, CK_, RES_) \
+    if (c.bn == BN_ && c.ck == CK_ && res == RES_) return launch_halo<BN_, CK_, RES_>(a, st, c.stages);
+    OMNI_HALO(32, 32, false) OMNI_HALO(32, 32, true) OMNI_HALO(32, 64, false) OMNI_HALO(32, 64, true)
+    OMNI_HALO(64, 32, false) OMNI_HALO(64, 32, true) OMNI_HALO(64, 64, false) OMNI_HALO(64, 64, true)
+#undef OMNI_HALO
+    return cudaErrorInvalidValue;
+  }
+  if (!pertap_ok(a.R, a.cin, a.cout, cr, c.bn, c.ck)) return cudaErrorInvalidValue;
+#define OMNI_TC(BN_, CK_, RES_) \
+  if (c.bn == BN_ && c.ck == CK_ && res == RES_) return launch_t<BN_, CK_, RES_>(a, st);
+  OMNI_TC(32, 32, false) OMNI_TC(32, 32, true) OMNI_TC(32, 64, false) OMNI_TC(32, 64, true)
+  OMNI_TC(64, 32, false) OMNI_TC(64, 32, true) OMNI_TC(64, 64, false) OMNI_TC(64, 64, true)
+  OMNI_TC(128, 32, false) OMNI_TC(128, 32, true) OMNI_TC(128, 64, false) OMNI_TC(128, 64, true)
+  OMNI_TC(256, 32, false) OMNI_TC(256, 64, false)
+#undef OMNI_TC
+  return cudaErrorInvalidValue;
+}
+
+#if !OMNI_TC_F16
+cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_t st) {
+  return a.f16 ? launch_conv_tc_cfg_f16(a, c, st) : launch_conv_tc_cfg_bf16(a, c, st);
+}
+
+cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st) {
+  const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
+  if (!conv_tc_supported(a.R, a.cin, a.cout, cr)) return cudaErrorInvalidValue;
+  return launch_conv_tc_cfg(a, tc_default(a.R, a.cin, a.cout, cr), st);
+}
+#endif
+
+}  // namespace omni

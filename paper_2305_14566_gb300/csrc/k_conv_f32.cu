@@ -7,6 +7,8 @@
 //   out = ReLU(g2 * conv3x3(ReLU(g1 * conv3x3(x) + b1)) + b2 + wp . x)
 // The SIMT implicit GEMM below computes one such convolution with the norm,
 // the 1x1 residual projection and the ReLU fused into its epilogue.
+#include <cuda_fp16.h>
+
 #include "omni_internal.cuh"
 
 namespace omni {
@@ -39,6 +41,26 @@ template <> struct Vec8<__nv_bfloat16> {
     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&q);
 #pragma unroll
     for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4*>(p) = q;
+  }
+};
+
+template <> struct Vec8<__half> {
+  static __device__ __forceinline__ void load(const __half* p, float v[8]) {
+    uint4 q = *reinterpret_cast<const uint4*>(p);
+    const __half2* h = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __half22float2(h[i]);
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+  static __device__ __forceinline__ void store(__half* p, const float v[8]) {
+    uint4 q;
+    __half2* h = reinterpret_cast<__half2*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
     *reinterpret_cast<uint4*>(p) = q;
   }
 };
@@ -342,7 +364,7 @@ __global__ void k_gap(int R, int C, const T* __restrict__ x, int x_cs, int x_co,
   float s = 0.f;
   for (int p = 0; p < R * R; ++p) {
     if constexpr (sizeof(T) == 4) s += (float)base[(long long)p * x_cs];
-    else s += __bfloat162float(base[(long long)p * x_cs]);
+    else s += static_cast<float>(base[(long long)p * x_cs]);
   }
   g[(long long)b * C + c] = s / (float)(R * R);
 }
@@ -371,7 +393,8 @@ cudaError_t first_p(const ConvArgs& a, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_conv_first(const ConvArgs& a, int precision, cudaStream_t st) {
-  return precision == OMNI_FP32 ? first_p<float>(a, st) : first_p<__nv_bfloat16>(a, st);
+  if (precision == OMNI_FP32) return first_p<float>(a, st);
+  return precision == OMNI_FP16 ? first_p<__half>(a, st) : first_p<__nv_bfloat16>(a, st);
 }
 
 cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
@@ -397,6 +420,8 @@ cudaError_t launch_maxpool(int precision, int B, int R, int C, const void* x, in
   dim3 grid((n + 127) / 128, R / 2, B);
   if (precision == OMNI_FP32)
     k_maxpool<float><<<grid, 128, 0, st>>>(R, C, (const float*)x, x_cs, x_co, (float*)y, y_cs, y_co);
+  else if (precision == OMNI_FP16)
+    k_maxpool<__half><<<grid, 128, 0, st>>>(R, C, (const __half*)x, x_cs, x_co, (__half*)y, y_cs, y_co);
   else
     k_maxpool<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co,
                                                    (__nv_bfloat16*)y, y_cs, y_co);
@@ -409,6 +434,8 @@ cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, i
   dim3 grid((n + 127) / 128, R, B);
   if (precision == OMNI_FP32)
     k_upsample<float><<<grid, 128, 0, st>>>(R, C, (const float*)x, x_cs, x_co, (float*)y, y_cs, y_co);
+  else if (precision == OMNI_FP16)
+    k_upsample<__half><<<grid, 128, 0, st>>>(R, C, (const __half*)x, x_cs, x_co, (__half*)y, y_cs, y_co);
   else
     k_upsample<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co,
                                                     (__nv_bfloat16*)y, y_cs, y_co);
@@ -420,6 +447,8 @@ cudaError_t launch_gap(int precision, int B, int R, int C, const void* x, int x_
   dim3 grid(B, (C + 127) / 128);
   if (precision == OMNI_FP32)
     k_gap<float><<<grid, 128, 0, st>>>(R, C, (const float*)x, x_cs, x_co, g);
+  else if (precision == OMNI_FP16)
+    k_gap<__half><<<grid, 128, 0, st>>>(R, C, (const __half*)x, x_cs, x_co, g);
   else
     k_gap<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co, g);
   return cudaGetLastError();

@@ -7,6 +7,8 @@
 // class of the scale (the controller weights are read once per batch, not once
 // per pixel block), and k_head runs the pre-head and all heads of the scale
 // over the tile pixels, writing FP32 logits.
+#include <cuda_fp16.h>
+
 #include "omni_internal.cuh"
 
 namespace omni {
@@ -51,6 +53,19 @@ template <> struct Load8<__nv_bfloat16> {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const float2 f = __bfloat1622float2(h[i]);
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
+};
+
+template <> struct Load8<__half> {
+  static __device__ __forceinline__ void f(const __half* p, float v[8]) {
+    const uint4 q = *reinterpret_cast<const uint4*>(p);
+    const __half2* h = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __half22float2(h[i]);
       v[2 * i] = f.x;
       v[2 * i + 1] = f.y;
     }
@@ -139,7 +154,8 @@ cudaError_t launch_controller(const HeadArgs& a, cudaStream_t st) {
 
 cudaError_t launch_head(const HeadArgs& a, cudaStream_t st) {
   if (a.n_cls_here < 1 || a.n_cls_here > OMNI_MAX_CLASSES) return cudaErrorInvalidValue;
-  return a.precision == OMNI_FP32 ? head_t<float>(a, st) : head_t<__nv_bfloat16>(a, st);
+  if (a.precision == OMNI_FP32) return head_t<float>(a, st);
+  return a.precision == OMNI_FP16 ? head_t<__half>(a, st) : head_t<__nv_bfloat16>(a, st);
 }
 
 }  // namespace omni

@@ -80,6 +80,7 @@ struct ConvArgs {
   // y2_cs); used by the backward's recomputation
   int raw;
   void* y2; int y2_cs;
+  int f16;                                // tensor-core operands: 0 BF16, 1 FP16
 };
 
 // k_conv_f32.cu (plain FP32 path + precision-generic helpers)
@@ -102,6 +103,8 @@ struct TcConfig {
 };
 cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st);
 cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
+cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
+cudaError_t launch_conv_tc_cfg_f16(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
 int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max);
 TcConfig tc_default(int R, int cin, int cout, int cr);
 bool conv_tc_supported(int R, int cin, int cout, int cr);

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "omni_internal.cuh"
 
 using namespace omni;
@@ -93,7 +95,8 @@ std::string validate(const omni_config& c) {
   if (c.n_classes < 1 || c.n_classes > OMNI_MAX_CLASSES) return "n_classes must be 1..16";
   for (int k = 0; k < c.n_classes; ++k)
     if (c.class_scale[k] < 0 || c.class_scale[k] >= c.n_scales) return "class_scale out of range";
-  if (c.precision != OMNI_FP32 && c.precision != OMNI_BF16) return "precision must be FP32 or BF16";
+  if (c.precision != OMNI_FP32 && c.precision != OMNI_BF16 && c.precision != OMNI_FP16)
+    return "precision must be FP32, BF16 or FP16";
   if (c.stitch_mode != OMNI_STITCH_AVG && c.stitch_mode != OMNI_STITCH_VOTE) return "bad stitch_mode";
   if (c.median_k < 1 || c.median_k % 2 == 0 || c.median_k > 255) return "median_k must be odd, 1..255";
   if (c.max_batch < 1 || c.max_batch > 4096) return "max_batch must be 1..4096";
@@ -227,6 +230,16 @@ uint16_t to_bf16(float f) {
   return (uint16_t)(u >> 16);
 }
 
+uint16_t to_fp16(float f) {
+  const __half h = __float2half_rn(f);
+  uint16_t u;
+  memcpy(&u, &h, 2);
+  return u;
+}
+
+// 16-bit operand bits of the tensor-core path (BF16 or FP16)
+uint16_t to_lp(float f, bool f16) { return f16 ? to_fp16(f) : to_bf16(f); }
+
 // ------------------------------------------------------------------ timing helpers
 struct Rec {
   omni_ctx* c;
@@ -315,6 +328,7 @@ int64_t omni_weights_count(const omni_config* cfg) {
 omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats) {
   if (!ctx || !blob) return fail(ctx, OMNI_EINVAL, "null argument");
   const omni_config& c = ctx->cfg;
+  const bool f16 = c.precision == OMNI_FP16;
   int64_t need = omni_weights_count(&c);
   if (n_floats != need)
     return fail(ctx, OMNI_EWEIGHTS, "weights blob has " + std::to_string(n_floats) +
@@ -348,7 +362,7 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
         for (int tap = 0; tap < 9; ++tap) {
           float v = src[((size_t)o * cin + ci) * 9 + tap];
           w32[((size_t)tap * cin + ci) * cout + o] = v;
-          w16[(size_t)o * 9 * cin + (size_t)tap * cin + ci] = to_bf16(v);
+          w16[(size_t)o * 9 * cin + (size_t)tap * cin + ci] = to_lp(v, f16);
         }
     src += (size_t)cout * cin * 9;
     memcpy(host.data() + q.g, src, cout * 4);
@@ -367,7 +381,7 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
       for (int ci = 0; ci < cproj; ++ci) {
         float v = src[(size_t)o * cproj + ci];
         wp32[(size_t)ci * q.cout + o] = v;
-        wp16[(size_t)o * cproj + ci] = to_bf16(v);
+        wp16[(size_t)o * cproj + ci] = to_lp(v, f16);
       }
     src += (size_t)q.cout * cproj;
     q.cproj = cproj;
@@ -607,6 +621,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   base.canvas_stride = cstride;
   base.tiles3 = tiles3;
   base.err = ctx->d_err;
+  base.f16 = c.precision == OMNI_FP16 ? 1 : 0;
   // encoder output location of level l
   auto enc_out = [&](int l, void*& ptr, int& cs, int& co) {
     if (l < L - 1) { ptr = ws + p.cat[l]; cs = 3 * C(l); co = 2 * C(l); }
@@ -949,8 +964,9 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
   if (repeat < 1) return OMNI_EINVAL;
   if (!x || !y || !w_host || !g_host || !b_host || B <= 0 || R <= 0 || cin <= 0 || cout <= 0) return OMNI_EINVAL;
   if (cin % 8 || cout % 8 || (r && (cr <= 0 || cr % 8 || !wp_host))) return OMNI_EINVAL;
-  if (precision != OMNI_FP32 && precision != OMNI_BF16) return OMNI_EINVAL;
-  if (precision == OMNI_BF16 && !conv_tc_supported(R, cin, cout, r ? cr : 0)) return OMNI_EINVAL;
+  if (precision != OMNI_FP32 && precision != OMNI_BF16 && precision != OMNI_FP16) return OMNI_EINVAL;
+  const bool f16 = precision == OMNI_FP16;
+  if (precision != OMNI_FP32 && !conv_tc_supported(R, cin, cout, r ? cr : 0)) return OMNI_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   size_t n9 = (size_t)9 * cin * cout, np = r ? (size_t)cr * cout : 0;
   std::vector<float> w32(n9), wp32(np);
@@ -960,13 +976,13 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
       for (int tap = 0; tap < 9; ++tap) {
         float v = w_host[((size_t)o * cin + ci) * 9 + tap];
         w32[((size_t)tap * cin + ci) * cout + o] = v;
-        w16[(size_t)o * 9 * cin + (size_t)tap * cin + ci] = to_bf16(v);
+        w16[(size_t)o * 9 * cin + (size_t)tap * cin + ci] = to_lp(v, f16);
       }
   for (int o = 0; o < cout && r; ++o)
     for (int ci = 0; ci < cr; ++ci) {
       float v = wp_host[(size_t)o * cr + ci];
       wp32[(size_t)ci * cout + o] = v;
-      wp16[(size_t)o * cr + ci] = to_bf16(v);
+      wp16[(size_t)o * cr + ci] = to_lp(v, f16);
     }
   size_t off = 0;
   size_t o32 = take(off, n9 * 4), o16 = take(off, n9 * 2), op32 = take(off, np * 4 + 4),
@@ -1002,6 +1018,7 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
     a.w.gamma = reinterpret_cast<float*>(d + og);
     a.w.beta = reinterpret_cast<float*>(d + ob);
     a.err = derr;
+    a.f16 = f16 ? 1 : 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms_per_launch) {
       cudaEventCreate(&e0);
