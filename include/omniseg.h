@@ -247,6 +247,20 @@ int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows);
  * default stream (NULL), which cannot be captured: pass a created stream. */
 omni_status omni_set_graphs(omni_ctx* ctx, int32_t enabled);
 
+/* Epilogue fusion (tensor-core contexts; on by default).  When enabled, the
+ * second conv of encoder levels 0..L-2 also writes the 2x2 max-pooled input
+ * of the next level (the pooling step of the encoder, Sec. 2.2) from its
+ * epilogue, and the last decoder conv runs the pre-head and the dynamic heads
+ * of the tile's classes (Sec. 2.2; at most two classes per scale) in its
+ * epilogue, writing the FP32 tile logits directly; its BF16
+ * output is then not stored.  Fusion applies only where the autotuned kernel
+ * supports it (the small-N and dx-in-N variants for pooling, the small-N
+ * variant for the head); elsewhere the separate kernels run.  With the head
+ * fused, the pre-head reads the FP32 epilogue value instead of its BF16
+ * rounding, so logits differ from the unfused path by that rounding only.
+ * Disabling is for testing and comparison. */
+omni_status omni_set_fusion(omni_ctx* ctx, int32_t enabled);
+
 /* Per-launch device times (ms) of the current timing record, with each
  * launch's kind (as above), tag and algorithmic
  * work (FLOPs for convolutions, else 0).  Tags: conv of encoder level l =

@@ -211,6 +211,10 @@ class Segmenter:
     def set_graphs(self, on: bool = True):
         L.check(self.lib.omni_set_graphs(self.ctx, int(on)), self.ctx)
 
+    def set_fusion(self, on: bool = True):
+        """Epilogue fusion of the encoder max-pool and of the pre-head + heads (default on)."""
+        L.check(self.lib.omni_set_fusion(self.ctx, int(on)), self.ctx)
+
     def tuned(self):
         """[(R, cin, cout, cr, res_kind, batch, kind, N tile, chunk, stages)] chosen by the autotuner."""
         n = self.lib.omni_get_tuned(self.ctx, None, 0)

@@ -65,9 +65,16 @@ struct TCParams {
   const uint8_t* canvas;
   long long canvas_stride;
   const int32_t* tiles3;
-  __nv_bfloat16* y;
+  __nv_bfloat16* y;                  // null: output not stored (fused head)
   int y_cs, y_co;
   unsigned* err;
+  __nv_bfloat16* pool;               // fused 2x2 max-pool output (small-N kernels) or null
+  int pool_cs;
+  const float* theta;                // fused pre-head + dynamic heads (kind 1) or null
+  const float* wh;
+  const float* bh;
+  float* logits;
+  int slot0, ncls;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -195,6 +202,101 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 
 __device__ __forceinline__ float norm_u8(uint8_t u) { return 2.0f * (float)u / 255.0f - 1.0f; }
 
+// Dynamic head of one class on the pre-head feature h0 (already through its
+// ReLU): logit = W3 ReLU(W2 ReLU(W1 h0 + b1) + b2) + b3, with theta laid out
+// as W1 (8x8, out-major), W2 (8x8), W3 (8), b1 (8), b2 (8), b3 (1).
+__device__ __forceinline__ float dyn_head(const float* th, const float h0[8]) {
+  float h1[8], h2[8];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    float s = th[136 + o];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s = fmaf(th[o * 8 + c], h0[c], s);
+    h1[o] = fmaxf(s, 0.f);
+  }
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    float s = th[144 + o];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s = fmaf(th[64 + o * 8 + c], h1[c], s);
+    h2[o] = fmaxf(s, 0.f);
+  }
+  float s = th[152];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s = fmaf(th[128 + c], h2[c], s);
+  return s;
+}
+
+// 2x2 max of a pixel's 16 channel values with the pixels of lanes lane^dxl
+// (horizontal neighbour) and lane^16 (next tile row), rounded and packed
+__device__ __forceinline__ void pool_pack(const float v[16], bool down1, uint32_t out[8]) {
+  float m[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float h = down1 ? __shfl_down_sync(0xffffffffu, v[j], 1) : __shfl_xor_sync(0xffffffffu, v[j], 1);
+    const float a = fmaxf(v[j], h);
+    m[j] = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 16));
+  }
+#pragma unroll
+  for (int j = 0; j < 16; j += 2) out[j / 2] = pack2(m[j], m[j + 1]);
+}
+
+// Accumulator ring in TMEM: four buffers where they fit in the 512 columns,
+// else two, so the MMA warp can run up to three tiles ahead of the epilogue
+// (the per-tile handoff latency, not the MMA or the copies, bounds the small
+// layers); allocations are a power of two of at least 32 columns.
+constexpr int kMaxTmemBufs = 4;
+__host__ __device__ constexpr int tmem_bufs(int buf_cols) { return 4 * buf_cols <= 512 ? 4 : 2; }
+__host__ __device__ constexpr int tmem_alloc_cols(int cols) {
+  return cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+}
+
+// Slot and phase parity of a pipeline ring with a runtime number of stages,
+// advanced without division: the producer and MMA roles run on one thread
+// each, where a division per step lengthens the whole pipeline.
+struct StageRing {
+  int s = 0;
+  uint32_t ph = 0;
+  bool lapped = false;     // every slot has been used once (waits on `empty` begin)
+  __device__ __forceinline__ void next(int n) {
+    if (++s == n) {
+      s = 0;
+      ph ^= 1u;
+      lapped = true;
+    }
+  }
+};
+
+// This CTA's tiles t = blockIdx.x + i * gridDim.x of an images x ny x nx tile
+// grid, kept as (img, ty, tx) and stepped by a mixed-radix add.
+struct TileWalk {
+  int t, img, ty, tx;
+  int s_img, s_ty, s_tx, ny, nx;
+  __device__ __forceinline__ void init(int ny_, int nx_) {
+    ny = ny_;
+    nx = nx_;
+    const int per = ny * nx;
+    t = blockIdx.x;
+    img = t / per;
+    ty = (t - img * per) / nx;
+    tx = t - img * per - ty * nx;
+    const int st = gridDim.x;
+    s_img = st / per;
+    s_ty = (st - s_img * per) / nx;
+    s_tx = st - s_img * per - s_ty * nx;
+  }
+  __device__ __forceinline__ void next() {
+    t += gridDim.x;
+    tx += s_tx;
+    int c = tx >= nx ? 1 : 0;
+    tx -= c * nx;
+    ty += s_ty + c;
+    c = ty >= ny ? 1 : 0;
+    ty -= c * ny;
+    img += s_img + c;
+  }
+};
+
 template <int BN, int CK, bool RES>
 struct TCCfg {
   static constexpr int kABytes = kBM * CK * 2;
@@ -203,7 +305,8 @@ struct TCCfg {
   static constexpr int kStages0 = (kSmemBudget - 2048) / kStageBytes;
   static constexpr int kStages = kStages0 > 16 ? 16 : kStages0;
   static constexpr int kBufCols = RES ? 2 * BN : BN;     // TMEM columns per accumulator buffer
-  static constexpr int kTmemCols = 2 * kBufCols;          // double buffered
+  static constexpr int kBufs = tmem_bufs(kBufCols);       // accumulator ring depth
+  static constexpr int kTmemCols = tmem_alloc_cols(kBufs * kBufCols);
   static constexpr int kSW = CK * 2;                      // row bytes = swizzle span
   static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*align*/ +
                                   2 * 512 * 4 /*gamma, beta*/;
@@ -223,10 +326,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)ST * Cfg::kStageBytes);
   uint64_t* full = bars;                 // [ST]
   uint64_t* empty = bars + ST;           // [ST]
-  uint64_t* tfull = bars + 2 * ST;       // [2]
-  uint64_t* tempty = bars + 2 * ST + 2;  // [2]
-  uint64_t* drain = bars + 2 * ST + 4;   // [1]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * ST + 5);
+  uint64_t* tfull = bars + 2 * ST;                      // [kMaxTmemBufs]
+  uint64_t* tempty = bars + 2 * ST + kMaxTmemBufs;      // [kMaxTmemBufs]
+  uint64_t* drain = bars + 2 * ST + 2 * kMaxTmemBufs;   // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * ST + 2 * kMaxTmemBufs + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* sg = reinterpret_cast<float*>(smem + (size_t)ST * Cfg::kStageBytes + 1024);   // gamma[cout]
   float* sb = sg + 512;                                                                // beta[cout]
@@ -241,7 +344,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < Cfg::kBufs; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
       mbar_init(smem_u32(&tempty[b]), kEpiWarps);
     }
@@ -268,15 +371,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (lane == 0) {
       // ---------------------------------------------------------------- producer
       int it = 0;
+      StageRing ring;
       bool ok = true;
+      const int cpt = p.cin / CK;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
         const int mt = tile / p.n_tiles_n, nt = tile % p.n_tiles_n;
         const int m0 = mt * kBM;
         const int img = m0 / RR, rem = m0 % RR;
         const int h0 = rem / p.R, w0 = rem % p.R;
-        for (int k = 0; k < k_total; ++k, ++it) {
-          const int s = it % ST;
-          if (it >= ST && !mbar_wait(smem_u32(&empty[s]), ((it / ST) & 1) ^ 1, abort_flag, p.err)) {
+        int cc = 0, tdx = 0, tdy = 0;        // channel chunk and tap of the main segment
+        for (int k = 0; k < k_total; ++k, ++it, ring.next(ST)) {
+          const int s = ring.s;
+          if (ring.lapped && !mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
             ok = false;
             break;
           }
@@ -285,10 +391,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           const uint32_t da = smem_u32(sA + (size_t)s * Cfg::kABytes);
           const uint32_t db = smem_u32(sB + (size_t)s * Cfg::kBBytes);
           if (k < p.k_main) {
-            const int cpt = p.cin / CK;
-            const int tap = k / cpt, c0 = (k % cpt) * CK;
-            tma_load_4d(da, &mapA, fb, c0, w0 + tap % 3 - 1, h0 + tap / 3 - 1, img);
-            tma_load_2d(db, &mapB, fb, tap * p.cin + c0, nt * BN);
+            const int c0 = cc * CK;
+            tma_load_4d(da, &mapA, fb, c0, w0 + tdx - 1, h0 + tdy - 1, img);
+            tma_load_2d(db, &mapB, fb, (tdy * 3 + tdx) * p.cin + c0, nt * BN);
+            if (++cc == cpt) {
+              cc = 0;
+              if (++tdx == 3) {
+                tdx = 0;
+                ++tdy;
+              }
+            }
           } else {
             const int c0 = (k - p.k_main) * CK;
             tma_load_4d(da, &mapA2, fb, c0, w0, h0, img);
@@ -306,10 +418,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       constexpr uint32_t idesc = idesc_bf16(BN);
       const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
       const uint64_t b_desc0 = smem_desc(smem_u32(sB), Cfg::kSW);
-      int it = 0, tcount = 0;
+      int tcount = 0;
+      StageRing ring;
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
-        const int buf = tcount & 1, use = tcount >> 1;
+        const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
         if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
           ok = false;
           break;
@@ -317,9 +430,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         tc_fence_after();
         const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
         const uint32_t acc1 = acc0 + BN;
-        for (int k = 0; k < k_total; ++k, ++it) {
-          const int s = it % ST;
-          if (!mbar_wait(smem_u32(&full[s]), (it / ST) & 1, abort_flag, p.err)) {
+        for (int k = 0; k < k_total; ++k, ring.next(ST)) {
+          const int s = ring.s;
+          if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
             ok = false;
             break;
           }
@@ -349,7 +462,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int c_beg = ((warp - 2) >> 2) * (BN / 2), c_end = c_beg + BN / 2;
     int tcount = 0;
     for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
-      const int buf = tcount & 1, use = tcount >> 1;
+      const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
       // every lane waits; the vote keeps the warp converged for tcgen05.ld
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
@@ -426,7 +539,8 @@ struct HaloCfg {
   static constexpr int kStageBytes = 3 * kBoxBytes;
   static constexpr int kWTileBytes = BN * CK * 2;
   static constexpr int kBufCols = RES ? 2 * BN : BN;
-  static constexpr int kTmemCols = 2 * kBufCols;
+  static constexpr int kBufs = tmem_bufs(kBufCols);
+  static constexpr int kTmemCols = tmem_alloc_cols(kBufs * kBufCols);
   static constexpr int kSW = CK * 2;
 };
 
@@ -452,17 +566,21 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * Cfg::kStageBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + ST;
-  uint64_t* tfull = bars + 2 * ST;
-  uint64_t* tempty = bars + 2 * ST + 2;
-  uint64_t* drain = bars + 2 * ST + 4;
-  uint64_t* wbar = bars + 2 * ST + 5;
-  float* sg = reinterpret_cast<float*>(bars + 2 * ST + 6);    // gamma[BN]
+  uint64_t* tfull = bars + 2 * ST;                      // [kMaxTmemBufs]
+  uint64_t* tempty = bars + 2 * ST + kMaxTmemBufs;      // [kMaxTmemBufs]
+  uint64_t* drain = bars + 2 * ST + 2 * kMaxTmemBufs;
+  uint64_t* wbar = bars + 2 * ST + 2 * kMaxTmemBufs + 1;
+  float* sg = reinterpret_cast<float*>(bars + 2 * ST + 2 * kMaxTmemBufs + 2);    // gamma[BN]
   float* sb = sg + BN;                                          // beta[BN]
   float* swp = sb + BN;                                         // wp_rgb[3][BN]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(swp + 3 * BN);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* swh = reinterpret_cast<float*>(tmem_slot + 4);             // fused head: wh[8][BN]
+  float* sbh = swh + kHeadCh * BN;                                  // bh[8]
+  float* sthe = sbh + kHeadCh;                                      // theta copy per epilogue warp
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool fuse_head = p.theta != nullptr;
   for (int i = threadIdx.x; i < BN; i += blockDim.x) {
     sg[i] = p.gamma[i];
     sb[i] = p.beta[i];
@@ -472,14 +590,19 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       swp[2 * BN + i] = p.wp_rgb[2 * p.cout + i];
     }
   }
+  if (fuse_head) {
+    for (int i = threadIdx.x; i < kHeadCh * BN; i += blockDim.x) swh[i] = p.wh[i];
+    if (threadIdx.x < kHeadCh) sbh[threadIdx.x] = p.bh[threadIdx.x];
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < Cfg::kBufs; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
-      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+      // fused head: one warpgroup per TMEM buffer
+      mbar_init(smem_u32(&tempty[b]), fuse_head ? kEpiWarps / 2 : kEpiWarps);
     }
     mbar_init(smem_u32(drain), 1);
     mbar_init(smem_u32(wbar), 1);
@@ -513,13 +636,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       for (int r = 0; r < hp.res_chunks; ++r)
         tma_load_2d(smem_u32(sW + (size_t)(9 * hp.cpt + r) * Cfg::kWTileBytes), &mapB2, wb, r * CK, 0);
       int it = 0;
+      StageRing ring;
+      TileWalk tw;
+      tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
       bool ok = true;
-      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-        const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
-        const int h0 = (rem / hp.tiles_w) * kHTH, w0 = (rem % hp.tiles_w) * kHTW;
-        for (int k = 0; k < k_total; ++k, ++it) {
-          const int s = it % ST;
-          if (it >= ST && !mbar_wait(smem_u32(&empty[s]), ((it / ST) & 1) ^ 1, abort_flag, p.err)) {
+      for (; tw.t < p.n_tiles && ok; tw.next()) {
+        const int img = tw.img;
+        const int h0 = tw.ty * kHTH, w0 = tw.tx * kHTW;
+        for (int k = 0; k < k_total; ++k, ++it, ring.next(ST)) {
+          const int s = ring.s;
+          if (ring.lapped && !mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
             ok = false;
             break;
           }
@@ -551,9 +677,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       const uint64_t b_desc0 = smem_desc(smem_u32(sW), Cfg::kSW);
       const uint64_t b_tap_step = (uint64_t)(hp.cpt * (Cfg::kWTileBytes >> 4));
       bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, p.err);
-      int it = 0, tcount = 0;
+      int tcount = 0;
+      StageRing ring;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
-        const int buf = tcount & 1, use = tcount >> 1;
+        const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
         if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
           ok = false;
           break;
@@ -561,9 +688,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         tc_fence_after();
         const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
         const uint32_t acc1 = acc0 + BN;
-        for (int k = 0; k < k_total; ++k, ++it) {
-          const int s = it % ST;
-          if (!mbar_wait(smem_u32(&full[s]), (it / ST) & 1, abort_flag, p.err)) {
+        for (int k = 0; k < k_total; ++k, ring.next(ST)) {
+          const int s = ring.s;
+          if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
             ok = false;
             break;
           }
@@ -603,18 +730,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
   } else {
     // ------------------------------------------------------------------ epilogue
-    const int q = warp & 3;
+    // Default: warps w and w+4 share TMEM lane quarter w%4 and split the
+    // columns.  Fused head: each warpgroup owns the TMEM buffers of one parity
+    // (alternate tiles) and reads every column, so a thread holds its pixel.
+    const int q = warp & 3, grp = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    const int c_beg = ((warp - 2) >> 2) * (BN / 2), c_end = c_beg + BN / 2;
+    const int c_beg = fuse_head ? 0 : grp * (BN / 2), c_end = fuse_head ? BN : c_beg + BN / 2;
+    const int Rh = p.R >> 1;
+    float* sth = sthe + (warp - 2) * (2 * kHeadParams);
+    int th_img = -1;
     int tcount = 0;
-    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
-      const int buf = tcount & 1, use = tcount >> 1;
+    TileWalk tw;
+    tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
+    for (; tw.t < p.n_tiles; tw.next(), ++tcount) {
+      const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
+      if (fuse_head && (buf & 1) != grp) continue;
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
-      const int hh = (rem / hp.tiles_w) * kHTH + row / kHTW;
-      const int ww = (rem % hp.tiles_w) * kHTW + row % kHTW;
+      const int img = tw.img;
+      const int hh = tw.ty * kHTH + row / kHTW;
+      const int ww = tw.tx * kHTW + row % kHTW;
       const long long m = (long long)img * RR + (long long)hh * p.R + ww;
       float v0 = 0.f, v1 = 0.f, v2 = 0.f;
       if (p.res_mode == RES_RGB) {
@@ -624,34 +760,66 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         v1 = norm_u8(px[1]);
         v2 = norm_u8(px[2]);
       }
-      __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
+      float h0[kHeadCh];
+#pragma unroll
+      for (int o = 0; o < kHeadCh; ++o) h0[o] = fuse_head ? sbh[o] : 0.f;
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
 #pragma unroll 1
       for (int c = c_beg; c < c_end; c += 16) {
-        float a[16], r[16];
+        float a[16], r[16], o16[16];
         tmem_ld16(tb + c, a);
         if constexpr (RES) tmem_ld16(tb + BN + c, r);
-        uint32_t packed[8];
 #pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-          float o[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int n = c + j + u;
-            float z = fmaf(sg[n], a[j + u], sb[n]);
-            if constexpr (RES) z += r[j + u];
-            if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[BN + n], v2 * swp[2 * BN + n]));
-            o[u] = fmaxf(z, 0.f);
-          }
-          packed[j / 2] = pack2(o[0], o[1]);
+        for (int j = 0; j < 16; ++j) {
+          const int n = c + j;
+          float z = fmaf(sg[n], a[j], sb[n]);
+          if constexpr (RES) z += r[j];
+          if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[BN + n], v2 * swp[2 * BN + n]));
+          o16[j] = fmaxf(z, 0.f);
         }
-        uint4* dst = reinterpret_cast<uint4*>(out + c);
-        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        if (p.y) {
+          uint32_t packed[8];
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) packed[j / 2] = pack2(o16[j], o16[j + 1]);
+          uint4* dst = reinterpret_cast<uint4*>(p.y + m * p.y_cs + p.y_co + c);
+          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+        if (p.pool) {
+          // lanes 0-15 / 16-31 hold tile rows 2k / 2k+1 (even row and column origins)
+          uint32_t pk[8];
+          pool_pack(o16, false, pk);
+          if ((lane & 17) == 0) {
+            uint4* dst = reinterpret_cast<uint4*>(
+                p.pool + (((long long)img * Rh + (hh >> 1)) * Rh + (ww >> 1)) * p.pool_cs + c);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          }
+        }
+        if (fuse_head) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaf(swh[o * BN + c + j], o16[j], h0[o]);
+        }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+      if (fuse_head) {
+        // the TMEM buffer is released; the heads run on registers and shared memory
+#pragma unroll
+        for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaxf(h0[o], 0.f);
+        if (img != th_img) {
+          __syncwarp();
+          const float* src = p.theta + (long long)img * p.ncls * kHeadParams;
+          for (int i = lane; i < p.ncls * kHeadParams; i += 32) sth[i] = src[i];
+          __syncwarp();
+          th_img = img;
+        }
+        float* lo = p.logits + (long long)(p.slot0 + img) * p.ncls * RR + (long long)hh * p.R + ww;
+        for (int ci = 0; ci < p.ncls; ++ci) lo[(long long)ci * RR] = dyn_head(sth + ci * kHeadParams, h0);
+      }
     }
   }
   __syncwarp();
@@ -684,7 +852,8 @@ struct DxnCfg {
   static constexpr int kWTileBytes = kN * CK * 2;          // 3 dx slices of cout x CK
   static constexpr int kRTileBytes = CO * CK * 2;          // projection weights
   static constexpr int kBufCols = RES ? kN + CO : kN;
-  static constexpr int kTmemCols = 2 * kBufCols <= 64 ? 64 : (2 * kBufCols <= 128 ? 128 : (2 * kBufCols <= 256 ? 256 : 512));
+  static constexpr int kBufs = tmem_bufs(kBufCols);
+  static constexpr int kTmemCols = tmem_alloc_cols(kBufs * kBufCols);
   static constexpr int kSW = CK * 2;
 };
 
@@ -711,11 +880,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * Cfg::kStageBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + ST;
-  uint64_t* tfull = bars + 2 * ST;
-  uint64_t* tempty = bars + 2 * ST + 2;
-  uint64_t* drain = bars + 2 * ST + 4;
-  uint64_t* wbar = bars + 2 * ST + 5;
-  float* sg = reinterpret_cast<float*>(bars + 2 * ST + 6);
+  uint64_t* tfull = bars + 2 * ST;                      // [kMaxTmemBufs]
+  uint64_t* tempty = bars + 2 * ST + kMaxTmemBufs;      // [kMaxTmemBufs]
+  uint64_t* drain = bars + 2 * ST + 2 * kMaxTmemBufs;
+  uint64_t* wbar = bars + 2 * ST + 2 * kMaxTmemBufs + 1;
+  float* sg = reinterpret_cast<float*>(bars + 2 * ST + 2 * kMaxTmemBufs + 2);
   float* sb = sg + CO;
   float* swp = sb + CO;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(swp + 3 * CO);
@@ -736,7 +905,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < Cfg::kBufs; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
       mbar_init(smem_u32(&tempty[b]), kEpiWarps);
     }
@@ -773,13 +942,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       for (int r = 0; r < hp.res_chunks; ++r)
         tma_load_2d(smem_u32(sR + (size_t)r * Cfg::kRTileBytes), &mapB2, wb, r * CK, 0);
       int it = 0;
+      StageRing ring;
+      TileWalk tw;
+      tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
       bool ok = true;
-      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-        const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
-        const int h0 = (rem / hp.tiles_w) * kHTH, w0 = (rem % hp.tiles_w) * kXTW;
-        for (int k = 0; k < k_total; ++k, ++it) {
-          const int s = it % ST;
-          if (it >= ST && !mbar_wait(smem_u32(&empty[s]), ((it / ST) & 1) ^ 1, abort_flag, p.err)) {
+      for (; tw.t < p.n_tiles && ok; tw.next()) {
+        const int img = tw.img;
+        const int h0 = tw.ty * kHTH, w0 = tw.tx * kXTW;
+        for (int k = 0; k < k_total; ++k, ++it, ring.next(ST)) {
+          const int s = ring.s;
+          if (ring.lapped && !mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
             ok = false;
             break;
           }
@@ -808,9 +980,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       const uint64_t r_desc0 = smem_desc(smem_u32(sR), Cfg::kSW);
       const uint64_t dy_step = (uint64_t)(hp.cpt * (Cfg::kWTileBytes >> 4));
       bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, p.err);
-      int it = 0, tcount = 0;
+      int tcount = 0;
+      StageRing ring;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
-        const int buf = tcount & 1, use = tcount >> 1;
+        const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
         if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
           ok = false;
           break;
@@ -818,9 +991,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         tc_fence_after();
         const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
         const uint32_t acc1 = acc0 + Cfg::kN;
-        for (int k = 0; k < k_total; ++k, ++it) {
-          const int s = it % ST;
-          if (!mbar_wait(smem_u32(&full[s]), (it / ST) & 1, abort_flag, p.err)) {
+        for (int k = 0; k < k_total; ++k, ring.next(ST)) {
+          const int s = ring.s;
+          if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
             ok = false;
             break;
           }
@@ -860,14 +1033,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int col = row % kHTW;                        // column inside the 16-lane row group
     const int co_beg = ((warp - 2) >> 2) * (CO / 2), co_end = co_beg + CO / 2;
     int tcount = 0;
-    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
-      const int buf = tcount & 1, use = tcount >> 1;
+    TileWalk tw;
+    tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
+    for (; tw.t < p.n_tiles; tw.next(), ++tcount) {
+      const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const int img = tile / hp.tiles_per_img, rem = tile % hp.tiles_per_img;
-      const int hh = (rem / hp.tiles_w) * kHTH + row / kHTW;
-      const int ww = (rem % hp.tiles_w) * kXTW + col - 1;           // this lane's pixel column
+      const int img = tw.img;
+      const int hh = tw.ty * kHTH + row / kHTW;
+      const int ww = tw.tx * kXTW + col - 1;                        // this lane's pixel column
       const bool writes = col >= 1 && col <= kXTW && ww < p.R;
       const long long m = (long long)img * RR + (long long)hh * p.R + (ww < 0 ? 0 : ww);
       float v0 = 0.f, v1 = 0.f, v2 = 0.f;
@@ -882,32 +1057,41 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
 #pragma unroll 1
       for (int c = co_beg; c < co_end; c += 16) {
-        float d0[16], d1[16], d2[16], r[16];
+        float d0[16], d1[16], d2[16], r[16], o16[16];
         tmem_ld16(tb + c, d0);                   // dx = 0 block
         tmem_ld16(tb + CO + c, d1);              // dx = 1 block
         tmem_ld16(tb + 2 * CO + c, d2);          // dx = 2 block
         if constexpr (RES) tmem_ld16(tb + Cfg::kN + c, r);
-        uint32_t packed[8];
 #pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-          float o[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int n = c + j + u;
-            // lane-1 holds the left neighbour's dx=0 sum, lane+1 the right's dx=2 sum
-            const float left = __shfl_up_sync(0xffffffffu, d0[j + u], 1);
-            const float right = __shfl_down_sync(0xffffffffu, d2[j + u], 1);
-            float z = fmaf(sg[n], left + d1[j + u] + right, sb[n]);
-            if constexpr (RES) z += r[j + u];
-            if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[CO + n], v2 * swp[2 * CO + n]));
-            o[u] = fmaxf(z, 0.f);
-          }
-          packed[j / 2] = pack2(o[0], o[1]);
+        for (int j = 0; j < 16; ++j) {
+          const int n = c + j;
+          // lane-1 holds the left neighbour's dx=0 sum, lane+1 the right's dx=2 sum
+          const float left = __shfl_up_sync(0xffffffffu, d0[j], 1);
+          const float right = __shfl_down_sync(0xffffffffu, d2[j], 1);
+          float z = fmaf(sg[n], left + d1[j] + right, sb[n]);
+          if constexpr (RES) z += r[j];
+          if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[CO + n], v2 * swp[2 * CO + n]));
+          o16[j] = fmaxf(z, 0.f);
         }
-        if (writes) {
+        if (writes && p.y) {
+          uint32_t packed[8];
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) packed[j / 2] = pack2(o16[j], o16[j + 1]);
           uint4* dst = reinterpret_cast<uint4*>(out + c);
           dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
           dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+        if (p.pool) {
+          // valid columns are lanes 1..14 of a row group (tile origin even), so
+          // an odd lane pairs with lane+1; lanes 0-15 / 16-31 hold rows 2k / 2k+1
+          uint32_t pk[8];
+          pool_pack(o16, true, pk);
+          if (lane < 16 && (col & 1) && col < kXTW && ww < p.R) {
+            uint4* dst = reinterpret_cast<uint4*>(
+                p.pool + (((long long)img * (p.R >> 1) + (hh >> 1)) * (p.R >> 1) + (ww >> 1)) * p.pool_cs + c);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          }
         }
       }
       tc_fence_before();
@@ -1037,6 +1221,7 @@ cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
   p.y_cs = a.y_cs;
   p.y_co = a.y_co;
   p.err = a.err;
+  if (a.pool || a.head_theta || !a.y) return cudaErrorInvalidValue;   // no fused outputs here
   auto kern = k_conv_tc<BN, CK, RES>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -1051,6 +1236,22 @@ cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
 
 constexpr int kHaloSmemMax = 227 * 1024;
 constexpr int kHaloSmemExtra = 3072;   // barriers, gamma/beta, alignment slack
+// fused head: wh[8][64] + bh[8] + a 2-class theta copy per epilogue warp
+constexpr int kHeadSmem = (kHeadCh * 64 + kHeadCh + kEpiWarps * 2 * kHeadParams) * 4 + 16;
+
+// copy the optional fused outputs of a launch into the kernel parameters
+void set_fused(const ConvArgs& a, TCParams& p, bool head_ok) {
+  p.pool = static_cast<__nv_bfloat16*>(a.pool);
+  p.pool_cs = a.pool_cs;
+  if (head_ok && a.head_theta) {
+    p.theta = a.head_theta;
+    p.wh = a.head_wh;
+    p.bh = a.head_bh;
+    p.logits = a.head_logits;
+    p.slot0 = a.head_slot0;
+    p.ncls = a.head_ncls;
+  }
+}
 
 // stages of the small-N variant for a layer and channel chunk (0: does not fit)
 int halo_stages(int cin, int cout, int cr, int ck) {
@@ -1104,7 +1305,17 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
   p.y_cs = a.y_cs;
   p.y_co = a.y_co;
   p.err = a.err;
-  const size_t smem = (size_t)hp.n_wtiles * Cfg::kWTileBytes + (size_t)stages * Cfg::kStageBytes + kHaloSmemExtra;
+  const bool head = a.head_theta != nullptr;
+  if (head && (a.head_ncls < 1 || a.head_ncls > 2 || !a.head_wh || !a.head_bh || !a.head_logits))
+    return cudaErrorInvalidValue;
+  if (!head && !a.y) return cudaErrorInvalidValue;
+  set_fused(a, p, true);
+  const size_t fixed = (size_t)hp.n_wtiles * Cfg::kWTileBytes + kHaloSmemExtra + (head ? kHeadSmem : 0);
+  if (head && fixed + (size_t)stages * Cfg::kStageBytes > (size_t)kHaloSmemMax)
+    stages = (int)(((size_t)kHaloSmemMax - fixed) / Cfg::kStageBytes);   // room for the head's arrays
+  if (stages < 2) return cudaErrorInvalidValue;
+  hp.stages = stages;
+  const size_t smem = fixed + (size_t)stages * Cfg::kStageBytes;
   if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
   auto kern = k_conv_tc_halo<BN, CK, RES>;
   static bool attr_set = false;
@@ -1169,6 +1380,8 @@ cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
   p.y_cs = a.y_cs;
   p.y_co = a.y_co;
   p.err = a.err;
+  if (!a.y || a.head_theta) return cudaErrorInvalidValue;   // no fused head in this variant
+  set_fused(a, p, false);
   const size_t smem = (size_t)hp.wbytes + (size_t)stages * Cfg::kStageBytes + kHaloSmemExtra;
   if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
   auto kern = k_conv_tc_dxn<CO, CK, RES>;
@@ -1239,6 +1452,12 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
     for (int ck = 32; ck <= 64; ck *= 2)
       if (pertap_ok(R, cin, cout, cr, bn, ck) && n < max) out[n++] = TcConfig{0, bn, ck, 0};
   return n;
+}
+
+bool tc_fuses_pool(const TcConfig& c) { return c.kind == 1 || c.kind == 2; }
+
+bool tc_fuses_head(const TcConfig& c, int cout, int ncls) {
+  return c.kind == 1 && (cout == 32 || cout == 64) && ncls >= 1 && ncls <= 2;
 }
 
 TcConfig tc_default(int R, int cin, int cout, int cr) {

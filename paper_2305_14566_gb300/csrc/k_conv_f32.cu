@@ -323,50 +323,111 @@ __global__ void k_maxpool(int R, int C, const T* __restrict__ x, int x_cs, int x
   Vec8<T>::store(y + (((long long)b * Ro + i) * Ro + j) * y_cs + y_co + c, m);
 }
 
-// bilinear x2, half-pixel centres (align_corners = False), edge clamp:
-// even output 2k mixes source k-1 (0.25) and k (0.75); odd 2k+1 mixes k (0.75)
-// and k+1 (0.25).  R is the OUTPUT size; grid as for k_maxpool.
+// bilinear x2, half-pixel centres (align_corners = False), edge clamp.
+// Output rows (and columns) come in pairs (2k+1, 2k+2) that depend on input
+// rows k and k+1 only: row 2k+1 = 0.75 in(k) + 0.25 in(k+1), row 2k+2 =
+// 0.25 in(k) + 0.75 in(k+1), k = -1 .. Ri-1, input indices clamped to the
+// image (so row 0 = in(0) and row 2Ri-1 = in(Ri-1)); the same in x.  A thread
+// owns one output row pair, 8 channels and kUpSeg column pairs: it walks
+// along x carrying the previous input column, so each step loads one new
+// input column (two rows) and writes a 2 x 2 output block.
+// grid: x = (column segment, channel group), y = row pair k + 1, z = tile.
+constexpr int kUpSeg = 8;
 template <typename T>
-__global__ void k_upsample(int R, int C, const T* __restrict__ x, int x_cs, int x_co,
-                           T* __restrict__ y, int y_cs, int y_co) {
-  const int cg = C >> 3, Ri = R >> 1;
+__global__ void __launch_bounds__(128) k_upsample(int Ri, int C, const T* __restrict__ x, int x_cs, int x_co,
+                                                  T* __restrict__ y, int y_cs, int y_co) {
+  const int cg = C >> 3, R = 2 * Ri;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= R * cg) return;
-  const int j = t / cg, c = (t - j * cg) * 8;
-  const int i = blockIdx.y, b = blockIdx.z;
-  const int k = i >> 1, l = j >> 1;
-  int i0, i1, j0, j1;
-  float wi0, wi1, wj0, wj1;
-  if (i & 1) { i0 = k; i1 = min(k + 1, Ri - 1); wi0 = 0.75f; wi1 = 0.25f; }
-  else       { i0 = max(k - 1, 0); i1 = k; wi0 = 0.25f; wi1 = 0.75f; }
-  if (j & 1) { j0 = l; j1 = min(l + 1, Ri - 1); wj0 = 0.75f; wj1 = 0.25f; }
-  else       { j0 = max(l - 1, 0); j1 = l; wj0 = 0.25f; wj1 = 0.75f; }
-  const T* base = x + ((long long)b * Ri * Ri) * x_cs + x_co + c;
-  float a00[8], a01[8], a10[8], a11[8], o[8];
-  Vec8<T>::load(base + ((long long)i0 * Ri + j0) * x_cs, a00);
-  Vec8<T>::load(base + ((long long)i0 * Ri + j1) * x_cs, a01);
-  Vec8<T>::load(base + ((long long)i1 * Ri + j0) * x_cs, a10);
-  Vec8<T>::load(base + ((long long)i1 * Ri + j1) * x_cs, a11);
+  const int nseg = (Ri + 1 + kUpSeg - 1) / kUpSeg;
+  if (t >= nseg * cg) return;
+  const int seg = t / cg, c = (t - seg * cg) * 8;
+  const int k = (int)blockIdx.y - 1, b = blockIdx.z;
+  const int ka = max(k, 0), kb = min(k + 1, Ri - 1);
+  const T* xa = x + ((long long)b * Ri + ka) * Ri * x_cs + x_co + c;
+  const T* xb = x + ((long long)b * Ri + kb) * Ri * x_cs + x_co + c;
+  T* y0 = y + ((long long)b * R + (2 * k + 1)) * R * y_cs + y_co + c;   // row 2k+1
+  T* y1 = y0 + (long long)R * y_cs;                                      // row 2k+2
+  const bool w0 = k >= 0, w1 = k + 1 < Ri;
+  const int l_beg = seg * kUpSeg - 1, l_end = min(l_beg + kUpSeg, Ri);   // column pairs l_beg .. l_end-1
+  float pa[8], pb[8], ca[8], cb[8], top0[8], bot0[8];
+  Vec8<T>::load(xa + (long long)max(l_beg, 0) * x_cs, pa);
+  Vec8<T>::load(xb + (long long)max(l_beg, 0) * x_cs, pb);
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    o[q] = wi0 * (wj0 * a00[q] + wj1 * a01[q]) + wi1 * (wj0 * a10[q] + wj1 * a11[q]);
-  Vec8<T>::store(y + (((long long)b * R + i) * R + j) * y_cs + y_co + c, o);
+  for (int q = 0; q < 8; ++q) {
+    top0[q] = 0.75f * pa[q] + 0.25f * pb[q];
+    bot0[q] = 0.25f * pa[q] + 0.75f * pb[q];
+  }
+  for (int l = l_beg; l < l_end; ++l) {
+    const int ln = min(l + 1, Ri - 1);
+    Vec8<T>::load(xa + (long long)ln * x_cs, ca);
+    Vec8<T>::load(xb + (long long)ln * x_cs, cb);
+    float top1[8], bot1[8], o[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      top1[q] = 0.75f * ca[q] + 0.25f * cb[q];
+      bot1[q] = 0.25f * ca[q] + 0.75f * cb[q];
+    }
+    const int j0 = 2 * l + 1, j1 = 2 * l + 2;       // output columns of this pair
+    if (w0) {
+      if (l >= 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = 0.75f * top0[q] + 0.25f * top1[q];
+        Vec8<T>::store(y0 + (long long)j0 * y_cs, o);
+      }
+      if (j1 < R) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = 0.25f * top0[q] + 0.75f * top1[q];
+        Vec8<T>::store(y0 + (long long)j1 * y_cs, o);
+      }
+    }
+    if (w1) {
+      if (l >= 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = 0.75f * bot0[q] + 0.25f * bot1[q];
+        Vec8<T>::store(y1 + (long long)j0 * y_cs, o);
+      }
+      if (j1 < R) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = 0.25f * bot0[q] + 0.75f * bot1[q];
+        Vec8<T>::store(y1 + (long long)j1 * y_cs, o);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      top0[q] = top1[q];
+      bot0[q] = bot1[q];
+    }
+  }
 }
 
-// g[b][c] = mean over the R x R pixels of tile b (fixed summation order)
+// g[b][c] = mean over the R x R pixels of tile b.  Block (b, 32-channel group):
+// 8 pixel phases x 32 channels; phase h sums pixels h, h+8, ... in order, then
+// the 8 phase sums are added in phase order (a fixed summation order).
+constexpr int kGapPhases = 8;
 template <typename T>
-__global__ void k_gap(int R, int C, const T* __restrict__ x, int x_cs, int x_co,
-                      float* __restrict__ g) {
-  int b = blockIdx.x;
-  int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  const T* base = x + ((long long)b * R * R) * x_cs + x_co + c;
+__global__ void __launch_bounds__(256) k_gap(int R, int C, const T* __restrict__ x, int x_cs, int x_co,
+                                             float* __restrict__ g) {
+  __shared__ float part[kGapPhases][32];
+  const int b = blockIdx.x;
+  const int ph = threadIdx.x >> 5, cl = threadIdx.x & 31;
+  const int c = blockIdx.y * 32 + cl;
+  const int RR = R * R;
   float s = 0.f;
-  for (int p = 0; p < R * R; ++p) {
-    if constexpr (sizeof(T) == 4) s += (float)base[(long long)p * x_cs];
-    else s += static_cast<float>(base[(long long)p * x_cs]);
+  if (c < C) {
+    const T* base = x + ((long long)b * RR) * x_cs + x_co + c;
+    for (int p = ph; p < RR; p += kGapPhases) {
+      if constexpr (sizeof(T) == 4) s += (float)base[(long long)p * x_cs];
+      else s += static_cast<float>(base[(long long)p * x_cs]);
+    }
   }
-  g[(long long)b * C + c] = s / (float)(R * R);
+  part[ph][cl] = s;
+  __syncthreads();
+  if (ph == 0 && c < C) {
+    float t = 0.f;
+#pragma unroll
+    for (int h = 0; h < kGapPhases; ++h) t += part[h][cl];
+    g[(long long)b * C + c] = t / (float)RR;
+  }
 }
 
 template <int C0, typename T>
@@ -430,27 +491,29 @@ cudaError_t launch_maxpool(int precision, int B, int R, int C, const void* x, in
 
 cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, int x_cs,
                             int x_co, void* y, int y_cs, int y_co, cudaStream_t st) {
-  const int n = R * (C / 8);
-  dim3 grid((n + 127) / 128, R, B);
+  if (R % 2 || C % 8) return cudaErrorInvalidValue;
+  const int Ri = R / 2;
+  const int n = ((Ri + 1 + kUpSeg - 1) / kUpSeg) * (C / 8);
+  dim3 grid((n + 127) / 128, Ri + 1, B);
   if (precision == OMNI_FP32)
-    k_upsample<float><<<grid, 128, 0, st>>>(R, C, (const float*)x, x_cs, x_co, (float*)y, y_cs, y_co);
+    k_upsample<float><<<grid, 128, 0, st>>>(Ri, C, (const float*)x, x_cs, x_co, (float*)y, y_cs, y_co);
   else if (precision == OMNI_FP16)
-    k_upsample<__half><<<grid, 128, 0, st>>>(R, C, (const __half*)x, x_cs, x_co, (__half*)y, y_cs, y_co);
+    k_upsample<__half><<<grid, 128, 0, st>>>(Ri, C, (const __half*)x, x_cs, x_co, (__half*)y, y_cs, y_co);
   else
-    k_upsample<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co,
+    k_upsample<__nv_bfloat16><<<grid, 128, 0, st>>>(Ri, C, (const __nv_bfloat16*)x, x_cs, x_co,
                                                     (__nv_bfloat16*)y, y_cs, y_co);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gap(int precision, int B, int R, int C, const void* x, int x_cs, int x_co,
                        float* g, cudaStream_t st) {
-  dim3 grid(B, (C + 127) / 128);
+  dim3 grid(B, (C + 31) / 32);
   if (precision == OMNI_FP32)
-    k_gap<float><<<grid, 128, 0, st>>>(R, C, (const float*)x, x_cs, x_co, g);
+    k_gap<float><<<grid, 256, 0, st>>>(R, C, (const float*)x, x_cs, x_co, g);
   else if (precision == OMNI_FP16)
-    k_gap<__half><<<grid, 128, 0, st>>>(R, C, (const __half*)x, x_cs, x_co, g);
+    k_gap<__half><<<grid, 256, 0, st>>>(R, C, (const __half*)x, x_cs, x_co, g);
   else
-    k_gap<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co, g);
+    k_gap<__nv_bfloat16><<<grid, 256, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co, g);
   return cudaGetLastError();
 }
 

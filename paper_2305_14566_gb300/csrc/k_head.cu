@@ -18,13 +18,13 @@ constexpr int kHeadThreads = 256;
 constexpr int kPixPerBlock = 4096;
 constexpr int kCtrlRows = 32;          // controller rows per block
 
-// grid.x = ceil(153 / kCtrlRows); block = 8 warps, one (row, tile) dot per warp step
+// grid = (ceil(153 / kCtrlRows), tiles); block = 8 warps, one theta row per warp step
 __global__ void __launch_bounds__(256) k_controller(HeadArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int zdim = a.Cb + a.n_classes + a.n_scales;
-  const int r0 = blockIdx.x * kCtrlRows;
-  for (int q = warp; q < kCtrlRows * a.B; q += 8) {
-    const int row = r0 + q % kCtrlRows, b = q / kCtrlRows;
+  const int r0 = blockIdx.x * kCtrlRows, b = blockIdx.y;
+  for (int q = warp; q < kCtrlRows; q += 8) {
+    const int row = r0 + q;
     if (row >= kHeadParams) continue;
     const float* w = a.wc + (long long)row * zdim;
     const float* g = a.g + (long long)b * a.Cb;
@@ -148,7 +148,8 @@ cudaError_t head_t(const HeadArgs& a, cudaStream_t st) {
 
 cudaError_t launch_controller(const HeadArgs& a, cudaStream_t st) {
   if (a.n_cls_here < 1 || a.n_cls_here > OMNI_MAX_CLASSES) return cudaErrorInvalidValue;
-  k_controller<<<(kHeadParams + kCtrlRows - 1) / kCtrlRows, 256, 0, st>>>(a);
+  if (a.B < 1) return cudaErrorInvalidValue;
+  k_controller<<<dim3((kHeadParams + kCtrlRows - 1) / kCtrlRows, a.B), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

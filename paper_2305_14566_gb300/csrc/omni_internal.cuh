@@ -81,6 +81,15 @@ struct ConvArgs {
   int raw;
   void* y2; int y2_cs;
   int f16;                                // tensor-core operands: 0 BF16, 1 FP16
+  // Optional outputs fused into the epilogue of the small-N tensor-core
+  // kernels (TcConfig kinds 1 and 2; see tc_fuses_pool / tc_fuses_head):
+  // pool = 2x2 max-pool of y, NHWC [B][R/2][R/2] with channel stride pool_cs;
+  // head_* = pre-head + dynamic heads of the tile (as launch_head), written as
+  // FP32 logits [slot0 + b][head_ncls][R*R]; y may then be null (not stored).
+  void* pool; int pool_cs;
+  const float* head_theta;                // [B][head_ncls][153]
+  const float* head_wh; const float* head_bh;   // [8][cout], [8]
+  float* head_logits; int head_slot0, head_ncls;
 };
 
 // k_conv_f32.cu (plain FP32 path + precision-generic helpers)
@@ -106,6 +115,9 @@ cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_
 cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
 cudaError_t launch_conv_tc_cfg_f16(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
 int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max);
+// whether a configuration's epilogue computes ConvArgs::pool / the fused head
+bool tc_fuses_pool(const TcConfig& c);
+bool tc_fuses_head(const TcConfig& c, int cout, int ncls);
 TcConfig tc_default(int R, int cin, int cout, int cr);
 bool conv_tc_supported(int R, int cin, int cout, int cr);
 

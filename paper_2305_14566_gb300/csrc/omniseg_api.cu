@@ -42,6 +42,7 @@ struct omni_ctx {
   std::map<std::array<int, 6>, TcConfig> tuned;
   // CUDA graph of the post-tiling launch chain (network + stitch)
   bool graphs = false;
+  bool fuse = true;            // epilogue fusion of max-pool and head
   std::vector<uint64_t> last_key, graph_key;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_launches = 0, graph_tiles = 0;
@@ -119,7 +120,7 @@ struct Plan {
   size_t canvas, c20, c10, c5, blk8, grey, blur, hist, otsu, mask, tiles, counts, flags, slot;
   size_t tile_end;
   // network stage
-  size_t logits, tmp, pooled, cat[kMaxLevels], bott, ydec[kMaxLevels], gap, theta;
+  size_t logits, tmp, pooled, pooled2, cat[kMaxLevels], bott, ydec[kMaxLevels], gap, theta;
   size_t net_end;
   // host-buffer variant
   size_t in, lab[OMNI_MAX_CLASSES];
@@ -186,7 +187,11 @@ bool make_plan(const omni_config& c, int H, int W, Plan& p) {
   p.logits = take(off, lmax * PP * 4);
   const int L = c.levels;
   p.tmp = take(off, B * PP * widths(c, 0) * e);
+  // pooled encoder inputs ping-pong between two buffers (level l reads buffer
+  // (l-1) % 2 while its second conv's epilogue may write the next level's
+  // pooled input into the other): level 1's input is the larger
   p.pooled = take(off, B * PP / 4 * widths(c, 0) * e);
+  p.pooled2 = take(off, B * PP / 16 * widths(c, std::min(1, L - 1)) * e);
   for (int l = 0; l < L - 1; ++l) {
     size_t R = (size_t)(c.patch >> l);
     p.cat[l] = take(off, B * R * R * 3 * widths(c, l) * e);
@@ -550,6 +555,17 @@ double conv_flops(const ConvArgs& a) {
 // Times every legal tensor-core configuration of a layer on the real operands
 // (two warm-up launches, then three timed with events) and returns the
 // fastest; the launches only rewrite the layer's own output.  Synchronises.
+// the launch arguments for configuration c: fused outputs it cannot compute
+// are dropped (the caller then runs the separate kernels); with the head
+// fused, the block output itself is not stored
+ConvArgs fit_fused(const ConvArgs& in, const TcConfig& c) {
+  ConvArgs a = in;
+  if (!tc_fuses_pool(c)) a.pool = nullptr;
+  if (a.head_theta && tc_fuses_head(c, a.cout, a.head_ncls)) a.y = nullptr;
+  else a.head_theta = nullptr;
+  return a;
+}
+
 TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st) {
   const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
   TcConfig cands[16];
@@ -560,10 +576,11 @@ TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st) {
   if (cudaEventCreate(&e0) != cudaSuccess) return best;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return best; }
   for (int i = 0; i < n; ++i) {
-    bool ok = launch_conv_tc_cfg(a, cands[i], st) == cudaSuccess &&
-              launch_conv_tc_cfg(a, cands[i], st) == cudaSuccess;
+    const ConvArgs ai = fit_fused(a, cands[i]);
+    bool ok = launch_conv_tc_cfg(ai, cands[i], st) == cudaSuccess &&
+              launch_conv_tc_cfg(ai, cands[i], st) == cudaSuccess;
     ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
-    for (int r = 0; r < 3 && ok; ++r) ok = launch_conv_tc_cfg(a, cands[i], st) == cudaSuccess;
+    for (int r = 0; r < 3 && ok; ++r) ok = launch_conv_tc_cfg(ai, cands[i], st) == cudaSuccess;
     ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
     float ms = 0;
     if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
@@ -577,10 +594,16 @@ TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st) {
   return best;
 }
 
-omni_status run_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, int tag) {
-  Rec r(ctx, st, 0, tag, conv_flops(a));
+// run one conv layer; the fused pool / head requested in `in` run only where
+// the chosen kernel supports them, and *pooled / *headed report whether they did
+omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag, bool* pooled = nullptr,
+                     bool* headed = nullptr) {
+  Rec r(ctx, st, 0, tag, conv_flops(in));
+  ConvArgs a = in;
   cudaError_t e;
   if (ctx->cfg.precision == OMNI_FP32) {
+    a.pool = nullptr;
+    a.head_theta = nullptr;
     e = launch_conv_f32(a, st);
   } else {
     if (!conv_tc_supported(a.R, a.cin, a.cout, a.res_mode == RES_TENSOR ? a.cr : 0))
@@ -598,10 +621,13 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, int tag)
         ctx->tuned[key] = cfg;
       }
     }
+    a = fit_fused(in, cfg);
     e = launch_conv_tc_cfg(a, cfg, st);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv");
   ctx->launches++;
+  if (pooled) *pooled = a.pool != nullptr;
+  if (headed) *headed = a.head_theta != nullptr;
   return OMNI_OK;
 }
 
@@ -613,7 +639,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   const int L = c.levels, prec = c.precision;
   auto C = [&](int l) { return widths(c, l); };
   void* tmp = ws + p.tmp;
-  void* pooled = ws + p.pooled;
+  void* pool_buf[2] = {ws + p.pooled, ws + p.pooled2};
   void* bott = ws + p.bott;
   ConvArgs base{};
   base.B = nb;
@@ -637,6 +663,8 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_first");
     ctx->launches++;
   }
+  // pooled_done: the previous level's second conv wrote the pooled input
+  bool pooled_done = false;
   {
     ConvArgs a = base;
     a.R = c.patch; a.cin = C(0); a.cout = C(0);
@@ -644,14 +672,16 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     a.res_mode = RES_RGB; a.cr = 3;
     enc_out(0, a.y, a.y_cs, a.y_co);
     a.w = ctx->enc2[0];
-    omni_status r = run_conv(ctx, a, st, 1);
+    if (L > 1 && ctx->fuse) { a.pool = pool_buf[0]; a.pool_cs = C(0); }
+    omni_status r = run_conv(ctx, a, st, 1, &pooled_done);
     if (r) return r;
   }
   for (int l = 1; l < L; ++l) {
     const int R = c.patch >> l;
+    void* pooled = pool_buf[(l - 1) & 1];
     void* pp; int pcs, pco;
     enc_out(l - 1, pp, pcs, pco);
-    {
+    if (!pooled_done) {
       Rec r(ctx, st, 3, 200 + l);
       OMNI_CU(launch_maxpool(prec, nb, 2 * R, C(l - 1), pp, pcs, pco, pooled, C(l - 1), 0, st), "maxpool");
       ctx->launches++;
@@ -669,7 +699,9 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     b2.res_mode = RES_TENSOR; b2.r = pooled; b2.r_cs = C(l - 1); b2.r_co = 0; b2.cr = C(l - 1);
     enc_out(l, b2.y, b2.y_cs, b2.y_co);
     b2.w = ctx->enc2[l];
-    r = run_conv(ctx, b2, st, 10 * l + 1);
+    if (l < L - 1 && ctx->fuse) { b2.pool = pool_buf[l & 1]; b2.pool_cs = C(l); }
+    pooled_done = false;
+    r = run_conv(ctx, b2, st, 10 * l + 1, &pooled_done);
     if (r) return r;
   }
   float* gap = reinterpret_cast<float*>(ws + p.gap);
@@ -695,6 +727,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   }
   const void* y = bott;
   int y_cs = C(L - 1);
+  bool head_done = false;   // the last decoder conv ran the pre-head and heads in its epilogue
   for (int l = L - 2; l >= 0; --l) {
     const int R = c.patch >> l;
     void* cat = ws + p.cat[l];
@@ -717,13 +750,17 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     b2.res_mode = RES_TENSOR; b2.r = cat; b2.r_cs = 3 * C(l); b2.r_co = 0; b2.cr = 3 * C(l);
     b2.y = ws + p.ydec[l]; b2.y_cs = C(l); b2.y_co = 0;
     b2.w = ctx->dec2[l];
-    r = run_conv(ctx, b2, st, 100 + 10 * l + 1);
+    if (l == 0 && ctx->fuse) {
+      b2.head_theta = h.theta; b2.head_wh = h.wh; b2.head_bh = h.bh;
+      b2.head_logits = h.logits; b2.head_slot0 = h.slot0; b2.head_ncls = h.n_cls_here;
+    }
+    r = run_conv(ctx, b2, st, 100 + 10 * l + 1, nullptr, l == 0 ? &head_done : nullptr);
     if (r) return r;
     y = ws + p.ydec[l];
     y_cs = C(l);
   }
-  h.y0 = y;
-  {
+  if (!head_done) {
+    h.y0 = y;
     Rec r(ctx, st, 2, 500);
     OMNI_CU(launch_head(h, st), "head");
     ctx->launches++;
@@ -1088,6 +1125,14 @@ omni_status omni_set_graphs(omni_ctx* ctx, int32_t enabled) {
     cudaGraphExecDestroy(ctx->graph_exec);
     ctx->graph_exec = nullptr;
   }
+  ctx->last_key.clear();
+  ctx->graph_key.clear();
+  return OMNI_OK;
+}
+
+omni_status omni_set_fusion(omni_ctx* ctx, int32_t enabled) {
+  if (!ctx) return OMNI_EINVAL;
+  ctx->fuse = enabled != 0;
   ctx->last_key.clear();
   ctx->graph_key.clear();
   return OMNI_OK;
