@@ -1109,6 +1109,243 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                  : "memory");
 }
 
+// ------------------------------------------------------------------ first layer
+// conv3x3 of the normalised RGB tile (cin = 3) on the tensor cores.  No TMA
+// box can read the uint8 canvas as an im2col operand, so the operand is built
+// in two steps per 128-pixel tile (8 rows x 16 columns):
+//   1. a TMA load of the tile's raw window, 10 canvas rows x 80 bytes starting
+//      at the 16-byte boundary at or left of the window (the 18-pixel, 54-byte
+//      window sits at byte offset 0..15 of each row; OOB rows read as zero);
+//   2. builder thread r gathers the 27 values v = 2u/255 - 1 of its pixel's
+//      3x3 window from shared memory (zero outside the tile), rounds them to
+//      FP16 (whatever the pipeline's 16-bit type: 8-bit colour values need the
+//      11-bit mantissa) and stores one 64-byte K row (K = 27 padded to 32) in
+//      the 64-byte-swizzled K-major layout the MMA reads (16-byte chunk j of
+//      row r at chunk j ^ ((r >> 1) & 3)).
+// Two FP16 MMAs (K = 16 each) per tile, N = cout; the epilogue writes the
+// pipeline's type.
+//   warps 0-3  builders, warp 4 MMA issuer + TMEM owner, warps 5-8 epilogue
+//   (lane quarters 1, 2, 3, 0), warp 9 TMA producer of the raw windows.
+__host__ __device__ constexpr uint32_t idesc_f16_ops(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+__device__ __forceinline__ uint32_t pack2_f16(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+constexpr int kFirstBuilders = 128;
+constexpr int kThreadsFirst = kFirstBuilders + 32 + 128 + 32;
+constexpr int kFirstStages = 8;
+constexpr int kFirstRowBytes = 64;                        // 32 K values x 2 bytes
+constexpr int kFirstStageBytes = kBM * kFirstRowBytes;    // 8 KB
+constexpr int kRawW = 80, kRawH = kHTH + 2;               // raw window box (bytes x rows)
+constexpr int kRawStageBytes = 1024;                      // 800 bytes used
+
+template <int CO>
+struct FirstCfg {
+  static constexpr int kWBytes = CO * kFirstRowBytes;
+  static constexpr int kBufCols = CO;
+  static constexpr int kBufs = tmem_bufs(kBufCols);
+  static constexpr int kTmemCols = tmem_alloc_cols(kBufs * kBufCols);
+  static constexpr size_t kSmem =
+      1024 + (size_t)kFirstStages * (kFirstStageBytes + kRawStageBytes) + kWBytes + 2048;
+};
+
+template <int CO>
+__global__ void __launch_bounds__(kThreadsFirst, 1)
+    k_conv_tc_first(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapC,
+                    TCParams p) {
+  using Cfg = FirstCfg<CO>;
+  constexpr int ST = kFirstStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sRaw = sA + (size_t)ST * kFirstStageBytes;
+  uint8_t* sW = sRaw + (size_t)ST * kRawStageBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sW + Cfg::kWBytes);
+  uint64_t* full = bars;                           // A stage built (4 builder warps)
+  uint64_t* empty = bars + ST;                     // A stage consumed (MMA commit)
+  uint64_t* rfull = bars + 2 * ST;                 // raw window landed (TMA)
+  uint64_t* rempty = bars + 3 * ST;                // raw window read (4 builder warps)
+  uint64_t* tfull = bars + 4 * ST;
+  uint64_t* tempty = bars + 4 * ST + kMaxTmemBufs;
+  uint64_t* drain = bars + 4 * ST + 2 * kMaxTmemBufs;
+  uint64_t* wbar = drain + 1;
+  float* sg = reinterpret_cast<float*>(wbar + 1);
+  float* sb = sg + CO;
+  float* snorm = sb + CO;                          // v(u) = 2u/255 - 1 for every byte value
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(snorm + 256);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < CO; i += blockDim.x) {
+    sg[i] = p.gamma[i];
+    sb[i] = p.beta[i];
+  }
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) snorm[i] = norm_u8((uint8_t)i);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 4);
+      mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&rfull[s]), 1);
+      mbar_init(smem_u32(&rempty[s]), 4);
+    }
+    for (int b = 0; b < Cfg::kBufs; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 4);
+    }
+    mbar_init(smem_u32(drain), 1);
+    mbar_init(smem_u32(wbar), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int RR = p.R * p.R;
+
+  if (warp == 9) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- raw-window producer
+      StageRing ring;
+      TileWalk tw;
+      tw.init(p.R / kHTH, p.R / kHTW);
+      int it = 0;
+      for (; tw.t < p.n_tiles; tw.next(), ring.next(ST), ++it) {
+        const int s = ring.s;
+        if (ring.lapped && !mbar_wait(smem_u32(&rempty[s]), ring.ph ^ 1u, abort_flag, p.err)) break;
+        const int y0 = p.tiles3[3 * tw.img + 1] + tw.ty * kHTH - 1;
+        const int xb = (p.tiles3[3 * tw.img + 2] + tw.tx * kHTW - 1) * 3;
+        const uint32_t fb = smem_u32(&rfull[s]);
+        mbar_expect_tx(fb, kRawW * kRawH);
+        tma_load_2d(smem_u32(sRaw + (size_t)s * kRawStageBytes), &mapC, fb, xb & ~15, y0);
+      }
+      for (int q = it - 1; q >= 0 && q >= it - ST; --q) mbar_drain(smem_u32(&rfull[q % ST]), (q / ST) & 1);
+    }
+  } else if (warp < 4) {
+    // ------------------------------------------------------------------ builders
+    const int r = threadIdx.x;                       // pixel row of the A tile
+    const int rh = r / kHTW, rw = r % kHTW;          // its place in the 8 x 16 tile
+    const int swz = (r >> 1) & 3;
+    StageRing ring;
+    TileWalk tw;
+    tw.init(p.R / kHTH, p.R / kHTW);
+    for (; tw.t < p.n_tiles; tw.next(), ring.next(ST)) {
+      const int s = ring.s;
+      bool ok = !ring.lapped || mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err);
+      ok = ok && mbar_wait(smem_u32(&rfull[s]), ring.ph, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      const int off = ((p.tiles3[3 * tw.img + 2] + tw.tx * kHTW - 1) * 3) & 15;
+      const uint8_t* raw = sRaw + (size_t)s * kRawStageBytes + off;
+      const int h_in = tw.ty * kHTH + rh - 1, w_in = tw.tx * kHTW + rw - 1;   // tile coords of tap (0, 0)
+      float v[32];
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int yy = h_in + dy, xx = w_in + dx;
+          const bool in = yy >= 0 && yy < p.R && xx >= 0 && xx < p.R;
+          const uint8_t* px = raw + (rh + dy) * kRawW + (rw + dx) * 3;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[(dy * 3 + dx) * 3 + c] = in ? snorm[px[c]] : 0.f;
+        }
+#pragma unroll
+      for (int k = 27; k < 32; ++k) v[k] = 0.f;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&rempty[s]));
+      uint8_t* row = sA + (size_t)s * kFirstStageBytes + r * kFirstRowBytes;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint4 q = make_uint4(pack2_f16(v[8 * j], v[8 * j + 1]), pack2_f16(v[8 * j + 2], v[8 * j + 3]),
+                             pack2_f16(v[8 * j + 4], v[8 * j + 5]), pack2_f16(v[8 * j + 6], v[8 * j + 7]));
+        *reinterpret_cast<uint4*>(row + ((j ^ swz) << 4)) = q;
+      }
+      // make this thread's generic-proxy stores visible to the tensor core's reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+    }
+  } else if (warp == 4) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- MMA issuer
+      const uint32_t wb = smem_u32(wbar);
+      mbar_expect_tx(wb, (uint32_t)Cfg::kWBytes);
+      tma_load_2d(smem_u32(sW), &mapB, wb, 0, 0);
+      constexpr uint32_t idesc = idesc_f16_ops(CO);
+      const uint64_t a_desc0 = smem_desc(smem_u32(sA), kFirstRowBytes);
+      const uint64_t b_desc = smem_desc(smem_u32(sW), kFirstRowBytes);
+      bool ok = mbar_wait(wb, 0, abort_flag, p.err);
+      int tcount = 0;
+      StageRing ring;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount, ring.next(ST)) {
+        const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
+        if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) break;
+        const int s = ring.s;
+        if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
+        const uint64_t ad = a_desc0 + (uint64_t)((s * kFirstStageBytes) >> 4);
+        mma_bf16(acc, ad, b_desc, idesc, 0u);
+        mma_bf16(acc, ad + 2, b_desc + 2, idesc, 1u);
+        mma_commit(smem_u32(&empty[s]));
+        mma_commit(smem_u32(&tfull[buf]));
+      }
+      mma_commit(smem_u32(drain));
+      mbar_drain(smem_u32(drain), 0);
+      mbar_drain(wb, 0);
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int tcount = 0;
+    TileWalk tw;
+    tw.init(p.R / kHTH, p.R / kHTW);
+    for (; tw.t < p.n_tiles; tw.next(), ++tcount) {
+      const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
+      const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int hh = tw.ty * kHTH + row / kHTW, ww = tw.tx * kHTW + row % kHTW;
+      const long long m = (long long)tw.img * RR + (long long)hh * p.R + ww;
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
+#pragma unroll
+      for (int c = 0; c < CO; c += 16) {
+        float a[16];
+        tmem_ld16(tb + c, a);
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2)
+          packed[j / 2] = pack2(fmaxf(fmaf(sg[c + j], a[j], sb[c + j]), 0.f),
+                                fmaxf(fmaf(sg[c + j + 1], a[j + 1], sb[c + j + 1]), 0.f));
+        uint4* dst = reinterpret_cast<uint4*>(p.y + m * p.y_cs + p.y_co + c);
+        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 4)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+}
+
 // ------------------------------------------------------------------ host side
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
@@ -1396,6 +1633,53 @@ cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
   return cudaGetLastError();
 }
 
+
+// the uint8 canvas as a 2D byte tensor {row bytes, rows}: raw-window boxes
+bool map_canvas(CUtensorMap* m, const uint8_t* canvas, long long stride, int canvas_h) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)stride, (cuuint64_t)canvas_h};
+  cuuint64_t strides[1] = {(cuuint64_t)stride};
+  cuuint32_t box[2] = {(cuuint32_t)kRawW, (cuuint32_t)kRawH};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(canvas), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int CO>
+cudaError_t launch_first(const ConvArgs& a, cudaStream_t st) {
+  using Cfg = FirstCfg<CO>;
+  CUtensorMap mB, mC;
+  if (!map_w(&mB, a.w.w_bf16, 32, a.cout, CO, 32)) return cudaErrorInvalidValue;
+  if (!map_canvas(&mC, a.canvas, a.canvas_stride, a.canvas_h)) return cudaErrorInvalidValue;
+  TCParams p{};
+  p.B = a.B; p.R = a.R; p.cin = 3; p.cout = a.cout;
+  p.n_tiles_m = a.B * (a.R / kHTH) * (a.R / kHTW);
+  p.n_tiles_n = 1;
+  p.n_tiles = p.n_tiles_m;
+  p.gamma = a.w.gamma;
+  p.beta = a.w.beta;
+  p.canvas = a.canvas;
+  p.canvas_stride = a.canvas_stride;
+  p.tiles3 = a.tiles3;
+  p.y = static_cast<__nv_bfloat16*>(a.y);
+  p.y_cs = a.y_cs;
+  p.y_co = a.y_co;
+  p.err = a.err;
+  auto kern = k_conv_tc_first<CO>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
+  kern<<<grid, kThreadsFirst, Cfg::kSmem, st>>>(mB, mC, p);
+  return cudaGetLastError();
+}
+
 int pick_bn(int cout, bool res) {
   const int cap = res ? 128 : 256;
   return cout < cap ? cout : cap;
@@ -1523,7 +1807,30 @@ cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaSt
   return cudaErrorInvalidValue;
 }
 
+#if OMNI_TC_F16
+cudaError_t launch_conv_first_tc_f16(const ConvArgs& a, cudaStream_t st) {
+#else
+cudaError_t launch_conv_first_tc_bf16(const ConvArgs& a, cudaStream_t st) {
+#endif
+  if (a.R < 16 || a.R % 16 || a.y_cs % 8 || a.y_co % 8 || reinterpret_cast<uintptr_t>(a.y) % 16 ||
+      reinterpret_cast<uintptr_t>(a.w.w_bf16) % 16 || !a.canvas || !a.tiles3 || a.canvas_h < 1 ||
+      reinterpret_cast<uintptr_t>(a.canvas) % 16 || a.canvas_stride % 16)
+    return cudaErrorInvalidValue;
+  if (a.cout == 32) return launch_first<32>(a, st);
+  if (a.cout == 64) return launch_first<64>(a, st);
+  return cudaErrorInvalidValue;
+}
+
 #if !OMNI_TC_F16
+bool conv_first_tc_supported(int R, int cout, const uint8_t* canvas, long long stride) {
+  return R >= 16 && R % 16 == 0 && (cout == 32 || cout == 64) && reinterpret_cast<uintptr_t>(canvas) % 16 == 0 &&
+         stride % 16 == 0;
+}
+
+cudaError_t launch_conv_first_tc(const ConvArgs& a, cudaStream_t st) {
+  return a.f16 ? launch_conv_first_tc_f16(a, st) : launch_conv_first_tc_bf16(a, st);
+}
+
 cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_t st) {
   return a.f16 ? launch_conv_tc_cfg_f16(a, c, st) : launch_conv_tc_cfg_bf16(a, c, st);
 }

@@ -14,7 +14,7 @@
 namespace omni {
 namespace {
 
-constexpr int kHeadThreads = 256;
+constexpr int kHeadThreads = 128;
 constexpr int kPixPerBlock = 4096;
 constexpr int kCtrlRows = 32;          // controller rows per block
 
@@ -72,10 +72,18 @@ template <> struct Load8<__half> {
   }
 };
 
+// Each thread evaluates kHeadPx pixels (kHeadThreads apart, so a warp's loads
+// cover consecutive pixels) and reuses every weight it reads from shared
+// memory for all of them; theta rows are padded to 160 floats so they are
+// 16-byte aligned for vector loads.
+constexpr int kHeadPx = 4;
+constexpr int kThetaStride = 160;
+
 template <int C0, typename T>
 __global__ void __launch_bounds__(kHeadThreads) k_head(HeadArgs a) {
-  __shared__ float theta[OMNI_MAX_CLASSES][kHeadParams];
-  __shared__ float wh[kHeadCh * C0], bh[kHeadCh];
+  __shared__ __align__(16) float theta[OMNI_MAX_CLASSES][kThetaStride];
+  __shared__ __align__(16) float wh[kHeadCh * C0];
+  __shared__ float bh[kHeadCh];
   const int b = blockIdx.y;
   const int t = threadIdx.x;
   for (int i = t; i < kHeadCh * C0; i += kHeadThreads) wh[i] = a.wh[i];
@@ -88,44 +96,86 @@ __global__ void __launch_bounds__(kHeadThreads) k_head(HeadArgs a) {
   const T* Y = static_cast<const T*>(a.y0) + (long long)b * PP * C0;
   float* out = a.logits + (long long)(a.slot0 + b) * a.n_cls_here * PP;
   const long long p0 = (long long)blockIdx.x * kPixPerBlock;
-  for (int q = t; q < kPixPerBlock; q += kHeadThreads) {
-    const long long p = p0 + q;
-    if (p >= PP) break;
-    float h0[kHeadCh];
+  for (int q0 = 0; q0 < kPixPerBlock; q0 += kHeadThreads * kHeadPx) {
+    long long pix[kHeadPx];
+    bool live[kHeadPx];
 #pragma unroll
-    for (int o = 0; o < kHeadCh; ++o) h0[o] = bh[o];
+    for (int u = 0; u < kHeadPx; ++u) {
+      pix[u] = p0 + q0 + u * kHeadThreads + t;
+      live[u] = pix[u] < PP;
+    }
+    if (!live[0]) break;
+    float h0[kHeadPx][kHeadCh];
+#pragma unroll
+    for (int u = 0; u < kHeadPx; ++u)
+#pragma unroll
+      for (int o = 0; o < kHeadCh; ++o) h0[u][o] = bh[o];
 #pragma unroll
     for (int c0 = 0; c0 < C0; c0 += 8) {
-      float y[8];
-      Load8<T>::f(Y + p * C0 + c0, y);
+      float y[kHeadPx][8];
 #pragma unroll
-      for (int o = 0; o < kHeadCh; ++o)
+      for (int u = 0; u < kHeadPx; ++u) {
+        if (live[u]) Load8<T>::f(Y + pix[u] * C0 + c0, y[u]);
+        else
 #pragma unroll
-        for (int c = 0; c < 8; ++c) h0[o] = fmaf(wh[o * C0 + c0 + c], y[c], h0[o]);
+          for (int c = 0; c < 8; ++c) y[u][c] = 0.f;
+      }
+#pragma unroll
+      for (int o = 0; o < kHeadCh; ++o) {
+        const float4 w0 = *reinterpret_cast<const float4*>(&wh[o * C0 + c0]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&wh[o * C0 + c0 + 4]);
+        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+          for (int u = 0; u < kHeadPx; ++u) h0[u][o] = fmaf(w[c], y[u][c], h0[u][o]);
+      }
     }
 #pragma unroll
-    for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaxf(h0[o], 0.f);
+    for (int u = 0; u < kHeadPx; ++u)
+#pragma unroll
+      for (int o = 0; o < kHeadCh; ++o) h0[u][o] = fmaxf(h0[u][o], 0.f);
     for (int ci = 0; ci < a.n_cls_here; ++ci) {
       const float* th = theta[ci];
-      float h1[kHeadCh], h2[kHeadCh];
+      float h1[kHeadPx][kHeadCh], h2[kHeadPx][kHeadCh];
 #pragma unroll
       for (int o = 0; o < kHeadCh; ++o) {
-        float s = th[136 + o];
+        const float4 w0 = *reinterpret_cast<const float4*>(&th[o * 8]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&th[o * 8 + 4]);
+        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        const float bias = th[136 + o];
 #pragma unroll
-        for (int c = 0; c < kHeadCh; ++c) s = fmaf(th[o * 8 + c], h0[c], s);
-        h1[o] = fmaxf(s, 0.f);
+        for (int u = 0; u < kHeadPx; ++u) {
+          float s = bias;
+#pragma unroll
+          for (int c = 0; c < kHeadCh; ++c) s = fmaf(w[c], h0[u][c], s);
+          h1[u][o] = fmaxf(s, 0.f);
+        }
       }
 #pragma unroll
       for (int o = 0; o < kHeadCh; ++o) {
-        float s = th[144 + o];
+        const float4 w0 = *reinterpret_cast<const float4*>(&th[64 + o * 8]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&th[64 + o * 8 + 4]);
+        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        const float bias = th[144 + o];
 #pragma unroll
-        for (int c = 0; c < kHeadCh; ++c) s = fmaf(th[64 + o * 8 + c], h1[c], s);
-        h2[o] = fmaxf(s, 0.f);
+        for (int u = 0; u < kHeadPx; ++u) {
+          float s = bias;
+#pragma unroll
+          for (int c = 0; c < kHeadCh; ++c) s = fmaf(w[c], h1[u][c], s);
+          h2[u][o] = fmaxf(s, 0.f);
+        }
       }
-      float s = th[152];
+      const float4 w0 = *reinterpret_cast<const float4*>(&th[128]);
+      const float4 w1 = *reinterpret_cast<const float4*>(&th[132]);
+      const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-      for (int c = 0; c < kHeadCh; ++c) s = fmaf(th[128 + c], h2[c], s);
-      out[ci * PP + p] = s;
+      for (int u = 0; u < kHeadPx; ++u) {
+        float s = th[152];
+#pragma unroll
+        for (int c = 0; c < kHeadCh; ++c) s = fmaf(w[c], h2[u][c], s);
+        if (live[u]) out[ci * PP + pix[u]] = s;
+      }
     }
   }
 }

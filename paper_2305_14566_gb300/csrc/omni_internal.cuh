@@ -72,6 +72,7 @@ struct ConvArgs {
   // RES_RGB / first layer: tiles read straight from the uint8 canvas; tile b
   // has origin (tiles3[3 b + 1], tiles3[3 b + 2]) in canvas pixels
   const uint8_t* canvas; int64_t canvas_stride; const int32_t* tiles3;
+  int canvas_h;                           // canvas rows (first-layer tensor-core kernel)
   void* y; int y_cs, y_co;                // output NHWC
   ConvLayerW w;                           // device pointers, passed by value
   unsigned* err;
@@ -115,6 +116,13 @@ cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_
 cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
 cudaError_t launch_conv_tc_cfg_f16(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
 int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max);
+// first layer (cin = 3) on the tensor cores: operand rows gathered from the
+// uint8 canvas; weights w.w_bf16 hold FP16 values [cout][32] (K = tap * 3 +
+// channel, zero padded) in every precision; the output is the pipeline's type
+bool conv_first_tc_supported(int R, int cout, const uint8_t* canvas, long long stride);
+cudaError_t launch_conv_first_tc(const ConvArgs& a, cudaStream_t st);
+cudaError_t launch_conv_first_tc_bf16(const ConvArgs& a, cudaStream_t st);
+cudaError_t launch_conv_first_tc_f16(const ConvArgs& a, cudaStream_t st);
 // whether a configuration's epilogue computes ConvArgs::pool / the fused head
 bool tc_fuses_pool(const TcConfig& c);
 bool tc_fuses_head(const TcConfig& c, int cout, int ncls);

@@ -356,8 +356,11 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
     // blob: w1-style [cout][cin][3][3], g, b ; projection handled by caller
     Pending q{};
     q.cin = cin; q.cout = cout; q.cproj = cproj_used;
+    // 16-bit weights: [cout][9 cin] (tap-major K); the first layer's rows are
+    // FP16 in every precision and padded to K = 32 for its tensor-core kernel
+    const size_t kdim = cin == 3 ? 32 : (size_t)9 * cin;
     q.w32 = alloc((size_t)9 * cin * cout * 4);
-    q.w16 = alloc((size_t)9 * cin * cout * 2);
+    q.w16 = alloc(kdim * cout * 2);
     q.g = alloc((size_t)cout * 4);
     q.b = alloc((size_t)cout * 4);
     float* w32 = reinterpret_cast<float*>(host.data() + q.w32);
@@ -367,7 +370,7 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
         for (int tap = 0; tap < 9; ++tap) {
           float v = src[((size_t)o * cin + ci) * 9 + tap];
           w32[((size_t)tap * cin + ci) * cout + o] = v;
-          w16[(size_t)o * 9 * cin + (size_t)tap * cin + ci] = to_lp(v, f16);
+          w16[(size_t)o * kdim + (size_t)tap * cin + ci] = to_lp(v, f16 || cin == 3);
         }
     src += (size_t)cout * cin * 9;
     memcpy(host.data() + q.g, src, cout * 4);
@@ -498,6 +501,7 @@ namespace {
 struct Prep {
   const uint8_t* c[OMNI_MAX_SCALES];
   int64_t cs[OMNI_MAX_SCALES];
+  int ch[OMNI_MAX_SCALES];      // canvas rows
 };
 
 // Sec. 2.1 stages on the device; fills `pr` with every scale's canvas.
@@ -528,6 +532,7 @@ omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Pl
     int f = c.factors[s];
     pr.c[s] = f == 1 ? c40 : f == 2 ? c20 : f == 4 ? c10 : c5;
     pr.cs[s] = f == 1 ? s40 : (int64_t)(g.Wp / f) * 3;
+    pr.ch[s] = g.Hp / f;
     if (!pr.c[s]) return fail(ctx, OMNI_EINVAL, "internal: no canvas for scale " + std::to_string(s));
   }
   {
@@ -566,7 +571,27 @@ ConvArgs fit_fused(const ConvArgs& in, const TcConfig& c) {
   return a;
 }
 
-TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st) {
+// device time of one separate head launch (for the autotuner's comparison);
+// it writes the batch's logit slots, which the real launch later overwrites
+float time_head(omni_ctx* ctx, const HeadArgs& h, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  float ms = 0.f;
+  if (cudaEventCreate(&e0) != cudaSuccess) return 0.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return 0.f; }
+  bool ok = launch_head(h, st) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess;
+  for (int r = 0; r < 3 && ok; ++r) ok = launch_head(h, st) == cudaSuccess;
+  ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+       cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->launches += 4;
+  return ok ? ms / 3.f : 0.f;
+}
+
+// Times every candidate configuration on the real operands and keeps the
+// fastest.  unfused_ms is added to candidates that cannot compute the
+// requested fused head, which then needs its own kernel (measured by the caller).
+TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, float unfused_ms = 0.f) {
   const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
   TcConfig cands[16];
   const int n = tc_candidates(a.R, a.cin, a.cout, cr, cands, 16);
@@ -583,7 +608,9 @@ TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st) {
     for (int r = 0; r < 3 && ok; ++r) ok = launch_conv_tc_cfg(ai, cands[i], st) == cudaSuccess;
     ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
     float ms = 0;
-    if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+    ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    if (a.head_theta && !ai.head_theta) ms += 3.f * unfused_ms;   // three timed launches
+    if (ok && ms < best_ms) {
       best_ms = ms;
       best = cands[i];
     }
@@ -597,7 +624,7 @@ TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st) {
 // run one conv layer; the fused pool / head requested in `in` run only where
 // the chosen kernel supports them, and *pooled / *headed report whether they did
 omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag, bool* pooled = nullptr,
-                     bool* headed = nullptr) {
+                     bool* headed = nullptr, const HeadArgs* head = nullptr) {
   Rec r(ctx, st, 0, tag, conv_flops(in));
   ConvArgs a = in;
   cudaError_t e;
@@ -617,7 +644,9 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag
       if (it != ctx->tuned.end()) {
         cfg = it->second;
       } else if (!ctx->capturing) {
-        cfg = tune_conv(ctx, a, st);
+        float head_ms = 0.f;
+        if (a.head_theta && head) head_ms = time_head(ctx, *head, st);
+        cfg = tune_conv(ctx, a, st, head_ms);
         ctx->tuned[key] = cfg;
       }
     }
@@ -633,7 +662,7 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag
 
 // U-Net + heads for `nb` tiles of one scale.
 omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const uint8_t* canvas,
-                      int64_t cstride, const int32_t* tiles3, int nb, int slot0, int ncls,
+                      int64_t cstride, int canvas_h, const int32_t* tiles3, int nb, int slot0, int ncls,
                       const int* cls, cudaStream_t st, bool stop_before_dec0 = false) {
   const omni_config& c = ctx->cfg;
   const int L = c.levels, prec = c.precision;
@@ -645,6 +674,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   base.B = nb;
   base.canvas = canvas;
   base.canvas_stride = cstride;
+  base.canvas_h = canvas_h;
   base.tiles3 = tiles3;
   base.err = ctx->d_err;
   base.f16 = c.precision == OMNI_FP16 ? 1 : 0;
@@ -659,7 +689,9 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     a.y = tmp; a.y_cs = C(0); a.y_co = 0;
     a.w = ctx->enc1[0];
     Rec r(ctx, st, 0, 0, conv_flops(a));
-    cudaError_t e = launch_conv_first(a, prec, st);
+    cudaError_t e = prec != OMNI_FP32 && conv_first_tc_supported(a.R, a.cout, canvas, cstride)
+                        ? launch_conv_first_tc(a, st)
+                        : launch_conv_first(a, prec, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_first");
     ctx->launches++;
   }
@@ -754,7 +786,9 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
       b2.head_theta = h.theta; b2.head_wh = h.wh; b2.head_bh = h.bh;
       b2.head_logits = h.logits; b2.head_slot0 = h.slot0; b2.head_ncls = h.n_cls_here;
     }
-    r = run_conv(ctx, b2, st, 100 + 10 * l + 1, nullptr, l == 0 ? &head_done : nullptr);
+    HeadArgs h_here = h;
+    h_here.y0 = ws + p.ydec[0];
+    r = run_conv(ctx, b2, st, 100 + 10 * l + 1, nullptr, l == 0 ? &head_done : nullptr, l == 0 ? &h_here : nullptr);
     if (r) return r;
     y = ws + p.ydec[l];
     y_cs = C(l);
@@ -787,7 +821,7 @@ omni_status run_network(omni_ctx* ctx, const omni_config& c, const Plan& p, uint
     if (want) {
       for (int start = 0; start < n_s; start += c.max_batch) {
         int nb = std::min(c.max_batch, n_s - start);
-        r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], tiles + 3 * (toff + start), nb, start, ncls, cls, st);
+        r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], pr.ch[s], tiles + 3 * (toff + start), nb, start, ncls, cls, st);
         if (r) return r;
       }
       ctx->tiles_done += n_s;
@@ -1420,7 +1454,7 @@ extern "C" omni_status omni_backward(omni_ctx* ctx, const uint8_t* rgb, int32_t 
       const int nb = std::min(c.max_batch, n_s - start);
       const int32_t* t3 = tiles + 3 * (toff + start);
       const long long npx = (long long)nb * PP;
-      r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], t3, nb, start, ncls, cls, st, true);
+      r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], pr.ch[s], t3, nb, start, ncls, cls, st, true);
       if (r) return r;
       void* cat0 = ws + p.cat[0];
       ConvArgs a{};
