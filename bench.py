@@ -11,6 +11,7 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -30,6 +31,20 @@ WORKLOAD = (f"needle-biopsy slide {WORK.H}x{WORK.W} at 40x, scales 40x/10x/5x, t
             f"{WORK.P} stride {WORK.S}, residual U-Net base {WORK.base} x {WORK.levels} levels, "
             f"6 class heads, tissue filter on")
 METRIC = "segmented slide Mpx/s (6 classes x 3 scales)"
+
+
+def conv_traffic(bf16, tiles_per_step, conv_launches_per_step):
+    """DRAM bytes of the conv kernels from the committed ncu counters (per
+    foreground tile), valid only while the conv source is the one captured."""
+    p = os.path.join(ROOT, "profiles", "conv_traffic_needle_bf16.json")
+    src = os.path.join(ROOT, "paper_2305_14566_gb300", "csrc", "conv_tc_impl.cuh")
+    if not bf16 or not os.path.exists(p) or conv_launches_per_step <= 0:
+        return None, None
+    d = json.load(open(p))
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != d.get("conv_source_sha256"):
+        return None, None
+    per_step = d["bytes_per_tile"] * tiles_per_step
+    return per_step / conv_launches_per_step, per_step
 
 
 def peaks():
@@ -274,8 +289,12 @@ def main():
     ap.add_argument("--ragged", action="store_true",
                     help="the 12-slide ragged workload: per-slide latency and aggregate Mpx/s")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--workload", default="needle", choices=["needle", "small"],
+                    help="small: a 2048x8192 slice of the needle configuration, for multi-pass ncu "
+                         "captures that must stay a few GB (never a bench line)")
     ap.add_argument("--profile-step", action="store_true",
-                    help="run exactly one slide step after the generator (for ncu launch lists)")
+                    help="one slide step after the tuning call, bracketed by cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--layer", default=None,
                     help="R,cin,cout,cr,B,repeat: time one fused conv layer instead")
     args = ap.parse_args()
@@ -304,16 +323,26 @@ def main():
     if args.ragged:
         run_ragged(args, api, _lib, dev, prec)
         return
-    spec = synth.spec_for(WORK)
+    work = WORK if args.workload == "needle" else WORK.with_(name="needle_small", H=2048, W=8192)
+    if work is not WORK and not args.profile_step:
+        raise SystemExit("--workload small is for --profile-step captures only")
+    spec = synth.spec_for(work)
     rgb = api.synth_slide(spec, device=dev)
-    blob = synth.gen_weights(WORK)
-    seg = api.Segmenter(WORK, blob, precision=prec)
+    blob = synth.gen_weights(work)
+    seg = api.Segmenter(work, blob, precision=prec)
     if prec != _lib.FP32 and not args.no_autotune:
         seg.set_autotune(True)          # the first (untimed) call tunes every conv shape
     out = seg.segment(rgb)
     torch.cuda.synchronize()
     if args.profile_step:
-        print(json.dumps({"profile_step": True, "launches": seg.launch_count()}))
+        # one step after tuning, bracketed for `ncu --profile-from-start off`
+        seg.segment(rgb, out=out)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        seg.segment(rgb, out=out)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_step": True, "workload": work.name, "launches": seg.launch_count()}))
         seg.close()
         return
 
@@ -357,9 +386,15 @@ def main():
         bound, peak_note = "alu", "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock"
     conv_per_launch_ms = conv_ms / max(conv_n, 1)
     achieved = (conv_flops / max(conv_n, 1)) / (conv_per_launch_ms / 1e3) / 1e12
+    tiles_step = int(round(conv_flops / max(args.steps, 1) / seg.query(WORK.H, WORK.W).flops_per_tile))
+    traffic, traffic_step = conv_traffic(prec == _lib.BF16, tiles_step, conv_n / args.steps)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "conv (all U-Net layers)",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "conv (all U-Net layers)",
             "peak_source": peak_note,
+            "traffic_note": ("DRAM bytes per conv launch, averaged over a step; from the ncu counters of a "
+                             "2048x8192 slice scaled by foreground tiles" if traffic else
+                             "no ncu counters for this conv build / precision"),
+            "traffic_per_step": traffic_step,
             "share_of_step": conv_ms / args.steps / ms_step}
     stitch = {"achieved_gbs": st_bytes / (st_ms / 1e3) / 1e9 if st_ms else None,
               "peak_gbs": pk["hbm_gbs"], "ms_per_step": st_ms / args.steps}
@@ -419,8 +454,7 @@ def main():
                 "config": {"workload": WORKLOAD, "slide_px": WORK.H * WORK.W,
                            "l2": "no flush: inputs (2.4 GB slide) larger than L2",
                            "parallelism": f"replicas x{world}",
-                           "tiles_per_step": int(conv_flops / max(args.steps, 1) /
-                                                 seg.query(WORK.H, WORK.W).flops_per_tile)},
+                           "tiles_per_step": tiles_step},
                 "roofline": roof, "stitch": stitch, "e2e": e2e, "gpu_launches": int(launches),
                 "breakdown": breakdown, "graph_replay": graph,
                 "autotuned": [list(t) for t in seg.tuned()],
