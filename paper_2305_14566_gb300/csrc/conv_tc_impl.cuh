@@ -303,7 +303,11 @@ struct TCCfg {
   static constexpr int kBBytes = BN * CK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStages0 = (kSmemBudget - 2048) / kStageBytes;
-  static constexpr int kStages = kStages0 > 16 ? 16 : kStages0;
+  static constexpr int kStages = kStages0 > 16 ? 16 : kStages0;       // (A, B) slots
+  // slots per pipeline stage: one wait and one commit cover kGroup K steps,
+  // with at least three stages in flight
+  static constexpr int kGroup = kStages / 3 > 1 ? kStages / 3 : 1;
+  static constexpr int kRing = kStages / kGroup;
   static constexpr int kBufCols = RES ? 2 * BN : BN;     // TMEM columns per accumulator buffer
   static constexpr int kBufs = tmem_bufs(kBufCols);       // accumulator ring depth
   static constexpr int kTmemCols = tmem_alloc_cols(kBufs * kBufCols);
@@ -318,7 +322,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
               const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
               TCParams p) {
   using Cfg = TCCfg<BN, CK, RES>;
-  constexpr int ST = Cfg::kStages;
+  constexpr int ST = Cfg::kStages;     // (A, B) slots
+  constexpr int G = Cfg::kGroup;       // slots per stage
+  constexpr int RING = Cfg::kRing;     // stages
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -380,37 +386,41 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int img = m0 / RR, rem = m0 % RR;
         const int h0 = rem / p.R, w0 = rem % p.R;
         int cc = 0, tdx = 0, tdy = 0;        // channel chunk and tap of the main segment
-        for (int k = 0; k < k_total; ++k, ++it, ring.next(ST)) {
+        for (int k0 = 0; k0 < k_total; k0 += G, ++it, ring.next(RING)) {
           const int s = ring.s;
           if (ring.lapped && !mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
             ok = false;
             break;
           }
+          const int nb = min(G, k_total - k0);
           const uint32_t fb = smem_u32(&full[s]);
-          mbar_expect_tx(fb, Cfg::kStageBytes);
-          const uint32_t da = smem_u32(sA + (size_t)s * Cfg::kABytes);
-          const uint32_t db = smem_u32(sB + (size_t)s * Cfg::kBBytes);
-          if (k < p.k_main) {
-            const int c0 = cc * CK;
-            tma_load_4d(da, &mapA, fb, c0, w0 + tdx - 1, h0 + tdy - 1, img);
-            tma_load_2d(db, &mapB, fb, (tdy * 3 + tdx) * p.cin + c0, nt * BN);
-            if (++cc == cpt) {
-              cc = 0;
-              if (++tdx == 3) {
-                tdx = 0;
-                ++tdy;
+          mbar_expect_tx(fb, (uint32_t)(nb * Cfg::kStageBytes));
+          for (int j = 0; j < nb; ++j) {
+            const int k = k0 + j, slot = s * G + j;
+            const uint32_t da = smem_u32(sA + (size_t)slot * Cfg::kABytes);
+            const uint32_t db = smem_u32(sB + (size_t)slot * Cfg::kBBytes);
+            if (k < p.k_main) {
+              const int c0 = cc * CK;
+              tma_load_4d(da, &mapA, fb, c0, w0 + tdx - 1, h0 + tdy - 1, img);
+              tma_load_2d(db, &mapB, fb, (tdy * 3 + tdx) * p.cin + c0, nt * BN);
+              if (++cc == cpt) {
+                cc = 0;
+                if (++tdx == 3) {
+                  tdx = 0;
+                  ++tdy;
+                }
               }
+            } else {
+              const int c0 = (k - p.k_main) * CK;
+              tma_load_4d(da, &mapA2, fb, c0, w0, h0, img);
+              tma_load_2d(db, &mapB2, fb, c0, nt * BN);
             }
-          } else {
-            const int c0 = (k - p.k_main) * CK;
-            tma_load_4d(da, &mapA2, fb, c0, w0, h0, img);
-            tma_load_2d(db, &mapB2, fb, c0, nt * BN);
           }
         }
       }
       // make sure no copy of ours is still landing in shared memory
       const int last = it;
-      for (int q = last - 1; q >= 0 && q >= last - ST; --q) mbar_drain(smem_u32(&full[q % ST]), (q / ST) & 1);
+      for (int q = last - 1; q >= 0 && q >= last - RING; --q) mbar_drain(smem_u32(&full[q % RING]), (q / RING) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -430,22 +440,26 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         tc_fence_after();
         const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
         const uint32_t acc1 = acc0 + BN;
-        for (int k = 0; k < k_total; ++k, ring.next(ST)) {
+        for (int k0 = 0; k0 < k_total; k0 += G, ring.next(RING)) {
           const int s = ring.s;
+          // TMA-filled stage: the mbarrier's complete_tx orders the copy before the MMAs
           if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
             ok = false;
             break;
           }
-          tc_fence_after();
-          const uint64_t ad = a_desc0 + (uint64_t)(s * (Cfg::kABytes >> 4));
-          const uint64_t bd = b_desc0 + (uint64_t)(s * (Cfg::kBBytes >> 4));
-          const bool second = RES && k >= p.k_main;
-          const uint32_t d = second ? acc1 : acc0;
-          const int kfirst = second ? p.k_main : 0;
+          const int nb = min(G, k_total - k0);
+          for (int j = 0; j < nb; ++j) {
+            const int k = k0 + j, slot = s * G + j;
+            const uint64_t ad = a_desc0 + (uint64_t)(slot * (Cfg::kABytes >> 4));
+            const uint64_t bd = b_desc0 + (uint64_t)(slot * (Cfg::kBBytes >> 4));
+            const bool second = RES && k >= p.k_main;
+            const uint32_t d = second ? acc1 : acc0;
+            const int kfirst = second ? p.k_main : 0;
 #pragma unroll
-          for (int kk = 0; kk < CK / 16; ++kk)
-            mma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                     (k > kfirst || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < CK / 16; ++kk)
+              mma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                       (k > kfirst || kk > 0) ? 1u : 0u);
+          }
           mma_commit(smem_u32(&empty[s]));
         }
         if (!ok) break;
@@ -690,11 +704,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const uint32_t acc1 = acc0 + BN;
         for (int k = 0; k < k_total; ++k, ring.next(ST)) {
           const int s = ring.s;
+          // TMA-filled stage: the mbarrier's complete_tx orders the copy before the MMAs
           if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
             ok = false;
             break;
           }
-          tc_fence_after();
           // descriptor start addresses advance in 16-byte units: add (bytes >> 4)
           const uint64_t ad = a_desc0 + (uint64_t)((s * Cfg::kStageBytes) >> 4);
           if (k < p.k_main) {
@@ -848,7 +862,7 @@ template <int CO, int CK, bool RES>
 struct DxnCfg {
   static constexpr int kN = 3 * CO;                        // MMA N (dx blocks)
   static constexpr int kBoxBytes = kHBoxPix * CK * 2;      // 10 x 16 pixels
-  static constexpr int kStageBytes = kBoxBytes;            // one box per stage
+  static constexpr int kStageBytes = kBoxBytes;            // one box slot (a stage holds cps slots)
   static constexpr int kWTileBytes = kN * CK * 2;          // 3 dx slices of cout x CK
   static constexpr int kRTileBytes = CO * CK * 2;          // projection weights
   static constexpr int kBufCols = RES ? kN + CO : kN;
@@ -862,6 +876,8 @@ struct DxnParams {
   int res_chunks, stages, cpt;
   int tiles_per_img, tiles_w;      // (R/8) * ceil(R/14), ceil(R/14)
   int wbytes;                      // resident weight bytes (main + projection)
+  int cps;                         // channel chunks per pipeline stage (one box slot each)
+  int main_stages;                 // ceil(cpt / cps); t.k_res = ceil(res_chunks / cps)
 };
 
 template <int CO, int CK, bool RES>
@@ -877,7 +893,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   uint8_t* sW = smem;                                              // [3 dy][cpt][3 cout x CK]
   uint8_t* sR = sW + (size_t)9 * hp.cpt * Cfg::kRTileBytes;        // [res_chunks][cout x CK]
   uint8_t* sA = smem + hp.wbytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * Cfg::kStageBytes);
+  const int stage_bytes = hp.cps * Cfg::kStageBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * stage_bytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + ST;
   uint64_t* tfull = bars + 2 * ST;                      // [kMaxTmemBufs]
@@ -956,13 +973,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             break;
           }
           const uint32_t fb = smem_u32(&full[s]);
-          uint8_t* st = sA + (size_t)s * Cfg::kStageBytes;
-          if (k < p.k_main) {
-            mbar_expect_tx(fb, Cfg::kBoxBytes);
-            tma_load_4d(smem_u32(st), &mapA, fb, k * CK, w0 - 1, h0 - 1, img);
+          uint8_t* st = sA + (size_t)s * stage_bytes;
+          if (k < hp.main_stages) {
+            const int c0 = k * hp.cps, nb = min(hp.cps, hp.cpt - c0);
+            mbar_expect_tx(fb, (uint32_t)(nb * Cfg::kBoxBytes));
+            for (int j = 0; j < nb; ++j)
+              tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA, fb, (c0 + j) * CK, w0 - 1, h0 - 1, img);
           } else {
-            mbar_expect_tx(fb, kBM * CK * 2);
-            tma_load_4d(smem_u32(st), &mapA2, fb, (k - p.k_main) * CK, w0 - 1, h0, img);
+            const int r0 = (k - hp.main_stages) * hp.cps, nb = min(hp.cps, hp.res_chunks - r0);
+            mbar_expect_tx(fb, (uint32_t)(nb * kBM * CK * 2));
+            for (int j = 0; j < nb; ++j)
+              tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA2, fb, (r0 + j) * CK, w0 - 1, h0, img);
           }
         }
       }
@@ -993,29 +1014,38 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const uint32_t acc1 = acc0 + Cfg::kN;
         for (int k = 0; k < k_total; ++k, ring.next(ST)) {
           const int s = ring.s;
+          // TMA-filled stage: the mbarrier's complete_tx orders the copy before the MMAs
           if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
             ok = false;
             break;
           }
-          tc_fence_after();
-          const uint64_t ad = a_desc0 + (uint64_t)((s * Cfg::kStageBytes) >> 4);
-          if (k < p.k_main) {
-            const uint64_t bk = w_desc0 + (uint64_t)(k * (Cfg::kWTileBytes >> 4));
+          const uint64_t ad = a_desc0 + (uint64_t)((s * stage_bytes) >> 4);
+          if (k < hp.main_stages) {
+            const int c0 = k * hp.cps, nb = min(hp.cps, hp.cpt - c0);
+            for (int j = 0; j < nb; ++j) {
+              const int c = c0 + j;
+              const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
+              const uint64_t bk = w_desc0 + (uint64_t)(c * (Cfg::kWTileBytes >> 4));
 #pragma unroll
-            for (int dy = 0; dy < 3; ++dy) {
-              const uint64_t at = ad + (uint64_t)((dy * kHTW * CK * 2) >> 4);
-              const uint64_t bt = bk + (uint64_t)dy * dy_step;
+              for (int dy = 0; dy < 3; ++dy) {
+                const uint64_t at = aj + (uint64_t)((dy * kHTW * CK * 2) >> 4);
+                const uint64_t bt = bk + (uint64_t)dy * dy_step;
 #pragma unroll
-              for (int kk = 0; kk < CK / 16; ++kk)
-                mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc_n,
-                         (k > 0 || dy > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < CK / 16; ++kk)
+                  mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc_n,
+                           (c > 0 || dy > 0 || kk > 0) ? 1u : 0u);
+              }
             }
           } else if (RES) {
-            const uint64_t bd = r_desc0 + (uint64_t)((k - p.k_main) * (Cfg::kRTileBytes >> 4));
+            const int r0 = (k - hp.main_stages) * hp.cps, nb = min(hp.cps, hp.res_chunks - r0);
+            for (int j = 0; j < nb; ++j) {
+              const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
+              const uint64_t bd = r_desc0 + (uint64_t)((r0 + j) * (Cfg::kRTileBytes >> 4));
 #pragma unroll
-            for (int kk = 0; kk < CK / 16; ++kk)
-              mma_bf16(acc1, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc_r,
-                       (k > p.k_main || kk > 0) ? 1u : 0u);
+              for (int kk = 0; kk < CK / 16; ++kk)
+                mma_bf16(acc1, aj + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc_r,
+                         (r0 + j > 0 || kk > 0) ? 1u : 0u);
+            }
           }
           mma_commit(smem_u32(&empty[s]));
         }
@@ -1601,10 +1631,15 @@ cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
   p.n_tiles_m = a.B * hp.tiles_per_img;
   p.n_tiles_n = 1;
   p.n_tiles = p.n_tiles_m;
-  p.k_main = a.cin / CK;
-  hp.res_chunks = RES ? a.cr / CK : 0;
-  p.k_res = hp.res_chunks;
   hp.cpt = a.cin / CK;
+  hp.res_chunks = RES ? a.cr / CK : 0;
+  // group box slots into stages of up to a tile's channel chunks, keeping at
+  // least three stages in flight: fewer waits and commits per MMA
+  hp.cps = max(1, min(hp.cpt, stages / 3));
+  hp.main_stages = (hp.cpt + hp.cps - 1) / hp.cps;
+  p.k_main = hp.main_stages;
+  p.k_res = (hp.res_chunks + hp.cps - 1) / hp.cps;
+  stages /= hp.cps;
   hp.stages = stages;
   hp.wbytes = dxn_wbytes(a.cin, a.cout, RES ? a.cr : 0, CK);
   p.gamma = a.w.gamma;
@@ -1619,8 +1654,8 @@ cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
   p.err = a.err;
   if (!a.y || a.head_theta) return cudaErrorInvalidValue;   // no fused head in this variant
   set_fused(a, p, false);
-  const size_t smem = (size_t)hp.wbytes + (size_t)stages * Cfg::kStageBytes + kHaloSmemExtra;
-  if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)hp.wbytes + (size_t)stages * hp.cps * Cfg::kStageBytes + kHaloSmemExtra;
+  if (stages < 2 || smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
   auto kern = k_conv_tc_dxn<CO, CK, RES>;
   static bool attr_set = false;
   if (!attr_set) {
