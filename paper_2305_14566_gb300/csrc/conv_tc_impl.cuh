@@ -270,23 +270,24 @@ struct StageRing {
 // This CTA's tiles t = blockIdx.x + i * gridDim.x of an images x ny x nx tile
 // grid, kept as (img, ty, tx) and stepped by a mixed-radix add.
 struct TileWalk {
-  int t, img, ty, tx;
+  int t, img, ty, tx, step;
   int s_img, s_ty, s_tx, ny, nx;
-  __device__ __forceinline__ void init(int ny_, int nx_) {
+  // tiles t0, t0 + step, ... (default: this CTA's tiles)
+  __device__ __forceinline__ void init(int ny_, int nx_, int t0 = -1, int step_ = 0) {
     ny = ny_;
     nx = nx_;
     const int per = ny * nx;
-    t = blockIdx.x;
+    t = t0 < 0 ? (int)blockIdx.x : t0;
+    step = step_ > 0 ? step_ : (int)gridDim.x;
     img = t / per;
     ty = (t - img * per) / nx;
     tx = t - img * per - ty * nx;
-    const int st = gridDim.x;
-    s_img = st / per;
-    s_ty = (st - s_img * per) / nx;
-    s_tx = st - s_img * per - s_ty * nx;
+    s_img = step / per;
+    s_ty = (step - s_img * per) / nx;
+    s_tx = step - s_img * per - s_ty * nx;
   }
   __device__ __forceinline__ void next() {
-    t += gridDim.x;
+    t += step;
     tx += s_tx;
     int c = tx >= nx ? 1 : 0;
     tx -= c * nx;
@@ -559,10 +560,11 @@ struct HaloCfg {
 };
 
 struct HaloParams {
-  TCParams t;                       // t.k_res = stages of the projection segment (3 chunks each)
+  TCParams t;                       // t.k_res = slots of the projection segment (3 chunks each)
   int res_chunks;                   // channel chunks of the projection input
-  int stages, n_wtiles, cpt;        // cpt = channel chunks of the main input
+  int stages, n_wtiles, cpt;        // stages of the ring; cpt = channel chunks of the main input
   int tiles_per_img, tiles_w;       // (R/8)*(R/16), R/16
+  int group;                        // slots (one chunk's 3 boxes, or 3 projection chunks) per stage
 };
 
 template <int BN, int CK, bool RES>
@@ -577,7 +579,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sW = smem;
   uint8_t* sA = smem + (size_t)hp.n_wtiles * Cfg::kWTileBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * Cfg::kStageBytes);
+  const int G = hp.group;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)ST * G * Cfg::kStageBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + ST;
   uint64_t* tfull = bars + 2 * ST;                      // [kMaxTmemBufs]
@@ -657,25 +660,34 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       for (; tw.t < p.n_tiles && ok; tw.next()) {
         const int img = tw.img;
         const int h0 = tw.ty * kHTH, w0 = tw.tx * kHTW;
-        for (int k = 0; k < k_total; ++k, ++it, ring.next(ST)) {
+        for (int k0 = 0; k0 < k_total; k0 += G, ++it, ring.next(ST)) {
           const int s = ring.s;
           if (ring.lapped && !mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
             ok = false;
             break;
           }
           const uint32_t fb = smem_u32(&full[s]);
-          uint8_t* st = sA + (size_t)s * Cfg::kStageBytes;
-          if (k < p.k_main) {
-            mbar_expect_tx(fb, Cfg::kStageBytes);
-            const int c0 = k * CK;
-            for (int dx = 0; dx < 3; ++dx)
-              tma_load_4d(smem_u32(st + dx * Cfg::kBoxBytes), &mapA, fb, c0, w0 + dx - 1, h0 - 1, img);
-          } else {
-            // up to three projection chunks per stage, one per box slot
-            const int c0 = (k - p.k_main) * 3, nbx = min(3, hp.res_chunks - c0);
-            mbar_expect_tx(fb, (uint32_t)(nbx * kBM * CK * 2));
-            for (int j = 0; j < nbx; ++j)
-              tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA2, fb, (c0 + j) * CK, w0, h0, img);
+          const int nsl = min(G, k_total - k0);
+          uint32_t bytes = 0;
+          for (int j = 0; j < nsl; ++j) {
+            const int k = k0 + j;
+            bytes += k < p.k_main ? (uint32_t)Cfg::kStageBytes
+                                  : (uint32_t)(min(3, hp.res_chunks - (k - p.k_main) * 3) * kBM * CK * 2);
+          }
+          mbar_expect_tx(fb, bytes);
+          for (int j = 0; j < nsl; ++j) {
+            const int k = k0 + j;
+            uint8_t* st = sA + (size_t)(s * G + j) * Cfg::kStageBytes;
+            if (k < p.k_main) {
+              const int c0 = k * CK;
+              for (int dx = 0; dx < 3; ++dx)
+                tma_load_4d(smem_u32(st + dx * Cfg::kBoxBytes), &mapA, fb, c0, w0 + dx - 1, h0 - 1, img);
+            } else {
+              // up to three projection chunks per slot, one per box
+              const int c0 = (k - p.k_main) * 3, nbx = min(3, hp.res_chunks - c0);
+              for (int b = 0; b < nbx; ++b)
+                tma_load_4d(smem_u32(st + b * Cfg::kBoxBytes), &mapA2, fb, (c0 + b) * CK, w0, h0, img);
+            }
           }
         }
       }
@@ -702,36 +714,41 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         tc_fence_after();
         const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
         const uint32_t acc1 = acc0 + BN;
-        for (int k = 0; k < k_total; ++k, ring.next(ST)) {
+        for (int k0 = 0; k0 < k_total; k0 += G, ring.next(ST)) {
           const int s = ring.s;
           // TMA-filled stage: the mbarrier's complete_tx orders the copy before the MMAs
           if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
             ok = false;
             break;
           }
-          // descriptor start addresses advance in 16-byte units: add (bytes >> 4)
-          const uint64_t ad = a_desc0 + (uint64_t)((s * Cfg::kStageBytes) >> 4);
-          if (k < p.k_main) {
-            const uint64_t bd = b_desc0 + (uint64_t)(k * (Cfg::kWTileBytes >> 4));
-            const uint32_t acc_first = k > 0 ? 1u : 0u;
+          const int nsl = min(G, k_total - k0);
+          for (int j = 0; j < nsl; ++j) {
+            const int k = k0 + j;
+            // descriptor start addresses advance in 16-byte units: add (bytes >> 4)
+            const uint64_t ad = a_desc0 + (uint64_t)(((s * G + j) * Cfg::kStageBytes) >> 4);
+            if (k < p.k_main) {
+              const uint64_t bd = b_desc0 + (uint64_t)(k * (Cfg::kWTileBytes >> 4));
+              const uint32_t acc_first = k > 0 ? 1u : 0u;
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-              const uint64_t at = ad + (uint64_t)(((tap % 3) * Cfg::kBoxBytes + (tap / 3) * kHTW * CK * 2) >> 4);
-              const uint64_t bt = bd + (uint64_t)tap * b_tap_step;
+              for (int tap = 0; tap < 9; ++tap) {
+                const uint64_t at =
+                    ad + (uint64_t)(((tap % 3) * Cfg::kBoxBytes + (tap / 3) * kHTW * CK * 2) >> 4);
+                const uint64_t bt = bd + (uint64_t)tap * b_tap_step;
 #pragma unroll
-              for (int kk = 0; kk < CK / 16; ++kk)
-                mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc,
-                         (tap > 0 || kk > 0) ? 1u : acc_first);
-            }
-          } else if (RES) {
-            const int c0 = (k - p.k_main) * 3, nbx = min(3, hp.res_chunks - c0);
-            for (int j = 0; j < nbx; ++j) {
-              const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
-              const uint64_t bd = b_desc0 + (uint64_t)((9 * hp.cpt + c0 + j) * (Cfg::kWTileBytes >> 4));
+                for (int kk = 0; kk < CK / 16; ++kk)
+                  mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc,
+                           (tap > 0 || kk > 0) ? 1u : acc_first);
+              }
+            } else if (RES) {
+              const int c0 = (k - p.k_main) * 3, nbx = min(3, hp.res_chunks - c0);
+              for (int b = 0; b < nbx; ++b) {
+                const uint64_t ab = ad + (uint64_t)((b * Cfg::kBoxBytes) >> 4);
+                const uint64_t bd = b_desc0 + (uint64_t)((9 * hp.cpt + c0 + b) * (Cfg::kWTileBytes >> 4));
 #pragma unroll
-              for (int kk = 0; kk < CK / 16; ++kk)
-                mma_bf16(acc1, aj + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                         (c0 + j > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < CK / 16; ++kk)
+                  mma_bf16(acc1, ab + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                           (c0 + b > 0 || kk > 0) ? 1u : 0u);
+              }
             }
           }
           mma_commit(smem_u32(&empty[s]));
@@ -1154,8 +1171,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 //      row r at chunk j ^ ((r >> 1) & 3)).
 // Two FP16 MMAs (K = 16 each) per tile, N = cout; the epilogue writes the
 // pipeline's type.
-//   warps 0-3  builders, warp 4 MMA issuer + TMEM owner, warps 5-8 epilogue
-//   (lane quarters 1, 2, 3, 0), warp 9 TMA producer of the raw windows.
+//   warps 0-7  builders in two groups of four (group g builds the CTA's tiles
+//              g, g + 2, ...: two tiles in flight), warp 8 MMA issuer + TMEM
+//              owner, warps 9-12 epilogue (lane quarters 1, 2, 3, 0), warp 13
+//              TMA producer of the raw windows.
 __host__ __device__ constexpr uint32_t idesc_f16_ops(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
@@ -1163,9 +1182,11 @@ __device__ __forceinline__ uint32_t pack2_f16(float a, float b) {
   __half2 h = __floats2half2_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
 }
-constexpr int kFirstBuilders = 128;
+constexpr int kFirstBuilders = 256;                       // two groups of 128
 constexpr int kThreadsFirst = kFirstBuilders + 32 + 128 + 32;
+constexpr int kFirstMmaWarp = kFirstBuilders / 32, kFirstProducerWarp = kFirstMmaWarp + 5;
 constexpr int kFirstStages = 8;
+static_assert(kFirstStages % 2 == 0, "the two builder groups own the even and the odd ring slots");
 constexpr int kFirstRowBytes = 64;                        // 32 K values x 2 bytes
 constexpr int kFirstStageBytes = kBM * kFirstRowBytes;    // 8 KB
 constexpr int kRawW = 80, kRawH = kHTH + 2;               // raw window box (bytes x rows)
@@ -1230,7 +1251,7 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  if (warp == 4) {
+  if (warp == kFirstMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(Cfg::kTmemCols)
@@ -1243,7 +1264,7 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
   const uint32_t tmem_base = *tmem_slot;
   const int RR = p.R * p.R;
 
-  if (warp == 9) {
+  if (warp == kFirstProducerWarp) {
     if (lane == 0) {
       // ---------------------------------------------------------------- raw-window producer
       StageRing ring;
@@ -1261,18 +1282,20 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
       }
       for (int q = it - 1; q >= 0 && q >= it - ST; --q) mbar_drain(smem_u32(&rfull[q % ST]), (q / ST) & 1);
     }
-  } else if (warp < 4) {
+  } else if (warp < kFirstMmaWarp) {
     // ------------------------------------------------------------------ builders
-    const int r = threadIdx.x;                       // pixel row of the A tile
+    const int grp = threadIdx.x / 128;               // builds the CTA's tiles grp, grp + 2, ...
+    const int r = threadIdx.x % 128;                 // pixel row of the A tile
     const int rh = r / kHTW, rw = r % kHTW;          // its place in the 8 x 16 tile
     const int swz = (r >> 1) & 3;
-    StageRing ring;
+    int s = grp;                                     // ring slot of the tile (ST is even)
+    uint32_t ph = 0;
+    bool lapped = false;
     TileWalk tw;
-    tw.init(p.R / kHTH, p.R / kHTW);
-    for (; tw.t < p.n_tiles; tw.next(), ring.next(ST)) {
-      const int s = ring.s;
-      bool ok = !ring.lapped || mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err);
-      ok = ok && mbar_wait(smem_u32(&rfull[s]), ring.ph, abort_flag, p.err);
+    tw.init(p.R / kHTH, p.R / kHTW, (int)blockIdx.x + grp * (int)gridDim.x, 2 * (int)gridDim.x);
+    for (; tw.t < p.n_tiles; tw.next()) {
+      bool ok = !lapped || mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag, p.err);
+      ok = ok && mbar_wait(smem_u32(&rfull[s]), ph, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       const int off = ((p.tiles3[3 * tw.img + 2] + tw.tx * kHTW - 1) * 3) & 15;
       const uint8_t* raw = sRaw + (size_t)s * kRawStageBytes + off;
@@ -1303,8 +1326,14 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+      s += 2;
+      if (s >= ST) {
+        s -= ST;
+        ph ^= 1u;
+        lapped = true;
+      }
     }
-  } else if (warp == 4) {
+  } else if (warp == kFirstMmaWarp) {
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuer
       const uint32_t wb = smem_u32(wbar);
@@ -1370,7 +1399,7 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 4)
+  if (warp == kFirstMmaWarp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"(Cfg::kTmemCols)
                  : "memory");
@@ -1561,6 +1590,9 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
   p.k_res = (hp.res_chunks + 2) / 3;
   hp.cpt = a.cin / CK;
   hp.n_wtiles = 9 * hp.cpt + hp.res_chunks;
+  // stages hold up to a tile's slots while at least three stages stay in flight
+  hp.group = max(1, min(p.k_main + p.k_res, stages / 3));
+  stages /= hp.group;
   hp.stages = stages;
   p.gamma = a.w.gamma;
   p.beta = a.w.beta;
@@ -1578,11 +1610,12 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
   if (!head && !a.y) return cudaErrorInvalidValue;
   set_fused(a, p, true);
   const size_t fixed = (size_t)hp.n_wtiles * Cfg::kWTileBytes + kHaloSmemExtra + (head ? kHeadSmem : 0);
-  if (head && fixed + (size_t)stages * Cfg::kStageBytes > (size_t)kHaloSmemMax)
-    stages = (int)(((size_t)kHaloSmemMax - fixed) / Cfg::kStageBytes);   // room for the head's arrays
+  const size_t stage_bytes = (size_t)hp.group * Cfg::kStageBytes;
+  if (head && fixed + (size_t)stages * stage_bytes > (size_t)kHaloSmemMax)
+    stages = (int)(((size_t)kHaloSmemMax - fixed) / stage_bytes);   // room for the head's arrays
   if (stages < 2) return cudaErrorInvalidValue;
   hp.stages = stages;
-  const size_t smem = fixed + (size_t)stages * Cfg::kStageBytes;
+  const size_t smem = fixed + (size_t)stages * stage_bytes;
   if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
   auto kern = k_conv_tc_halo<BN, CK, RES>;
   static bool attr_set = false;
