@@ -14,6 +14,9 @@
 namespace omni {
 namespace {
 
+// Classes are the outer loop so only one class's sums and votes are live
+// (the tile slots are re-read per class from L1); this keeps the register
+// count low enough for the occupancy a bandwidth-bound pass needs.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
   constexpr int NV = VEC ? 4 : 1;
@@ -27,38 +30,6 @@ __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
   const int j_lo = max(0, (cx - a.P) / a.S + ((cx - a.P) >= 0 ? 1 : 0));
   const int j_hi = min(a.gw - 1, cx / a.S);
 
-  float sum[OMNI_MAX_CLASSES][NV];
-  int votes[OMNI_MAX_CLASSES][NV];
-#pragma unroll
-  for (int c = 0; c < OMNI_MAX_CLASSES; ++c)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { sum[c][v] = 0.f; votes[c][v] = 0; }
-  int cov = 0;
-  for (int i = i_lo; i <= i_hi; ++i) {
-    for (int j = j_lo; j <= j_hi; ++j) {
-      const int slot = a.slot_map[i * a.gw + j];
-      if (slot < 0) continue;
-      ++cov;
-      const float* base = a.logits + (long long)slot * a.n_cls * PP +
-                          (long long)(cy - i * a.S) * a.P + (cx - j * a.S);
-#pragma unroll
-      for (int c = 0; c < OMNI_MAX_CLASSES; ++c) {
-        if (c >= a.n_cls) break;
-        float l[NV];
-        if constexpr (VEC) {
-          float4 q = __ldg(reinterpret_cast<const float4*>(base + c * PP));
-          l[0] = q.x; l[1] = q.y; l[2] = q.z; l[3] = q.w;
-        } else {
-          l[0] = __ldg(base + c * PP);
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          sum[c][v] += l[v];
-          votes[c][v] += l[v] > 0.f ? 1 : 0;
-        }
-      }
-    }
-  }
   bool tis = true;
   if (a.tissue) {
     const int ty = (int)(((long long)cy * a.f) / kThumb), tx = (int)(((long long)cx * a.f) / kThumb);
@@ -69,16 +40,41 @@ __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
   int arg[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) { best[v] = 0.f; arg[v] = 0; }
+  int cov = 0;
+  for (int c = 0; c < a.n_cls; ++c) {
+    float sum[NV];
+    int votes[NV];
 #pragma unroll
-  for (int c = 0; c < OMNI_MAX_CLASSES; ++c) {
-    if (c >= a.n_cls) break;
+    for (int v = 0; v < NV; ++v) { sum[v] = 0.f; votes[v] = 0; }
+    int n = 0;
+    for (int i = i_lo; i <= i_hi; ++i) {
+      for (int j = j_lo; j <= j_hi; ++j) {
+        const int slot = a.slot_map[i * a.gw + j];
+        if (slot < 0) continue;
+        ++n;
+        const float* base = a.logits + ((long long)slot * a.n_cls + c) * PP +
+                            (long long)(cy - i * a.S) * a.P + (cx - j * a.S);
+        float l[NV];
+        if constexpr (VEC) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(base));
+          l[0] = q.x; l[1] = q.y; l[2] = q.z; l[3] = q.w;
+        } else {
+          l[0] = __ldg(base);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          sum[v] += l[v];
+          votes[v] += l[v] > 0.f ? 1 : 0;
+        }
+      }
+    }
+    cov = n;
     float L[NV];
     uint8_t lab[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      L[v] = cov > 0 ? sum[c][v] / (float)cov : 0.f;
-      bool on = a.mode == OMNI_STITCH_AVG ? (cov > 0 && L[v] > 0.f)
-                                          : (cov > 0 && 2 * votes[c][v] >= cov);
+      L[v] = cov > 0 ? sum[v] / (float)cov : 0.f;
+      const bool on = a.mode == OMNI_STITCH_AVG ? (cov > 0 && L[v] > 0.f) : (cov > 0 && 2 * votes[v] >= cov);
       lab[v] = (on && tis) ? 1 : 0;
       if (L[v] > best[v]) { best[v] = L[v]; arg[v] = a.cls_ids[c] + 1; }
     }
