@@ -220,6 +220,77 @@ def run_ragged(args, api, _lib, dev, prec):
     seg.close()
 
 
+def run_large(args, api, _lib, dev, prec):
+    """The large throughput sweep: four 32768x98304 needle-biopsy slides (35% tissue,
+    seeds 200-203) with 1024-px tiles at stride 512; one step segments all four.
+    With --compare-fp32 the first slide is also segmented by the plain FP32 path
+    and the per-class label agreement and Dice against it are reported."""
+    import torch
+    works = [synth.LARGE.with_(name=f"large{k}", seed=200 + k) for k in range(4)]
+    blob = synth.gen_weights(works[0])
+    seg = api.Segmenter(works[0], blob, precision=prec)
+    if prec != _lib.FP32 and not args.no_autotune:
+        seg.set_autotune(True)
+    seg.workspace(seg.query(works[0].H, works[0].W).workspace_bytes, dev)
+    rgbs = [api.synth_slide(synth.spec_for(w), device=dev) for w in works]
+    outs = [seg.segment(r) for r in rgbs]
+    torch.cuda.synchronize()
+    for _ in range(max(0, args.warmup - 1)):
+        for r, o in zip(rgbs, outs):
+            seg.segment(r, out=o)
+    torch.cuda.synchronize()
+    seg.set_timing(True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        t0.record()
+        for _ in range(args.steps):
+            for r, o in zip(rgbs, outs):
+                seg.segment(r, out=o)
+        t1.record()
+        torch.cuda.synchronize()
+    conv_ms, conv_n, conv_flops = seg.timing(0)
+    seg.set_timing(False)
+    ms_step = t0.elapsed_time(t1) / args.steps
+    mpx = sum(w.H * w.W for w in works) / 1e6
+    pk, src = peaks()
+    peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    achieved = conv_flops / (conv_ms / 1e3) / 1e12 if conv_ms else None
+    line = {"metric": "large 4-slide segmentation Mpx/s", "value": mpx / (ms_step / 1e3), "unit": "Mpx/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "4 needle-biopsy slides 32768x98304 at 40x, 35% tissue, tiles 1024 "
+                                   "stride 512, base 32 x 5 levels, 6 heads", "slides_mpx": mpx,
+                       "tiles_per_step": int(round(conv_flops / args.steps /
+                                                   seg.query(works[0].H, works[0].W).flops_per_tile))},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "kernel": "conv (all U-Net layers)", "peak_source": f"bf16 dense sustained ({src})"},
+            "clocks": clk.summary()}
+    if args.compare_fp32 and prec != _lib.FP32:
+        keep = {c: t.clone() for c, t in outs[0]["labels"].items()}
+        seg.close()
+        seg._ws = None                     # the BF16 workspace
+        del outs, seg
+        rgbs = rgbs[:1]
+        torch.cuda.empty_cache()
+        seg32 = api.Segmenter(works[0], blob, precision=_lib.FP32)
+        o32 = seg32.segment(rgbs[0])
+        torch.cuda.synchronize()
+        rows = []
+        for c, lab in keep.items():
+            a, b = lab > 0, o32["labels"][c] > 0
+            den = int(a.sum().item() + b.sum().item())
+            inter = int((a & b).sum().item())
+            rows.append({"class": int(c), "agree": float((a == b).float().mean().item()),
+                         "dice": 1.0 if den == 0 else 2.0 * inter / den, "positives_fp32": int(b.sum().item())})
+        line["labels_vs_fp32_slide0"] = rows
+        seg32.close()
+    else:
+        seg.close()
+    print(json.dumps(line))
+
+
 def cpu_baseline(max_tiles: int = 4):
     """The FP64 oracle timed on a bounded sample: the first foreground 40x tiles
     of the needle slide (generated on the CPU), through U-Net, heads and the
@@ -289,6 +360,8 @@ def main():
     ap.add_argument("--ragged", action="store_true",
                     help="the 12-slide ragged workload: per-slide latency and aggregate Mpx/s")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--large", action="store_true",
+                    help="the large sweep: four 32768x98304 slides, 1024-px tiles (its own JSON line)")
     ap.add_argument("--workload", default="needle", choices=["needle", "small"],
                     help="small: a 2048x8192 slice of the needle configuration, for multi-pass ncu "
                          "captures that must stay a few GB (never a bench line)")
@@ -322,6 +395,9 @@ def main():
 
     if args.ragged:
         run_ragged(args, api, _lib, dev, prec)
+        return
+    if args.large:
+        run_large(args, api, _lib, dev, prec)
         return
     work = WORK if args.workload == "needle" else WORK.with_(name="needle_small", H=2048, W=8192)
     if work is not WORK and not args.profile_step:
