@@ -548,12 +548,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 constexpr int kHTH = 8, kHTW = 16;
 constexpr int kHBoxPix = (kHTH + 2) * kHTW;   // 160 input pixels per dx box
 
-template <int BN, int CK, bool RES>
+// MB = 2: a tile is two vertically adjacent 8 x 16 blocks (16 x 16 pixels);
+// the boxes are 18 rows high and every synchronisation of the pipeline
+// covers twice the MMAs (the per-tile waits dominate at small N).
+template <int BN, int CK, bool RES, int MB>
 struct HaloCfg {
-  static constexpr int kBoxBytes = kHBoxPix * CK * 2;
+  static constexpr int kBoxRows = kHTH * MB + 2;
+  static constexpr int kBoxBytes = kBoxRows * kHTW * CK * 2;
   static constexpr int kStageBytes = 3 * kBoxBytes;
   static constexpr int kWTileBytes = BN * CK * 2;
-  static constexpr int kBufCols = RES ? 2 * BN : BN;
+  static constexpr int kBlkCols = RES ? 2 * BN : BN;     // one 128-pixel block: conv | projection
+  static constexpr int kBufCols = MB * kBlkCols;
   static constexpr int kBufs = tmem_bufs(kBufCols);
   static constexpr int kTmemCols = tmem_alloc_cols(kBufs * kBufCols);
   static constexpr int kSW = CK * 2;
@@ -563,16 +568,16 @@ struct HaloParams {
   TCParams t;                       // t.k_res = slots of the projection segment (3 chunks each)
   int res_chunks;                   // channel chunks of the projection input
   int stages, n_wtiles, cpt;        // stages of the ring; cpt = channel chunks of the main input
-  int tiles_per_img, tiles_w;       // (R/8)*(R/16), R/16
+  int tiles_per_img, tiles_w;       // (R/(8 MB))*(R/16), R/16
   int group;                        // slots (one chunk's 3 boxes, or 3 projection chunks) per stage
 };
 
-template <int BN, int CK, bool RES>
+template <int BN, int CK, bool RES, int MB>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_conv_tc_halo(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
                    HaloParams hp) {
-  using Cfg = HaloCfg<BN, CK, RES>;
+  using Cfg = HaloCfg<BN, CK, RES, MB>;
   const TCParams& p = hp.t;
   const int ST = hp.stages;
   extern __shared__ uint8_t smem_raw[];
@@ -618,8 +623,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
     for (int b = 0; b < Cfg::kBufs; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
-      // fused head: one warpgroup per TMEM buffer
-      mbar_init(smem_u32(&tempty[b]), fuse_head ? kEpiWarps / 2 : kEpiWarps);
+      // one block: with the fused head each warpgroup owns the buffers of one parity
+      mbar_init(smem_u32(&tempty[b]), MB == 1 && fuse_head ? kEpiWarps / 2 : kEpiWarps);
     }
     mbar_init(smem_u32(drain), 1);
     mbar_init(smem_u32(wbar), 1);
@@ -659,7 +664,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       bool ok = true;
       for (; tw.t < p.n_tiles && ok; tw.next()) {
         const int img = tw.img;
-        const int h0 = tw.ty * kHTH, w0 = tw.tx * kHTW;
+        const int h0 = tw.ty * (kHTH * MB), w0 = tw.tx * kHTW;
         for (int k0 = 0; k0 < k_total; k0 += G, ++it, ring.next(ST)) {
           const int s = ring.s;
           if (ring.lapped && !mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
@@ -672,7 +677,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           for (int j = 0; j < nsl; ++j) {
             const int k = k0 + j;
             bytes += k < p.k_main ? (uint32_t)Cfg::kStageBytes
-                                  : (uint32_t)(min(3, hp.res_chunks - (k - p.k_main) * 3) * kBM * CK * 2);
+                                  : (uint32_t)(min(3, hp.res_chunks - (k - p.k_main) * 3) * MB * kBM * CK * 2);
           }
           mbar_expect_tx(fb, bytes);
           for (int j = 0; j < nsl; ++j) {
@@ -730,24 +735,32 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
               const uint64_t bd = b_desc0 + (uint64_t)(k * (Cfg::kWTileBytes >> 4));
               const uint32_t acc_first = k > 0 ? 1u : 0u;
 #pragma unroll
-              for (int tap = 0; tap < 9; ++tap) {
-                const uint64_t at =
-                    ad + (uint64_t)(((tap % 3) * Cfg::kBoxBytes + (tap / 3) * kHTW * CK * 2) >> 4);
-                const uint64_t bt = bd + (uint64_t)tap * b_tap_step;
+              for (int blk = 0; blk < MB; ++blk) {
 #pragma unroll
-                for (int kk = 0; kk < CK / 16; ++kk)
-                  mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc,
-                           (tap > 0 || kk > 0) ? 1u : acc_first);
+                for (int tap = 0; tap < 9; ++tap) {
+                  // tap (dy, dx): box dx, rows dy + 8 blk .. (whole swizzle atoms)
+                  const uint64_t at = ad + (uint64_t)(((tap % 3) * Cfg::kBoxBytes +
+                                                       (tap / 3 + kHTH * blk) * kHTW * CK * 2) >> 4);
+                  const uint64_t bt = bd + (uint64_t)tap * b_tap_step;
+#pragma unroll
+                  for (int kk = 0; kk < CK / 16; ++kk)
+                    mma_bf16(acc0 + (uint32_t)(blk * Cfg::kBlkCols), at + (uint64_t)(kk * 2),
+                             bt + (uint64_t)(kk * 2), idesc, (tap > 0 || kk > 0) ? 1u : acc_first);
+                }
               }
             } else if (RES) {
               const int c0 = (k - p.k_main) * 3, nbx = min(3, hp.res_chunks - c0);
               for (int b = 0; b < nbx; ++b) {
-                const uint64_t ab = ad + (uint64_t)((b * Cfg::kBoxBytes) >> 4);
                 const uint64_t bd = b_desc0 + (uint64_t)((9 * hp.cpt + c0 + b) * (Cfg::kWTileBytes >> 4));
 #pragma unroll
-                for (int kk = 0; kk < CK / 16; ++kk)
-                  mma_bf16(acc1, ab + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                           (c0 + b > 0 || kk > 0) ? 1u : 0u);
+                for (int blk = 0; blk < MB; ++blk) {
+                  const uint64_t ab =
+                      ad + (uint64_t)((b * Cfg::kBoxBytes + kHTH * blk * kHTW * CK * 2) >> 4);
+#pragma unroll
+                  for (int kk = 0; kk < CK / 16; ++kk)
+                    mma_bf16(acc1 + (uint32_t)(blk * Cfg::kBlkCols), ab + (uint64_t)(kk * 2),
+                             bd + (uint64_t)(kk * 2), idesc, (c0 + b > 0 || kk > 0) ? 1u : 0u);
+                }
               }
             }
           }
@@ -764,9 +777,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // Default: warps w and w+4 share TMEM lane quarter w%4 and split the
     // columns.  Fused head: each warpgroup owns the TMEM buffers of one parity
     // (alternate tiles) and reads every column, so a thread holds its pixel.
+    // MB = 2: warpgroup g takes block g of every tile, all columns.
     const int q = warp & 3, grp = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    const int c_beg = fuse_head ? 0 : grp * (BN / 2), c_end = fuse_head ? BN : c_beg + BN / 2;
+    const bool split = MB == 1 && !fuse_head;
+    const int blk = MB == 2 ? grp : 0;
+    const int c_beg = split ? grp * (BN / 2) : 0, c_end = split ? c_beg + BN / 2 : BN;
     const int Rh = p.R >> 1;
     float* sth = sthe + (warp - 2) * (2 * kHeadParams);
     int th_img = -1;
@@ -775,12 +791,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
     for (; tw.t < p.n_tiles; tw.next(), ++tcount) {
       const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
-      if (fuse_head && (buf & 1) != grp) continue;
+      if (MB == 1 && fuse_head && (buf & 1) != grp) continue;
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const int img = tw.img;
-      const int hh = tw.ty * kHTH + row / kHTW;
+      const int hh = tw.ty * (kHTH * MB) + blk * kHTH + row / kHTW;
       const int ww = tw.tx * kHTW + row % kHTW;
       const long long m = (long long)img * RR + (long long)hh * p.R + ww;
       float v0 = 0.f, v1 = 0.f, v2 = 0.f;
@@ -794,7 +810,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       float h0[kHeadCh];
 #pragma unroll
       for (int o = 0; o < kHeadCh; ++o) h0[o] = fuse_head ? sbh[o] : 0.f;
-      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) +
+                          (uint32_t)(buf * Cfg::kBufCols + blk * Cfg::kBlkCols);
 #pragma unroll 1
       for (int c = c_beg; c < c_end; c += 16) {
         float a[16], r[16], o16[16];
@@ -1549,11 +1566,11 @@ void set_fused(const ConvArgs& a, TCParams& p, bool head_ok) {
   }
 }
 
-// stages of the small-N variant for a layer and channel chunk (0: does not fit)
-int halo_stages(int cin, int cout, int cr, int ck) {
+// slots of the small-N variant for a layer, channel chunk and blocks per tile (0: does not fit)
+int halo_stages(int cin, int cout, int cr, int ck, int mb = 1) {
   if (cin % ck || cr % ck) return 0;
   const long long wbytes = (long long)(9 * (cin / ck) + cr / ck) * cout * ck * 2;
-  const long long stage = 3LL * kHBoxPix * ck * 2;
+  const long long stage = 3LL * (kHTH * mb + 2) * kHTW * ck * 2;
   long long st = (kHaloSmemMax - wbytes - kHaloSmemExtra) / stage;
   return st < 2 ? 0 : (int)(st > 8 ? 8 : st);
 }
@@ -1563,14 +1580,15 @@ bool halo_ok(int R, int cout, int cin, int cr) {
   return halo_stages(cin, cout, cr, 32) >= 2;
 }
 
-template <int BN, int CK, bool RES>
+template <int BN, int CK, bool RES, int MB>
 cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
-  using Cfg = HaloCfg<BN, CK, RES>;
+  using Cfg = HaloCfg<BN, CK, RES, MB>;
   CUtensorMap mA, mB, mA2, mB2;
-  if (!map_act_box(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, kHTW, kHTH + 2)) return cudaErrorInvalidValue;
+  if (a.R % (kHTH * MB)) return cudaErrorInvalidValue;
+  if (!map_act_box(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, kHTW, Cfg::kBoxRows)) return cudaErrorInvalidValue;
   if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, BN, CK)) return cudaErrorInvalidValue;
   if (RES) {
-    if (!map_act_box(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK, kHTW, kHTH)) return cudaErrorInvalidValue;
+    if (!map_act_box(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK, kHTW, kHTH * MB)) return cudaErrorInvalidValue;
     if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, BN, CK)) return cudaErrorInvalidValue;
   } else {
     mA2 = mA;
@@ -1581,7 +1599,7 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
   p.B = a.B; p.R = a.R; p.cin = a.cin; p.cout = a.cout; p.cr = RES ? a.cr : 0;
   p.res_mode = a.res_mode;
   hp.tiles_w = a.R / kHTW;
-  hp.tiles_per_img = (a.R / kHTH) * hp.tiles_w;
+  hp.tiles_per_img = (a.R / (kHTH * MB)) * hp.tiles_w;
   p.n_tiles_m = a.B * hp.tiles_per_img;
   p.n_tiles_n = 1;
   p.n_tiles = p.n_tiles_m;
@@ -1617,7 +1635,7 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
   hp.stages = stages;
   const size_t smem = fixed + (size_t)stages * stage_bytes;
   if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
-  auto kern = k_conv_tc_halo<BN, CK, RES>;
+  auto kern = k_conv_tc_halo<BN, CK, RES, MB>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloSmemMax);
@@ -1795,21 +1813,24 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
       const int stg = dxn_stages(cin, cout, cr, ck);
       if (stg >= 2 && n < max) out[n++] = TcConfig{2, cout, ck, stg};
     }
-  if (halo_ok(R, cout, cin, cr))
+  if (halo_ok(R, cout, cin, cr)) {
     for (int ck = 32; ck <= 64; ck *= 2) {
       const int stg = halo_stages(cin, cout, cr, ck);
       if (stg >= 2 && n < max) out[n++] = TcConfig{1, cout, ck, stg};
     }
+    const int stg2 = halo_stages(cin, cout, cr, 32, 2);
+    if (stg2 >= 2 && n < max) out[n++] = TcConfig{3, cout, 32, stg2};
+  }
   for (int bn = 32; bn <= 256; bn *= 2)
     for (int ck = 32; ck <= 64; ck *= 2)
       if (pertap_ok(R, cin, cout, cr, bn, ck) && n < max) out[n++] = TcConfig{0, bn, ck, 0};
   return n;
 }
 
-bool tc_fuses_pool(const TcConfig& c) { return c.kind == 1 || c.kind == 2; }
+bool tc_fuses_pool(const TcConfig& c) { return c.kind >= 1 && c.kind <= 3; }
 
 bool tc_fuses_head(const TcConfig& c, int cout, int ncls) {
-  return c.kind == 1 && (cout == 32 || cout == 64) && ncls >= 1 && ncls <= 2;
+  return (c.kind == 1 || c.kind == 3) && (cout == 32 || cout == 64) && ncls >= 1 && ncls <= 2;
 }
 
 TcConfig tc_default(int R, int cin, int cout, int cr) {
@@ -1825,6 +1846,9 @@ TcConfig tc_default(int R, int cin, int cout, int cr) {
     int ck = 32, stg = halo_stages(cin, cout, cr, 32);
     const int stg64 = halo_stages(cin, cout, cr, 64);
     if (stg64 >= 3) { ck = 64; stg = stg64; }
+    // 32-channel chunks: two blocks per tile halve the per-tile synchronisation
+    const int stg2 = halo_stages(cin, cout, cr, 32, 2);
+    if (ck == 32 && stg2 >= 2) return TcConfig{3, cout, 32, stg2};
     return TcConfig{1, cout, ck, stg};
   }
   const bool res = cr > 0;
@@ -1858,10 +1882,18 @@ cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaSt
         c.stages > halo_stages(a.cin, a.cout, cr, c.ck))
       return cudaErrorInvalidValue;
 #define OMNI_HALO(BN_, CK_, RES_) \
-    if (c.bn == BN_ && c.ck == CK_ && res == RES_) return launch_halo<BN_, CK_, RES_>(a, st, c.stages);
+    if (c.bn == BN_ && c.ck == CK_ && res == RES_) return launch_halo<BN_, CK_, RES_, 1>(a, st, c.stages);
     OMNI_HALO(32, 32, false) OMNI_HALO(32, 32, true) OMNI_HALO(32, 64, false) OMNI_HALO(32, 64, true)
     OMNI_HALO(64, 32, false) OMNI_HALO(64, 32, true) OMNI_HALO(64, 64, false) OMNI_HALO(64, 64, true)
 #undef OMNI_HALO
+    return cudaErrorInvalidValue;
+  }
+  if (c.kind == 3) {
+    if (!halo_ok(a.R, a.cout, a.cin, cr) || c.bn != a.cout || c.ck != 32 || c.stages < 2 ||
+        c.stages > halo_stages(a.cin, a.cout, cr, 32, 2))
+      return cudaErrorInvalidValue;
+    if (c.bn == 32) return res ? launch_halo<32, 32, true, 2>(a, st, c.stages) : launch_halo<32, 32, false, 2>(a, st, c.stages);
+    if (c.bn == 64) return res ? launch_halo<64, 32, true, 2>(a, st, c.stages) : launch_halo<64, 32, false, 2>(a, st, c.stages);
     return cudaErrorInvalidValue;
   }
   if (!pertap_ok(a.R, a.cin, a.cout, cr, c.bn, c.ck)) return cudaErrorInvalidValue;
