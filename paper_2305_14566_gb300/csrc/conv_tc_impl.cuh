@@ -52,7 +52,7 @@ constexpr int kBM = 128;
 constexpr int kEpiWarps = 8;                         // two epilogue warpgroups
 constexpr int kThreadsTC = 64 + 32 * kEpiWarps;      // producer warp, MMA warp, epilogue
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
-constexpr int kSmemBudget = 200 * 1024;
+constexpr int kSmemBudget = 222 * 1024;      // per-tap operand slots (+ barriers, norm arrays, alignment)
 
 struct TCParams {
   int B, R, cin, cout, cr;
