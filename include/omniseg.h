@@ -235,7 +235,8 @@ int64_t omni_last_launch_count(const omni_ctx* ctx);
  * real operands and the fastest is kept for the context's lifetime.  Tuning
  * synchronises the stream, so run one untimed call first.  omni_get_tuned
  * writes 10 int32 per tuned shape: R, cin, cout, cr, residual kind, batch,
- * kind (0 per-tap, 1 small-N, 2 dx-in-N, 3 small-N with two blocks per tile),
+ * kind (0 per-tap, 1 small-N, 2 dx-in-N, 3 small-N with two blocks per tile,
+ * 4 dx-in-N with two blocks per tile),
  * N tile, channel chunk, stages; returns the count. */
 omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled);
 int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows);

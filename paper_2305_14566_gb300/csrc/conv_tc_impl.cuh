@@ -892,14 +892,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 // one halo column on each side (lanes 0 and 15 of each row group write nothing).
 constexpr int kXTW = 14;                       // valid output columns per tile row
 
-template <int CO, int CK, bool RES>
+// MB = 2: two vertically adjacent 8-row blocks per tile (16 x 14 outputs),
+// 18-row boxes, one pipeline synchronisation per two blocks.
+template <int CO, int CK, bool RES, int MB>
 struct DxnCfg {
   static constexpr int kN = 3 * CO;                        // MMA N (dx blocks)
-  static constexpr int kBoxBytes = kHBoxPix * CK * 2;      // 10 x 16 pixels
+  static constexpr int kBoxRows = kHTH * MB + 2;
+  static constexpr int kBoxBytes = kBoxRows * kHTW * CK * 2;
   static constexpr int kStageBytes = kBoxBytes;            // one box slot (a stage holds cps slots)
   static constexpr int kWTileBytes = kN * CK * 2;          // 3 dx slices of cout x CK
   static constexpr int kRTileBytes = CO * CK * 2;          // projection weights
-  static constexpr int kBufCols = RES ? kN + CO : kN;
+  static constexpr int kBlkCols = RES ? kN + CO : kN;      // one 128-lane block: dx blocks | projection
+  static constexpr int kBufCols = MB * kBlkCols;
   static constexpr int kBufs = tmem_bufs(kBufCols);
   static constexpr int kTmemCols = tmem_alloc_cols(kBufs * kBufCols);
   static constexpr int kSW = CK * 2;
@@ -914,12 +918,12 @@ struct DxnParams {
   int main_stages;                 // ceil(cpt / cps); t.k_res = ceil(res_chunks / cps)
 };
 
-template <int CO, int CK, bool RES>
+template <int CO, int CK, bool RES, int MB>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_conv_tc_dxn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
                   DxnParams hp) {
-  using Cfg = DxnCfg<CO, CK, RES>;
+  using Cfg = DxnCfg<CO, CK, RES, MB>;
   const TCParams& p = hp.t;
   const int ST = hp.stages;
   extern __shared__ uint8_t smem_raw[];
@@ -999,7 +1003,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       bool ok = true;
       for (; tw.t < p.n_tiles && ok; tw.next()) {
         const int img = tw.img;
-        const int h0 = tw.ty * kHTH, w0 = tw.tx * kXTW;
+        const int h0 = tw.ty * (kHTH * MB), w0 = tw.tx * kXTW;
         for (int k = 0; k < k_total; ++k, ++it, ring.next(ST)) {
           const int s = ring.s;
           if (ring.lapped && !mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
@@ -1015,7 +1019,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
               tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA, fb, (c0 + j) * CK, w0 - 1, h0 - 1, img);
           } else {
             const int r0 = (k - hp.main_stages) * hp.cps, nb = min(hp.cps, hp.res_chunks - r0);
-            mbar_expect_tx(fb, (uint32_t)(nb * kBM * CK * 2));
+            mbar_expect_tx(fb, (uint32_t)(nb * MB * kBM * CK * 2));
             for (int j = 0; j < nb; ++j)
               tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA2, fb, (r0 + j) * CK, w0 - 1, h0, img);
           }
@@ -1061,24 +1065,31 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
               const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
               const uint64_t bk = w_desc0 + (uint64_t)(c * (Cfg::kWTileBytes >> 4));
 #pragma unroll
-              for (int dy = 0; dy < 3; ++dy) {
-                const uint64_t at = aj + (uint64_t)((dy * kHTW * CK * 2) >> 4);
-                const uint64_t bt = bk + (uint64_t)dy * dy_step;
+              for (int blk = 0; blk < MB; ++blk) {
 #pragma unroll
-                for (int kk = 0; kk < CK / 16; ++kk)
-                  mma_bf16(acc0, at + (uint64_t)(kk * 2), bt + (uint64_t)(kk * 2), idesc_n,
-                           (c > 0 || dy > 0 || kk > 0) ? 1u : 0u);
+                for (int dy = 0; dy < 3; ++dy) {
+                  const uint64_t at = aj + (uint64_t)(((dy + kHTH * blk) * kHTW * CK * 2) >> 4);
+                  const uint64_t bt = bk + (uint64_t)dy * dy_step;
+#pragma unroll
+                  for (int kk = 0; kk < CK / 16; ++kk)
+                    mma_bf16(acc0 + (uint32_t)(blk * Cfg::kBlkCols), at + (uint64_t)(kk * 2),
+                             bt + (uint64_t)(kk * 2), idesc_n, (c > 0 || dy > 0 || kk > 0) ? 1u : 0u);
+                }
               }
             }
           } else if (RES) {
             const int r0 = (k - hp.main_stages) * hp.cps, nb = min(hp.cps, hp.res_chunks - r0);
             for (int j = 0; j < nb; ++j) {
-              const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
               const uint64_t bd = r_desc0 + (uint64_t)((r0 + j) * (Cfg::kRTileBytes >> 4));
 #pragma unroll
-              for (int kk = 0; kk < CK / 16; ++kk)
-                mma_bf16(acc1, aj + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc_r,
-                         (r0 + j > 0 || kk > 0) ? 1u : 0u);
+              for (int blk = 0; blk < MB; ++blk) {
+                const uint64_t aj =
+                    ad + (uint64_t)((j * Cfg::kBoxBytes + kHTH * blk * kHTW * CK * 2) >> 4);
+#pragma unroll
+                for (int kk = 0; kk < CK / 16; ++kk)
+                  mma_bf16(acc1 + (uint32_t)(blk * Cfg::kBlkCols), aj + (uint64_t)(kk * 2),
+                           bd + (uint64_t)(kk * 2), idesc_r, (r0 + j > 0 || kk > 0) ? 1u : 0u);
+              }
             }
           }
           mma_commit(smem_u32(&empty[s]));
@@ -1091,11 +1102,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
   } else {
     // ------------------------------------------------------------------ epilogue
-    // warps w and w+4 share lane quarter w%4 and split the output channels
-    const int q = warp & 3;
+    // MB = 1: warps w and w+4 share lane quarter w%4 and split the output
+    // channels; MB = 2: warpgroup g takes block g, all channels
+    const int q = warp & 3, grp = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     const int col = row % kHTW;                        // column inside the 16-lane row group
-    const int co_beg = ((warp - 2) >> 2) * (CO / 2), co_end = co_beg + CO / 2;
+    const int blk = MB == 2 ? grp : 0;
+    const int co_beg = MB == 1 ? grp * (CO / 2) : 0, co_end = MB == 1 ? co_beg + CO / 2 : CO;
     int tcount = 0;
     TileWalk tw;
     tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
@@ -1105,7 +1118,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const int img = tw.img;
-      const int hh = tw.ty * kHTH + row / kHTW;
+      const int hh = tw.ty * (kHTH * MB) + blk * kHTH + row / kHTW;
       const int ww = tw.tx * kXTW + col - 1;                        // this lane's pixel column
       const bool writes = col >= 1 && col <= kXTW && ww < p.R;
       const long long m = (long long)img * RR + (long long)hh * p.R + (ww < 0 ? 0 : ww);
@@ -1118,7 +1131,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         v2 = norm_u8(px[2]);
       }
       __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
-      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) +
+                          (uint32_t)(buf * Cfg::kBufCols + blk * Cfg::kBlkCols);
 #pragma unroll 1
       for (int c = co_beg; c < co_end; c += 16) {
         float d0[16], d1[16], d2[16], r[16], o16[16];
@@ -1649,10 +1663,10 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
 
 // dx-in-N variant: resident weights + one 10 x 16 box per stage
 int dxn_wbytes(int cin, int cout, int cr, int ck) { return (9 * (cin / ck) + cr / ck) * cout * ck * 2; }
-int dxn_stages(int cin, int cout, int cr, int ck) {
+int dxn_stages(int cin, int cout, int cr, int ck, int mb = 1) {
   if (cin % ck || cr % ck) return 0;
   const long long st = (kHaloSmemMax - (long long)dxn_wbytes(cin, cout, cr, ck) - kHaloSmemExtra) /
-                       ((long long)kHBoxPix * ck * 2);
+                       ((long long)(kHTH * mb + 2) * kHTW * ck * 2);
   return st < 2 ? 0 : (int)(st > 12 ? 12 : st);
 }
 bool dxn_ok(int R, int cout, int cin, int cr) {
@@ -1660,14 +1674,15 @@ bool dxn_ok(int R, int cout, int cin, int cr) {
   return dxn_stages(cin, cout, cr, 32) >= 2;
 }
 
-template <int CO, int CK, bool RES>
+template <int CO, int CK, bool RES, int MB>
 cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
-  using Cfg = DxnCfg<CO, CK, RES>;
+  using Cfg = DxnCfg<CO, CK, RES, MB>;
   CUtensorMap mA, mB, mA2, mB2;
-  if (!map_act_box(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, kHTW, kHTH + 2)) return cudaErrorInvalidValue;
+  if (a.R % (kHTH * MB)) return cudaErrorInvalidValue;
+  if (!map_act_box(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, kHTW, Cfg::kBoxRows)) return cudaErrorInvalidValue;
   if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, CO, CK)) return cudaErrorInvalidValue;
   if (RES) {
-    if (!map_act_box(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK, kHTW, kHTH)) return cudaErrorInvalidValue;
+    if (!map_act_box(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK, kHTW, kHTH * MB)) return cudaErrorInvalidValue;
     if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, CO, CK)) return cudaErrorInvalidValue;
   } else {
     mA2 = mA;
@@ -1678,7 +1693,7 @@ cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
   p.B = a.B; p.R = a.R; p.cin = a.cin; p.cout = a.cout; p.cr = RES ? a.cr : 0;
   p.res_mode = a.res_mode;
   hp.tiles_w = (a.R + kXTW - 1) / kXTW;
-  hp.tiles_per_img = (a.R / kHTH) * hp.tiles_w;
+  hp.tiles_per_img = (a.R / (kHTH * MB)) * hp.tiles_w;
   p.n_tiles_m = a.B * hp.tiles_per_img;
   p.n_tiles_n = 1;
   p.n_tiles = p.n_tiles_m;
@@ -1707,7 +1722,7 @@ cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
   set_fused(a, p, false);
   const size_t smem = (size_t)hp.wbytes + (size_t)stages * hp.cps * Cfg::kStageBytes + kHaloSmemExtra;
   if (stages < 2 || smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
-  auto kern = k_conv_tc_dxn<CO, CK, RES>;
+  auto kern = k_conv_tc_dxn<CO, CK, RES, MB>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloSmemMax);
@@ -1808,11 +1823,14 @@ bool pertap_ok(int R, int cin, int cout, int cr, int bn, int ck) {
 #if !OMNI_TC_F16
 int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
   int n = 0;
-  if (dxn_ok(R, cout, cin, cr))
+  if (dxn_ok(R, cout, cin, cr)) {
     for (int ck = 32; ck <= 64; ck *= 2) {
       const int stg = dxn_stages(cin, cout, cr, ck);
       if (stg >= 2 && n < max) out[n++] = TcConfig{2, cout, ck, stg};
     }
+    const int stg2 = dxn_stages(cin, cout, cr, 32, 2);
+    if (cout == 32 && R % 16 == 0 && stg2 >= 2 && n < max) out[n++] = TcConfig{4, 32, 32, stg2};
+  }
   if (halo_ok(R, cout, cin, cr)) {
     for (int ck = 32; ck <= 64; ck *= 2) {
       const int stg = halo_stages(cin, cout, cr, ck);
@@ -1827,7 +1845,7 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
   return n;
 }
 
-bool tc_fuses_pool(const TcConfig& c) { return c.kind >= 1 && c.kind <= 3; }
+bool tc_fuses_pool(const TcConfig& c) { return c.kind >= 1 && c.kind <= 4; }
 
 bool tc_fuses_head(const TcConfig& c, int cout, int ncls) {
   return (c.kind == 1 || c.kind == 3) && (cout == 32 || cout == 64) && ncls >= 1 && ncls <= 2;
@@ -1840,6 +1858,8 @@ TcConfig tc_default(int R, int cin, int cout, int cr) {
     int ck = 32, stg = dxn_stages(cin, cout, cr, 32);
     const int stg64 = dxn_stages(cin, cout, cr, 64);
     if (stg64 >= 4) { ck = 64; stg = stg64; }
+    const int stg2 = dxn_stages(cin, cout, cr, 32, 2);
+    if (cout == 32 && ck == 32 && R % 16 == 0 && stg2 >= 4) return TcConfig{4, 32, 32, stg2};
     return TcConfig{2, cout, ck, stg};
   }
   if (halo_ok(R, cout, cin, cr)) {
@@ -1871,11 +1891,18 @@ cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaSt
         c.stages > dxn_stages(a.cin, a.cout, cr, c.ck))
       return cudaErrorInvalidValue;
 #define OMNI_DXN(CO_, CK_, RES_) \
-    if (c.bn == CO_ && c.ck == CK_ && res == RES_) return launch_dxn<CO_, CK_, RES_>(a, st, c.stages);
+    if (c.bn == CO_ && c.ck == CK_ && res == RES_) return launch_dxn<CO_, CK_, RES_, 1>(a, st, c.stages);
     OMNI_DXN(32, 32, false) OMNI_DXN(32, 32, true) OMNI_DXN(32, 64, false) OMNI_DXN(32, 64, true)
     OMNI_DXN(64, 32, false) OMNI_DXN(64, 32, true) OMNI_DXN(64, 64, false) OMNI_DXN(64, 64, true)
 #undef OMNI_DXN
     return cudaErrorInvalidValue;
+  }
+  if (c.kind == 4) {
+    // two blocks per tile: cout 32 only (TMEM holds two buffers of 2 x (96 + 32) columns)
+    if (!dxn_ok(a.R, a.cout, a.cin, cr) || a.cout != 32 || c.bn != 32 || c.ck != 32 || a.R % 16 ||
+        c.stages < 2 || c.stages > dxn_stages(a.cin, a.cout, cr, 32, 2))
+      return cudaErrorInvalidValue;
+    return res ? launch_dxn<32, 32, true, 2>(a, st, c.stages) : launch_dxn<32, 32, false, 2>(a, st, c.stages);
   }
   if (c.kind == 1) {
     if (!halo_ok(a.R, a.cout, a.cin, cr) || c.bn != a.cout || c.stages < 2 ||
