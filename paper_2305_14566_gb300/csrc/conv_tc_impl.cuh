@@ -914,8 +914,7 @@ struct DxnParams {
   int res_chunks, stages, cpt;
   int tiles_per_img, tiles_w;      // (R/8) * ceil(R/14), ceil(R/14)
   int wbytes;                      // resident weight bytes (main + projection)
-  int cps;                         // channel chunks per pipeline stage (one box slot each)
-  int main_stages;                 // ceil(cpt / cps); t.k_res = ceil(res_chunks / cps)
+  int cps;                         // slots per pipeline stage; a tile has cpt + res_chunks slots
 };
 
 template <int CO, int CK, bool RES, int MB>
@@ -944,8 +943,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   float* swp = sb + CO;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(swp + 3 * CO);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* swh = reinterpret_cast<float*>(tmem_slot + 4);             // fused head (MB = 2): wh[8][CO]
+  float* sbh = swh + kHeadCh * CO;                                  // bh[8]
+  float* sthe = sbh + kHeadCh;                                      // theta copy per epilogue warp
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool fuse_head = MB == 2 && p.theta != nullptr;
   for (int i = threadIdx.x; i < CO; i += blockDim.x) {
     sg[i] = p.gamma[i];
     sb[i] = p.beta[i];
@@ -954,6 +957,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       swp[CO + i] = p.wp_rgb[p.cout + i];
       swp[2 * CO + i] = p.wp_rgb[2 * p.cout + i];
     }
+  }
+  if (fuse_head) {
+    for (int i = threadIdx.x; i < kHeadCh * CO; i += blockDim.x) swh[i] = p.wh[i];
+    if (threadIdx.x < kHeadCh) sbh[threadIdx.x] = p.bh[threadIdx.x];
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -1004,7 +1011,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       for (; tw.t < p.n_tiles && ok; tw.next()) {
         const int img = tw.img;
         const int h0 = tw.ty * (kHTH * MB), w0 = tw.tx * kXTW;
-        for (int k = 0; k < k_total; ++k, ++it, ring.next(ST)) {
+        // slots of a tile: cpt main chunks, then res_chunks projection chunks;
+        // a stage carries cps consecutive slots
+        for (int k0 = 0; k0 < k_total; k0 += hp.cps, ++it, ring.next(ST)) {
           const int s = ring.s;
           if (ring.lapped && !mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
             ok = false;
@@ -1012,16 +1021,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           }
           const uint32_t fb = smem_u32(&full[s]);
           uint8_t* st = sA + (size_t)s * stage_bytes;
-          if (k < hp.main_stages) {
-            const int c0 = k * hp.cps, nb = min(hp.cps, hp.cpt - c0);
-            mbar_expect_tx(fb, (uint32_t)(nb * Cfg::kBoxBytes));
-            for (int j = 0; j < nb; ++j)
-              tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA, fb, (c0 + j) * CK, w0 - 1, h0 - 1, img);
-          } else {
-            const int r0 = (k - hp.main_stages) * hp.cps, nb = min(hp.cps, hp.res_chunks - r0);
-            mbar_expect_tx(fb, (uint32_t)(nb * MB * kBM * CK * 2));
-            for (int j = 0; j < nb; ++j)
-              tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA2, fb, (r0 + j) * CK, w0 - 1, h0, img);
+          const int nb = min(hp.cps, k_total - k0);
+          uint32_t bytes = 0;
+          for (int j = 0; j < nb; ++j)
+            bytes += k0 + j < hp.cpt ? (uint32_t)Cfg::kBoxBytes : (uint32_t)(MB * kBM * CK * 2);
+          mbar_expect_tx(fb, bytes);
+          for (int j = 0; j < nb; ++j) {
+            const int k = k0 + j;
+            if (k < hp.cpt)
+              tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA, fb, k * CK, w0 - 1, h0 - 1, img);
+            else
+              tma_load_4d(smem_u32(st + j * Cfg::kBoxBytes), &mapA2, fb, (k - hp.cpt) * CK, w0 - 1, h0, img);
           }
         }
       }
@@ -1050,7 +1060,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         tc_fence_after();
         const uint32_t acc0 = tmem_base + (uint32_t)(buf * Cfg::kBufCols);
         const uint32_t acc1 = acc0 + Cfg::kN;
-        for (int k = 0; k < k_total; ++k, ring.next(ST)) {
+        for (int k0 = 0; k0 < k_total; k0 += hp.cps, ring.next(ST)) {
           const int s = ring.s;
           // TMA-filled stage: the mbarrier's complete_tx orders the copy before the MMAs
           if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
@@ -1058,10 +1068,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             break;
           }
           const uint64_t ad = a_desc0 + (uint64_t)((s * stage_bytes) >> 4);
-          if (k < hp.main_stages) {
-            const int c0 = k * hp.cps, nb = min(hp.cps, hp.cpt - c0);
-            for (int j = 0; j < nb; ++j) {
-              const int c = c0 + j;
+          const int nb = min(hp.cps, k_total - k0);
+          for (int j = 0; j < nb; ++j) {
+            const int c = k0 + j;
+            if (c < hp.cpt) {
               const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
               const uint64_t bk = w_desc0 + (uint64_t)(c * (Cfg::kWTileBytes >> 4));
 #pragma unroll
@@ -1076,11 +1086,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                              bt + (uint64_t)(kk * 2), idesc_n, (c > 0 || dy > 0 || kk > 0) ? 1u : 0u);
                 }
               }
-            }
-          } else if (RES) {
-            const int r0 = (k - hp.main_stages) * hp.cps, nb = min(hp.cps, hp.res_chunks - r0);
-            for (int j = 0; j < nb; ++j) {
-              const uint64_t bd = r_desc0 + (uint64_t)((r0 + j) * (Cfg::kRTileBytes >> 4));
+            } else if (RES) {
+              const int r = c - hp.cpt;
+              const uint64_t bd = r_desc0 + (uint64_t)(r * (Cfg::kRTileBytes >> 4));
 #pragma unroll
               for (int blk = 0; blk < MB; ++blk) {
                 const uint64_t aj =
@@ -1088,7 +1096,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
                 for (int kk = 0; kk < CK / 16; ++kk)
                   mma_bf16(acc1 + (uint32_t)(blk * Cfg::kBlkCols), aj + (uint64_t)(kk * 2),
-                           bd + (uint64_t)(kk * 2), idesc_r, (r0 + j > 0 || kk > 0) ? 1u : 0u);
+                           bd + (uint64_t)(kk * 2), idesc_r, (r > 0 || kk > 0) ? 1u : 0u);
               }
             }
           }
@@ -1109,6 +1117,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int col = row % kHTW;                        // column inside the 16-lane row group
     const int blk = MB == 2 ? grp : 0;
     const int co_beg = MB == 1 ? grp * (CO / 2) : 0, co_end = MB == 1 ? co_beg + CO / 2 : CO;
+    float* sth = sthe + (warp - 2) * (2 * kHeadParams);
+    int th_img = -1;
     int tcount = 0;
     TileWalk tw;
     tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
@@ -1133,6 +1143,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) +
                           (uint32_t)(buf * Cfg::kBufCols + blk * Cfg::kBlkCols);
+      float h0[kHeadCh];
+#pragma unroll
+      for (int o = 0; o < kHeadCh; ++o) h0[o] = fuse_head ? sbh[o] : 0.f;
 #pragma unroll 1
       for (int c = co_beg; c < co_end; c += 16) {
         float d0[16], d1[16], d2[16], r[16], o16[16];
@@ -1171,10 +1184,32 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
           }
         }
+        if (fuse_head) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaf(swh[o * CO + c + j], o16[j], h0[o]);
+        }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+      if (fuse_head) {
+        // the TMEM buffer is released; the heads run on registers and shared memory
+#pragma unroll
+        for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaxf(h0[o], 0.f);
+        if (img != th_img) {
+          __syncwarp();
+          const float* src = p.theta + (long long)img * p.ncls * kHeadParams;
+          for (int i2 = lane; i2 < p.ncls * kHeadParams; i2 += 32) sth[i2] = src[i2];
+          __syncwarp();
+          th_img = img;
+        }
+        if (writes) {
+          float* lo = p.logits + (long long)(p.slot0 + img) * p.ncls * RR + (long long)hh * p.R + ww;
+          for (int ci = 0; ci < p.ncls; ++ci) lo[(long long)ci * RR] = dyn_head(sth + ci * kHeadParams, h0);
+        }
+      }
     }
   }
   __syncwarp();
@@ -1699,14 +1734,14 @@ cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
   p.n_tiles = p.n_tiles_m;
   hp.cpt = a.cin / CK;
   hp.res_chunks = RES ? a.cr / CK : 0;
-  // group box slots into stages of up to a tile's channel chunks, keeping at
-  // least three stages in flight: fewer waits and commits per MMA
-  hp.cps = max(1, min(hp.cpt, stages / 3));
-  hp.main_stages = (hp.cpt + hp.cps - 1) / hp.cps;
-  p.k_main = hp.main_stages;
-  p.k_res = (hp.res_chunks + hp.cps - 1) / hp.cps;
+  // a tile's slots (main chunks, then projection chunks) are grouped into
+  // stages of up to the whole tile, keeping at least three stages in flight:
+  // fewer waits and commits per MMA
+  const int slots = hp.cpt + hp.res_chunks;
+  hp.cps = max(1, min(slots, stages / 3));
+  p.k_main = slots;                   // the loops walk slots 0 .. slots-1 in steps of cps
+  p.k_res = 0;
   stages /= hp.cps;
-  hp.stages = stages;
   hp.wbytes = dxn_wbytes(a.cin, a.cout, RES ? a.cr : 0, CK);
   p.gamma = a.w.gamma;
   p.beta = a.w.beta;
@@ -1718,9 +1753,18 @@ cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
   p.y_cs = a.y_cs;
   p.y_co = a.y_co;
   p.err = a.err;
-  if (!a.y || a.head_theta) return cudaErrorInvalidValue;   // no fused head in this variant
-  set_fused(a, p, false);
-  const size_t smem = (size_t)hp.wbytes + (size_t)stages * hp.cps * Cfg::kStageBytes + kHaloSmemExtra;
+  // the fused head needs a thread to hold all channels of its pixel: two blocks only
+  const bool head = a.head_theta != nullptr;
+  if (head && (MB != 2 || a.head_ncls < 1 || a.head_ncls > 2 || !a.head_wh || !a.head_bh || !a.head_logits))
+    return cudaErrorInvalidValue;
+  if (!head && !a.y) return cudaErrorInvalidValue;
+  set_fused(a, p, MB == 2);
+  const size_t fixed = (size_t)hp.wbytes + kHaloSmemExtra + (head ? kHeadSmem : 0);
+  const size_t stage_bytes = (size_t)hp.cps * Cfg::kStageBytes;
+  if (head && fixed + (size_t)stages * stage_bytes > (size_t)kHaloSmemMax)
+    stages = (int)(((size_t)kHaloSmemMax - fixed) / stage_bytes);   // room for the head's arrays
+  hp.stages = stages;
+  const size_t smem = fixed + (size_t)stages * stage_bytes;
   if (stages < 2 || smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
   auto kern = k_conv_tc_dxn<CO, CK, RES, MB>;
   static bool attr_set = false;
@@ -1848,7 +1892,8 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
 bool tc_fuses_pool(const TcConfig& c) { return c.kind >= 1 && c.kind <= 4; }
 
 bool tc_fuses_head(const TcConfig& c, int cout, int ncls) {
-  return (c.kind == 1 || c.kind == 3) && (cout == 32 || cout == 64) && ncls >= 1 && ncls <= 2;
+  return ((c.kind == 1 || c.kind == 3) && (cout == 32 || cout == 64) || (c.kind == 4 && cout == 32)) &&
+         ncls >= 1 && ncls <= 2;
 }
 
 TcConfig tc_default(int R, int cin, int cout, int cr) {
