@@ -1069,25 +1069,28 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           }
           const uint64_t ad = a_desc0 + (uint64_t)((s * stage_bytes) >> 4);
           const int nb = min(hp.cps, k_total - k0);
-          for (int j = 0; j < nb; ++j) {
+          // the stage's main slots, then its projection slots: no branch between MMAs
+          const int nmain = RES ? max(0, min(nb, hp.cpt - k0)) : nb;
+          for (int j = 0; j < nmain; ++j) {
             const int c = k0 + j;
-            if (c < hp.cpt) {
-              const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
-              const uint64_t bk = w_desc0 + (uint64_t)(c * (Cfg::kWTileBytes >> 4));
+            const uint64_t aj = ad + (uint64_t)((j * Cfg::kBoxBytes) >> 4);
+            const uint64_t bk = w_desc0 + (uint64_t)(c * (Cfg::kWTileBytes >> 4));
 #pragma unroll
-              for (int blk = 0; blk < MB; ++blk) {
+            for (int blk = 0; blk < MB; ++blk) {
 #pragma unroll
-                for (int dy = 0; dy < 3; ++dy) {
-                  const uint64_t at = aj + (uint64_t)(((dy + kHTH * blk) * kHTW * CK * 2) >> 4);
-                  const uint64_t bt = bk + (uint64_t)dy * dy_step;
+              for (int dy = 0; dy < 3; ++dy) {
+                const uint64_t at = aj + (uint64_t)(((dy + kHTH * blk) * kHTW * CK * 2) >> 4);
+                const uint64_t bt = bk + (uint64_t)dy * dy_step;
 #pragma unroll
-                  for (int kk = 0; kk < CK / 16; ++kk)
-                    mma_bf16(acc0 + (uint32_t)(blk * Cfg::kBlkCols), at + (uint64_t)(kk * 2),
-                             bt + (uint64_t)(kk * 2), idesc_n, (c > 0 || dy > 0 || kk > 0) ? 1u : 0u);
-                }
+                for (int kk = 0; kk < CK / 16; ++kk)
+                  mma_bf16(acc0 + (uint32_t)(blk * Cfg::kBlkCols), at + (uint64_t)(kk * 2),
+                           bt + (uint64_t)(kk * 2), idesc_n, (c > 0 || dy > 0 || kk > 0) ? 1u : 0u);
               }
-            } else if (RES) {
-              const int r = c - hp.cpt;
+            }
+          }
+          if constexpr (RES) {
+            for (int j = nmain; j < nb; ++j) {
+              const int r = k0 + j - hp.cpt;
               const uint64_t bd = r_desc0 + (uint64_t)(r * (Cfg::kRTileBytes >> 4));
 #pragma unroll
               for (int blk = 0; blk < MB; ++blk) {
@@ -1237,10 +1240,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 //      row r at chunk j ^ ((r >> 1) & 3)).
 // Two FP16 MMAs (K = 16 each) per tile, N = cout; the epilogue writes the
 // pipeline's type.
-//   warps 0-7  builders in two groups of four (group g builds the CTA's tiles
-//              g, g + 2, ...: two tiles in flight), warp 8 MMA issuer + TMEM
-//              owner, warps 9-12 epilogue (lane quarters 1, 2, 3, 0), warp 13
-//              TMA producer of the raw windows.
+//   warps 0-7  builders in two groups of four (group g builds the CTA's
+//              tiles g, g + 2, ...: two tiles in flight), warp 8 MMA issuer +
+//              TMEM owner, warps 9-12 epilogue (lane quarters 1, 2, 3, 0),
+//              warp 13 TMA producer of the raw windows.
 __host__ __device__ constexpr uint32_t idesc_f16_ops(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
@@ -1248,11 +1251,12 @@ __device__ __forceinline__ uint32_t pack2_f16(float a, float b) {
   __half2 h = __floats2half2_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
 }
-constexpr int kFirstBuilders = 256;                       // two groups of 128
+constexpr int kFirstGroups = 2;                           // builder groups, 128 threads each
+constexpr int kFirstBuilders = 128 * kFirstGroups;
 constexpr int kThreadsFirst = kFirstBuilders + 32 + 128 + 32;
 constexpr int kFirstMmaWarp = kFirstBuilders / 32, kFirstProducerWarp = kFirstMmaWarp + 5;
 constexpr int kFirstStages = 8;
-static_assert(kFirstStages % 2 == 0, "the two builder groups own the even and the odd ring slots");
+static_assert(kFirstStages % kFirstGroups == 0, "builder group g owns the ring slots s = g (mod groups)");
 constexpr int kFirstRowBytes = 64;                        // 32 K values x 2 bytes
 constexpr int kFirstStageBytes = kBM * kFirstRowBytes;    // 8 KB
 constexpr int kRawW = 80, kRawH = kHTH + 2;               // raw window box (bytes x rows)
@@ -1350,15 +1354,15 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
     }
   } else if (warp < kFirstMmaWarp) {
     // ------------------------------------------------------------------ builders
-    const int grp = threadIdx.x / 128;               // builds the CTA's tiles grp, grp + 2, ...
+    const int grp = threadIdx.x / 128;               // builds the CTA's tiles grp, grp + groups, ...
     const int r = threadIdx.x % 128;                 // pixel row of the A tile
     const int rh = r / kHTW, rw = r % kHTW;          // its place in the 8 x 16 tile
     const int swz = (r >> 1) & 3;
-    int s = grp;                                     // ring slot of the tile (ST is even)
+    int s = grp;                                     // ring slot of the tile (ST is a multiple of the groups)
     uint32_t ph = 0;
     bool lapped = false;
     TileWalk tw;
-    tw.init(p.R / kHTH, p.R / kHTW, (int)blockIdx.x + grp * (int)gridDim.x, 2 * (int)gridDim.x);
+    tw.init(p.R / kHTH, p.R / kHTW, (int)blockIdx.x + grp * (int)gridDim.x, kFirstGroups * (int)gridDim.x);
     for (; tw.t < p.n_tiles; tw.next()) {
       bool ok = !lapped || mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag, p.err);
       ok = ok && mbar_wait(smem_u32(&rfull[s]), ph, abort_flag, p.err);
@@ -1392,7 +1396,7 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&full[s]));
-      s += 2;
+      s += kFirstGroups;
       if (s >= ST) {
         s -= ST;
         ph ^= 1u;
