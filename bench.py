@@ -27,9 +27,19 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORK = synth.NEEDLE
-WORKLOAD = (f"needle-biopsy slide {WORK.H}x{WORK.W} at 40x, scales 40x/10x/5x, tiles "
-            f"{WORK.P} stride {WORK.S}, residual U-Net base {WORK.base} x {WORK.levels} levels, "
+
+
+def describe(w) -> str:
+    if w.strides:
+        st = "strides " + "/".join(str(x) for x in w.strides) + " per scale, majority vote"
+    else:
+        st = f"stride {w.S}"
+    return (f"needle-biopsy slide {w.H}x{w.W} at 40x, scales 40x/10x/5x, tiles "
+            f"{w.P} {st}, residual U-Net base {w.base} x {w.levels} levels, "
             f"6 class heads, tissue filter on")
+
+
+WORKLOAD = describe(WORK)
 METRIC = "segmented slide Mpx/s (6 classes x 3 scales)"
 
 
@@ -365,6 +375,9 @@ def main():
     ap.add_argument("--workload", default="needle", choices=["needle", "small"],
                     help="small: a 2048x8192 slice of the needle configuration, for multi-pass ncu "
                          "captures that must stay a few GB (never a bench line)")
+    ap.add_argument("--paper-strides", action="store_true",
+                    help="the needle slide tiled with the per-scale strides of Sec. 3.2 (256 at 40x, "
+                         "64 at 10x and 5x) and majority-vote labels (its own JSON line)")
     ap.add_argument("--profile-step", action="store_true",
                     help="one slide step after the tuning call, bracketed by cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
@@ -399,8 +412,9 @@ def main():
     if args.large:
         run_large(args, api, _lib, dev, prec)
         return
-    work = WORK if args.workload == "needle" else WORK.with_(name="needle_small", H=2048, W=8192)
-    if work is not WORK and not args.profile_step:
+    base_work = synth.NEEDLE_PAPER if args.paper_strides else WORK
+    work = base_work if args.workload == "needle" else base_work.with_(name="needle_small", H=2048, W=8192)
+    if work is not base_work and not args.profile_step:
         raise SystemExit("--workload small is for --profile-step captures only")
     spec = synth.spec_for(work)
     rgb = api.synth_slide(spec, device=dev)
@@ -448,7 +462,7 @@ def main():
     ms_l, kinds_l, tags_l, work_l = seg.launch_times()
     seg.set_timing(False)
     ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, device=dev)
-    mpx = WORK.H * WORK.W / 1e6
+    mpx = work.H * work.W / 1e6
     value = whole_job_value(mpx, ms_step, world)
     breakdown = summarize(ms_l, tags_l, work_l, args.steps)
 
@@ -462,7 +476,7 @@ def main():
         bound, peak_note = "alu", "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock"
     conv_per_launch_ms = conv_ms / max(conv_n, 1)
     achieved = (conv_flops / max(conv_n, 1)) / (conv_per_launch_ms / 1e3) / 1e12
-    tiles_step = int(round(conv_flops / max(args.steps, 1) / seg.query(WORK.H, WORK.W).flops_per_tile))
+    tiles_step = int(round(conv_flops / max(args.steps, 1) / seg.query(work.H, work.W).flops_per_tile))
     traffic, traffic_step = conv_traffic(prec == _lib.BF16, tiles_step, conv_n / args.steps)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": "conv (all U-Net layers)",
@@ -513,7 +527,7 @@ def main():
 
     fp32 = None
     if args.compare_fp32 and prec != _lib.FP32:
-        seg32 = api.Segmenter(WORK, blob, precision=_lib.FP32)
+        seg32 = api.Segmenter(work, blob, precision=_lib.FP32)
         o32 = seg32.segment(rgb)
         torch.cuda.synchronize()
         a = time.perf_counter()
@@ -527,7 +541,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": args.precision, "data": "synthetic",
-                "config": {"workload": WORKLOAD, "slide_px": WORK.H * WORK.W,
+                "config": {"workload": describe(work), "slide_px": work.H * work.W,
                            "l2": "no flush: inputs (2.4 GB slide) larger than L2",
                            "parallelism": f"replicas x{world}",
                            "tiles_per_step": tiles_step},
@@ -537,7 +551,7 @@ def main():
                 "clocks": clocks}
         if fp32 is not None:
             line["fp32_plain"] = fp32
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and not args.paper_strides:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
     seg.close()

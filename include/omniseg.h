@@ -66,7 +66,8 @@ typedef struct omni_ctx omni_ctx;
 /* Network and pipeline configuration (fixed for the life of a context). */
 typedef struct omni_config {
   int32_t patch;        /* tile size P at every scale (Sec. 2.2: 512)                  */
-  int32_t stride;       /* tile stride S (Sec. 3.2: 256 at 40x); P % S == 0            */
+  int32_t stride;       /* tile stride S (Sec. 3.2: 256 at 40x); P % S == 0; the stride
+                           of every scale whose scale_stride entry is 0                  */
   int32_t levels;       /* U-Net levels L (2..6)                                        */
   int32_t base;         /* channels of level 0; level l has base << l (multiple of 8)   */
   int32_t n_scales;     /* number of magnifications (1..4)                              */
@@ -80,6 +81,11 @@ typedef struct omni_config {
   int32_t pad_lead;     /* border added on all sides before tiling (Sec. 2.1: 4096)     */
   int32_t median_k;     /* odd median-blur window on the 32x thumbnail (Sec. 3.2: 59)   */
   int32_t max_batch;    /* tiles per network batch (workspace scales with it)           */
+  int32_t scale_stride[OMNI_MAX_SCALES]; /* per-scale tile stride S_s in that scale's
+                           pixels; 0 = `stride`.  Sec. 3.2 uses 256 at 40x and 64 at 10x
+                           and 5x.  Each S_s divides P, is a multiple of 4, and f_s * S_s
+                           is a multiple of 32 (tile borders on thumbnail cells).  The
+                           canvas is padded to a multiple of lcm_s(f_s * S_s).        */
 } omni_config;
 
 /* Sizes derived from a configuration and a slide size (omni_query). */

@@ -27,6 +27,8 @@ from __future__ import annotations
 from fractions import Fraction
 from typing import Dict, List, Sequence, Tuple
 
+import math
+
 import numpy as np
 import torch
 
@@ -45,16 +47,19 @@ def padded_dims(work, H: int | None = None, W: int | None = None) -> Tuple[int, 
 
     [reading] Sec. 2.1 pads the slide so edge tiles are not truncated (4096 px
     in the paper; ``pad_lead`` here, default 0).  Every scale's canvas must be
-    covered exactly by the P/S patch grid and by 32x32 thumbnail blocks, so
-    the canvas is extended right/bottom to a multiple of f_max * S (f_max =
-    largest downsample factor) and to at least f_max * P.
+    covered exactly by its P/S_s patch grid and by 32x32 thumbnail blocks, so
+    the canvas is extended right/bottom to a multiple of f_s * S_s for every
+    scale s (their least common multiple) and to at least f_max * P (f_max =
+    largest downsample factor).
     """
     H = work.H if H is None else H
     W = work.W if W is None else W
     lead = work.pad_lead
     fmax = max(work.factors)
-    unit = fmax * work.S
-    assert unit % THUMB == 0
+    unit = 1
+    for s, f in enumerate(work.factors):
+        assert (f * scale_stride(work, s)) % THUMB == 0
+        unit = math.lcm(unit, f * scale_stride(work, s))
     minimum = -(-(fmax * work.P) // unit) * unit
 
     def ext(d):
@@ -193,10 +198,20 @@ def tissue_mask(canvas: np.ndarray, k: int):
 # ----------------------------------------------------------------------------
 
 
+def scale_stride(work, s: int) -> int:
+    """Tile stride of scale s in its own pixels.  Sec. 3.2 strides the 40x
+    scale by 256 and the 10x and 5x scales by 64 (8 overlapping tiles per
+    axis there, 2 at 40x); an empty or zero per-scale entry means the common
+    stride S."""
+    st = tuple(getattr(work, "strides", ()) or ())
+    return st[s] if st and st[s] else work.S
+
+
 def grid(work, Hp: int, Wp: int, s: int) -> Tuple[int, int]:
     f = work.factors[s]
     hs, ws = Hp // f, Wp // f
-    return (hs - work.P) // work.S + 1, (ws - work.P) // work.S + 1
+    S = scale_stride(work, s)
+    return (hs - work.P) // S + 1, (ws - work.P) // S + 1
 
 
 def tile_list(work, mask: np.ndarray, Hp: int, Wp: int):
@@ -213,7 +228,7 @@ def tile_list(work, mask: np.ndarray, Hp: int, Wp: int):
         fl = np.zeros((ny, nx), bool)
         for i in range(ny):
             for j in range(nx):
-                y, x = i * work.S, j * work.S
+                y, x = i * scale_stride(work, s), j * scale_stride(work, s)
                 if work.tissue_filter:
                     r0, r1 = y * f // THUMB, (y + work.P) * f // THUMB
                     c0, c1 = x * f // THUMB, (x + work.P) * f // THUMB

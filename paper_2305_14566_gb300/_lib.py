@@ -35,7 +35,7 @@ class Config(C.Structure):
                 ("class_scale", C.c_int32 * MAX_CLASSES), ("precision", C.c_int32),
                 ("stitch_mode", C.c_int32), ("tissue_filter", C.c_int32),
                 ("tissue_and", C.c_int32), ("pad_lead", C.c_int32), ("median_k", C.c_int32),
-                ("max_batch", C.c_int32)]
+                ("max_batch", C.c_int32), ("scale_stride", C.c_int32 * MAX_SCALES)]
 
 
 class Sizes(C.Structure):

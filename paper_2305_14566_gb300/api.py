@@ -40,6 +40,8 @@ def make_config(work, precision: int = L.FP32, max_batch: Optional[int] = None) 
     c.pad_lead = work.pad_lead
     c.median_k = work.median_k
     c.max_batch = max_batch if max_batch is not None else work.max_batch
+    for i in range(c.n_scales):
+        c.scale_stride[i] = work.stride(i)
     return c
 
 

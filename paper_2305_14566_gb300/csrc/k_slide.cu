@@ -299,8 +299,8 @@ __global__ void k_mask(const uint8_t* __restrict__ blurred, long long n,
 }
 
 // ------------------------------------------------------------------ tile lists
-// A tile of scale s at grid (i, j) covers thumbnail rows i*S*f/32 ..
-// (i*S+P)*f/32 - 1 (and the same for columns); it is foreground when any
+// A tile of scale s at grid (i, j) covers thumbnail rows i*S_s*f/32 ..
+// (i*S_s+P)*f/32 - 1 (and the same for columns); it is foreground when any
 // tissue pixel lies there.
 __global__ void k_tile_flags(const uint8_t* __restrict__ mask, SlideGeom g, int filter,
                              uint8_t* __restrict__ flags) {
@@ -314,8 +314,9 @@ __global__ void k_tile_flags(const uint8_t* __restrict__ mask, SlideGeom g, int 
   uint8_t fg = 1;
   if (filter) {
     int f = g.factors[s];
-    int r0 = i * g.S * f / kThumb, r1 = (i * g.S + g.P) * f / kThumb;
-    int c0 = j * g.S * f / kThumb, c1 = (j * g.S + g.P) * f / kThumb;
+    const int S = g.S[s];
+    int r0 = i * S * f / kThumb, r1 = (i * S + g.P) * f / kThumb;
+    int c0 = j * S * f / kThumb, c1 = (j * S + g.P) * f / kThumb;
     fg = 0;
     for (int r = r0; r < r1 && !fg; ++r)
       for (int c = c0; c < c1; ++c)
@@ -356,8 +357,8 @@ __global__ void __launch_bounds__(1024) k_tile_compact(const uint8_t* __restrict
         if (f) {
           int o = total_count + pos;
           tiles[o * 3 + 0] = s;
-          tiles[o * 3 + 1] = (cell / g.gw[s]) * g.S;
-          tiles[o * 3 + 2] = (cell % g.gw[s]) * g.S;
+          tiles[o * 3 + 1] = (cell / g.gw[s]) * g.S[s];
+          tiles[o * 3 + 2] = (cell % g.gw[s]) * g.S[s];
         }
       }
       __syncthreads();

@@ -31,7 +31,8 @@ struct SlideGeom {
   int factors[OMNI_MAX_SCALES];
   int gh[OMNI_MAX_SCALES], gw[OMNI_MAX_SCALES];
   int grid_off[OMNI_MAX_SCALES + 1];   // offsets of per-scale grids in the flag array
-  int P, S;
+  int P;
+  int S[OMNI_MAX_SCALES];             // tile stride of each scale, in its pixels
 };
 
 // k_slide.cu

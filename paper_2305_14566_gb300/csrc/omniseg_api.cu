@@ -77,6 +77,23 @@ size_t take(size_t& off, size_t bytes) {
 
 int widths(const omni_config& c, int l) { return c.base << l; }
 
+// Tile stride of scale s in its own pixels (Sec. 3.2 strides the 40x scale by
+// 256 and the 10x and 5x scales by 64); 0 in scale_stride means `stride`.
+int stride_of(const omni_config& c, int s) { return c.scale_stride[s] > 0 ? c.scale_stride[s] : c.stride; }
+
+// The padded canvas is a whole number of every scale's stride (f_s * S_s 40x
+// pixels), hence of 32-pixel thumbnail cells: lcm over the scales.
+long long canvas_unit(const omni_config& c) {
+  long long u = 1;
+  for (int s = 0; s < c.n_scales; ++s) {
+    long long v = (long long)c.factors[s] * stride_of(c, s), a = u, b = v;
+    while (b) { long long t = a % b; a = b; b = t; }
+    u = u / a * v;
+    if (u > (1LL << 30)) return u;
+  }
+  return u;
+}
+
 std::string validate(const omni_config& c) {
   if (c.levels < 2 || c.levels > kMaxLevels) return "levels must be in 2..6";
   if (c.base < 8 || c.base > 64 || c.base % 8) return "base must be 8, 16, 32 or 64";
@@ -91,8 +108,12 @@ std::string validate(const omni_config& c) {
     for (int q = 0; q < s; ++q)
       if (c.factors[q] == f) return "factors must be distinct";
     fmax = std::max(fmax, f);
+    const int st = stride_of(c, s);
+    if (c.scale_stride[s] < 0 || c.patch % st || st % 4)
+      return "every scale stride must divide patch and be a multiple of 4";
+    if ((f * st) % kThumb) return "factor times stride must be a multiple of 32 at every scale";
   }
-  if ((fmax * c.stride) % kThumb) return "largest factor times stride must be a multiple of 32";
+  if (canvas_unit(c) > (1 << 20)) return "the lcm of factor times stride over the scales is too large";
   if (c.n_classes < 1 || c.n_classes > OMNI_MAX_CLASSES) return "n_classes must be 1..16";
   for (int k = 0; k < c.n_classes; ++k)
     if (c.class_scale[k] < 0 || c.class_scale[k] >= c.n_scales) return "class_scale out of range";
@@ -132,11 +153,11 @@ bool make_plan(const omni_config& c, int H, int W, Plan& p) {
   if (H <= 0 || W <= 0) return false;
   memset(&p, 0, sizeof(p));
   const int fmax = fmax_of(c);
-  const int unit = fmax * c.stride;
-  const int minimum = (fmax * c.patch + unit - 1) / unit * unit;
+  const long long unit = canvas_unit(c);
+  const long long minimum = (fmax * (long long)c.patch + unit - 1) / unit * unit;
   auto ext = [&](long long d) {
     long long v = (d + 2LL * c.pad_lead + unit - 1) / unit * unit;
-    return (int)std::max<long long>(v, minimum);
+    return std::max<long long>(v, minimum);
   };
   SlideGeom& g = p.g;
   g.H = H; g.W = W; g.lead = c.pad_lead;
@@ -144,13 +165,14 @@ bool make_plan(const omni_config& c, int H, int W, Plan& p) {
   if (Hp > (1LL << 30) || Wp > (1LL << 30)) return false;
   g.Hp = (int)Hp; g.Wp = (int)Wp;
   g.th = g.Hp / kThumb; g.tw = g.Wp / kThumb;
-  g.n_scales = c.n_scales; g.P = c.patch; g.S = c.stride;
+  g.n_scales = c.n_scales; g.P = c.patch;
   g.grid_off[0] = 0;
   for (int s = 0; s < c.n_scales; ++s) {
     int f = c.factors[s];
     g.factors[s] = f;
-    g.gh[s] = (g.Hp / f - c.patch) / c.stride + 1;
-    g.gw[s] = (g.Wp / f - c.patch) / c.stride + 1;
+    g.S[s] = stride_of(c, s);
+    g.gh[s] = (g.Hp / f - c.patch) / g.S[s] + 1;
+    g.gw[s] = (g.Wp / f - c.patch) / g.S[s] + 1;
     g.grid_off[s + 1] = g.grid_off[s] + g.gh[s] * g.gw[s];
     p.ncls_s[s] = 0;
   }
@@ -830,7 +852,7 @@ omni_status run_network(omni_ctx* ctx, const omni_config& c, const Plan& p, uint
       a.hs = p.g.Hp / f; a.ws = p.g.Wp / f;
       a.oy0 = c.pad_lead / f; a.ox0 = c.pad_lead / f;
       a.oh = (H + f - 1) / f; a.ow = (W + f - 1) / f;
-      a.P = c.patch; a.S = c.stride; a.gh = p.g.gh[s]; a.gw = p.g.gw[s]; a.f = f;
+      a.P = c.patch; a.S = p.g.S[s]; a.gh = p.g.gh[s]; a.gw = p.g.gw[s]; a.f = f;
       a.slot_map = slot + p.g.grid_off[s];
       a.logits = reinterpret_cast<const float*>(ws + p.logits);
       a.n_cls = ncls;

@@ -49,6 +49,7 @@ class Workload:
     pad_lead: int = 0              # the paper's 4096 border; 0 for these workloads
     max_batch: int = 32
     head_offset: float = 0.0       # controller bias of the head's final bias b3 (weights init)
+    strides: Tuple[int, ...] = ()  # per-scale tile stride; () or 0 = S (Sec. 3.2: 256, 64, 64)
 
     @property
     def n_classes(self) -> int:
@@ -57,6 +58,10 @@ class Workload:
     @property
     def n_scales(self) -> int:
         return len(self.factors)
+
+    def stride(self, s: int) -> int:
+        """Tile stride of scale index s, in that scale's pixels."""
+        return self.strides[s] if self.strides and self.strides[s] else self.S
 
     @property
     def widths(self) -> List[int]:
@@ -90,6 +95,12 @@ LARGE = Workload(
     name="large", H=32768, W=98304, seed=200, tissue=0.35, layout="cores", n_blobs=4,
     factors=(1, 4, 8), P=1024, S=512, base=32, levels=5,
     class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=8, head_offset=3.3)
+
+
+# The paper's own overlap setting (Sec. 3.2): 40x tiles strided by 256 (two
+# overlapping tiles per axis, vote threshold 1), 10x and 5x tiles by 64 (eight
+# per axis, threshold 4), labels by majority vote.
+NEEDLE_PAPER = NEEDLE.with_(name="needle_paper", strides=(256, 64, 64), stitch_mode=STITCH_VOTE)
 
 
 def ragged_workloads(n: int = 12, seed0: int = 100) -> List[Workload]:

@@ -1,5 +1,6 @@
 """Write needle_tiles.json (the oracle's tissue threshold and foreground tile
-counts) and needle_tissue_mask.npz (its 512 x 1536 tissue mask, bit-packed)
+counts, with the common stride and with the per-scale strides of Sec. 3.2)
+and needle_tissue_mask.npz (its 512 x 1536 tissue mask, bit-packed)
 for the 16384 x 49152 needle-biopsy workload.
 
 Calls only the input generator and the FP64 oracle.  The slide is generated
@@ -30,10 +31,17 @@ def main():
     mask = b.astype(np.int64) <= t
     tiles, flags = O.tile_list(w, mask, w.H, w.W)
     per = [sum(1 for q in tiles if q[0] == s) for s in range(w.n_scales)]
+    # the same slide tiled with the per-scale strides of Sec. 3.2 (256 / 64 / 64)
+    wp = synth.NEEDLE_PAPER
+    ptiles, pflags = O.tile_list(wp, mask, *O.padded_dims(wp)[:2])
+    pper = [sum(1 for q in ptiles if q[0] == s) for s in range(wp.n_scales)]
     out = {"_source": "oracle tile list of synth.NEEDLE (tests/golden/make_needle_tiles.py)",
            "otsu": int(t), "tissue_fraction": float(mask.mean()),
            "tiles_per_scale": per, "tiles_total": len(tiles),
-           "grid_per_scale": [int(f.size) for f in flags]}
+           "grid_per_scale": [int(f.size) for f in flags],
+           "paper_strides": list(wp.strides),
+           "paper_strides_tiles_per_scale": pper, "paper_strides_tiles_total": len(ptiles),
+           "paper_strides_grid_per_scale": [int(f.size) for f in pflags]}
     here = os.path.dirname(os.path.abspath(__file__))
     with open(os.path.join(here, "needle_tiles.json"), "w") as f:
         json.dump(out, f, indent=1)

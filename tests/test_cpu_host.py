@@ -64,6 +64,16 @@ def test_invalid_configs_rejected_without_device(L, field, value):
     assert L.lib().omni_query(C.byref(c), 1000, 1000, C.byref(s)) == L.EINVAL
 
 
+@pytest.mark.parametrize("s,value", [(1, 100), (0, 16), (2, -64), (1, 1024)])
+def test_bad_scale_strides_rejected(L, s, value):
+    """A per-scale stride must divide P (512), be a multiple of 4, and put tile
+    borders on 32-pixel thumbnail cells (16 at 40x does not)."""
+    c = _cfg(L, synth.NEEDLE_PAPER)
+    c.scale_stride[s] = value
+    sz = L.Sizes()
+    assert L.lib().omni_query(C.byref(c), 1000, 1000, C.byref(sz)) == L.EINVAL
+
+
 def test_bad_factors_rejected(L):
     c = _cfg(L, synth.NEEDLE)
     c.factors[1] = 3
@@ -76,7 +86,9 @@ def test_bad_factors_rejected(L):
 
 @pytest.mark.parametrize("work,H,W", [(synth.TINY, 512, 512), (synth.NEEDLE, 16384, 49152),
                                       (synth.DIFF, 2048, 2048), (synth.LARGE, 32768, 98304),
-                                      (synth.NEEDLE, 5000, 9000), (synth.NEEDLE, 300, 700)])
+                                      (synth.NEEDLE, 5000, 9000), (synth.NEEDLE, 300, 700),
+                                      (synth.NEEDLE_PAPER, 16384, 49152),
+                                      (synth.NEEDLE_PAPER, 5000, 9000)])
 def test_query_sizes_match_oracle(L, work, H, W):
     c = _cfg(L, work)
     s = L.Sizes()

@@ -38,11 +38,13 @@ def test_pad_colour_is_rounded_2x2_mean():
 
 
 def test_padded_dims_cover_every_scale_grid():
-    for w in (synth.TINY, synth.NEEDLE, synth.DIFF, synth.LARGE):
+    for w in (synth.TINY, synth.NEEDLE, synth.DIFF, synth.LARGE, synth.NEEDLE_PAPER,
+              synth.NEEDLE_PAPER.with_(H=5000, W=9000)):
         Hp, Wp, lead = O.padded_dims(w)
-        for f in w.factors:
+        strides = w.strides or (w.S,) * w.n_scales
+        for f, S in zip(w.factors, strides):
             for d in (Hp, Wp):
-                assert d % f == 0 and (d // f - w.P) % w.S == 0 and d // f >= w.P
+                assert d % f == 0 and (d // f - w.P) % S == 0 and d // f >= w.P
         assert Hp % synth.THUMB == 0 and Wp % synth.THUMB == 0
     # needle / large need no padding (their sizes already sit on the grid)
     assert O.padded_dims(synth.NEEDLE)[:2] == (16384, 49152)
@@ -53,6 +55,9 @@ def test_padded_dims_cover_every_scale_grid():
     w2 = w.with_(pad_lead=4096)
     Hp, Wp, lead = O.padded_dims(w2)
     assert lead == 4096 and Hp >= 5000 + 8192 and Wp >= 9000 + 8192
+    # per-scale strides 256 / 64 / 64 (Sec. 3.2): units 256, 4 * 64, 8 * 64 -> 512,
+    # at least 8 * 512 = 4096: 5000 -> 5120, 9000 -> 9216
+    assert O.padded_dims(synth.NEEDLE_PAPER.with_(H=5000, W=9000))[:2] == (5120, 9216)
 
 
 def test_pad_slide_places_image_and_colour():
@@ -158,24 +163,60 @@ def test_tile_counts_closed_form():
         got = [int(np.prod(O.grid(w, Hp, Wp, s))) for s in range(w.n_scales)]
         assert got == expect, (w.name, got)
     assert sum([63 * 191, 15 * 47, 7 * 23]) == 12899
+    # Sec. 3.2 strides: the 10x canvas 4096 x 12288 holds (4096 - 512) / 64 + 1 = 57
+    # by (12288 - 512) / 64 + 1 = 185 tiles, the 5x canvas 2048 x 6144 25 by 89
+    w = synth.NEEDLE_PAPER
+    Hp, Wp, _ = O.padded_dims(w)
+    assert (Hp, Wp) == (16384, 49152)
+    assert [O.grid(w, Hp, Wp, s) for s in range(3)] == [(63, 191), (57, 185), (25, 89)]
 
 
-def test_tile_list_foreground_brute_force():
-    w = synth.NEEDLE.with_(H=2048, W=4096, P=512, S=256, tissue_filter=True)
+def test_per_scale_strides_tile_positions_and_overlap():
+    """Tile origins step by each scale's own stride; an interior pixel is
+    covered by (P / S_s)^2 tiles: 4 at 40x, 64 at 10x and 5x (Sec. 3.2 counts
+    2 and 8 per axis).  Equal per-scale strides reproduce the common-stride
+    tiling exactly."""
+    w = synth.NEEDLE_PAPER.with_(H=8192, W=8192, tissue_filter=False)
+    Hp, Wp, _ = O.padded_dims(w)
+    mask = np.ones((Hp // 32, Wp // 32), bool)
+    tiles, flags = O.tile_list(w, mask, Hp, Wp)
+    for s, (f, S) in enumerate(zip(w.factors, (256, 64, 64))):
+        ts = [(y, x) for (q, y, x) in tiles if q == s]
+        ys, xs = sorted({y for y, _ in ts}), sorted({x for _, x in ts})
+        assert ys == list(range(0, Hp // f - w.P + 1, S))
+        assert xs == list(range(0, Wp // f - w.P + 1, S))
+        cy, cx = Hp // f // 2 + 3, Wp // f // 2 + 5
+        n = sum(1 for y, x in ts if y <= cy < y + w.P and x <= cx < x + w.P)
+        assert n == (w.P // S) ** 2
+    assert [len([t for t in tiles if t[0] == s]) for s in range(3)] == [
+        (Hp // 256 - 1) * (Wp // 256 - 1),
+        ((Hp // 4 - 512) // 64 + 1) * ((Wp // 4 - 512) // 64 + 1),
+        ((Hp // 8 - 512) // 64 + 1) * ((Wp // 8 - 512) // 64 + 1)]
+    same = synth.NEEDLE.with_(H=8192, W=8192)
+    m2 = rng(5).random((Hp // 32, Wp // 32)) < 0.01
+    a = O.tile_list(same, m2, Hp, Wp)
+    b = O.tile_list(same.with_(strides=(256, 256, 256)), m2, Hp, Wp)
+    assert a[0] == b[0] and all(np.array_equal(x, y) for x, y in zip(a[1], b[1]))
+
+
+@pytest.mark.parametrize("strides", [(256, 256, 256), (256, 64, 64)])
+def test_tile_list_foreground_brute_force(strides):
+    w = synth.NEEDLE.with_(H=2048, W=4096, P=512, S=256, tissue_filter=True, strides=strides)
     Hp, Wp, _ = O.padded_dims(w)
     mask = np.zeros((Hp // 32, Wp // 32), bool)
     mask[10, 70] = True          # 40x pixel rows 320..351, cols 2240..2271
     tiles, flags = O.tile_list(w, mask, Hp, Wp)
     for s, f in enumerate(w.factors):
+        S = strides[s]
         ny, nx = O.grid(w, Hp, Wp, s)
         for i in range(ny):
             for j in range(nx):
-                y0, x0 = i * w.S * f, j * w.S * f         # 40x footprint
+                y0, x0 = i * S * f, j * S * f             # 40x footprint
                 y1, x1 = y0 + w.P * f, x0 + w.P * f
                 hit = y0 <= 320 < y1 and x0 <= 2240 < x1
                 assert flags[s][i, j] == hit
     assert tiles == sorted(tiles)
-    assert all(flags[s][y // w.S, x // w.S] for (s, y, x) in tiles)
+    assert all(flags[s][y // strides[s], x // strides[s]] for (s, y, x) in tiles)
 
 
 # ---------------------------------------------------------------- network pieces
