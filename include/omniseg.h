@@ -58,6 +58,13 @@ typedef int omni_status;
 #define OMNI_STITCH_AVG 0   /* label = mean logit of covering tiles > 0            */
 #define OMNI_STITCH_VOTE 1  /* label = at least half of covering tiles vote > 0    */
 
+/* Weight of a tile's logit at a pixel in the overlap average (average mode;
+ * votes are always counted with weight 1).  The weight is separable,
+ * w(u, v) = t(u) t(v) at tile coordinates (u, v), 0 <= u, v < P:            */
+#define OMNI_WINDOW_FLAT 0  /* t(u) = 1: the plain mean of Sec. 2.3                 */
+#define OMNI_WINDOW_TENT 1  /* t(u) = min(u + 1, P - u)                              */
+#define OMNI_WINDOW_HANN 2  /* t(u) = sin^2(pi (u + 1/2) / P)                         */
+
 #define OMNI_MAX_SCALES 4
 #define OMNI_MAX_CLASSES 16
 
@@ -86,6 +93,8 @@ typedef struct omni_config {
                            and 5x.  Each S_s divides P, is a multiple of 4, and f_s * S_s
                            is a multiple of 32 (tile borders on thumbnail cells).  The
                            canvas is padded to a multiple of lcm_s(f_s * S_s).        */
+  int32_t stitch_window;/* OMNI_WINDOW_*: overlap-average weight (omni_backward needs
+                           OMNI_WINDOW_FLAT)                                             */
 } omni_config;
 
 /* Sizes derived from a configuration and a slide size (omni_query). */
@@ -199,6 +208,32 @@ omni_status omni_segment_slide_host(omni_ctx* ctx, const uint8_t* rgb_host, int3
  * pixel (y, x) of a slide_w-wide slide drawn from `n_ell` rotated ellipses
  * (int64 rows cy, cx, a, b, cos_q14, sin_q14) and SplitMix64 noise seeded
  * with `seed`; writes rows y0..y0+h-1, cols x0..x0+w-1 to out_dev. */
+/* Final products of the slide-wise aggregation (Sec. 2.3): every class's
+ * merged label map stained onto the 40x slide in its own colour, and the
+ * lower-magnification product resized directly from that stained image.
+ *   rgb_dev      the H x W x 3 u8 slide, row_stride bytes per row.
+ *   labels_dev   HOST array of n_maps (<= 16) DEVICE pointers, NULL = skip:
+ *                map k is ceil(H / f_k) x ceil(W / f_k) u8, row-major, nonzero =
+ *                on (the label maps omni_segment_slide writes).
+ *   factors, colours, alpha   HOST arrays: f_k in {1, 2, 4, 8}; colour_k as
+ *                n_maps x 3 u8; alpha_k in 0..256.
+ *   Stained pixel: starting from the slide colour c, for k = 0 .. n_maps-1
+ *   in order, where map k is on at (y / f_k, x / f_k):
+ *     c = (c * (256 - alpha_k) + colour_k * alpha_k + 128) >> 8 per channel.
+ *   out40_dev    H x W x 3 u8 (out40_stride bytes per row), or NULL.
+ *   down, outd_dev   2, 4 or 8 (Sec. 2.3: 4, the 10x product) and a
+ *                ceil(H/down) x ceil(W/down) x 3 u8 image (outd_stride), or NULL:
+ *                pixel = rounded mean (sum + n/2) / n of the n stained 40x
+ *                pixels of its down x down block (fewer at the right and
+ *                bottom edges of a ragged slide).
+ * At least one output must be given.  Asynchronous on `stream`; OMNI_EINVAL
+ * for bad sizes, factors, alphas or strides, OMNI_ECUDA on a launch error. */
+omni_status omni_stain(const uint8_t* rgb_dev, int32_t H, int32_t W, int64_t row_stride,
+                       int32_t n_maps, const uint8_t* const* labels_dev, const int32_t* factors,
+                       const uint8_t* colours, const int32_t* alpha, uint8_t* out40_dev,
+                       int64_t out40_stride, int32_t down, uint8_t* outd_dev, int64_t outd_stride,
+                       void* stream);
+
 omni_status omni_synth_slide(const int64_t* ellipses_host, int32_t n_ell, uint64_t seed,
                              int32_t slide_w, int32_t y0, int32_t x0, int32_t h, int32_t w,
                              uint8_t* out_dev, int64_t row_stride, void* stream);

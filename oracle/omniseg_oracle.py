@@ -32,7 +32,8 @@ import math
 import numpy as np
 import torch
 
-from synth.configs import HEAD_CH, N_HEAD_PARAMS, THUMB, STITCH_AVG, STITCH_VOTE
+from synth.configs import (HEAD_CH, N_HEAD_PARAMS, THUMB, STITCH_AVG, STITCH_VOTE, WINDOW_FLAT,
+                           WINDOW_TENT, WINDOW_HANN)
 from synth.weights import layout
 
 F64 = torch.float64
@@ -409,21 +410,43 @@ def patch_forward(patches_u8: np.ndarray, p, work, scl: int):
 # ----------------------------------------------------------------------------
 
 
-def stitch(patch_logits: Dict[Tuple[int, int], np.ndarray], hs: int, ws: int, P: int):
+def window_weights(P: int, window: int) -> np.ndarray:
+    """[reading] Weight of a tile's logit at tile pixel (u, v) in the overlap
+    average: w = t(u) t(v) with t = 1 (flat, the plain mean of Sec. 2.3),
+    t(u) = min(u + 1, P - u) (tent) or t(u) = sin^2(pi (u + 1/2) / P) (Hann).
+    The paper names no window; every choice is positive at every pixel."""
+    u = np.arange(P, dtype=np.float64)
+    if window == WINDOW_FLAT:
+        t = np.ones(P)
+    elif window == WINDOW_TENT:
+        t = np.minimum(u + 1.0, P - u)
+    elif window == WINDOW_HANN:
+        t = np.sin(np.pi * (u + 0.5) / P) ** 2
+    else:
+        raise ValueError(window)
+    return t[:, None] * t[None, :]
+
+
+def stitch(patch_logits: Dict[Tuple[int, int], np.ndarray], hs: int, ws: int, P: int,
+           window: int = 0):
     """Overlap average of the processed tiles covering each pixel.
 
-    L(x) = sum_p l_p(x) / cov(x); votes(x) = #{p : l_p(x) > 0}; pixels with no
-    covering tile keep L = 0, cov = 0.  Sum in float64 in ascending tile order.
+    L(x) = sum_p w_p(x) l_p(x) / sum_p w_p(x) (w = 1: the mean over cov(x)
+    tiles); votes(x) = #{p : l_p(x) > 0}; pixels with no covering tile keep
+    L = 0, cov = 0.  Sum in float64 in ascending tile order.
     """
     acc = np.zeros((hs, ws), np.float64)
+    wsum = np.zeros((hs, ws), np.float64)
     cov = np.zeros((hs, ws), np.int64)
     votes = np.zeros((hs, ws), np.int64)
+    w = window_weights(P, window)
     for (y, x) in sorted(patch_logits):
         lp = patch_logits[(y, x)]
-        acc[y:y + P, x:x + P] += lp
+        acc[y:y + P, x:x + P] += w * lp
+        wsum[y:y + P, x:x + P] += w
         cov[y:y + P, x:x + P] += 1
         votes[y:y + P, x:x + P] += (lp > 0)
-    L = np.where(cov > 0, acc / np.maximum(cov, 1), 0.0)
+    L = np.where(cov > 0, acc / np.where(cov > 0, wsum, 1.0), 0.0)
     return L, cov, votes
 
 
@@ -459,6 +482,42 @@ def argmax_map(Ls: Sequence[np.ndarray], class_ids: Sequence[int]) -> np.ndarray
     mx = np.max(stack, axis=0)
     ids = np.asarray(class_ids)[best] + 1
     return np.where(mx > 0, ids, 0).astype(np.uint8)
+
+
+def stain(rgb: np.ndarray, maps: Sequence, factors: Sequence[int], colours, alphas) -> np.ndarray:
+    """Sec. 2.3: the merged label map of every tissue type is stained onto the
+    40x slide in its own colour.
+
+    [reading] Map k (at its scale, ceil(H/f_k) x ceil(W/f_k)) covers 40x pixel
+    (y, x) through pixel (y // f_k, x // f_k).  Stains are applied in map
+    order; where map k is on, each channel becomes the alpha blend
+    (c (256 - a_k) + colour_k a_k + 128) >> 8 with a_k in 0..256.
+    """
+    H, W, _ = rgb.shape
+    out = rgb.astype(np.int64).copy()
+    for m, f, col, a in zip(maps, factors, colours, alphas):
+        if m is None:
+            continue
+        on = np.repeat(np.repeat(np.asarray(m) != 0, f, axis=0), f, axis=1)[:H, :W]
+        c = np.asarray(col, np.int64)
+        out[on] = (out[on] * (256 - a) + c * a + 128) >> 8
+    return out.astype(np.uint8)
+
+
+def resize_down(img: np.ndarray, r: int) -> np.ndarray:
+    """Sec. 2.3: the 10x product is resized directly from the stained 40x
+    image.  [reading] Resizing by r is the r x r box mean rounded half up,
+    (sum + n // 2) // n over the n image pixels of the block (edge blocks of a
+    ragged image have fewer)."""
+    H, W, _ = img.shape
+    oh, ow = -(-H // r), -(-W // r)
+    out = np.zeros((oh, ow, 3), np.uint8)
+    for i in range(oh):
+        for j in range(ow):
+            blk = img[i * r:(i + 1) * r, j * r:(j + 1) * r].reshape(-1, 3).astype(np.int64)
+            n = blk.shape[0]
+            out[i, j] = (blk.sum(axis=0) + n // 2) // n
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -511,7 +570,7 @@ def segment(rgb: np.ndarray, work, blob: np.ndarray, window=None, batch: int = 4
                     per_class[c][(y, x)] = lg[ci, bi].numpy()
         tis = tissue_at_scale(prep["mask"], f, hs, ws) if work.tissue_and else None
         for c in classes:
-            L, cov, votes = stitch(per_class[c], hs, ws, P)
+            L, cov, votes = stitch(per_class[c], hs, ws, P, getattr(work, "stitch_window", 0))
             sl = (slice(wy0, wy0 + wh), slice(wx0, wx0 + ww))
             out["L"][c] = L[sl]
             out["cov"][c] = cov[sl]
@@ -561,8 +620,10 @@ def segment_window_regions(get40, mask: np.ndarray, work, blob: np.ndarray, wind
                     per_class[c][(y, x)] = lg[ci, bi].numpy()
         # stitch only the window: shift tile origins into window coordinates
         tis = tissue_at_scale(mask, f, hs, ws)[wy0:wy0 + wh, wx0:wx0 + ww] if work.tissue_and else None
+        wt = window_weights(P, getattr(work, "stitch_window", 0))
         for c in classes:
             acc = np.zeros((wh, ww), np.float64)
+            wsum = np.zeros((wh, ww), np.float64)
             cov = np.zeros((wh, ww), np.int64)
             votes = np.zeros((wh, ww), np.int64)
             for (y, x) in sorted(per_class[c]):
@@ -570,10 +631,12 @@ def segment_window_regions(get40, mask: np.ndarray, work, blob: np.ndarray, wind
                 ya, yb = max(y, wy0), min(y + P, wy0 + wh)
                 xa, xb = max(x, wx0), min(x + P, wx0 + ww)
                 sub = lp[ya - y:yb - y, xa - x:xb - x]
-                acc[ya - wy0:yb - wy0, xa - wx0:xb - wx0] += sub
+                wsub = wt[ya - y:yb - y, xa - x:xb - x]
+                acc[ya - wy0:yb - wy0, xa - wx0:xb - wx0] += wsub * sub
+                wsum[ya - wy0:yb - wy0, xa - wx0:xb - wx0] += wsub
                 cov[ya - wy0:yb - wy0, xa - wx0:xb - wx0] += 1
                 votes[ya - wy0:yb - wy0, xa - wx0:xb - wx0] += (sub > 0)
-            L = np.where(cov > 0, acc / np.maximum(cov, 1), 0.0)
+            L = np.where(cov > 0, acc / np.where(cov > 0, wsum, 1.0), 0.0)
             out["L"][c] = L
             out["cov"][c] = cov
             out["labels"][c] = labels(L, cov, votes, work.stitch_mode, tis)

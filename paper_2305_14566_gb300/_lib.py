@@ -25,7 +25,8 @@ EXPORTS = ("omni_create", "omni_destroy", "omni_last_error", "omni_weights_count
            "omni_segment_slide_host", "omni_synth_slide", "omni_conv_layer", "omni_set_timing",
            "omni_get_timing", "omni_last_launch_count", "omni_get_launch_times",
            "omni_tile_slide_noalloc", "omni_backward", "omni_backward_workspace",
-           "omni_set_autotune", "omni_set_graphs", "omni_set_fusion", "omni_get_tuned")
+           "omni_set_autotune", "omni_set_graphs", "omni_set_fusion", "omni_get_tuned",
+           "omni_stain")
 
 
 class Config(C.Structure):
@@ -35,7 +36,8 @@ class Config(C.Structure):
                 ("class_scale", C.c_int32 * MAX_CLASSES), ("precision", C.c_int32),
                 ("stitch_mode", C.c_int32), ("tissue_filter", C.c_int32),
                 ("tissue_and", C.c_int32), ("pad_lead", C.c_int32), ("median_k", C.c_int32),
-                ("max_batch", C.c_int32), ("scale_stride", C.c_int32 * MAX_SCALES)]
+                ("max_batch", C.c_int32), ("scale_stride", C.c_int32 * MAX_SCALES),
+                ("stitch_window", C.c_int32)]
 
 
 class Sizes(C.Structure):
@@ -91,6 +93,8 @@ def lib() -> C.CDLL:
         "omni_segment_slide_host": (i32, [vp, vp, i32, i32, i64, u32, u32, vp, u64,
                                           C.POINTER(vp), vp]),
         "omni_synth_slide": (i32, [vp, i32, u64, i32, i32, i32, i32, i32, vp, i64, vp]),
+        "omni_stain": (i32, [vp, i32, i32, i64, i32, C.POINTER(vp), vp, vp, vp, vp, i64, i32, vp,
+                             i64, vp]),
         "omni_conv_layer": (i32, [i32, i32, i32, i32, i32, vp, i32, i32, vp, vp, vp, vp, i32,
                                   i32, i32, vp, vp, i32, i32, i32, vp, vp]),
         "omni_set_timing": (i32, [vp, i32]),

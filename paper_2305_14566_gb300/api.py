@@ -42,6 +42,7 @@ def make_config(work, precision: int = L.FP32, max_batch: Optional[int] = None) 
     c.max_batch = max_batch if max_batch is not None else work.max_batch
     for i in range(c.n_scales):
         c.scale_stride[i] = work.stride(i)
+    c.stitch_window = work.stitch_window
     return c
 
 
@@ -280,6 +281,44 @@ def tile_slide_noalloc(work, rgb: torch.Tensor) -> Dict[str, torch.Tensor]:
                                             C.byref(tl), _stream()),
             None, "omni_tile_slide_noalloc rejected the call")
     return out
+
+
+# Class colours of the stained product (PTC, VES, PT, DT, TUFT, CAP), 50% opacity.
+STAIN_COLOURS = ((230, 25, 75), (60, 180, 75), (255, 225, 25), (0, 130, 200), (245, 130, 48),
+                 (145, 30, 180))
+
+
+def stain(rgb: torch.Tensor, labels: Dict[int, torch.Tensor], factors: Dict[int, int],
+          colours=None, alpha=128, out40: Optional[torch.Tensor] = None, down: int = 4,
+          outd: Optional[torch.Tensor] = None, want40: bool = True, want_down: bool = True):
+    """omni_stain: stain the class label maps onto the 40x slide (Sec. 2.3) and
+    resize the stained image by ``down`` (the 10x product for 4).
+
+    ``labels``: class id -> u8 device map at that class's scale; ``factors``:
+    class id -> its downsample factor.  Maps are applied in ascending class id.
+    Returns (stained 40x image or None, resized image or None)."""
+    H, W, _ = rgb.shape
+    ids = sorted(labels)
+    n = len(ids)
+    cols = colours if colours is not None else [STAIN_COLOURS[c % len(STAIN_COLOURS)] for c in ids]
+    alphas = alpha if isinstance(alpha, (list, tuple)) else [alpha] * n
+    dev = rgb.device
+    if want40 and out40 is None:
+        out40 = torch.empty((H, W, 3), dtype=torch.uint8, device=dev)
+    if want_down and outd is None:
+        outd = torch.empty((-(-H // down), -(-W // down), 3), dtype=torch.uint8, device=dev)
+    maps = (C.c_void_p * max(n, 1))(*[labels[c].data_ptr() for c in ids])
+    fac = np.array([factors[c] for c in ids] or [1], dtype=np.int32)
+    col = np.array(cols or [(0, 0, 0)], dtype=np.uint8).reshape(-1)
+    alp = np.array(alphas or [0], dtype=np.int32)
+    L.check(L.lib().omni_stain(_ptr(rgb), H, W, rgb.stride(0), n, maps,
+                               fac.ctypes.data_as(C.c_void_p), col.ctypes.data_as(C.c_void_p),
+                               alp.ctypes.data_as(C.c_void_p),
+                               _ptr(out40) if want40 else None, out40.stride(0) if want40 else 0,
+                               down, _ptr(outd) if want_down else None,
+                               outd.stride(0) if want_down else 0, _stream()),
+            None, "omni_stain: bad arguments")
+    return (out40 if want40 else None), (outd if want_down else None)
 
 
 def synth_slide(spec, y0: int = 0, x0: int = 0, h: Optional[int] = None,

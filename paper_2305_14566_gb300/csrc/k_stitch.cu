@@ -9,6 +9,8 @@
 // stitched logits, coverage and per-scale argmax map.
 // Each thread handles four consecutive pixels with 16-byte loads when the
 // crop is 4-aligned (tile borders fall on multiples of the stride S, S % 4 == 0).
+// With a stitch window the average is weighted: L = sum_p w_p l_p / sum_p w_p,
+// w_p = t(y - y_p) t(x - x_p) from a P-entry table (votes stay unweighted).
 #include "omni_internal.cuh"
 
 namespace omni {
@@ -17,7 +19,7 @@ namespace {
 // Classes are the outer loop so only one class's sums and votes are live
 // (the tile slots are re-read per class from L1); this keeps the register
 // count low enough for the occupancy a bandwidth-bound pass needs.
-template <bool VEC>
+template <bool VEC, bool WIN>
 __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
   constexpr int NV = VEC ? 4 : 1;
   const int ox = (blockIdx.x * 64 + (threadIdx.x & 63)) * NV;
@@ -42,12 +44,13 @@ __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
   for (int v = 0; v < NV; ++v) { best[v] = 0.f; arg[v] = 0; }
   int cov = 0;
   for (int c = 0; c < a.n_cls; ++c) {
-    float sum[NV];
+    float sum[NV], wsum[NV];
     int votes[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) { sum[v] = 0.f; votes[v] = 0; }
+    for (int v = 0; v < NV; ++v) { sum[v] = 0.f; wsum[v] = 0.f; votes[v] = 0; }
     int n = 0;
     for (int i = i_lo; i <= i_hi; ++i) {
+      const float wy = WIN ? __ldg(a.window + (cy - i * a.S)) : 1.f;
       for (int j = j_lo; j <= j_hi; ++j) {
         const int slot = a.slot_map[i * a.gw + j];
         if (slot < 0) continue;
@@ -61,9 +64,21 @@ __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
         } else {
           l[0] = __ldg(base);
         }
+        float w[NV];
+        if constexpr (WIN && VEC) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(a.window + (cx - j * a.S)));
+          w[0] = wy * q.x; w[1] = wy * q.y; w[2] = wy * q.z; w[3] = wy * q.w;
+        } else if constexpr (WIN) {
+          w[0] = wy * __ldg(a.window + (cx - j * a.S));
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          sum[v] += l[v];
+          if constexpr (WIN) {
+            sum[v] = fmaf(w[v], l[v], sum[v]);
+            wsum[v] += w[v];
+          } else {
+            sum[v] += l[v];
+          }
           votes[v] += l[v] > 0.f ? 1 : 0;
         }
       }
@@ -73,7 +88,8 @@ __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
     uint8_t lab[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      L[v] = cov > 0 ? sum[v] / (float)cov : 0.f;
+      if constexpr (WIN) L[v] = cov > 0 ? sum[v] / wsum[v] : 0.f;
+      else L[v] = cov > 0 ? sum[v] / (float)cov : 0.f;
       const bool on = a.mode == OMNI_STITCH_AVG ? (cov > 0 && L[v] > 0.f) : (cov > 0 && 2 * votes[v] >= cov);
       lab[v] = (on && tis) ? 1 : 0;
       if (L[v] > best[v]) { best[v] = L[v]; arg[v] = a.cls_ids[c] + 1; }
@@ -111,10 +127,12 @@ cudaError_t launch_stitch(const StitchArgs& a, cudaStream_t st) {
   const bool vec = (a.ow % 4 == 0) && (a.ox0 % 4 == 0) && (a.S % 4 == 0) && (a.P % 4 == 0);
   if (vec) {
     dim3 grid((a.ow / 4 + 63) / 64, (a.oh + 3) / 4);
-    k_stitch<true><<<grid, 256, 0, st>>>(a);
+    if (a.window) k_stitch<true, true><<<grid, 256, 0, st>>>(a);
+    else k_stitch<true, false><<<grid, 256, 0, st>>>(a);
   } else {
     dim3 grid((a.ow + 63) / 64, (a.oh + 3) / 4);
-    k_stitch<false><<<grid, 256, 0, st>>>(a);
+    if (a.window) k_stitch<false, true><<<grid, 256, 0, st>>>(a);
+    else k_stitch<false, false><<<grid, 256, 0, st>>>(a);
   }
   return cudaGetLastError();
 }

@@ -158,6 +158,7 @@ struct StitchArgs {
   const float* logits;        // [slot][n_cls][P*P]
   int n_cls; int cls_ids[OMNI_MAX_CLASSES];
   int mode;                   // OMNI_STITCH_*
+  const float* window;        // [P] separable overlap-average weight t(u); null = flat
   const uint8_t* tissue; int th, tw;   // thumbnail mask (null: no AND)
   uint8_t* labels[OMNI_MAX_CLASSES];
   float* out_logits[OMNI_MAX_CLASSES];

@@ -28,6 +28,7 @@ struct omni_ctx {
   ConvLayerW dec2t0{};                              // last block's second conv, transposed + flipped
   float *wh = nullptr, *bh = nullptr, *wc = nullptr, *bc = nullptr;
   unsigned* d_err = nullptr;
+  float* d_window = nullptr;                        // [P] overlap-average weight t(u), or null (flat)
   int32_t* h_counts = nullptr;                      // pinned
   // timing
   bool timing = false;
@@ -120,6 +121,7 @@ std::string validate(const omni_config& c) {
   if (c.precision != OMNI_FP32 && c.precision != OMNI_BF16 && c.precision != OMNI_FP16)
     return "precision must be FP32, BF16 or FP16";
   if (c.stitch_mode != OMNI_STITCH_AVG && c.stitch_mode != OMNI_STITCH_VOTE) return "bad stitch_mode";
+  if (c.stitch_window < OMNI_WINDOW_FLAT || c.stitch_window > OMNI_WINDOW_HANN) return "bad stitch_window";
   if (c.median_k < 1 || c.median_k % 2 == 0 || c.median_k > 255) return "median_k must be odd, 1..255";
   if (c.max_batch < 1 || c.max_batch > 4096) return "max_batch must be 1..4096";
   if (c.pad_lead < 0 || c.pad_lead % fmax) return "pad_lead must be a non-negative multiple of the largest factor";
@@ -315,6 +317,21 @@ omni_status omni_create(const omni_config* cfg, omni_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counts, (OMNI_MAX_SCALES + 1) * sizeof(int32_t));
+  if (e == cudaSuccess && cfg->stitch_window != OMNI_WINDOW_FLAT) {
+    // one-dimensional weight of the stitch window, from its definition
+    const int P = cfg->patch;
+    std::vector<float> t(P);
+    for (int u = 0; u < P; ++u) {
+      if (cfg->stitch_window == OMNI_WINDOW_TENT) {
+        t[u] = (float)std::min(u + 1, P - u);
+      } else {
+        const double sn = std::sin(M_PI * (u + 0.5) / P);
+        t[u] = (float)(sn * sn);
+      }
+    }
+    e = cudaMalloc(&ctx->d_window, P * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_window, t.data(), P * sizeof(float), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     fprintf(stderr, "omni_create: %s\n", cudaGetErrorString(e));
     omni_destroy(ctx);
@@ -329,6 +346,7 @@ void omni_destroy(omni_ctx* ctx) {
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->wdev) cudaFree(ctx->wdev);
   if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->d_window) cudaFree(ctx->d_window);
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   for (auto& e : ctx->evs) {
     cudaEventDestroy(e.a);
@@ -852,7 +870,7 @@ omni_status run_network(omni_ctx* ctx, const omni_config& c, const Plan& p, uint
       a.hs = p.g.Hp / f; a.ws = p.g.Wp / f;
       a.oy0 = c.pad_lead / f; a.ox0 = c.pad_lead / f;
       a.oh = (H + f - 1) / f; a.ow = (W + f - 1) / f;
-      a.P = c.patch; a.S = p.g.S[s]; a.gh = p.g.gh[s]; a.gw = p.g.gw[s]; a.f = f;
+      a.window = ctx->d_window; a.P = c.patch; a.S = p.g.S[s]; a.gh = p.g.gh[s]; a.gw = p.g.gw[s]; a.f = f;
       a.slot_map = slot + p.g.grid_off[s];
       a.logits = reinterpret_cast<const float*>(ws + p.logits);
       a.n_cls = ncls;
@@ -1417,6 +1435,8 @@ extern "C" omni_status omni_backward(omni_ctx* ctx, const uint8_t* rgb, int32_t 
   if (!ctx->have_weights) return fail(ctx, OMNI_ESTATE, "omni_load_weights has not been called");
   const omni_config& c = ctx->cfg;
   if (c.precision != OMNI_FP32) return fail(ctx, OMNI_EINVAL, "omni_backward needs an OMNI_FP32 context");
+  if (c.stitch_window != OMNI_WINDOW_FLAT)
+    return fail(ctx, OMNI_EINVAL, "omni_backward differentiates the flat overlap average only");
   for (int k = 0; k < c.n_classes; ++k)
     if (!gt_dev[k]) return fail(ctx, OMNI_EINVAL, "missing ground-truth mask for class " + std::to_string(k));
   BwdPlan bp;

@@ -24,6 +24,9 @@ CLASS_NAMES = ("PTC", "VES", "PT", "DT", "TUFT", "CAP")
 
 STITCH_AVG = 0
 STITCH_VOTE = 1
+WINDOW_FLAT = 0        # overlap-average weight per tile pixel: 1
+WINDOW_TENT = 1        # min(u + 1, P - u) per axis
+WINDOW_HANN = 2        # sin^2(pi (u + 1/2) / P) per axis
 
 
 @dataclass(frozen=True)
@@ -50,6 +53,7 @@ class Workload:
     max_batch: int = 32
     head_offset: float = 0.0       # controller bias of the head's final bias b3 (weights init)
     strides: Tuple[int, ...] = ()  # per-scale tile stride; () or 0 = S (Sec. 3.2: 256, 64, 64)
+    stitch_window: int = WINDOW_FLAT
 
     @property
     def n_classes(self) -> int:

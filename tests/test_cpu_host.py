@@ -54,7 +54,8 @@ def test_weights_count_matches_blob_layout(L):
 
 @pytest.mark.parametrize("field,value", [("levels", 1), ("base", 12), ("stride", 100),
                                          ("median_k", 4), ("max_batch", 0), ("pad_lead", 3),
-                                         ("n_classes", 17)])
+                                         ("n_classes", 17), ("stitch_window", 3),
+                                         ("stitch_window", -1)])
 def test_invalid_configs_rejected_without_device(L, field, value):
     c = _cfg(L, synth.NEEDLE, **{field: value})
     ctx = C.c_void_p()

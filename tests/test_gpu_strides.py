@@ -1,7 +1,9 @@
-"""Per-scale tile strides (Sec. 3.2: 256 at 40x, 64 at 10x and 5x, majority
-vote) through the whole GPU path: the tile lists equal the oracle's, the FP32
-maps match the FP64 oracle on a window, the tensor-core precisions agree
-with FP32, and the needle slide tiles to the oracle's stored counts."""
+"""Overlap variants through the whole GPU path.  Per-scale tile strides
+(Sec. 3.2: 256 at 40x, 64 at 10x and 5x, majority vote): the tile lists
+equal the oracle's, the FP32 maps match the FP64 oracle on a window, the
+tensor-core precisions agree with FP32, and the needle slide tiles to the
+oracle's stored counts.  Weighted overlap averages (tent and Hann windows)
+match the oracle's."""
 import json
 import os
 
@@ -118,3 +120,49 @@ def test_needle_slide_tiles_to_the_oracle_counts(api):
     assert counts[1:] == gold["paper_strides_tiles_per_scale"]
     assert counts[0] == gold["paper_strides_tiles_total"]
     assert np.array_equal(t["tissue"].cpu().numpy().astype(bool), mask)
+
+
+@pytest.mark.parametrize("window", [synth.WINDOW_TENT, synth.WINDOW_HANN])
+@pytest.mark.parametrize("strides", [(), (64, 16, 16)])
+def test_windowed_average_fp32_against_oracle(api, slide, window, strides):
+    """L = sum_p w_p l_p / sum_p w_p with a tent or Hann tile window: logits
+    within 1e-4 of the oracle, labels equal wherever |L| >= 1e-3, coverage
+    exact; the flat-window run of the same slide differs (the window is used)."""
+    w = SMALL.with_(strides=strides, stitch_window=window, stitch_mode=synth.STITCH_AVG)
+    blob = synth.gen_weights(w)
+    rgb = torch.from_numpy(slide).cuda()
+    seg = api.Segmenter(w, blob)
+    out = seg.segment(rgb, logits=True, coverage=True)
+    out = {k: {c: t.clone() for c, t in d.items()} for k, d in out.items()}
+    seg.close()
+    flat = api.Segmenter(w.with_(stitch_window=synth.WINDOW_FLAT), blob)
+    fo = flat.segment(rgb, logits=True)
+    torch.cuda.synchronize()
+    orc = O.segment(slide, w, blob, window=(256, 512, 256, 256), batch=8)
+    for c, s in enumerate(w.class_scale):
+        wy, wx, wh, ww = orc["window"][s]
+        g = out["logits"][c][wy:wy + wh, wx:wx + ww].double().cpu().numpy()
+        o = orc["L"][c]
+        assert np.abs(g - o).max() <= LOGIT_TOL, c
+        gl = out["labels"][c][wy:wy + wh, wx:wx + ww].cpu().numpy()
+        assert not ((gl != orc["labels"][c]) & (np.abs(o) >= 1e-3)).any(), c
+        cov = out["coverage"][s][wy:wy + wh, wx:wx + ww].cpu().numpy().astype(np.int64)
+        assert np.array_equal(cov, orc["cov"][c]), c
+    assert any(not torch.equal(out["logits"][c], fo["logits"][c]) for c in fo["logits"])
+    flat.close()
+
+
+def test_backward_refuses_a_weighted_window(api):
+    """omni_backward differentiates the flat overlap average only; a context
+    with a tent window gets OMNI_EINVAL and a message, nothing launches."""
+    from paper_2305_14566_gb300 import _lib as L
+    w = synth.DIFF.with_(H=512, W=512, stitch_window=synth.WINDOW_TENT)
+    seg = api.Segmenter(w, synth.gen_weights(w))
+    rgb = torch.full((512, 512, 3), 200, dtype=torch.uint8, device="cuda")
+    sz = seg.query(512, 512)
+    gts = [torch.zeros((sz.out_h[s], sz.out_w[s]), dtype=torch.uint8, device="cuda")
+           for s in w.class_scale]
+    with pytest.raises(L.OmniError) as e:
+        seg.backward(rgb, gts)
+    assert e.value.status == L.EINVAL and "flat" in str(e.value)
+    seg.close()

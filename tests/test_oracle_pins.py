@@ -353,6 +353,56 @@ def test_stitch_constant_field_and_missing_tiles():
     assert (L[:8, :12] == 2.5).all() and (L[8:] == 0).all() and (cov[8:] == 0).all()
 
 
+@pytest.mark.parametrize("window", [synth.WINDOW_TENT, synth.WINDOW_HANN])
+def test_weighted_stitch_constant_and_known_canvas(window):
+    """A weighted average of equal values is that value: a constant field
+    stays constant and tiles cut from a canvas re-stitch to it (exactly for
+    the integer tent weights and dyadic values, to rounding for Hann)."""
+    hs, ws, P, S = 96, 128, 32, 16
+    canvas = rng(15).integers(-512, 512, (hs, ws)) / 64.0
+    tiles = {(y, x): canvas[y:y + P, x:x + P].copy()
+             for y in range(0, hs - P + 1, S) for x in range(0, ws - P + 1, S)}
+    L, cov, _ = O.stitch(tiles, hs, ws, P, window)
+    if window == synth.WINDOW_TENT:
+        assert np.array_equal(L, canvas)
+    else:
+        assert np.abs(L - canvas).max() < 1e-12
+    assert cov[40, 40] == 4
+    const = {k: np.full((P, P), -1.75) for k in tiles}
+    Lc, _, _ = O.stitch(const, hs, ws, P, window)
+    assert np.abs(Lc + 1.75).max() < 1e-12
+
+
+def test_weighted_stitch_hand_values():
+    """P = 4, two tiles at x = 0 and x = 2 holding 3 and 6.  Tent weights per
+    axis are 1, 2, 2, 1: pixel x = 2 sees weights 2 (first tile) and 1, so
+    L = (2*3 + 6) / 3 = 4; pixel x = 3 sees 1 and 2, L = 5.  Hann weights
+    sin^2(pi (u + 1/2) / 4) of the two tiles sum to 1 there (sin^2 + cos^2),
+    so L = 3 cos^2(pi/8) + 6 sin^2(pi/8) = 3 + 1.5 (1 - sqrt(2)/2).  The flat
+    window gives the plain mean 4.5."""
+    tiles = {(0, 0): np.full((4, 4), 3.0), (0, 2): np.full((4, 4), 6.0)}
+    Lt, cov, _ = O.stitch(tiles, 4, 6, 4, synth.WINDOW_TENT)
+    assert Lt[1, 2] == 4.0 and Lt[1, 3] == 5.0 and Lt[1, 0] == 3.0 and Lt[1, 5] == 6.0
+    assert cov[1].tolist() == [1, 1, 2, 2, 1, 1]
+    Lh, _, _ = O.stitch(tiles, 4, 6, 4, synth.WINDOW_HANN)
+    assert abs(Lh[2, 2] - (3 + 1.5 * (1 - np.sqrt(2) / 2))) < 1e-12
+    assert abs(Lh[2, 3] - (6 - 1.5 * (1 - np.sqrt(2) / 2))) < 1e-12
+    Lf, _, _ = O.stitch(tiles, 4, 6, 4, synth.WINDOW_FLAT)
+    assert Lf[0, 2] == 4.5 and Lf[0, 3] == 4.5
+
+
+def test_hann_window_is_a_partition_of_unity_at_half_overlap():
+    """With S = P / 2 every interior pixel's four Hann weights sum to 1."""
+    P, S = 16, 8
+    w = O.window_weights(P, synth.WINDOW_HANN)
+    tot = np.zeros((64, 64))
+    for y in range(0, 64 - P + 1, S):
+        for x in range(0, 64 - P + 1, S):
+            tot[y:y + P, x:x + P] += w
+    assert np.abs(tot[S:-S, S:-S] - 1.0).max() < 1e-14
+    assert np.array_equal(O.window_weights(P, synth.WINDOW_FLAT), np.ones((P, P)))
+
+
 def test_overlap_counts_match_paper():
     g = json.load(open(GOLDEN))
     P = g["tile_size"]["value"]
@@ -457,3 +507,56 @@ def test_generator_windows_are_consistent():
     assert np.array_equal(synth.gen_window(spec, 37, 111, 50, 70), full[37:87, 111:181])
     bg = full[full.min(axis=2) > 225]
     assert abs(bg.mean() - 235) < 2 and bg.std() > 3
+
+
+# ---------------------------------------------------------------- stained products (Sec. 2.3)
+
+
+def test_stain_hand_values_identities_and_order():
+    """(100, 200, 50) stained red (255, 0, 0) at alpha 128: (100*128 + 255*128 +
+    128) >> 8 = 178, (200*128 + 128) >> 8 = 100, (50*128 + 128) >> 8 = 25.
+    Alpha 0 leaves the slide, alpha 256 paints the colour, later maps paint
+    over earlier ones."""
+    rgb = np.zeros((4, 4, 3), np.uint8)
+    rgb[...] = (100, 200, 50)
+    on = np.ones((4, 4), np.uint8)
+    assert O.stain(rgb, [on], [1], [(255, 0, 0)], [128])[0, 0].tolist() == [178, 100, 25]
+    assert np.array_equal(O.stain(rgb, [on], [1], [(255, 0, 0)], [0]), rgb)
+    assert O.stain(rgb, [on], [1], [(7, 8, 9)], [256])[2, 3].tolist() == [7, 8, 9]
+    two = O.stain(rgb, [on, on], [1, 1], [(7, 8, 9), (1, 2, 3)], [256, 256])
+    assert (two.reshape(-1, 3) == (1, 2, 3)).all()
+    assert np.array_equal(O.stain(rgb, [None], [1], [(1, 2, 3)], [256]), rgb)
+
+
+def test_stain_maps_lower_scales_by_their_factor():
+    """A 10x map pixel (1, 2) covers 40x rows 4..7 and columns 8..11 exactly
+    (brute force over the slide)."""
+    rgb = rng(21).integers(0, 256, (13, 17, 3)).astype(np.uint8)
+    m = np.zeros((4, 5), np.uint8)
+    m[1, 2] = 1
+    out = O.stain(rgb, [m], [4], [(0, 0, 0)], [256])
+    for y in range(13):
+        for x in range(17):
+            inside = 4 <= y < 8 and 8 <= x < 12
+            assert out[y, x].tolist() == ([0, 0, 0] if inside else rgb[y, x].tolist())
+
+
+def test_resize_down_rounding_edges_and_pyramid():
+    """Box mean rounded half up: eight 5s and eight 0s in a 4 x 4 block give
+    (40 + 8) // 16 = 3; a 5 x 7 image resized by 4 is 2 x 2, its corner block
+    averaging the 1 x 3 remaining pixels; a constant-block image resizes
+    exactly; resizing by 2 equals the pyramid's 2 x 2 mean."""
+    img = np.zeros((4, 4, 3), np.uint8)
+    img[:2] = 5
+    assert O.resize_down(img, 4)[0, 0].tolist() == [3, 3, 3]
+    r = rng(22).integers(0, 256, (5, 7, 3)).astype(np.uint8)
+    d = O.resize_down(r, 4)
+    assert d.shape == (2, 2, 3)
+    blk = r[4:5, 4:7].reshape(-1, 3).astype(np.int64)
+    assert d[1, 1].tolist() == ((blk.sum(0) + 1) // 3).tolist()
+    blk = r[0:4, 4:7].reshape(-1, 3).astype(np.int64)
+    assert d[0, 1].tolist() == ((blk.sum(0) + 6) // 12).tolist()
+    c = np.repeat(np.repeat(rng(23).integers(0, 256, (3, 5, 3)), 8, 0), 8, 1).astype(np.uint8)
+    assert np.array_equal(O.resize_down(c, 8), c[::8, ::8])
+    e = rng(24).integers(0, 256, (16, 24, 3)).astype(np.uint8)
+    assert np.array_equal(O.resize_down(e, 2), O.half(e))
