@@ -269,6 +269,27 @@ struct StageRing {
 
 // This CTA's tiles t = blockIdx.x + i * gridDim.x of an images x ny x nx tile
 // grid, kept as (img, ty, tx) and stepped by a mixed-radix add.
+// RGB residual input of one epilogue lane, fetched one tile ahead: the
+// canvas bytes stay in registers until the tile that needs them, so their
+// latency overlaps the current tile instead of following its TMEM wait.
+struct RgbPrefetch {
+  int t = -1, img = -1, y0 = 0, x0 = 0;
+  uint32_t b0 = 0, b1 = 0, b2 = 0;
+  __device__ __forceinline__ void fetch(const uint8_t* canvas, long long cs, const int32_t* tiles3, int tile,
+                                        int im, int hh, int ww) {
+    if (im != img) {
+      img = im;
+      y0 = __ldg(tiles3 + 3 * im + 1);
+      x0 = __ldg(tiles3 + 3 * im + 2);
+    }
+    const uint8_t* px = canvas + (long long)(y0 + hh) * cs + (long long)(x0 + ww) * 3;
+    b0 = __ldg(px);
+    b1 = __ldg(px + 1);
+    b2 = __ldg(px + 2);
+    t = tile;
+  }
+};
+
 struct TileWalk {
   int t, img, ty, tx, step;
   int s_img, s_ty, s_tx, ny, nx;
@@ -787,11 +808,25 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float* sth = sthe + (warp - 2) * (2 * kHeadParams);
     int th_img = -1;
     int tcount = 0;
+    const bool rgb = p.res_mode == RES_RGB;
+    RgbPrefetch pf;
     TileWalk tw;
     tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
     for (; tw.t < p.n_tiles; tw.next(), ++tcount) {
       const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
       if (MB == 1 && fuse_head && (buf & 1) != grp) continue;
+      uint32_t u0 = 0, u1 = 0, u2 = 0;
+      if (rgb) {
+        if (pf.t != tw.t)
+          pf.fetch(p.canvas, p.canvas_stride, p.tiles3, tw.t, tw.img,
+                   tw.ty * (kHTH * MB) + blk * kHTH + row / kHTW, tw.tx * kHTW + row % kHTW);
+        u0 = pf.b0; u1 = pf.b1; u2 = pf.b2;
+        TileWalk nx = tw;
+        nx.next();
+        if (nx.t < p.n_tiles)
+          pf.fetch(p.canvas, p.canvas_stride, p.tiles3, nx.t, nx.img,
+                   nx.ty * (kHTH * MB) + blk * kHTH + row / kHTW, nx.tx * kHTW + row % kHTW);
+      }
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
@@ -800,12 +835,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       const int ww = tw.tx * kHTW + row % kHTW;
       const long long m = (long long)img * RR + (long long)hh * p.R + ww;
       float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-      if (p.res_mode == RES_RGB) {
-        const uint8_t* px = p.canvas + (long long)(p.tiles3[3 * img + 1] + hh) * p.canvas_stride +
-                            (long long)(p.tiles3[3 * img + 2] + ww) * 3;
-        v0 = norm_u8(px[0]);
-        v1 = norm_u8(px[1]);
-        v2 = norm_u8(px[2]);
+      if (rgb) {
+        v0 = norm_u8((uint8_t)u0);
+        v1 = norm_u8((uint8_t)u1);
+        v2 = norm_u8((uint8_t)u2);
       }
       float h0[kHeadCh];
 #pragma unroll
@@ -1123,10 +1156,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float* sth = sthe + (warp - 2) * (2 * kHeadParams);
     int th_img = -1;
     int tcount = 0;
+    const bool rgb = p.res_mode == RES_RGB;
+    RgbPrefetch pf;
     TileWalk tw;
     tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
     for (; tw.t < p.n_tiles; tw.next(), ++tcount) {
       const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
+      uint32_t u0 = 0, u1 = 0, u2 = 0;
+      if (rgb) {
+        // lanes without an output column (halo lanes, columns past R) fetch nothing
+        const int wc = tw.tx * kXTW + col - 1;
+        if (pf.t != tw.t && col >= 1 && col <= kXTW && wc < p.R)
+          pf.fetch(p.canvas, p.canvas_stride, p.tiles3, tw.t, tw.img,
+                   tw.ty * (kHTH * MB) + blk * kHTH + row / kHTW, wc);
+        u0 = pf.b0; u1 = pf.b1; u2 = pf.b2;
+        TileWalk nx = tw;
+        nx.next();
+        const int wn = nx.tx * kXTW + col - 1;
+        if (nx.t < p.n_tiles && col >= 1 && col <= kXTW && wn < p.R)
+          pf.fetch(p.canvas, p.canvas_stride, p.tiles3, nx.t, nx.img,
+                   nx.ty * (kHTH * MB) + blk * kHTH + row / kHTW, wn);
+      }
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
@@ -1136,12 +1186,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       const bool writes = col >= 1 && col <= kXTW && ww < p.R;
       const long long m = (long long)img * RR + (long long)hh * p.R + (ww < 0 ? 0 : ww);
       float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-      if (p.res_mode == RES_RGB && writes) {
-        const uint8_t* px = p.canvas + (long long)(p.tiles3[3 * img + 1] + hh) * p.canvas_stride +
-                            (long long)(p.tiles3[3 * img + 2] + ww) * 3;
-        v0 = norm_u8(px[0]);
-        v1 = norm_u8(px[1]);
-        v2 = norm_u8(px[2]);
+      if (rgb && writes) {
+        v0 = norm_u8((uint8_t)u0);
+        v1 = norm_u8((uint8_t)u1);
+        v2 = norm_u8((uint8_t)u2);
       }
       __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) +
@@ -1363,11 +1411,16 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
     bool lapped = false;
     TileWalk tw;
     tw.init(p.R / kHTH, p.R / kHTW, (int)blockIdx.x + grp * (int)gridDim.x, kFirstGroups * (int)gridDim.x);
+    int cimg = -1, cx0 = 0;                          // tile origin column of the current image
     for (; tw.t < p.n_tiles; tw.next()) {
+      if (tw.img != cimg) {
+        cimg = tw.img;
+        cx0 = __ldg(p.tiles3 + 3 * tw.img + 2);
+      }
       bool ok = !lapped || mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag, p.err);
       ok = ok && mbar_wait(smem_u32(&rfull[s]), ph, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
-      const int off = ((p.tiles3[3 * tw.img + 2] + tw.tx * kHTW - 1) * 3) & 15;
+      const int off = ((cx0 + tw.tx * kHTW - 1) * 3) & 15;
       const uint8_t* raw = sRaw + (size_t)s * kRawStageBytes + off;
       const int h_in = tw.ty * kHTH + rh - 1, w_in = tw.tx * kHTW + rw - 1;   // tile coords of tap (0, 0)
       float v[32];
