@@ -126,3 +126,34 @@ def test_flops_per_tile_needle():
 def test_workload_padding_matches_config_sizes():
     assert O.padded_dims(synth.TINY)[:2] == (512, 512)
     assert O.padded_dims(synth.DIFF)[:2] == (2048, 2048)
+
+
+@pytest.mark.parametrize("case", ["down", "factor", "alpha", "no_output", "stride", "n_maps"])
+def test_stain_rejects_bad_arguments_without_device(L, case):
+    """omni_stain checks sizes, factors, alphas, resize factor and strides on
+    the host and returns OMNI_EINVAL before touching the device (the
+    pointers below are never dereferenced)."""
+    fake = C.c_void_p(0x1000)
+    maps = (C.c_void_p * 1)(fake)
+    fac = np.array([1], np.int32)
+    col = np.array([1, 2, 3], np.uint8)
+    alp = np.array([128], np.int32)
+    args = dict(H=64, W=64, rs=192, n=1, fac=fac, alp=alp, out40=fake, os=192, down=4, outd=fake, ds=48)
+    if case == "down":
+        args["down"] = 3
+    elif case == "factor":
+        args["fac"] = np.array([3], np.int32)
+    elif case == "alpha":
+        args["alp"] = np.array([257], np.int32)
+    elif case == "no_output":
+        args["out40"] = None
+        args["outd"] = None
+    elif case == "stride":
+        args["rs"] = 100
+    elif case == "n_maps":
+        args["n"] = 17
+    st = L.lib().omni_stain(fake, args["H"], args["W"], args["rs"], args["n"], maps,
+                            args["fac"].ctypes.data_as(C.c_void_p), col.ctypes.data_as(C.c_void_p),
+                            args["alp"].ctypes.data_as(C.c_void_p), args["out40"], args["os"],
+                            args["down"], args["outd"], args["ds"], None)
+    assert st == L.EINVAL
