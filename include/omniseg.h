@@ -8,6 +8,7 @@
  *   Sec. 2.2  Omni-Seg segmentation of overlapping 40x/10x/5x tiles
  *   Sec. 2.3  slide-wise aggregation into per-class label maps
  *                                                    -> omni_segment_slide
+ *             and the stained 40x product with its 10x resize -> omni_stain
  * plus a hand-written backward of the stitched soft-Dice + BCE loss through
  * the dynamic head, controller, pre-head and last decoder block
  * (omni_backward).
