@@ -1,6 +1,7 @@
-"""Randomised invariants of the oracle's aggregation and product steps (CPU):
-properties that hold for any input, so a misapplied weight, a wrong index or
-a dropped term in the oracle shows up on inputs no fixed case covers."""
+"""Randomised invariants of the oracle (CPU): stitching, staining, resizing,
+median blur, tiling and the network pieces obey properties that hold for
+any input, so a misapplied weight, a wrong index or a dropped term in the
+oracle shows up on inputs no fixed case covers."""
 import numpy as np
 import pytest
 
@@ -125,3 +126,65 @@ def test_tile_list_full_and_empty_masks(factors, hy, wx):
     empty, _ = O.tile_list(w, np.zeros((Hp // 32, Wp // 32), bool), Hp, Wp)
     assert len(full) == sum(int(np.prod(O.grid(w, Hp, Wp, s))) for s in range(len(factors)))
     assert empty == [] and full == sorted(full)
+
+
+@settings(max_examples=25, deadline=None)
+@given(st.integers(1, 6), st.integers(1, 6), st.integers(0, 2 ** 31 - 1))
+def test_upsample_commutes_with_flips_and_is_linear(H, W, seed):
+    """Half-pixel bilinear x2 with edge clamp is symmetric: flipping the input
+    along an axis flips the output; it is linear; its outputs stay within the
+    input's range (convex weights)."""
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    x = torch.randn((1, 2, H, W), generator=g, dtype=torch.float64)
+    y = torch.randn((1, 2, H, W), generator=g, dtype=torch.float64)
+    u = O.upsample2(x)
+    for d in (2, 3):
+        assert torch.allclose(O.upsample2(x.flip(d)), u.flip(d), atol=1e-12)
+    assert torch.allclose(O.upsample2(2.0 * x - y), 2.0 * u - O.upsample2(y), atol=1e-12)
+    assert u.shape == (1, 2, 2 * H, 2 * W)
+    assert float(u.min()) >= float(x.min()) - 1e-12 and float(u.max()) <= float(x.max()) + 1e-12
+
+
+@settings(max_examples=25, deadline=None)
+@given(st.integers(1, 6), st.integers(1, 6), st.integers(1, 3), st.integers(1, 3), st.integers(0, 2 ** 31 - 1))
+def test_conv3x3_flip_equivariance_and_linearity(H, W, C, O_, seed):
+    """Flipping the input and the kernel along an axis flips the output (zero
+    padding is symmetric); the conv is linear in the input and the weights."""
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    x = torch.randn((2, C, H, W), generator=g, dtype=torch.float64)
+    x2 = torch.randn((2, C, H, W), generator=g, dtype=torch.float64)
+    w = torch.randn((O_, C, 3, 3), generator=g, dtype=torch.float64)
+    w2 = torch.randn((O_, C, 3, 3), generator=g, dtype=torch.float64)
+    y = O.conv3x3(x, w)
+    for d in (2, 3):
+        assert torch.allclose(O.conv3x3(x.flip(d), w.flip(d)), y.flip(d), atol=1e-12)
+    assert torch.allclose(O.conv3x3(x + 3.0 * x2, w), y + 3.0 * O.conv3x3(x2, w), atol=1e-10)
+    assert torch.allclose(O.conv3x3(x, w - w2), y - O.conv3x3(x, w2), atol=1e-10)
+
+
+@settings(max_examples=25, deadline=None)
+@given(st.integers(1, 5), st.integers(1, 5), st.integers(0, 2 ** 31 - 1))
+def test_maxpool_picks_the_window_maximum(H, W, seed):
+    """Each pooled value is one of its 2 x 2 window's values and not below any."""
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    x = torch.randn((1, 3, 2 * H, 2 * W), generator=g, dtype=torch.float64)
+    m = O.maxpool2(x)
+    win = x.reshape(1, 3, H, 2, W, 2).permute(0, 1, 2, 4, 3, 5).reshape(1, 3, H, W, 4)
+    assert torch.equal(m, win.max(dim=-1).values)
+
+
+@settings(max_examples=25, deadline=None)
+@given(st.integers(1, 4), st.integers(0, 2 ** 31 - 1))
+def test_dynamic_head_is_per_tile(B, seed):
+    """Tile b's logits depend only on tile b's features and parameters:
+    permuting the batch permutes the output."""
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    h0 = torch.relu(torch.randn((B, 8, 3, 5), generator=g, dtype=torch.float64))
+    th = torch.randn((B, synth.N_HEAD_PARAMS), generator=g, dtype=torch.float64)
+    out = O.dynamic_head(h0, th)
+    perm = torch.randperm(B, generator=g)
+    assert torch.allclose(O.dynamic_head(h0[perm], th[perm]), out[perm], atol=1e-12)
