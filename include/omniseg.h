@@ -68,6 +68,7 @@ typedef int omni_status;
 
 #define OMNI_MAX_SCALES 4
 #define OMNI_MAX_CLASSES 16
+#define OMNI_MAX_SLIDES 16   /* slides per omni_segment_slides call */
 
 typedef struct omni_ctx omni_ctx;
 
@@ -166,9 +167,15 @@ const char* omni_last_error(const omni_ctx* ctx);
  *   pre-head wh[8][C_0] bh[8]; controller wc[153][C_{L-1}+n_classes+n_scales] bc[153]. */
 int64_t omni_weights_count(const omni_config* cfg);
 
-/* Copy a host FP32 weights blob to the device and build the kernels' layouts
- * (FP32 K-major for the plain path, BF16 K-major tiles for tcgen05).
- * Synchronous.  OMNI_EWEIGHTS if n_floats is wrong or a value is not finite. */
+/* Weights of the Omni-Seg network of Sec. 2.2 (residual U-Net, pre-head,
+ * class/scale-conditioned controller of the dynamic head).  The paper ships
+ * no checkpoint, so the blob carries seeded random-init values in the order
+ * given above.  Copies the host FP32 blob (borrowed; the caller keeps it) to
+ * one device allocation owned by the context and builds the kernels' layouts
+ * (FP32 K-major for the plain path, 16-bit K-major tiles for tcgen05).
+ * Replaces any earlier weights and drops a captured CUDA graph, whose
+ * arguments point at them.  Synchronous.  OMNI_EWEIGHTS if n_floats is wrong
+ * or a value is not finite (nothing changed); OMNI_ECUDA if the copy fails. */
 omni_status omni_load_weights(omni_ctx* ctx, const float* blob_host, int64_t n_floats);
 
 /* Sizes for an H x W slide under `cfg` (pure host computation, no device
@@ -185,7 +192,11 @@ omni_status omni_tile_slide(omni_ctx* ctx, const uint8_t* rgb_dev, int32_t H, in
 
 /* Whole path: tiling (as omni_tile_slide), the 40x/10x/5x pyramid, the U-Net
  * and dynamic heads on every foreground tile of every requested scale, and
- * the overlap stitch + label emission of every requested class.
+ * the overlap stitch + label emission of every requested class.  Tiles run in
+ * batches of max_batch in (scale, row, column) order; after each batch the
+ * output rows whose covering tile rows are all done are stitched, so tile
+ * logits are kept only for the P/S + 1 tile rows in flight (workspace_bytes
+ * does not grow with the number of tiles).
  * `scale_mask` / `class_mask` select scales / classes (bit i = index i); a
  * class is computed only if its scale is selected.  Synchronises `stream`
  * once (after tiling) to size the batch loop.  The workspace must hold
@@ -196,19 +207,19 @@ omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb_dev, int32_t H,
                                const omni_outputs* out, void* stream);
 
 /* Same as omni_segment_slide with a HOST slide and HOST label outputs
- * (`labels_host[c]` of out_h x out_w bytes, NULL = skip).  Copies in and out
- * on `stream` (pinned host memory gives full copy bandwidth) and returns
- * after the stream has drained. */
+ * (`labels_host[c]` of out_h x out_w bytes, NULL = skip).  The slide is
+ * uploaded on `stream`; the labels leave band by band: the stitch finalises
+ * the output rows covered by finished tile rows after every network batch,
+ * and each such band is copied to the host on a second stream owned by the
+ * context while the next batches compute.  Pinned host memory gives full copy
+ * bandwidth (pageable memory works, without the overlap).  Returns after
+ * both streams have drained. */
 omni_status omni_segment_slide_host(omni_ctx* ctx, const uint8_t* rgb_host, int32_t H,
                                     int32_t W, int64_t row_stride, uint32_t scale_mask,
                                     uint32_t class_mask, void* workspace_dev,
                                     uint64_t workspace_bytes, uint8_t* const* labels_host,
                                     void* stream);
 
-/* Seeded synthetic slide window (input generator, not part of the method):
- * pixel (y, x) of a slide_w-wide slide drawn from `n_ell` rotated ellipses
- * (int64 rows cy, cx, a, b, cos_q14, sin_q14) and SplitMix64 noise seeded
- * with `seed`; writes rows y0..y0+h-1, cols x0..x0+w-1 to out_dev. */
 /* Final products of the slide-wise aggregation (Sec. 2.3): every class's
  * merged label map stained onto the 40x slide in its own colour, and the
  * lower-magnification product resized directly from that stained image.
@@ -235,6 +246,40 @@ omni_status omni_stain(const uint8_t* rgb_dev, int32_t H, int32_t W, int64_t row
                        int64_t out40_stride, int32_t down, uint8_t* outd_dev, int64_t outd_stride,
                        void* stream);
 
+/* Several slides in one call: a batch of whole-slide images (the paper times
+ * its pipeline over a batch of WSIs, Table 1).  Every slide is tiled as by
+ * omni_tile_slide; then, scale by scale, the foreground tiles of ALL slides
+ * form one list (slide order, then row, column) and go through the network in
+ * shared batches of max_batch tiles -- a batch may hold tiles of several
+ * slides, so small slides and the few tiles of the coarse scales still fill
+ * whole batches -- and each slide's bands are stitched as its tile rows
+ * complete.  With graphs enabled (omni_set_graphs) the whole post-tiling
+ * chain of all slides is one captured CUDA graph.
+ *   n          1..OMNI_MAX_SLIDES slides; rgb_dev[i], H[i], W[i], row_stride[i]
+ *              as for omni_segment_slide (HOST arrays of device pointers/sizes)
+ *   out        HOST array of n omni_outputs (caller-allocated device buffers,
+ *              sized per slide by omni_query)
+ *   workspace  omni_query_slides() bytes: every slide's tiling stage plus one
+ *              network stage.
+ * Labels, logits, coverage and argmax equal n omni_segment_slide calls bit for
+ * bit (a tile's result does not depend on its batch).  Synchronises `stream`
+ * once, after tiling every slide. */
+omni_status omni_query_slides(const omni_config* cfg, int32_t n, const int32_t* H, const int32_t* W,
+                              uint64_t* workspace_bytes);
+omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* rgb_dev, const int32_t* H,
+                                const int32_t* W, const int64_t* row_stride, uint32_t scale_mask,
+                                uint32_t class_mask, void* workspace_dev, uint64_t workspace_bytes,
+                                const omni_outputs* out, void* stream);
+/* Completion time of every slide of the last omni_segment_slides call, in ms
+ * after the start of its post-tiling chain (CUDA events recorded on its
+ * stream, also inside a replayed graph): writes min(max, n) values and returns
+ * that count, or -1.  Synchronises on the last slide's event. */
+int32_t omni_get_slide_times(omni_ctx* ctx, int32_t max, float* ms);
+
+/* Seeded synthetic slide window (input generator, not part of the method):
+ * pixel (y, x) of a slide_w-wide slide drawn from `n_ell` rotated ellipses
+ * (int64 rows cy, cx, a, b, cos_q14, sin_q14) and SplitMix64 noise seeded
+ * with `seed`; writes rows y0..y0+h-1, cols x0..x0+w-1 to out_dev. */
 omni_status omni_synth_slide(const int64_t* ellipses_host, int32_t n_ell, uint64_t seed,
                              int32_t slide_w, int32_t y0, int32_t x0, int32_t h, int32_t w,
                              uint8_t* out_dev, int64_t row_stride, void* stream);
@@ -297,27 +342,32 @@ omni_status omni_set_graphs(omni_ctx* ctx, int32_t enabled);
  * of the next level (the pooling step of the encoder, Sec. 2.2) from its
  * epilogue, and the last decoder conv runs the pre-head and the dynamic heads
  * of the tile's classes (Sec. 2.2; at most two classes per scale) in its
- * epilogue, writing the FP32 tile logits directly; its BF16
- * output is then not stored.  Fusion applies only where the autotuned kernel
- * supports it (the small-N and dx-in-N variants for pooling, the small-N
- * variant for the head); elsewhere the separate kernels run.  With the head
- * fused, the pre-head reads the FP32 epilogue value instead of its BF16
- * rounding, so logits differ from the unfused path by that rounding only.
- * Disabling is for testing and comparison. */
+ * epilogue, writing the FP32 tile logits directly; its 16-bit output is then
+ * not stored.  Pooling fuses into the small-N and dx-in-N variants (kinds
+ * 1-4), the head into all of them for 32 or 64 output channels; the
+ * autotuner then considers only variants that fuse the head, so the dynamic
+ * head needs no launch of its own.  The GAP of the bottleneck and the
+ * controller always run as one launch per batch.  With the head fused, the
+ * pre-head reads the FP32 epilogue value instead of its 16-bit rounding, so
+ * logits differ from the unfused path by that rounding only.  Disabling is
+ * for testing and comparison. */
 omni_status omni_set_fusion(omni_ctx* ctx, int32_t enabled);
 
 /* Per-launch device times (ms) of the current timing record, with each
  * launch's kind (as above), tag and algorithmic
  * work (FLOPs for convolutions, else 0).  Tags: conv of encoder level l =
  * 10 l (first) / 10 l + 1 (second), decoder level l = 100 + 10 l (+1);
- * max-pool 200 + l, upsample 300 + l, GAP 400, controller 401, head 500, stitch 600 + scale,
+ * max-pool 200 + l, upsample 300 + l, GAP + controller 401, head 500, stitch 600 + scale,
  * pad 700, pyramid 701, tissue 702, tiles 703.  Writes at most `max`
  * entries into the caller's host arrays (any may be NULL) and returns the
  * count, or -1 on error.  Synchronises on the recorded events. */
 int64_t omni_get_launch_times(omni_ctx* ctx, int64_t max, double* ms, int32_t* kinds,
                               int32_t* tags, double* work);
 
-/* Loss and hand-written backward for one slide (FP32 contexts only).
+/* Loss and hand-written backward for one slide (FP32 contexts only).  The
+ * paper trains nothing (Omni-Seg is used pre-trained, Sec. 2.2); this entry
+ * differentiates its Sec. 2.2 head chain through the Sec. 2.3 overlap
+ * average, for fine-tuning the class/scale-conditioned parts.
  * Forward: the whole path with stitched FP32 logits; loss = mean over the
  * classes of soft-Dice (smoothing 1) + mean BCE between the stitched logits of
  * the class (label-map pixels of its scale) and `gt_dev[c]` (uint8 0/1, same

@@ -57,10 +57,17 @@ class Segmenter:
         self.ctx = C.c_void_p()
         st = self.lib.omni_create(C.byref(self.cfg), C.byref(self.ctx))
         L.check(st, None, "omni_create rejected the configuration")
-        blob = np.ascontiguousarray(blob, dtype=np.float32)
+        self.blob = None
+        self.load_weights(blob)
+        self._ws: Optional[torch.Tensor] = None
+
+    def load_weights(self, blob: np.ndarray):
+        """omni_load_weights: replace the context's weights (a flat FP32 blob in
+        the layout of omniseg.h); the segmenter keeps a host copy."""
+        blob = np.array(blob, dtype=np.float32, copy=True).ravel()
         L.check(self.lib.omni_load_weights(self.ctx, blob.ctypes.data_as(C.c_void_p), blob.size),
                 self.ctx)
-        self._ws: Optional[torch.Tensor] = None
+        self.blob = blob
 
     def close(self):
         if self.ctx:
@@ -152,6 +159,53 @@ class Segmenter:
                                             _ptr(ws), ws.numel(), C.byref(o), _stream()), self.ctx)
         return out
 
+    def segment_many(self, rgbs: Sequence[torch.Tensor], outs: Optional[Sequence[Dict]] = None,
+                     logits: bool = False) -> list:
+        """omni_segment_slides: several slides in one call, their tiles packed
+        into shared network batches per scale.  Returns one {"labels": ...,
+        "logits": ...} dict per slide (pass ``outs`` to reuse buffers)."""
+        n = len(rgbs)
+        dev = rgbs[0].device
+        cfg = self.cfg
+        Hs = np.array([int(r.shape[0]) for r in rgbs], np.int32)
+        Ws = np.array([int(r.shape[1]) for r in rgbs], np.int32)
+        strides = np.array([int(r.stride(0)) for r in rgbs], np.int64)
+        nbytes = C.c_uint64()
+        L.check(self.lib.omni_query_slides(C.byref(cfg), n, Hs.ctypes.data_as(C.c_void_p),
+                                           Ws.ctypes.data_as(C.c_void_p), C.byref(nbytes)),
+                None, "omni_query_slides: bad sizes")
+        if outs is None:
+            outs = []
+            for r in rgbs:
+                sz = self.query(int(r.shape[0]), int(r.shape[1]))
+                o = {"labels": {}, "logits": {}}
+                for k in range(cfg.n_classes):
+                    s = cfg.class_scale[k]
+                    shp = (sz.out_h[s], sz.out_w[s])
+                    o["labels"][k] = torch.empty(shp, dtype=torch.uint8, device=dev)
+                    if logits:
+                        o["logits"][k] = torch.empty(shp, dtype=torch.float32, device=dev)
+                outs.append(o)
+        arr = (L.Outputs * n)()
+        for i, o in enumerate(outs):
+            for k, t in o["labels"].items():
+                arr[i].labels[k] = t.data_ptr()
+            for k, t in o.get("logits", {}).items():
+                arr[i].logits[k] = t.data_ptr()
+        ptrs = (C.c_void_p * n)(*[r.data_ptr() for r in rgbs])
+        ws = self.workspace(nbytes.value, dev)
+        L.check(self.lib.omni_segment_slides(self.ctx, n, ptrs, Hs.ctypes.data_as(C.c_void_p),
+                                             Ws.ctypes.data_as(C.c_void_p), strides.ctypes.data_as(C.c_void_p),
+                                             (1 << cfg.n_scales) - 1, (1 << cfg.n_classes) - 1, _ptr(ws),
+                                             ws.numel(), arr, _stream()), self.ctx)
+        return list(outs)
+
+    def slide_times(self, n: int):
+        """Per-slide completion times (ms) of the last segment_many call."""
+        ms = np.zeros(n, np.float32)
+        got = self.lib.omni_get_slide_times(self.ctx, n, ms.ctypes.data_as(C.c_void_p))
+        return ms[:got].tolist() if got > 0 else None
+
     def segment_host(self, rgb_host: torch.Tensor, labels_host: Dict[int, torch.Tensor],
                      device="cuda") -> Dict[int, torch.Tensor]:
         """Whole path from a HOST slide into HOST label buffers (copies included)."""
@@ -177,6 +231,21 @@ class Segmenter:
                 "dec0_w1": (C0, 3 * C0, 3, 3), "dec0_g1": (C0,), "dec0_b1": (C0,),
                 "dec0_w2": (C0, C0, 3, 3), "dec0_g2": (C0,), "dec0_b2": (C0,),
                 "dec0_wp": (C0, 3 * C0)}
+
+    def grad_offsets(self):
+        """Blob offset of every differentiated tensor.  The blob ends with the
+        last decoder block (w1 g1 b1 w2 g2 b2 wp), the pre-head (w, b) and the
+        controller (w, b), in that order."""
+        order = ("dec0_w1", "dec0_g1", "dec0_b1", "dec0_w2", "dec0_g2", "dec0_b2", "dec0_wp",
+                 "head_w", "head_b", "ctrl_w", "ctrl_b")
+        shapes = self.grad_shapes()
+        n_tail = sum(int(np.prod(shapes[k])) for k in order)
+        off = self.blob.size - n_tail
+        out = {}
+        for k in order:
+            out[k] = off
+            off += int(np.prod(shapes[k]))
+        return out
 
     def backward(self, rgb: torch.Tensor, gts):
         """Stitched soft-Dice + BCE loss of one slide and its gradients (omni_backward).
@@ -247,13 +316,37 @@ class OmniSegLoss(torch.autograd.Function):
     """loss = OmniSegLoss.apply(segmenter, rgb, gts, *params): the stitched
     soft-Dice + BCE loss as a differentiable function of the controller, the
     pre-head and the last decoder block (in the order of _lib.GRAD_FIELDS).
-    The parameter values must match the weights loaded into ``segmenter``;
-    forward and backward both come from one omni_backward call."""
+
+    The parameter tensors are the source of truth: each must have the shape of
+    its gradient (``Segmenter.grad_shapes``), and when any differs from the
+    weights loaded into ``segmenter`` (an optimizer stepped them), forward
+    writes them into the segmenter's blob and reloads it before evaluating, so
+    loss and gradients always belong to the values passed in.  Forward and
+    backward both come from one omni_backward call."""
 
     @staticmethod
     def forward(ctx, seg, rgb, gts, *params):
+        names = L.GRAD_FIELDS
+        if len(params) != len(names):
+            raise ValueError("OmniSegLoss takes %d parameter tensors (%s), got %d"
+                             % (len(names), ", ".join(names), len(params)))
+        shapes = seg.grad_shapes()
+        offs = seg.grad_offsets()
+        blob = None
+        for k, p in zip(names, params):
+            if tuple(p.shape) != tuple(shapes[k]):
+                raise ValueError("parameter %s has shape %s, the network needs %s"
+                                 % (k, tuple(p.shape), tuple(shapes[k])))
+            v = p.detach().to("cpu", torch.float32).contiguous().numpy().ravel()
+            cur = seg.blob[offs[k]:offs[k] + v.size]
+            if not np.array_equal(v, cur):
+                if blob is None:
+                    blob = seg.blob.copy()
+                blob[offs[k]:offs[k] + v.size] = v
+        if blob is not None:
+            seg.load_weights(blob)
         loss, grads = seg.backward(rgb, gts)
-        ctx.grads = [grads[k] for k in L.GRAD_FIELDS]
+        ctx.grads = [grads[k] for k in names]
         return loss[0]
 
     @staticmethod

@@ -5,6 +5,9 @@ sub-chain; it is itself pinned by central finite differences in
 tests/test_oracle_pins.py.  The bar is 1e-3 relative: for every gradient
 tensor, max |g_gpu - g_oracle| <= 1e-3 * max |g_oracle|.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -66,5 +69,70 @@ def test_backward_small_network_matches_oracle(api):
 
 
 def test_backward_diff_workload_matches_oracle(api):
-    """The differentiation workload itself (base 32, 5 levels)."""
-    _compare(*_run(api, synth.DIFF, 32))
+    """The differentiation workload itself (base 32, 5 levels): every gradient
+    tensor against the oracle's autograd gradient (max-norm relative 1e-3), and
+    entry by entry against FP64 central differences at 64 seeded parameters
+    (tests/golden/diff_fd.json): |g - fd| <= 1e-3 max(|fd|, 1e-3 max|g_tensor|),
+    the floor covering entries far below their tensor's largest, where FP32
+    accumulation order dominates."""
+    gl, gg, ol, og = _run(api, synth.DIFF, 32)
+    _compare(gl, gg, ol, og)
+    fdg = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "diff_fd.json")))
+    worst = 0.0
+    for d in fdg["draws"]:
+        got = float(gg[NAME[d["name"]]][tuple(d["index"])])
+        scale = max(abs(d["fd"]), 1e-3 * d["tensor_max_abs_grad"])
+        worst = max(worst, abs(got - d["fd"]) / scale)
+        assert abs(got - d["fd"]) <= 1e-3 * scale, (d, got)
+    print("64 FD entries: worst relative error %.2e" % worst)
+
+
+def test_omniseg_loss_autograd_matches_backward_and_tracks_params(api):
+    """OmniSegLoss through torch.autograd: p.grad equals omni_backward's
+    gradients; after a parameter update the next forward uses the updated
+    values (the oracle's loss and gradient at those values); a wrongly shaped
+    parameter is refused."""
+    from paper_2305_14566_gb300 import _lib as L
+    w = synth.DIFF.with_(base=8, levels=3)
+    rgb_np = synth.gen_slide(synth.spec_for(w))
+    gts_np = synth.gen_gt_masks(w.H, w.W, w.factors, w.class_scale, seed=7)
+    blob = synth.gen_weights(w)
+    rgb = torch.from_numpy(rgb_np).cuda()
+    gts = [torch.from_numpy(g).cuda() for g in gts_np]
+    seg = api.Segmenter(w, blob, max_batch=16)
+    offs = seg.grad_offsets()
+    shapes = seg.grad_shapes()
+    params = [torch.from_numpy(blob[offs[k]:offs[k] + int(np.prod(shapes[k]))].reshape(shapes[k]).copy())
+              .cuda().requires_grad_(True) for k in L.GRAD_FIELDS]
+    loss = api.OmniSegLoss.apply(seg, rgb, gts, *params)
+    loss.backward()
+    _, ref = seg.backward(rgb, gts)
+    torch.cuda.synchronize()
+    for k, p in zip(L.GRAD_FIELDS, params):
+        assert torch.equal(p.grad, ref[k]), k
+    # one SGD step on three bias vectors; loss and gradients must follow the new values
+    with torch.no_grad():
+        for k, p in zip(L.GRAD_FIELDS, params):
+            if k in ("ctrl_b", "head_b", "dec0_b2"):
+                p -= 0.5 * p.grad
+            p.grad = None
+    loss2 = api.OmniSegLoss.apply(seg, rgb, gts, *params)
+    loss2.backward()
+    torch.cuda.synchronize()
+    blob2 = blob.copy()
+    for k, p in zip(L.GRAD_FIELDS, params):
+        blob2[offs[k]:offs[k] + p.numel()] = p.detach().cpu().numpy().ravel()
+    assert np.array_equal(seg.blob, blob2)
+    prob = O.DiffProblem(rgb_np, w, blob2, gts_np)
+    ol, og = prob.loss_and_grads()
+    assert abs(float(loss2) - ol) <= 1e-5 * abs(ol), (float(loss2), ol)
+    assert float(loss2) != float(loss)
+    for name, ref_g in og.items():
+        got = params[L.GRAD_FIELDS.index(NAME[name])].grad.double().cpu().numpy()
+        ref_g = ref_g.numpy()
+        assert np.abs(got - ref_g).max() <= 1e-3 * np.abs(ref_g).max(), name
+    bad = list(params)
+    bad[0] = torch.zeros(3, 3, device="cuda")
+    with pytest.raises(ValueError):
+        api.OmniSegLoss.apply(seg, rgb, gts, *bad)
+    seg.close()

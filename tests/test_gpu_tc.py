@@ -20,6 +20,12 @@ from oracle import omniseg_oracle as O
 pytestmark = pytest.mark.gpu
 
 GOLDEN_MASK = os.path.join(os.path.dirname(__file__), "golden", "needle_tissue_mask.npz")
+GOLDEN_CROP = os.path.join(os.path.dirname(__file__), "golden", "needle_crop.npz")
+
+# Precision bar of the BF16 (and FP16) path against the FP64 oracle: pixel label
+# agreement and per-class Dice.  FP32 path: |dL| <= 1e-4, labels differ only
+# where the oracle's |L| < 1e-3.
+AGREE_MIN, DICE_MIN = 0.999, 0.995
 
 
 @pytest.fixture(scope="module")
@@ -99,9 +105,14 @@ def _agree_dice(a, b):
 
 def test_bf16_whole_path_window_against_oracle(api):
     """The needle network (base 32, 5 levels, 3 scales, 6 heads) with 256 px
-    tiles at stride 128 on a 2048 x 2048 slide with tissue filtering: BF16
-    labels against the oracle on a window, and against the FP32 path (which
-    matches the oracle within 1e-4) on the whole slide."""
+    tiles at stride 128 on a 2048 x 2048 slide with tissue filtering, against
+    the oracle on a window at every scale: coverage exact; BF16 logit error
+    within what BF16 rounding of every layer's operands gives on these
+    networks (a CPU emulation of it on needle tiles: p99 |dL| 0.06, max 0.32;
+    bound here p99 <= 0.1, max <= 0.5) and labels equal wherever the oracle's
+    |L| exceeds the largest error; FP32 within 1e-4.  (The class thresholds are calibrated for 512-px tiles, so
+    this smaller network's label rates are not the precision bar; the
+    benchmark-configuration crop test is.)"""
     from paper_2305_14566_gb300 import _lib as L
     w = synth.NEEDLE.with_(H=2048, W=2048, P=256, S=128, median_k=5, max_batch=16)
     spec = synth.make_spec(2048, 2048, 41, 0.5, "cores", 3)
@@ -113,84 +124,121 @@ def test_bf16_whole_path_window_against_oracle(api):
     seg32 = api.Segmenter(w, blob, precision=L.FP32)
     o32 = seg32.segment(rgb, logits=True)
     torch.cuda.synchronize()
-    for c in range(w.n_classes):
-        ag, dc, pos = _agree_dice(out["labels"][c].cpu().numpy(), o32["labels"][c].cpu().numpy())
-        d = (out["logits"][c] - o32["logits"][c]).abs()
-        print("slide class %d agree %.5f dice %.5f positives %d max|dL| %.3e" % (c, ag, dc, pos, float(d.max())))
-        assert ag >= 0.999
-        if pos >= 2000:
-            # measured 0.978 on a 0.3%-positive class: BF16 moves thin boundaries
-            assert dc >= 0.97
     orc = O.segment(rgb_np, w, blob, window=(640, 768, 512, 512), batch=8)
-    rows = []
     for c, s in enumerate(w.class_scale):
         wy, wx, wh, ww = orc["window"][s]
-        gl = out["labels"][c][wy:wy + wh, wx:wx + ww].cpu().numpy()
         gL = out["logits"][c][wy:wy + wh, wx:wx + ww].double().cpu().numpy()
-        rows.append((c,) + _stats(gl, gL, orc["labels"][c], orc["L"][c]))
+        fL = o32["logits"][c][wy:wy + wh, wx:wx + ww].double().cpu().numpy()
+        gl = out["labels"][c][wy:wy + wh, wx:wx + ww].cpu().numpy()
+        d = np.abs(gL - orc["L"][c])
+        p99 = float(np.percentile(d, 99))
+        decided = np.abs(orc["L"][c]) > d.max()
+        print("window class %d bf16 max|dL| %.3e p99 %.3e fp32 max|dL| %.2e labels decided %.4f"
+              % (c, d.max(), p99, np.abs(fL - orc["L"][c]).max(), decided.mean()))
+        assert np.abs(fL - orc["L"][c]).max() <= 1e-4
+        assert p99 <= 0.1 and d.max() <= 0.5, (c, p99, float(d.max()))
+        assert np.array_equal(gl[decided], orc["labels"][c][decided]), c
         cov = out["coverage"][s][wy:wy + wh, wx:wx + ww].cpu().numpy().astype(np.int64)
         assert np.array_equal(cov, orc["cov"][c])
-    for row in rows:
-        print("window class %d agree %.5f dice %.5f max|dL| %.3e p99|dL| %.3e positives %d" % row)
-    assert np.mean([r[1] for r in rows]) >= 0.999, rows
-    for r in rows:
-        if r[5] >= 2000:
-            assert r[2] >= 0.97, r
     seg.close()
     seg32.close()
 
 
-def test_needle_full_slide_bf16_against_fp32_and_oracle(api):
-    """The benchmark workload itself (16384 x 49152, 512 px tiles, 6 heads):
-    BF16 labels against the FP32 path over the whole slide, and against the
-    oracle on a 256 x 256 window inside a tissue core at every scale."""
+def test_needle_full_slide_bf16_against_fp32(api):
+    """The benchmark workload itself (16384 x 49152, 512 px tiles, 6 heads),
+    autotuned as benched: BF16 labels against the FP32 path (which the crop
+    test ties to the oracle) over the whole slide, agreement >= 0.999 and
+    Dice >= 0.995 for every class, each with positives; the tissue mask is the
+    oracle's."""
     from paper_2305_14566_gb300 import _lib as L
     w = synth.NEEDLE
     spec = synth.spec_for(w)
     rgb = api.synth_slide(spec)
     blob = synth.gen_weights(w)
     seg = api.Segmenter(w, blob, precision=L.BF16)
-    out = seg.segment(rgb, logits=True)
+    seg.set_autotune(True)
+    out = seg.segment(rgb)
     torch.cuda.synchronize()
     seg32 = api.Segmenter(w, blob, precision=L.FP32)
-    o32 = seg32.segment(rgb, logits=True)
+    o32 = seg32.segment(rgb)
     torch.cuda.synchronize()
     seg32.close()
-    worst = 1.0
     for c in range(w.n_classes):
         ag, dc, pos = _agree_dice(out["labels"][c].cpu().numpy(), o32["labels"][c].cpu().numpy())
         print("needle class %d agree %.6f dice %.5f positives %d" % (c, ag, dc, pos))
-        worst = min(worst, ag)
-        # measured agreement / Dice: class 0 (66M positives) 0.99864 / 0.9918,
-        # class 1 (25M) 0.99917 / 0.9865, class 3 (2.1M) 0.99741 / 0.970.  The
-        # 0.999 / 0.995 targets are not met with BF16: the random-init logit field
-        # is flat, and BF16 rounding of the activations moves its zero crossings
-        # (FP16 operands meet them, see the next test)
-        assert ag >= 0.997
-        # Dice is only meaningful on classes with a sizeable positive area
-        # (class 2 has 59K positives in 50M pixels: agreement 0.99981, Dice 0.924)
-        if pos >= 0.01 * out["labels"][c].numel():
-            assert dc >= 0.965
+        assert pos > 0.001 * out["labels"][c].numel(), (c, pos)
+        assert ag >= AGREE_MIN and dc >= DICE_MIN, (c, ag, dc)
     # the oracle's tissue mask of this slide (written by tests/golden/make_needle_tiles.py)
     gold = np.load(GOLDEN_MASK)
     mask = np.unpackbits(gold["bits"])[:int(np.prod(gold["shape"]))].reshape(gold["shape"]).astype(bool)
     t = seg.tile_slide(rgb)
     assert np.array_equal(t["tissue"].cpu().numpy().astype(bool), mask)
-    # a 256 x 256 window at 40x inside the first tissue core (4 covering tiles)
-    e = spec.ellipses[0]
-    win = ((e.cy // 256) * 256, (e.cx // 256) * 256, 256, 256)
-    orc = O.segment_window_regions(lambda y, x, h, wd: synth.gen_window(spec, y, x, h, wd), mask,
-                                   w, blob, win, w.H, w.W, scales=(0,))
-    wy, wx, wh, ww = orc["window"][0]
-    for c in (0, 1):
-        o = orc["L"][c]
-        g32 = o32["logits"][c][wy:wy + wh, wx:wx + ww].double().cpu().numpy()
-        assert np.abs(g32 - o).max() <= 1e-4
-        gb = out["labels"][c][wy:wy + wh, wx:wx + ww].cpu().numpy()
-        ag = float((gb == orc["labels"][c]).mean())
-        print("needle window class %d fp32 max|dL| %.2e bf16 agree %.5f" % (c, float(np.abs(g32 - o).max()), ag))
-        assert ag >= 0.999
     seg.close()
+
+
+def _load_crop():
+    d = np.load(GOLDEN_CROP)
+    out = {"origin": tuple(int(v) for v in d["origin"]), "offsets": d["head_offsets"], "cls": {}}
+    c = 0
+    while f"labels{c}" in d:
+        shp = tuple(int(v) for v in d[f"shape{c}"])
+        n = shp[0] * shp[1]
+        out["cls"][c] = dict(win=tuple(int(v) for v in d[f"win{c}"]), shape=shp,
+                             labels=np.unpackbits(d[f"labels{c}"])[:n].reshape(shp),
+                             nearzero=np.unpackbits(d[f"nearzero{c}"])[:n].reshape(shp).astype(bool),
+                             sub=int(d[f"sub{c}"][0]), L=d[f"L{c}"].astype(np.float64))
+        c += 1
+    return out
+
+
+def test_needle_crop_all_scales_against_oracle(api):
+    """The benchmark configuration (16384 x 49152 needle slide, 512-px tiles at
+    stride 256, base 32 x 5 levels, 6 heads) against the FP64 oracle on its
+    2048 x 2048 crop at 40x with the matching 512 x 512 at 10x and 256 x 256 at
+    5x (tests/golden/make_needle_crop.py).  FP32: logits within 1e-4 on the
+    stored subsample, labels equal except where the oracle's |L| < 1e-3.
+    BF16 and FP16 (the benched tensor-core path with its autotuned kernels,
+    fused pooling and fused heads): label agreement >= 0.999 and Dice >= 0.995
+    for every class, each class with positives in the crop."""
+    from paper_2305_14566_gb300 import _lib as L
+    gold = _load_crop()
+    w = synth.NEEDLE
+    assert np.allclose(gold["offsets"], w.head_offsets), "crop written with other head offsets"
+    spec = synth.spec_for(w)
+    rgb = api.synth_slide(spec)
+    blob = synth.gen_weights(w)
+    outs = {}
+    for name, prec in (("fp32", L.FP32), ("bf16", L.BF16), ("fp16", L.FP16)):
+        seg = api.Segmenter(w, blob, precision=prec)
+        if prec != L.FP32:
+            seg.set_autotune(True)
+        o = seg.segment(rgb, logits=(prec == L.FP32))
+        torch.cuda.synchronize()
+        outs[name] = {k: {c: t[ _win_slice(gold, c) ].cpu().numpy() for c, t in d.items()}
+                      for k, d in o.items() if k in ("labels", "logits")}
+        seg.close()
+        del o
+        torch.cuda.empty_cache()
+    for c, g in gold["cls"].items():
+        pos = int(g["labels"].sum())
+        assert pos > 0.01 * g["labels"].size, (c, pos)          # every class informative here
+        l32 = outs["fp32"]["labels"][c]
+        L32 = outs["fp32"]["logits"][c].astype(np.float64)
+        dL = np.abs(L32[::g["sub"], ::g["sub"]] - g["L"])
+        diff = l32 != g["labels"]
+        print("crop class %d fp32 max|dL| %.2e label diffs %d (all near zero: %s)"
+              % (c, dL.max(), int(diff.sum()), bool(np.all(g["nearzero"][diff]))))
+        assert dL.max() <= 1e-4, (c, float(dL.max()))
+        assert np.all(g["nearzero"][diff]), (c, int((diff & ~g["nearzero"]).sum()))
+        for name in ("bf16", "fp16"):
+            ag, dc, _ = _agree_dice(outs[name]["labels"][c], g["labels"])
+            print("crop class %d %s agree %.6f dice %.6f positives %d" % (c, name, ag, dc, pos))
+            assert ag >= AGREE_MIN and dc >= DICE_MIN, (c, name, ag, dc)
+
+
+def _win_slice(gold, c):
+    wy, wx, wh, ww = gold["cls"][c]["win"]
+    return (slice(wy, wy + wh), slice(wx, wx + ww))
 
 
 def test_graph_replay_is_bit_identical_and_autotune_agrees(api):
@@ -233,10 +281,47 @@ def test_graph_replay_is_bit_identical_and_autotune_agrees(api):
     tuned.close()
 
 
+def test_graph_is_dropped_when_weights_are_reloaded(api):
+    """A captured launch chain holds the weight pointers of the state it was
+    captured in: reloading weights (as a fine-tuning loop does) must make the
+    next call run with the new weights, identical to an eager context that
+    loaded them directly."""
+    from paper_2305_14566_gb300 import _lib as L
+    w = synth.NEEDLE.with_(H=2048, W=2048, P=256, S=128, median_k=5, max_batch=16)
+    spec = synth.make_spec(2048, 2048, 47, 0.5, "cores", 3)
+    rgb = api.synth_slide(spec)
+    blob_a = synth.gen_weights(w)
+    blob_b = synth.gen_weights(w, seed=w.weights_seed + 101)
+    seg = api.Segmenter(w, blob_a, precision=L.BF16)
+    seg.set_graphs(True)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    out = None
+    for _ in range(3):               # eager, capture + launch, replay
+        with torch.cuda.stream(stream):
+            out = seg.segment(rgb, logits=True, out=out)
+    torch.cuda.synchronize()
+    first = {c: t.clone() for c, t in out["logits"].items()}
+    seg.load_weights(blob_b)
+    for _ in range(3):
+        with torch.cuda.stream(stream):
+            out = seg.segment(rgb, logits=True, out=out)
+        torch.cuda.synchronize()
+        ref_b = api.Segmenter(w, blob_b, precision=L.BF16)
+        eager = ref_b.segment(rgb, logits=True)
+        torch.cuda.synchronize()
+        ref_b.close()
+        for c in eager["logits"]:
+            assert torch.equal(out["logits"][c], eager["logits"][c]), c
+            assert torch.equal(out["labels"][c], eager["labels"][c]), c
+    assert any(not torch.equal(first[c], out["logits"][c]) for c in first)
+    seg.close()
+
+
 def test_needle_full_slide_fp16_label_agreement(api):
     """FP16 operands (same tensor-core rate, 3 more mantissa bits than BF16) on
-    the benchmark slide: label agreement >= 0.999 on every class against the
-    FP32 path, and Dice on classes with a sizeable positive area."""
+    the benchmark slide: agreement >= 0.999 and Dice >= 0.995 for every class
+    against the FP32 path."""
     from paper_2305_14566_gb300 import _lib as L
     w = synth.NEEDLE
     spec = synth.spec_for(w)
@@ -250,17 +335,10 @@ def test_needle_full_slide_fp16_label_agreement(api):
     o32 = seg32.segment(rgb)
     torch.cuda.synchronize()
     seg32.close()
-    rows = []
     for c in range(w.n_classes):
         ag, dc, pos = _agree_dice(out["labels"][c].cpu().numpy(), o32["labels"][c].cpu().numpy())
         print("fp16 needle class %d agree %.6f dice %.5f positives %d" % (c, ag, dc, pos))
-        rows.append((c, ag, dc, pos, out["labels"][c].numel()))
-    for c, ag, dc, pos, n in rows:
-        assert ag >= 0.999, (c, ag)
-        # measured Dice on the classes with >= 1% positive area: 0.9972 (class 0,
-        # 66M positives), 0.9943 (class 1, 25M), 0.9897 (class 3, 2.1M at 10x)
-        if pos >= 0.01 * n:
-            assert dc >= 0.985, (c, dc)
+        assert ag >= AGREE_MIN and dc >= DICE_MIN, (c, ag, dc)
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
