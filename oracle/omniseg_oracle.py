@@ -450,6 +450,16 @@ def stitch(patch_logits: Dict[Tuple[int, int], np.ndarray], hs: int, ws: int, P:
     return L, cov, votes
 
 
+def vote_margin(patch_logits: Dict[Tuple[int, int], np.ndarray], hs: int, ws: int, P: int) -> np.ndarray:
+    """Smallest |l_p(x)| over the processed tiles p covering x (inf where no
+    tile covers x): a vote can change only if some covering tile's logit is
+    within the arithmetic error of zero."""
+    m = np.full((hs, ws), np.inf)
+    for (y, x), lp in patch_logits.items():
+        m[y:y + P, x:x + P] = np.minimum(m[y:y + P, x:x + P], np.abs(lp))
+    return m
+
+
 def tissue_at_scale(mask: np.ndarray, f: int, hs: int, ws: int) -> np.ndarray:
     """Thumbnail mask sampled at scale-f pixel (y, x) -> thumb (y f / 32, x f / 32)."""
     ys = (np.arange(hs) * f) // THUMB
@@ -548,7 +558,7 @@ def segment(rgb: np.ndarray, work, blob: np.ndarray, window=None, batch: int = 4
         prep = prepare(rgb, work)
     p = weights_f64(work, blob)
     Hp, Wp, P = prep["Hp"], prep["Wp"], work.P
-    out = {"prep": prep, "L": {}, "cov": {}, "votes": {}, "labels": {}, "window": {}}
+    out = {"prep": prep, "L": {}, "cov": {}, "votes": {}, "labels": {}, "window": {}, "margin": {}}
     for s, f in enumerate(work.factors):
         hs, ws = Hp // f, Wp // f
         if window is None:
@@ -575,6 +585,7 @@ def segment(rgb: np.ndarray, work, blob: np.ndarray, window=None, batch: int = 4
             out["L"][c] = L[sl]
             out["cov"][c] = cov[sl]
             out["votes"][c] = votes[sl]
+            out["margin"][c] = vote_margin(per_class[c], hs, ws, P)[sl]
             out["labels"][c] = labels(L[sl], cov[sl], votes[sl], work.stitch_mode,
                                       None if tis is None else tis[sl])
         out["window"][s] = (wy0, wx0, wh, ww)
@@ -714,6 +725,37 @@ class DiffProblem:
         for c in range(work.n_classes):
             L = torch.where(cov[c] > 0, acc[c] / torch.clamp(cov[c], min=1.0),
                             torch.zeros_like(acc[c]))
+            H, W = self.gts[c].shape
+            total = total + dice_bce(L[:H, :W], self.gts[c])
+        return total / work.n_classes
+
+    def loss_heads_only(self, q: Dict[str, torch.Tensor]) -> torch.Tensor:
+        """loss(q) for q holding only controller / pre-head parameters: the last
+        decoder block's output does not depend on them, so it is computed once
+        (with the blob's values) and reused; the value equals loss(q)."""
+        assert all(k.startswith("ctrl.") or k.startswith("head.") for k in q)
+        if not hasattr(self, "_y0"):
+            with torch.no_grad():
+                self._y0 = [res_block(cat0, self.p, "dec0") for (_, _, cat0, _) in self.cache]
+        work = self.work
+        p = dict(self.p)
+        p.update(q)
+        Hp, Wp, P = self.prep["Hp"], self.prep["Wp"], work.P
+        acc, cov = {}, {}
+        for c, s in enumerate(work.class_scale):
+            f = work.factors[s]
+            acc[c] = torch.zeros((Hp // f, Wp // f), dtype=F64)
+            cov[c] = torch.zeros((Hp // f, Wp // f), dtype=F64)
+        for (s, chunk, _, g), y0 in zip(self.cache, self._y0):
+            h0 = prehead(y0, p)
+            for c in [c for c, cs in enumerate(work.class_scale) if cs == s]:
+                lg = dynamic_head(h0, controller(g, c, s, p, work.n_classes, work.n_scales))
+                for bi, (y, x) in enumerate(chunk):
+                    acc[c][y:y + P, x:x + P] += lg[bi]
+                    cov[c][y:y + P, x:x + P] += 1.0
+        total = torch.zeros((), dtype=F64)
+        for c in range(work.n_classes):
+            L = torch.where(cov[c] > 0, acc[c] / torch.clamp(cov[c], min=1.0), torch.zeros_like(acc[c]))
             H, W = self.gts[c].shape
             total = total + dice_bce(L[:H, :W], self.gts[c])
         return total / work.n_classes

@@ -52,6 +52,7 @@ class Workload:
     pad_lead: int = 0              # the paper's 4096 border; 0 for these workloads
     max_batch: int = 32
     head_offset: float = 0.0       # controller bias of the head's final bias b3 (weights init)
+    head_offsets: Tuple[float, ...] = ()   # per-class addition to b3 through the class one-hot
     strides: Tuple[int, ...] = ()  # per-scale tile stride; () or 0 = S (Sec. 3.2: 256, 64, 64)
     stitch_window: int = WINDOW_FLAT
 
@@ -84,10 +85,17 @@ TINY = Workload(
     factors=(1,), P=128, S=64, base=8, levels=3, class_scale=(0, 0),
     weights_seed=10, tissue_filter=False, tissue_and=False, max_batch=49)
 
+# Per-class head calibration of the needle network (weights seed 11): class c's
+# threshold sits at the valley of its raw in-tissue response on calibration
+# tiles of the oracle, written by tests/golden/make_head_offsets.py into
+# tests/golden/head_offsets.json (a CPU test keeps the two equal).
+NEEDLE_HEAD_OFFSETS = (3.4945, 4.9902, 5.6952, 3.3357, 5.0212, 4.3994)
+
 NEEDLE = Workload(
     name="needle", H=16384, W=49152, seed=1, tissue=0.40, layout="cores", n_blobs=4,
     factors=(1, 4, 8), P=512, S=256, base=32, levels=5,
-    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=32, head_offset=3.3)
+    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=32,
+    head_offsets=NEEDLE_HEAD_OFFSETS)
 
 DIFF = Workload(
     name="diff", H=2048, W=2048, seed=7, tissue=0.40, layout="blobs", n_blobs=6,
@@ -98,7 +106,8 @@ DIFF = Workload(
 LARGE = Workload(
     name="large", H=32768, W=98304, seed=200, tissue=0.35, layout="cores", n_blobs=4,
     factors=(1, 4, 8), P=1024, S=512, base=32, levels=5,
-    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=8, head_offset=3.3)
+    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=8,
+    head_offsets=NEEDLE_HEAD_OFFSETS)
 
 
 # The paper's own overlap setting (Sec. 3.2): 40x tiles strided by 256 (two

@@ -20,11 +20,16 @@ bias ~ U[-0.05, 0.05]; controller He-normal with zero bias.  The second norm
 scale and the projection of every residual block are multiplied by 1/sqrt(2)
 so that the two branches of each residual sum add up to the variance of one
 (the residual-gain reading), which keeps activations and logits O(1) through
-the 2L-1 blocks.  Random weights make the head's output nearly constant within
-a tile and negative everywhere; the controller bias of theta[152] (the head's
-final bias b3) is therefore set to the workload's ``head_offset`` so that the
-decision threshold falls between tissue-interior and tissue-edge responses
-(3.3 for the base-32 workloads, 0 for the tiny one).
+the 2L-1 blocks.
+
+Head calibration.  Random weights give the head's output no trained decision
+threshold: it is negative everywhere.  The controller bias of theta[152] (the
+head's final bias b3) is the workload's ``head_offset``, and
+``head_offsets[c]`` is added to the controller weight that carries class c's
+one-hot input into theta[152], so each class gets its own threshold.  The
+needle workloads use per-class offsets placed at the valley of each class's
+in-tissue response (tests/golden/make_head_offsets.py); the differentiation
+workload uses one offset of 3.3, the tiny one 0.
 """
 from __future__ import annotations
 
@@ -89,6 +94,12 @@ def gen_weights(work, seed: int | None = None) -> np.ndarray:
         else:  # ctrl.b
             t = np.zeros(shape)
             t[-1] = getattr(work, "head_offset", 0.0)
+        if name == "ctrl.w" and getattr(work, "head_offsets", ()):
+            # class c's one-hot input reaches theta[152] (the head's final
+            # bias b3) through column C_{L-1} + c: a per-class threshold
+            cb = work.widths[-1]
+            for c, off in enumerate(work.head_offsets):
+                t[-1, cb + c] += off
         parts.append(np.asarray(t, np.float32).ravel())
     return np.concatenate(parts).astype(np.float32)
 

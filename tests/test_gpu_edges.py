@@ -85,9 +85,9 @@ def test_slide_smaller_than_one_tile_fp32_against_oracle(api):
 
 def test_vote_stitch_mode_fp32_against_oracle(api):
     """Vote stitching (a pixel is positive when at least half of its covering
-    tiles say so): labels equal the oracle's except where one tile's vote
-    flipping would flip the label (2 votes - coverage in [-2, 1]), which the
-    1e-4 logit agreement allows only for tile logits within 1e-4 of 0."""
+    tiles say so): labels equal the oracle's except where a covering tile's
+    logit is within 1e-3 of zero (its vote may differ) and that one vote
+    decides the label (2 votes - coverage in [-2, 1])."""
     w = SMALL.with_(H=1024, W=1536, stitch_mode=synth.STITCH_VOTE)
     spec = synth.make_spec(1024, 1536, 33, 0.5, "cores", 3)
     rgb_np = synth.gen_slide(spec)
@@ -104,7 +104,7 @@ def test_vote_stitch_mode_fp32_against_oracle(api):
         m = 2 * orc["votes"][c] - orc["cov"][c]
         bad = gl != ol
         assert not (bad & ((m < -2) | (m > 1))).any(), c
-        assert bad.mean() < 1e-3, (c, float(bad.mean()))
+        assert not (bad & (orc["margin"][c] >= 1e-3)).any(), (c, int(bad.sum()))
         n_pos += int(ol.sum())
         g = out["logits"][c][wy:wy + wh, wx:wx + ww].double().cpu().numpy()
         assert np.abs(g - orc["L"][c]).max() <= LOGIT_TOL

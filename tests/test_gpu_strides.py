@@ -60,8 +60,9 @@ def test_tile_list_matches_oracle(api, slide):
 
 def test_vote_maps_fp32_against_oracle(api, slide):
     """Coverage equals the oracle's (up to 64 tiles at 10x), logits agree
-    within 1e-4 and labels equal the oracle's except where one tile's vote
-    flipping would flip the label (2 votes - coverage in [-2, 1])."""
+    within 1e-4 and labels equal the oracle's except where a covering tile's
+    logit is within 1e-3 of zero (its vote may differ) and that one vote
+    decides the label (2 votes - coverage in [-2, 1])."""
     blob = synth.gen_weights(SMALL)
     seg = api.Segmenter(SMALL, blob)
     out = seg.segment(torch.from_numpy(slide).cuda(), logits=True, coverage=True)
@@ -78,7 +79,7 @@ def test_vote_maps_fp32_against_oracle(api, slide):
         m = 2 * orc["votes"][c] - orc["cov"][c]
         bad = gl != orc["labels"][c]
         assert not (bad & ((m < -2) | (m > 1))).any(), c
-        assert bad.mean() < 1e-3, (c, float(bad.mean()))
+        assert not (bad & (orc["margin"][c] >= 1e-3)).any(), (c, int(bad.sum()))
     seg.close()
 
 

@@ -430,6 +430,75 @@ def test_labels_modes_and_argmax():
     assert a.tolist() == [[5, 0, 6]]
 
 
+def test_needle_head_offsets_are_the_calibrated_ones():
+    """The needle workloads' per-class head offsets are the values the oracle
+    calibration (tests/golden/make_head_offsets.py) wrote, and each class's
+    threshold left between 1% and 99% of the calibration tiles' tissue pixels
+    positive (every class informative)."""
+    g = json.load(open(os.path.join(os.path.dirname(GOLDEN), "head_offsets.json")))
+    assert tuple(synth.NEEDLE.head_offsets) == tuple(g["head_offsets"])
+    assert tuple(synth.LARGE.head_offsets) == tuple(g["head_offsets"])
+    for c, row in g["classes"].items():
+        assert 0.01 <= row["positive_fraction_in_tissue"] <= 0.99, (c, row)
+        assert abs(row["offset"] + row["threshold"]) < 1e-12
+
+
+def test_per_class_offsets_shift_only_their_class():
+    """A class's offset enters theta[152] (the head's final bias) through that
+    class's one-hot input only: with the GAP zeroed, the controller output of
+    class c differs from the zero-offset network's exactly by offset_c in
+    entry 152 and nowhere else."""
+    w = synth.small_variant(synth.NEEDLE, H=256, W=256, P=64, S=32, base=4, levels=3,
+                            head_offsets=(0.5, -1.25, 2.0, 0.0, 3.0, -0.75))
+    w0 = w.with_(head_offsets=())
+    p = O.weights_f64(w, synth.gen_weights(w))
+    p0 = O.weights_f64(w0, synth.gen_weights(w0))
+    g = torch.zeros((1, w.widths[-1]), dtype=F64)
+    for c, s in enumerate(w.class_scale):
+        d = O.controller(g, c, s, p, w.n_classes, w.n_scales) - O.controller(g, c, s, p0, w.n_classes, w.n_scales)
+        expect = torch.zeros_like(d)
+        expect[0, 152] = float(np.float32(w.head_offsets[c]) + p0["ctrl.w"][152, w.widths[-1] + c].float()) \
+            - float(p0["ctrl.w"][152, w.widths[-1] + c])
+        assert torch.allclose(d, expect, atol=1e-7), c
+
+
+def test_vote_margin_brute_force():
+    """The vote margin is, pixel by pixel, the smallest |logit| among the tiles
+    whose footprint contains the pixel (counted by scanning every tile)."""
+    r = rng(22)
+    P, hs, ws = 4, 9, 11
+    tiles = {(y, x): r.standard_normal((P, P)) for (y, x) in [(0, 0), (2, 2), (4, 6), (5, 7), (0, 6)]}
+    m = O.vote_margin(tiles, hs, ws, P)
+    for y in range(hs):
+        for x in range(ws):
+            vals = [abs(lp[y - ty, x - tx]) for (ty, tx), lp in tiles.items()
+                    if ty <= y < ty + P and tx <= x < tx + P]
+            assert m[y, x] == (min(vals) if vals else np.inf), (y, x)
+
+
+def test_tissue_at_scale_brute_force_footprint():
+    """A scale-f pixel (y, x) covers the 40x pixels [y f, (y + 1) f) x [x f, (x + 1) f);
+    for f dividing the 32-pixel thumbnail cell the whole footprint lies in one
+    cell, found here by scanning the cells, and the pixel takes that cell's
+    mask value.  The mask has distinct neighbouring cells so an off-by-one in
+    either axis changes the result."""
+    r = rng(21)
+    mask = r.random((7, 9)) < 0.5
+    mask[0, 0], mask[0, 1], mask[1, 0] = True, False, False
+    for f in (1, 2, 4, 8):
+        hs, ws = 7 * 32 // f, 9 * 32 // f
+        got = O.tissue_at_scale(mask, f, hs, ws)
+        assert got.shape == (hs, ws)
+        for y in range(hs):
+            cy = [cy for cy in range(7) if all(32 * cy <= yy < 32 * (cy + 1) for yy in range(y * f, (y + 1) * f))]
+            assert len(cy) == 1
+            for x in range(ws):
+                cx = [cx for cx in range(9)
+                      if all(32 * cx <= xx < 32 * (cx + 1) for xx in range(x * f, (x + 1) * f))]
+                assert len(cx) == 1
+                assert got[y, x] == mask[cy[0], cx[0]], (f, y, x)
+
+
 # ---------------------------------------------------------------- loss, gradient
 
 
@@ -477,6 +546,35 @@ def test_gradient_matches_central_differences():
         assert abs(an - fd) / scale < 1e-4, (name, idx, an, fd)
         checked += 1
     assert checked == 48
+
+
+def test_heads_only_loss_equals_full_loss():
+    """The head-only evaluation (last block output reused) gives the same loss
+    as the full sub-chain for controller / pre-head perturbations."""
+    w = synth.small_variant(synth.DIFF, H=256, W=256, P=64, S=32, base=4, levels=3, max_batch=16)
+    rgb = synth.gen_slide(synth.spec_for(w))
+    gts = synth.gen_gt_masks(w.H, w.W, w.factors, w.class_scale, seed=7)
+    prob = O.DiffProblem(rgb, w, synth.gen_weights(w), gts)
+    base = prob.params()
+    r = rng(9)
+    for name in ("ctrl.w", "ctrl.b", "head.w", "head.b"):
+        q = {name: base[name] + 1e-3 * torch.from_numpy(r.standard_normal(tuple(base[name].shape)))}
+        with torch.no_grad():
+            a, b = float(prob.loss(q)), float(prob.loss_heads_only(q))
+        assert abs(a - b) <= 1e-13 * max(1.0, abs(a)), (name, a, b)
+
+
+def test_diff_workload_fd_golden_matches_autograd():
+    """tests/golden/diff_fd.json (make_diff_fd.py): on the differentiation
+    workload itself, the oracle's autograd gradient equals FP64 central
+    differences at 64 seeded parameters, entry by entry."""
+    p = os.path.join(os.path.dirname(GOLDEN), "diff_fd.json")
+    g = json.load(open(p))
+    assert len(g["draws"]) == 64
+    assert len({d["name"] for d in g["draws"]}) == len(O.GRAD_PARAMS)
+    for d in g["draws"]:
+        floor = 1e-4 * d["tensor_max_abs_grad"]
+        assert abs(d["autograd"] - d["fd"]) <= 1e-4 * max(abs(d["fd"]), floor), d
 
 
 def test_window_from_regions_equals_whole_slide():
