@@ -141,7 +141,7 @@ def tag_name(t: int) -> str:
     if t < 200:
         return f"conv dec{(t - 100) // 10}.{t % 10 + 1}"
     if t == 401:
-        return "controller"
+        return "gap+controller"
     names = {2: "maxpool", 3: "upsample", 4: "gap", 5: "head", 6: "stitch", 7: "prep"}
     return names.get(t // 100, str(t))
 
@@ -193,40 +193,50 @@ def run_layer(args):
 
 def run_ragged(args, api, _lib, dev, prec):
     """Twelve synthetic slides (long side U[8192, 49152], aspect U[1, 4], tissue
-    U[0.2, 0.6]); one step segments all of them.  One context and one
-    workspace serve every slide (sized for the largest)."""
+    U[0.2, 0.6]); one step segments all of them in ONE omni_segment_slides
+    call: every slide is tiled, then the foreground tiles of all slides share
+    the network batches of each scale, and the whole post-tiling chain is one
+    captured CUDA graph.  Per-slide latency = completion of the slide's last
+    stitch band after the chain's start (events inside the graph)."""
     import torch
     works = synth.ragged_workloads()
     blob = synth.gen_weights(works[0])
     seg = api.Segmenter(works[0], blob, precision=prec)
     if prec != _lib.FP32 and not args.no_autotune:
         seg.set_autotune(True)
-    need = max(seg.query(w.H, w.W).workspace_bytes for w in works)
-    seg.workspace(need, dev)
     rgbs = [api.synth_slide(synth.spec_for(w), device=dev) for w in works]
-    outs = [seg.segment(r) for r in rgbs]
+    outs = seg.segment_many(rgbs)            # tunes every conv shape
     torch.cuda.synchronize()
-    for _ in range(max(0, args.warmup - 1)):
-        for r, o in zip(rgbs, outs):
-            seg.segment(r, out=o)
-    torch.cuda.synchronize()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(works) + 1)] for _ in range(args.steps)]
-    for k in range(args.steps):
-        ev[k][0].record()
-        for i, (r, o) in enumerate(zip(rgbs, outs)):
-            seg.segment(r, out=o)
-            ev[k][i + 1].record()
-    torch.cuda.synchronize()
-    per = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(len(works))] for k in range(args.steps)])
-    total_ms = float(per.sum(axis=1).mean())
+    seg.set_graphs(True)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        for _ in range(max(2, args.warmup)):  # the second call captures the graph
+            seg.segment_many(rgbs, outs=outs)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        per = []
+        with Clocks(0) as clk:
+            e0.record()
+            for _ in range(args.steps):
+                seg.segment_many(rgbs, outs=outs)
+                per.append(seg.slide_times(len(works)))
+            e1.record()
+            torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1) / args.steps
     mpx = sum(w.H * w.W for w in works) / 1e6
+    lat = np.mean(np.array([p for p in per if p]), axis=0) if any(per) else None
     print(json.dumps({"metric": "ragged 12-slide segmentation Mpx/s", "value": mpx / (total_ms / 1e3),
                       "unit": "Mpx/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": total_ms, "higher_is_better": True, "dtype": args.precision,
                       "data": "synthetic",
-                      "config": {"workload": "12 ragged needle-like slides, seeds 100-111",
+                      "config": {"workload": "12 ragged needle-like slides, seeds 100-111, one "
+                                             "omni_segment_slides call per step (tiles of all slides "
+                                             "share batches; one CUDA graph after tiling)",
                                  "slides": [[w.H, w.W, round(w.tissue, 3)] for w in works]},
-                      "per_slide_ms": [round(float(v), 2) for v in per.mean(axis=0)]}))
+                      "per_slide_done_ms": None if lat is None else [round(float(v), 2) for v in lat],
+                      "clocks": clk.summary()}))
     seg.close()
 
 
@@ -301,57 +311,95 @@ def run_large(args, api, _lib, dev, prec):
     print(json.dumps(line))
 
 
-def cpu_baseline(max_tiles: int = 4):
-    """The FP64 oracle timed on a bounded sample: the first foreground 40x tiles
-    of the needle slide (generated on the CPU), through U-Net, heads and the
-    stitch of those tiles; scaled to the slide by the tile fraction."""
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _crop_origin():
+    """40x origin of the needle crop the oracle tests use (written by
+    tests/golden/make_needle_crop.py), else a fixed tissue-rich one."""
+    p = os.path.join(ROOT, "tests", "golden", "needle_crop.npz")
+    if os.path.exists(p):
+        d = np.load(p)
+        return int(d["origin"][0]), int(d["origin"][1])
+    return 8192, 24576
+
+
+def oracle_sample(per_scale: int = 1):
+    """The FP64 oracle on a bounded sample of the needle workload: ``per_scale``
+    foreground tiles of every scale taken from the 2048 x 2048 crop (U-Net,
+    GAP, controller and the scale's two heads, then the stitch of those
+    tiles).  Returns (seconds per tile per scale, the sample's description)."""
     import torch
     from oracle import omniseg_oracle as O
+    torch.set_num_threads(_host_cores())
     spec = synth.spec_for(WORK)
     blob = synth.gen_weights(WORK)
     p = O.weights_f64(WORK, blob)
-    # foreground tiles come from the slide's tissue; take tiles along the first core
-    e = spec.ellipses[0]
-    y0 = max(0, (e.cy // WORK.S) * WORK.S - WORK.S)
-    x0 = (e.cx // WORK.S) * WORK.S
-    h = WORK.P + WORK.S
-    w = WORK.P + WORK.S * (max_tiles - 1)
-    img = synth.gen_window(spec, y0, x0, h, w)
-    tiles = [(0, x) for x in range(0, w - WORK.P + 1, WORK.S)][:max_tiles]
-    t0 = time.perf_counter()
-    per = {}
-    for (y, x) in tiles:
-        lg, _ = O.patch_forward(img[None, y:y + WORK.P, x:x + WORK.P], p, WORK, 0)
-        per[(y, x)] = lg[0, 0].numpy()
-    O.stitch(per, h, w, WORK.P)
-    dt = time.perf_counter() - t0
-    # foreground tiles of the slide, as the oracle counts them (tests/golden/make_needle_tiles.py)
+    y0, x0 = _crop_origin()
+    per = []
+    for s, f in enumerate(WORK.factors):
+        P, S = WORK.P, WORK.stride(s)
+        span = P * f
+        # tiles whose 40x footprint starts inside the crop, on the scale's grid
+        ty = (y0 // (S * f)) * S * f
+        tiles = [(ty // f, (x0 // (S * f)) * S * f // f + k * S) for k in range(per_scale)]
+        t0 = time.perf_counter()
+        lg = {}
+        for (y, x) in tiles:
+            img = synth.gen_window(spec, y * f, x * f, span, span)
+            g = f
+            while g > 1:
+                img = O.half(img)
+                g //= 2
+            out, _ = O.patch_forward(img[None], p, WORK, s)
+            lg[(0, x - tiles[0][1])] = out[0, 0].numpy()
+        O.stitch(lg, P, P + S * (per_scale - 1), P)
+        per.append((time.perf_counter() - t0) / len(tiles))
+    return per, (f"{per_scale} tile(s) of each scale (40x, 10x, 5x) from the 2048x2048 needle crop at "
+                 f"{y0},{x0}: FP64 U-Net, GAP, controller, the scale's two heads and their stitch")
+
+
+def oracle_slide_rate(per_tile_s):
+    """Mpx/s the oracle would reach on the whole needle slide: the measured time
+    per tile of each scale times the slide's foreground tiles of that scale
+    (the oracle's own counts, tests/golden/needle_tiles.json)."""
     gold = os.path.join(ROOT, "tests", "golden", "needle_tiles.json")
-    total_tiles = json.load(open(gold))["tiles_total"] if os.path.exists(gold) else 12899 * 0.5
-    mpx = WORK.H * WORK.W / 1e6 * len(tiles) / total_tiles
-    return {"value": mpx / dt, "unit": "Mpx/s", "cores": torch.get_num_threads(),
-            "kind": "oracle",
-            "sample": f"{len(tiles)} foreground 512x512 tiles of the 40x scale (FP64 U-Net, head, "
-                      f"stitch) in {dt:.1f} s, scaled to the slide as {len(tiles)}/{total_tiles:.0f} "
-                      f"of its tiles"}
+    counts = json.load(open(gold))["tiles_per_scale"]
+    secs = sum(t * n for t, n in zip(per_tile_s, counts))
+    return WORK.H * WORK.W / 1e6 / secs, counts
+
+
+def cpu_baseline():
+    per, sample = oracle_sample()
+    v, counts = oracle_slide_rate(per)
+    return {"value": v, "unit": "Mpx/s", "cores": _host_cores(), "kind": "oracle",
+            "sample": sample + "; seconds per tile " + ", ".join(f"{t:.2f}" for t in per) +
+                      f", scaled by the slide's {'/'.join(str(n) for n in counts)} foreground tiles"}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores.  Each step times
+    one tile of every scale of the needle crop and converts it to the slide
+    rate; W untimed steps, then K timed ones; the value is their median."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cb = cpu_baseline()
-    steps = []
     for _ in range(args.warmup):
-        pass
-    for _ in range(max(1, min(args.steps, 2))):
-        steps.append(cpu_baseline(max_tiles=2)["value"])
-    v = float(np.median(steps + [cb["value"]]))
+        oracle_sample()
+    vals, sample = [], ""
+    for _ in range(args.steps):
+        per, sample = oracle_sample()
+        vals.append(oracle_slide_rate(per)[0])
+    v = float(np.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpx/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"],
+            "cpu_baseline": {"kind": "oracle", "cores": _host_cores(), "sample": sample,
                              "value": v, "unit": "Mpx/s"},
             "e2e": {"value": v, "unit": "Mpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -365,8 +413,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true",
+                    help="skip the step of the plain FP32 path that the line reports as fp32_plain")
     ap.add_argument("--compare-fp32", action="store_true",
-                    help="also time one step of the plain FP32 path")
+                    help="--large: also segment the first slide with the FP32 path and compare labels")
     ap.add_argument("--ragged", action="store_true",
                     help="the 12-slide ragged workload: per-slide latency and aggregate Mpx/s")
     ap.add_argument("--no-autotune", action="store_true")
@@ -545,16 +595,29 @@ def main():
            "d2h_bytes_per_step": int(sum(t.numel() for t in labs.values()))}
     del rgb_h, labs
 
+    tuned_rows = [list(t) for t in seg.tuned()]
     fp32 = None
-    if args.compare_fp32 and prec != _lib.FP32:
+    if not args.no_fp32 and prec != _lib.FP32 and world == 1:
+        # the plain FP32 path (FFMA convs, no tensor cores) on the same slide:
+        # one untimed step, one step timed with events on the launching stream
+        seg.close()
+        seg._ws = None
+        torch.cuda.empty_cache()
         seg32 = api.Segmenter(work, blob, precision=_lib.FP32)
         o32 = seg32.segment(rgb)
         torch.cuda.synchronize()
-        a = time.perf_counter()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
         seg32.segment(rgb, out=o32)
+        f1.record()
         torch.cuda.synchronize()
-        fp32 = {"value": mpx / (time.perf_counter() - a), "unit": "Mpx/s", "steps": 1}
+        ms32 = f0.elapsed_time(f1)
+        fp32 = {"value": mpx / (ms32 / 1e3), "unit": "Mpx/s", "steps": 1, "ms_per_step": ms32,
+                "speedup_of_value": value / (mpx / (ms32 / 1e3)),
+                "note": "plain FP32 path (FFMA implicit GEMM on the CUDA cores), same slide"}
         seg32.close()
+        del o32
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world,
@@ -567,7 +630,7 @@ def main():
                            "tiles_per_step": tiles_step},
                 "roofline": roof, "stitch": stitch, "stain": stain, "e2e": e2e, "gpu_launches": int(launches),
                 "breakdown": breakdown, "graph_replay": graph,
-                "autotuned": [list(t) for t in seg.tuned()],
+                "autotuned": tuned_rows,
                 "clocks": clocks}
         if fp32 is not None:
             line["fp32_plain"] = fp32

@@ -62,8 +62,7 @@ struct TCParams {
   const float* gamma;
   const float* beta;
   const float* wp_rgb;               // [3][cout] for RES_RGB
-  const uint8_t* canvas;
-  long long canvas_stride;
+  CanvasTab cv;                      // RES_RGB / first layer: canvas of tile b = cv.ptr[tiles3[3 b]]
   const int32_t* tiles3;
   __nv_bfloat16* y;                  // null: output not stored (fused head)
   int y_cs, y_co;
@@ -204,27 +203,46 @@ __device__ __forceinline__ float norm_u8(uint8_t u) { return 2.0f * (float)u / 2
 
 // Dynamic head of one class on the pre-head feature h0 (already through its
 // ReLU): logit = W3 ReLU(W2 ReLU(W1 h0 + b1) + b2) + b3, with theta laid out
-// as W1 (8x8, out-major), W2 (8x8), W3 (8), b1 (8), b2 (8), b3 (1).
+// as W1 (8x8, out-major), W2 (8x8), W3 (8), b1 (8), b2 (8), b3 (1).  theta is
+// a 16-byte aligned shared-memory row (all lanes of a warp read the same
+// tile's row: broadcast 16-byte loads, eight weights per two loads).
+constexpr int kThetaPad = 160;   // theta row stride in the fused heads' shared copies
 __device__ __forceinline__ float dyn_head(const float* th, const float h0[8]) {
+  const float4* t4 = reinterpret_cast<const float4*>(th);
   float h1[8], h2[8];
+  const float4 b1a = t4[34], b1b = t4[35], b2a = t4[36], b2b = t4[37];
+  const float b1[8] = {b1a.x, b1a.y, b1a.z, b1a.w, b1b.x, b1b.y, b1b.z, b1b.w};
+  const float b2[8] = {b2a.x, b2a.y, b2a.z, b2a.w, b2b.x, b2b.y, b2b.z, b2b.w};
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
-    float s = th[136 + o];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) s = fmaf(th[o * 8 + c], h0[c], s);
+    const float4 wa = t4[2 * o], wb = t4[2 * o + 1];
+    float s = b1[o];
+    s = fmaf(wa.x, h0[0], s); s = fmaf(wa.y, h0[1], s); s = fmaf(wa.z, h0[2], s); s = fmaf(wa.w, h0[3], s);
+    s = fmaf(wb.x, h0[4], s); s = fmaf(wb.y, h0[5], s); s = fmaf(wb.z, h0[6], s); s = fmaf(wb.w, h0[7], s);
     h1[o] = fmaxf(s, 0.f);
   }
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
-    float s = th[144 + o];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) s = fmaf(th[64 + o * 8 + c], h1[c], s);
+    const float4 wa = t4[16 + 2 * o], wb = t4[16 + 2 * o + 1];
+    float s = b2[o];
+    s = fmaf(wa.x, h1[0], s); s = fmaf(wa.y, h1[1], s); s = fmaf(wa.z, h1[2], s); s = fmaf(wa.w, h1[3], s);
+    s = fmaf(wb.x, h1[4], s); s = fmaf(wb.y, h1[5], s); s = fmaf(wb.z, h1[6], s); s = fmaf(wb.w, h1[7], s);
     h2[o] = fmaxf(s, 0.f);
   }
+  const float4 wa = t4[32], wb = t4[33];
   float s = th[152];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) s = fmaf(th[128 + c], h2[c], s);
+  s = fmaf(wa.x, h2[0], s); s = fmaf(wa.y, h2[1], s); s = fmaf(wa.z, h2[2], s); s = fmaf(wa.w, h2[3], s);
+  s = fmaf(wb.x, h2[4], s); s = fmaf(wb.y, h2[5], s); s = fmaf(wb.z, h2[6], s); s = fmaf(wb.w, h2[7], s);
   return s;
+}
+
+// h0 += W_h[:, n] v for one channel n: the pre-head weights are stored
+// channel-major (8 outputs of a channel contiguous, 16-byte aligned)
+__device__ __forceinline__ void prehead_acc(const float* swh_t, int n, float v, float h0[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(swh_t + 8 * n);
+  const float4 b = *reinterpret_cast<const float4*>(swh_t + 8 * n + 4);
+  h0[0] = fmaf(a.x, v, h0[0]); h0[1] = fmaf(a.y, v, h0[1]); h0[2] = fmaf(a.z, v, h0[2]); h0[3] = fmaf(a.w, v, h0[3]);
+  h0[4] = fmaf(b.x, v, h0[4]); h0[5] = fmaf(b.y, v, h0[5]); h0[6] = fmaf(b.z, v, h0[6]); h0[7] = fmaf(b.w, v, h0[7]);
 }
 
 // 2x2 max of a pixel's 16 channel values with the pixels of lanes lane^dxl
@@ -274,15 +292,20 @@ struct StageRing {
 // latency overlaps the current tile instead of following its TMEM wait.
 struct RgbPrefetch {
   int t = -1, img = -1, y0 = 0, x0 = 0;
+  const uint8_t* base = nullptr;
+  long long cs = 0;
   uint32_t b0 = 0, b1 = 0, b2 = 0;
-  __device__ __forceinline__ void fetch(const uint8_t* canvas, long long cs, const int32_t* tiles3, int tile,
-                                        int im, int hh, int ww) {
+  __device__ __forceinline__ void fetch(const CanvasTab& cv, const int32_t* tiles3, int tile, int im, int hh,
+                                        int ww) {
     if (im != img) {
       img = im;
+      const int sl = __ldg(tiles3 + 3 * im);
       y0 = __ldg(tiles3 + 3 * im + 1);
       x0 = __ldg(tiles3 + 3 * im + 2);
+      base = cv.ptr[sl];
+      cs = cv.stride[sl];
     }
-    const uint8_t* px = canvas + (long long)(y0 + hh) * cs + (long long)(x0 + ww) * 3;
+    const uint8_t* px = base + (long long)(y0 + hh) * cs + (long long)(x0 + ww) * 3;
     b0 = __ldg(px);
     b1 = __ldg(px + 1);
     b2 = __ldg(px + 2);
@@ -510,7 +533,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       if (p.res_mode == RES_RGB) {
         const int b = (int)(m / RR);
         const int rem = (int)(m - (long long)b * RR);
-        const uint8_t* px = p.canvas + (long long)(p.tiles3[3 * b + 1] + rem / p.R) * p.canvas_stride +
+        const int sl = p.tiles3[3 * b];
+        const uint8_t* px = p.cv.ptr[sl] + (long long)(p.tiles3[3 * b + 1] + rem / p.R) * p.cv.stride[sl] +
                             (long long)(p.tiles3[3 * b + 2] + rem % p.R) * 3;
         v0 = norm_u8(px[0]);
         v1 = norm_u8(px[1]);
@@ -618,9 +642,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   float* swp = sb + BN;                                         // wp_rgb[3][BN]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(swp + 3 * BN);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* swh = reinterpret_cast<float*>(tmem_slot + 4);             // fused head: wh[8][BN]
+  float* swh = reinterpret_cast<float*>(tmem_slot + 4);             // fused head: wh as [BN][8]
   float* sbh = swh + kHeadCh * BN;                                  // bh[8]
-  float* sthe = sbh + kHeadCh;                                      // theta copy per epilogue warp
+  float* sthe = sbh + kHeadCh;                                      // theta rows per epilogue warp
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool fuse_head = p.theta != nullptr;
@@ -634,7 +658,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
   }
   if (fuse_head) {
-    for (int i = threadIdx.x; i < kHeadCh * BN; i += blockDim.x) swh[i] = p.wh[i];
+    for (int i = threadIdx.x; i < kHeadCh * BN; i += blockDim.x) swh[(i % BN) * kHeadCh + i / BN] = p.wh[i];
     if (threadIdx.x < kHeadCh) sbh[threadIdx.x] = p.bh[threadIdx.x];
   }
   if (threadIdx.x == 0) {
@@ -805,7 +829,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int blk = MB == 2 ? grp : 0;
     const int c_beg = split ? grp * (BN / 2) : 0, c_end = split ? c_beg + BN / 2 : BN;
     const int Rh = p.R >> 1;
-    float* sth = sthe + (warp - 2) * (2 * kHeadParams);
+    float* sth = sthe + (warp - 2) * (2 * kThetaPad);
     int th_img = -1;
     int tcount = 0;
     const bool rgb = p.res_mode == RES_RGB;
@@ -818,13 +842,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       uint32_t u0 = 0, u1 = 0, u2 = 0;
       if (rgb) {
         if (pf.t != tw.t)
-          pf.fetch(p.canvas, p.canvas_stride, p.tiles3, tw.t, tw.img,
+          pf.fetch(p.cv, p.tiles3, tw.t, tw.img,
                    tw.ty * (kHTH * MB) + blk * kHTH + row / kHTW, tw.tx * kHTW + row % kHTW);
         u0 = pf.b0; u1 = pf.b1; u2 = pf.b2;
         TileWalk nx = tw;
         nx.next();
         if (nx.t < p.n_tiles)
-          pf.fetch(p.canvas, p.canvas_stride, p.tiles3, nx.t, nx.img,
+          pf.fetch(p.cv, p.tiles3, nx.t, nx.img,
                    nx.ty * (kHTH * MB) + blk * kHTH + row / kHTW, nx.tx * kHTW + row % kHTW);
       }
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
@@ -879,9 +903,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
         if (fuse_head) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-#pragma unroll
-            for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaf(swh[o * BN + c + j], o16[j], h0[o]);
+          for (int j = 0; j < 16; ++j) prehead_acc(swh, c + j, o16[j], h0);
         }
       }
       tc_fence_before();
@@ -894,12 +916,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         if (img != th_img) {
           __syncwarp();
           const float* src = p.theta + (long long)img * p.ncls * kHeadParams;
-          for (int i = lane; i < p.ncls * kHeadParams; i += 32) sth[i] = src[i];
+          for (int i = lane; i < p.ncls * kHeadParams; i += 32) sth[(i / kHeadParams) * kThetaPad + i % kHeadParams] = src[i];
           __syncwarp();
           th_img = img;
         }
         float* lo = p.logits + (long long)(p.slot0 + img) * p.ncls * RR + (long long)hh * p.R + ww;
-        for (int ci = 0; ci < p.ncls; ++ci) lo[(long long)ci * RR] = dyn_head(sth + ci * kHeadParams, h0);
+        for (int ci = 0; ci < p.ncls; ++ci) lo[(long long)ci * RR] = dyn_head(sth + ci * kThetaPad, h0);
       }
     }
   }
@@ -976,12 +998,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   float* swp = sb + CO;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(swp + 3 * CO);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* swh = reinterpret_cast<float*>(tmem_slot + 4);             // fused head (MB = 2): wh[8][CO]
+  float* swh = reinterpret_cast<float*>(tmem_slot + 4);             // fused head: wh as [CO][8]
   float* sbh = swh + kHeadCh * CO;                                  // bh[8]
-  float* sthe = sbh + kHeadCh;                                      // theta copy per epilogue warp
+  float* sthe = sbh + kHeadCh;                                      // theta rows per epilogue warp
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool fuse_head = MB == 2 && p.theta != nullptr;
+  const bool fuse_head = p.theta != nullptr;
   for (int i = threadIdx.x; i < CO; i += blockDim.x) {
     sg[i] = p.gamma[i];
     sb[i] = p.beta[i];
@@ -992,7 +1014,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
   }
   if (fuse_head) {
-    for (int i = threadIdx.x; i < kHeadCh * CO; i += blockDim.x) swh[i] = p.wh[i];
+    for (int i = threadIdx.x; i < kHeadCh * CO; i += blockDim.x) swh[(i % CO) * kHeadCh + i / CO] = p.wh[i];
     if (threadIdx.x < kHeadCh) sbh[threadIdx.x] = p.bh[threadIdx.x];
   }
   if (threadIdx.x == 0) {
@@ -1002,7 +1024,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
     for (int b = 0; b < Cfg::kBufs; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
-      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+      // one block with the fused head: each warpgroup owns the buffers of one parity
+      mbar_init(smem_u32(&tempty[b]), MB == 1 && fuse_head ? kEpiWarps / 2 : kEpiWarps);
     }
     mbar_init(smem_u32(drain), 1);
     mbar_init(smem_u32(wbar), 1);
@@ -1147,13 +1170,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   } else {
     // ------------------------------------------------------------------ epilogue
     // MB = 1: warps w and w+4 share lane quarter w%4 and split the output
-    // channels; MB = 2: warpgroup g takes block g, all channels
+    // channels, or, with the fused head (a thread needs all channels of its
+    // pixel), warpgroup g takes the TMEM buffers of parity g (alternate
+    // tiles) whole; MB = 2: warpgroup g takes block g, all channels
     const int q = warp & 3, grp = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     const int col = row % kHTW;                        // column inside the 16-lane row group
     const int blk = MB == 2 ? grp : 0;
-    const int co_beg = MB == 1 ? grp * (CO / 2) : 0, co_end = MB == 1 ? co_beg + CO / 2 : CO;
-    float* sth = sthe + (warp - 2) * (2 * kHeadParams);
+    const bool split = MB == 1 && !fuse_head;
+    const int co_beg = split ? grp * (CO / 2) : 0, co_end = split ? co_beg + CO / 2 : CO;
+    float* sth = sthe + (warp - 2) * (2 * kThetaPad);
     int th_img = -1;
     int tcount = 0;
     const bool rgb = p.res_mode == RES_RGB;
@@ -1162,19 +1188,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     tw.init(hp.tiles_per_img / hp.tiles_w, hp.tiles_w);
     for (; tw.t < p.n_tiles; tw.next(), ++tcount) {
       const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
+      if (MB == 1 && fuse_head && (buf & 1) != grp) continue;
       uint32_t u0 = 0, u1 = 0, u2 = 0;
       if (rgb) {
         // lanes without an output column (halo lanes, columns past R) fetch nothing
         const int wc = tw.tx * kXTW + col - 1;
         if (pf.t != tw.t && col >= 1 && col <= kXTW && wc < p.R)
-          pf.fetch(p.canvas, p.canvas_stride, p.tiles3, tw.t, tw.img,
+          pf.fetch(p.cv, p.tiles3, tw.t, tw.img,
                    tw.ty * (kHTH * MB) + blk * kHTH + row / kHTW, wc);
         u0 = pf.b0; u1 = pf.b1; u2 = pf.b2;
         TileWalk nx = tw;
         nx.next();
         const int wn = nx.tx * kXTW + col - 1;
         if (nx.t < p.n_tiles && col >= 1 && col <= kXTW && wn < p.R)
-          pf.fetch(p.canvas, p.canvas_stride, p.tiles3, nx.t, nx.img,
+          pf.fetch(p.cv, p.tiles3, nx.t, nx.img,
                    nx.ty * (kHTH * MB) + blk * kHTH + row / kHTW, wn);
       }
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
@@ -1237,9 +1264,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
         if (fuse_head) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-#pragma unroll
-            for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaf(swh[o * CO + c + j], o16[j], h0[o]);
+          for (int j = 0; j < 16; ++j) prehead_acc(swh, c + j, o16[j], h0);
         }
       }
       tc_fence_before();
@@ -1252,13 +1277,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         if (img != th_img) {
           __syncwarp();
           const float* src = p.theta + (long long)img * p.ncls * kHeadParams;
-          for (int i2 = lane; i2 < p.ncls * kHeadParams; i2 += 32) sth[i2] = src[i2];
+          for (int i2 = lane; i2 < p.ncls * kHeadParams; i2 += 32)
+            sth[(i2 / kHeadParams) * kThetaPad + i2 % kHeadParams] = src[i2];
           __syncwarp();
           th_img = img;
         }
         if (writes) {
           float* lo = p.logits + (long long)(p.slot0 + img) * p.ncls * RR + (long long)hh * p.R + ww;
-          for (int ci = 0; ci < p.ncls; ++ci) lo[(long long)ci * RR] = dyn_head(sth + ci * kHeadParams, h0);
+          for (int ci = 0; ci < p.ncls; ++ci) lo[(long long)ci * RR] = dyn_head(sth + ci * kThetaPad, h0);
         }
       }
     }
@@ -1320,9 +1346,14 @@ struct FirstCfg {
       1024 + (size_t)kFirstStages * (kFirstStageBytes + kRawStageBytes) + kWBytes + 2048;
 };
 
+// raw-window tensor maps of the batch's canvases (entry k for canvas cv.ptr[k])
+struct CanvasMaps {
+  CUtensorMap m[kMaxCanvases];
+};
+
 template <int CO>
 __global__ void __launch_bounds__(kThreadsFirst, 1)
-    k_conv_tc_first(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapC,
+    k_conv_tc_first(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CanvasMaps mapsC,
                     TCParams p) {
   using Cfg = FirstCfg<CO>;
   constexpr int ST = kFirstStages;
@@ -1392,11 +1423,12 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
       for (; tw.t < p.n_tiles; tw.next(), ring.next(ST), ++it) {
         const int s = ring.s;
         if (ring.lapped && !mbar_wait(smem_u32(&rempty[s]), ring.ph ^ 1u, abort_flag, p.err)) break;
+        const int sl = p.tiles3[3 * tw.img];
         const int y0 = p.tiles3[3 * tw.img + 1] + tw.ty * kHTH - 1;
         const int xb = (p.tiles3[3 * tw.img + 2] + tw.tx * kHTW - 1) * 3;
         const uint32_t fb = smem_u32(&rfull[s]);
         mbar_expect_tx(fb, kRawW * kRawH);
-        tma_load_2d(smem_u32(sRaw + (size_t)s * kRawStageBytes), &mapC, fb, xb & ~15, y0);
+        tma_load_2d(smem_u32(sRaw + (size_t)s * kRawStageBytes), &mapsC.m[sl], fb, xb & ~15, y0);
       }
       for (int q = it - 1; q >= 0 && q >= it - ST; --q) mbar_drain(smem_u32(&rfull[q % ST]), (q / ST) & 1);
     }
@@ -1633,8 +1665,7 @@ cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
   p.gamma = a.w.gamma;
   p.beta = a.w.beta;
   p.wp_rgb = a.w.wp_f32;
-  p.canvas = a.canvas;
-  p.canvas_stride = a.canvas_stride;
+  p.cv = a.cv;
   p.tiles3 = a.tiles3;
   p.y = static_cast<__nv_bfloat16*>(a.y);
   p.y_cs = a.y_cs;
@@ -1656,7 +1687,7 @@ cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
 constexpr int kHaloSmemMax = 227 * 1024;
 constexpr int kHaloSmemExtra = 3072;   // barriers, gamma/beta, alignment slack
 // fused head: wh[8][64] + bh[8] + a 2-class theta copy per epilogue warp
-constexpr int kHeadSmem = (kHeadCh * 64 + kHeadCh + kEpiWarps * 2 * kHeadParams) * 4 + 16;
+constexpr int kHeadSmem = (kHeadCh * 64 + kHeadCh + kEpiWarps * 2 * kThetaPad) * 4 + 16;
 
 // copy the optional fused outputs of a launch into the kernel parameters
 void set_fused(const ConvArgs& a, TCParams& p, bool head_ok) {
@@ -1721,8 +1752,7 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
   p.gamma = a.w.gamma;
   p.beta = a.w.beta;
   p.wp_rgb = a.w.wp_f32;
-  p.canvas = a.canvas;
-  p.canvas_stride = a.canvas_stride;
+  p.cv = a.cv;
   p.tiles3 = a.tiles3;
   p.y = static_cast<__nv_bfloat16*>(a.y);
   p.y_cs = a.y_cs;
@@ -1803,19 +1833,20 @@ cudaError_t launch_dxn(const ConvArgs& a, cudaStream_t st, int stages) {
   p.gamma = a.w.gamma;
   p.beta = a.w.beta;
   p.wp_rgb = a.w.wp_f32;
-  p.canvas = a.canvas;
-  p.canvas_stride = a.canvas_stride;
+  p.cv = a.cv;
   p.tiles3 = a.tiles3;
   p.y = static_cast<__nv_bfloat16*>(a.y);
   p.y_cs = a.y_cs;
   p.y_co = a.y_co;
   p.err = a.err;
-  // the fused head needs a thread to hold all channels of its pixel: two blocks only
+  // the fused head needs a thread to hold all channels of its pixel: with one
+  // block per tile the two epilogue warpgroups then take alternate tiles
   const bool head = a.head_theta != nullptr;
-  if (head && (MB != 2 || a.head_ncls < 1 || a.head_ncls > 2 || !a.head_wh || !a.head_bh || !a.head_logits))
+  if (head && (a.head_ncls < 1 || a.head_ncls > 2 || !a.head_wh || !a.head_bh || !a.head_logits ||
+               (MB == 1 && Cfg::kBufs % 2)))
     return cudaErrorInvalidValue;
   if (!head && !a.y) return cudaErrorInvalidValue;
-  set_fused(a, p, MB == 2);
+  set_fused(a, p, true);
   const size_t fixed = (size_t)hp.wbytes + kHaloSmemExtra + (head ? kHeadSmem : 0);
   const size_t stage_bytes = (size_t)hp.cps * Cfg::kStageBytes;
   if (head && fixed + (size_t)stages * stage_bytes > (size_t)kHaloSmemMax)
@@ -1853,9 +1884,19 @@ bool map_canvas(CUtensorMap* m, const uint8_t* canvas, long long stride, int can
 template <int CO>
 cudaError_t launch_first(const ConvArgs& a, cudaStream_t st) {
   using Cfg = FirstCfg<CO>;
-  CUtensorMap mB, mC;
+  CUtensorMap mB;
+  CanvasMaps mC;
   if (!map_w(&mB, a.w.w_bf16, 32, a.cout, CO, 32)) return cudaErrorInvalidValue;
-  if (!map_canvas(&mC, a.canvas, a.canvas_stride, a.canvas_h)) return cudaErrorInvalidValue;
+  for (int k = 0; k < kMaxCanvases; ++k) {
+    if (k > 0 && a.cv.ptr[k] == a.cv.ptr[k - 1] && a.cv.stride[k] == a.cv.stride[k - 1] &&
+        a.cv.rows[k] == a.cv.rows[k - 1]) {
+      mC.m[k] = mC.m[k - 1];
+    } else if (a.cv.ptr[k]) {
+      if (!map_canvas(&mC.m[k], a.cv.ptr[k], a.cv.stride[k], a.cv.rows[k])) return cudaErrorInvalidValue;
+    } else {
+      mC.m[k] = mC.m[0];     // unused entry: never indexed by a tile of this batch
+    }
+  }
   TCParams p{};
   p.B = a.B; p.R = a.R; p.cin = 3; p.cout = a.cout;
   p.n_tiles_m = a.B * (a.R / kHTH) * (a.R / kHTW);
@@ -1863,8 +1904,7 @@ cudaError_t launch_first(const ConvArgs& a, cudaStream_t st) {
   p.n_tiles = p.n_tiles_m;
   p.gamma = a.w.gamma;
   p.beta = a.w.beta;
-  p.canvas = a.canvas;
-  p.canvas_stride = a.canvas_stride;
+  p.cv = a.cv;
   p.tiles3 = a.tiles3;
   p.y = static_cast<__nv_bfloat16*>(a.y);
   p.y_cs = a.y_cs;
@@ -1949,7 +1989,8 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
 bool tc_fuses_pool(const TcConfig& c) { return c.kind >= 1 && c.kind <= 4; }
 
 bool tc_fuses_head(const TcConfig& c, int cout, int ncls) {
-  return ((c.kind == 1 || c.kind == 3) && (cout == 32 || cout == 64) || (c.kind == 4 && cout == 32)) &&
+  return ((c.kind == 1 || c.kind == 2 || c.kind == 3) && (cout == 32 || cout == 64) ||
+          (c.kind == 4 && cout == 32)) &&
          ncls >= 1 && ncls <= 2;
 }
 
@@ -2042,18 +2083,22 @@ cudaError_t launch_conv_first_tc_f16(const ConvArgs& a, cudaStream_t st) {
 cudaError_t launch_conv_first_tc_bf16(const ConvArgs& a, cudaStream_t st) {
 #endif
   if (a.R < 16 || a.R % 16 || a.y_cs % 8 || a.y_co % 8 || reinterpret_cast<uintptr_t>(a.y) % 16 ||
-      reinterpret_cast<uintptr_t>(a.w.w_bf16) % 16 || !a.canvas || !a.tiles3 || a.canvas_h < 1 ||
-      reinterpret_cast<uintptr_t>(a.canvas) % 16 || a.canvas_stride % 16)
+      reinterpret_cast<uintptr_t>(a.w.w_bf16) % 16 || !a.cv.ptr[0] || !a.tiles3)
     return cudaErrorInvalidValue;
+  for (int k = 0; k < kMaxCanvases; ++k)
+    if (a.cv.ptr[k] && (a.cv.rows[k] < 1 || reinterpret_cast<uintptr_t>(a.cv.ptr[k]) % 16 || a.cv.stride[k] % 16))
+      return cudaErrorInvalidValue;
   if (a.cout == 32) return launch_first<32>(a, st);
   if (a.cout == 64) return launch_first<64>(a, st);
   return cudaErrorInvalidValue;
 }
 
 #if !OMNI_TC_F16
-bool conv_first_tc_supported(int R, int cout, const uint8_t* canvas, long long stride) {
-  return R >= 16 && R % 16 == 0 && (cout == 32 || cout == 64) && reinterpret_cast<uintptr_t>(canvas) % 16 == 0 &&
-         stride % 16 == 0;
+bool conv_first_tc_supported(int R, int cout, const CanvasTab& cv) {
+  if (!(R >= 16 && R % 16 == 0 && (cout == 32 || cout == 64)) || !cv.ptr[0]) return false;
+  for (int k = 0; k < kMaxCanvases; ++k)
+    if (cv.ptr[k] && (reinterpret_cast<uintptr_t>(cv.ptr[k]) % 16 || cv.stride[k] % 16)) return false;
+  return true;
 }
 
 cudaError_t launch_conv_first_tc(const ConvArgs& a, cudaStream_t st) {

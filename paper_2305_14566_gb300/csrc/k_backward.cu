@@ -8,8 +8,12 @@
 //   loss   = mean over classes of (dice_c + bce_c)
 // dloss/dL = [ -(2 g (S+G+1) - (2 I + 1)) / (S+G+1)^2 * s (1 - s) + (s - g) / N_c ] / n_classes.
 // Through the overlap average, a tile's logit at a pixel receives dloss/dL / cov.
-// Every reduction is a fixed-order sum (block partials, then one ordered pass
-// in FP64), so the gradients are run-to-run deterministic.
+// All arithmetic is FP32.  Every reduction is a fixed-order sum (block or
+// chunk partials, then one ordered pass), so the gradients are run-to-run
+// deterministic; the ordered passes and the gradient accumulators that carry a
+// sum across batches are compensated (Kahan 1965: each addition also keeps
+// the rounding error it made and feeds it into the next), so their error does
+// not grow with the number of terms.  An accumulator is a float2 (sum, carry).
 #include "omni_internal.cuh"
 
 namespace omni {
@@ -18,6 +22,19 @@ namespace {
 constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// compensated addition: s + x with the running carry c of the errors so far
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+__device__ __forceinline__ void acc_add(float2* a, float x) {
+  float2 v = *a;
+  kahan_add(v.x, v.y, x);
+  *a = v;
+}
 
 template <typename T>
 __device__ T block_sum(T v, T* sh) {
@@ -35,20 +52,20 @@ __device__ T block_sum(T v, T* sh) {
 // partial[blk][4] = (S, I, G, BCE sum) over the block's pixels
 __global__ void __launch_bounds__(kRedThreads) k_loss_partial(const float* __restrict__ L,
                                                               const uint8_t* __restrict__ gt, long long n,
-                                                              double* __restrict__ partial) {
-  __shared__ double sh[32];
-  double s = 0, i = 0, g = 0, b = 0;
+                                                              float* __restrict__ partial) {
+  __shared__ float sh[32];
+  float s = 0, i = 0, g = 0, b = 0, cs = 0, ci = 0, cg = 0, cb = 0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const float l = L[k];
     const float gg = gt[k] ? 1.f : 0.f;
     const float sg = sigmoidf_(l);
-    s += sg;
-    i += sg * gg;
-    g += gg;
-    b += fmaxf(l, 0.f) - gg * l + log1pf(expf(-fabsf(l)));
+    kahan_add(s, cs, sg);
+    kahan_add(i, ci, sg * gg);
+    kahan_add(g, cg, gg);
+    kahan_add(b, cb, fmaxf(l, 0.f) - gg * l + log1pf(expf(-fabsf(l))));
   }
-  double r;
+  float r;
   r = block_sum(s, sh); if (threadIdx.x == 0) partial[blockIdx.x * 4 + 0] = r;
   r = block_sum(i, sh); if (threadIdx.x == 0) partial[blockIdx.x * 4 + 1] = r;
   r = block_sum(g, sh); if (threadIdx.x == 0) partial[blockIdx.x * 4 + 2] = r;
@@ -56,33 +73,33 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_partial(const float* __res
 }
 
 // sums[c][4] from the partials of every class (ordered); loss = mean_c(dice + bce)
-__global__ void k_loss_final(const double* __restrict__ partial, int blocks, int n_cls, NPix npix,
-                             double* __restrict__ sums, float* __restrict__ loss) {
+__global__ void k_loss_final(const float* __restrict__ partial, int blocks, int n_cls, NPix npix,
+                             float* __restrict__ sums, float* __restrict__ loss) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double total = 0;
+  float total = 0, ct = 0;
   for (int c = 0; c < n_cls; ++c) {
-    double a[4] = {0, 0, 0, 0};
+    float a[4] = {0, 0, 0, 0}, ca[4] = {0, 0, 0, 0};
     for (int k = 0; k < blocks; ++k)
-      for (int q = 0; q < 4; ++q) a[q] += partial[((long long)c * blocks + k) * 4 + q];
+      for (int q = 0; q < 4; ++q) kahan_add(a[q], ca[q], partial[((long long)c * blocks + k) * 4 + q]);
     for (int q = 0; q < 4; ++q) sums[c * 4 + q] = a[q];
-    const double dice = 1.0 - (2.0 * a[1] + 1.0) / (a[0] + a[2] + 1.0);
-    total += dice + a[3] / (double)npix.n[c];
+    const float dice = 1.0f - (2.0f * a[1] + 1.0f) / (a[0] + a[2] + 1.0f);
+    kahan_add(total, ct, dice + a[3] / (float)npix.n[c]);
   }
-  loss[0] = (float)(total / n_cls);
+  loss[0] = total / (float)n_cls;
 }
 
 __global__ void k_loss_grad(const float* __restrict__ L, const uint8_t* __restrict__ gt, long long n,
-                            const double* __restrict__ sums, double npix, int n_cls,
+                            const float* __restrict__ sums, float npix, int n_cls,
                             float* __restrict__ dL) {
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const double S = sums[0], I = sums[1], G = sums[2];
-  const double Bd = S + G + 1.0, A = 2.0 * I + 1.0;
+  const float S = sums[0], I = sums[1], G = sums[2];
+  const float Bd = S + G + 1.0f, A = 2.0f * I + 1.0f;
   const float l = L[k];
   const float gg = gt[k] ? 1.f : 0.f;
   const float s = sigmoidf_(l);
-  const float ddice = (float)(-(2.0 * gg * Bd - A) / (Bd * Bd));
-  dL[k] = (ddice * s * (1.f - s) + (s - gg) / (float)npix) / (float)n_cls;
+  const float ddice = -(2.0f * gg * Bd - A) / (Bd * Bd);
+  dL[k] = (ddice * s * (1.f - s) + (s - gg) / npix) / (float)n_cls;
 }
 
 // a = ReLU(g * c + b) over [n][C]
@@ -332,55 +349,57 @@ __global__ void k_colsum(const float* __restrict__ A, const float* __restrict__ 
   partial[(long long)blockIdx.x * C + c] = s;
 }
 
-// acc[i] += sum over chunks (in order) of partial[chunk][i]
-__global__ void k_reduce(const float* __restrict__ partial, int chunks, long long n, double* __restrict__ acc) {
+// acc[i] += sum over chunks (in order) of partial[chunk][i], both compensated
+__global__ void k_reduce(const float* __restrict__ partial, int chunks, long long n, float2* __restrict__ acc) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0;
-  for (int k = 0; k < chunks; ++k) s += partial[(long long)k * n + i];
-  acc[i] += s;
+  float s = 0, c = 0;
+  for (int k = 0; k < chunks; ++k) kahan_add(s, c, partial[(long long)k * n + i]);
+  acc_add(acc + i, s);
 }
 
 // Controller backward for a batch: dWc[row][k] += sum_{b, ci} dtheta[b][ci][row] z_{b,ci}[k],
 // dbc[row] += sum dtheta, with z = [g_b; onehot(class); onehot(scale)].
 __global__ void k_ctrl_bwd(const float* __restrict__ dtheta_partial, int hblocks, int B, int n_cls,
                            const int* __restrict__ cls_ids, int n_classes, int n_scales, int scale,
-                           const float* __restrict__ g, int Cb, double* __restrict__ dwc,
-                           double* __restrict__ dbc) {
+                           const float* __restrict__ g, int Cb, float2* __restrict__ dwc,
+                           float2* __restrict__ dbc) {
   const int row = blockIdx.x;
   const int zdim = Cb + n_classes + n_scales;
-  __shared__ double dt[64][OMNI_MAX_CLASSES];
+  __shared__ float dt[64][OMNI_MAX_CLASSES];
   for (int e = threadIdx.x; e < B * n_cls; e += blockDim.x) {
     const int b = e / n_cls, ci = e % n_cls;
-    double s = 0;
+    float s = 0, c = 0;
     for (int k = 0; k < hblocks; ++k)
-      s += dtheta_partial[(((long long)b * n_cls + ci) * hblocks + k) * kHeadParams + row];
+      kahan_add(s, c, dtheta_partial[(((long long)b * n_cls + ci) * hblocks + k) * kHeadParams + row]);
     dt[b][ci] = s;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < zdim; k += blockDim.x) {
-    double s = 0;
+    float s = 0, c = 0;
     for (int b = 0; b < B; ++b)
       for (int ci = 0; ci < n_cls; ++ci) {
-        double z = 0;
+        float z = 0;
         if (k < Cb) z = g[(long long)b * Cb + k];
-        else if (k == Cb + cls_ids[ci]) z = 1.0;
-        else if (k == Cb + n_classes + scale) z = 1.0;
-        s += dt[b][ci] * z;
+        else if (k == Cb + cls_ids[ci]) z = 1.0f;
+        else if (k == Cb + n_classes + scale) z = 1.0f;
+        kahan_add(s, c, dt[b][ci] * z);
       }
-    dwc[(long long)row * zdim + k] += s;
+    acc_add(dwc + (long long)row * zdim + k, s);
   }
   if (threadIdx.x == 0) {
-    double s = 0;
+    float s = 0, c = 0;
     for (int b = 0; b < B; ++b)
-      for (int ci = 0; ci < n_cls; ++ci) s += dt[b][ci];
-    dbc[row] += s;
+      for (int ci = 0; ci < n_cls; ++ci) kahan_add(s, c, dt[b][ci]);
+    acc_add(dbc + row, s);
   }
 }
 
-__global__ void k_to_f32(const double* __restrict__ a, long long n, float* __restrict__ out) {
+// accumulator (sum, carry) -> FP32 value: the carry holds the negated error
+// of the last additions
+__global__ void k_to_f32(const float2* __restrict__ a, long long n, float* __restrict__ out) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (float)a[i];
+  if (i < n) out[i] = a[i].x - a[i].y;
 }
 
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -389,17 +408,17 @@ unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 int loss_blocks() { return 256; }
 
-cudaError_t launch_loss_partial(const float* L, const uint8_t* gt, long long n, double* partial,
+cudaError_t launch_loss_partial(const float* L, const uint8_t* gt, long long n, float* partial,
                                 cudaStream_t st) {
   k_loss_partial<<<loss_blocks(), kRedThreads, 0, st>>>(L, gt, n, partial);
   return cudaGetLastError();
 }
-cudaError_t launch_loss_final(const double* partial, int n_cls, const NPix& npix, double* sums,
+cudaError_t launch_loss_final(const float* partial, int n_cls, const NPix& npix, float* sums,
                               float* loss, cudaStream_t st) {
   k_loss_final<<<1, 32, 0, st>>>(partial, loss_blocks(), n_cls, npix, sums, loss);
   return cudaGetLastError();
 }
-cudaError_t launch_loss_grad(const float* L, const uint8_t* gt, long long n, const double* sums, double npix,
+cudaError_t launch_loss_grad(const float* L, const uint8_t* gt, long long n, const float* sums, float npix,
                              int n_cls, float* dL, cudaStream_t st) {
   k_loss_grad<<<blocks_for(n, 256), 256, 0, st>>>(L, gt, n, sums, npix, n_cls, dL);
   return cudaGetLastError();
@@ -439,7 +458,7 @@ cudaError_t launch_prehead_bwd(const BwdHeadArgs& a, int C0, long long npx, cuda
 }
 int wgrad_chunks(long long npx) { return (int)((npx + kWgChunk - 1) / kWgChunk); }
 cudaError_t launch_wgrad(const float* dY, int O, const float* X, int x_cs, int cin, int taps, int P,
-                         long long npx, float* partial, double* acc, cudaStream_t st) {
+                         long long npx, float* partial, float2* acc, cudaStream_t st) {
   if (O > 64 || O % 4) return cudaErrorInvalidValue;
   const int K = taps * cin;
   const int chunks = wgrad_chunks(npx);
@@ -455,7 +474,7 @@ cudaError_t launch_wgrad(const float* dY, int O, const float* X, int x_cs, int c
   k_reduce<<<blocks_for(n, 256), 256, 0, st>>>(partial, chunks, n, acc);
   return cudaGetLastError();
 }
-cudaError_t launch_colsum(const float* A, const float* B, int C, long long npx, float* partial, double* acc,
+cudaError_t launch_colsum(const float* A, const float* B, int C, long long npx, float* partial, float2* acc,
                           cudaStream_t st) {
   if (C > 1024) return cudaErrorInvalidValue;
   const int chunks = wgrad_chunks(npx);
@@ -464,14 +483,14 @@ cudaError_t launch_colsum(const float* A, const float* B, int C, long long npx, 
   return cudaGetLastError();
 }
 cudaError_t launch_ctrl_bwd(const float* dtheta_partial, int hblocks, int B, int n_cls, const int* cls_ids_dev,
-                            int n_classes, int n_scales, int scale, const float* g, int Cb, double* dwc,
-                            double* dbc, cudaStream_t st) {
+                            int n_classes, int n_scales, int scale, const float* g, int Cb, float2* dwc,
+                            float2* dbc, cudaStream_t st) {
   if (B > 64) return cudaErrorInvalidValue;
   k_ctrl_bwd<<<kHeadParams, 256, 0, st>>>(dtheta_partial, hblocks, B, n_cls, cls_ids_dev, n_classes, n_scales,
                                           scale, g, Cb, dwc, dbc);
   return cudaGetLastError();
 }
-cudaError_t launch_to_f32(const double* a, long long n, float* out, cudaStream_t st) {
+cudaError_t launch_to_f32(const float2* a, long long n, float* out, cudaStream_t st) {
   k_to_f32<<<blocks_for(n, 256), 256, 0, st>>>(a, n, out);
   return cudaGetLastError();
 }

@@ -75,8 +75,7 @@ __device__ __forceinline__ float norm_u8(uint8_t u) { return 2.0f * (float)u / 2
 // from shared memory feeds four FMAs.  grid: x = column quads, y = row, z = tile.
 constexpr int kFirstPix = 4;
 template <int C0, typename T>
-__global__ void __launch_bounds__(128) k_conv_first(int P, const uint8_t* __restrict__ canvas,
-                                                    long long cstride,
+__global__ void __launch_bounds__(128) k_conv_first(int P, const CanvasTab cv,
                                                     const int32_t* __restrict__ tiles3,
                                                     const float* __restrict__ w27,  // [27][C0]
                                                     const float* __restrict__ gamma,
@@ -91,6 +90,8 @@ __global__ void __launch_bounds__(128) k_conv_first(int P, const uint8_t* __rest
   if (j0 >= P) return;
   const int i = blockIdx.y, b = blockIdx.z;
   const int ty = tiles3[3 * b + 1], tx = tiles3[3 * b + 2];
+  const uint8_t* __restrict__ canvas = cv.ptr[tiles3[3 * b]];
+  const long long cstride = cv.stride[tiles3[3 * b]];
   // 3 rows x 6 columns x 3 channels of normalised input around the four pixels
   float in[3][kFirstPix + 2][3];
 #pragma unroll
@@ -275,7 +276,8 @@ __global__ void __launch_bounds__(kThreads) k_conv_f32(ConvArgs a) {
       int b = (int)(m / RR);
       int rem = (int)(m - (long long)b * RR);
       int pi = rem / a.R, pj = rem % a.R;
-      const uint8_t* px = a.canvas + (long long)(a.tiles3[3 * b + 1] + pi) * a.canvas_stride +
+      const int sl = a.tiles3[3 * b];
+      const uint8_t* px = a.cv.ptr[sl] + (long long)(a.tiles3[3 * b + 1] + pi) * a.cv.stride[sl] +
                           (long long)(a.tiles3[3 * b + 2] + pj) * 3;
       float v0 = norm_u8(px[0]), v1 = norm_u8(px[1]), v2 = norm_u8(px[2]);
 #pragma unroll
@@ -403,38 +405,11 @@ __global__ void __launch_bounds__(128) k_upsample(int Ri, int C, const T* __rest
 // g[b][c] = mean over the R x R pixels of tile b.  Block (b, 32-channel group):
 // 8 pixel phases x 32 channels; phase h sums pixels h, h+8, ... in order, then
 // the 8 phase sums are added in phase order (a fixed summation order).
-constexpr int kGapPhases = 8;
-template <typename T>
-__global__ void __launch_bounds__(256) k_gap(int R, int C, const T* __restrict__ x, int x_cs, int x_co,
-                                             float* __restrict__ g) {
-  __shared__ float part[kGapPhases][32];
-  const int b = blockIdx.x;
-  const int ph = threadIdx.x >> 5, cl = threadIdx.x & 31;
-  const int c = blockIdx.y * 32 + cl;
-  const int RR = R * R;
-  float s = 0.f;
-  if (c < C) {
-    const T* base = x + ((long long)b * RR) * x_cs + x_co + c;
-    for (int p = ph; p < RR; p += kGapPhases) {
-      if constexpr (sizeof(T) == 4) s += (float)base[(long long)p * x_cs];
-      else s += static_cast<float>(base[(long long)p * x_cs]);
-    }
-  }
-  part[ph][cl] = s;
-  __syncthreads();
-  if (ph == 0 && c < C) {
-    float t = 0.f;
-#pragma unroll
-    for (int h = 0; h < kGapPhases; ++h) t += part[h][cl];
-    g[(long long)b * C + c] = t / (float)RR;
-  }
-}
-
 template <int C0, typename T>
 cudaError_t first_t(const ConvArgs& a, cudaStream_t st) {
   if (a.R % kFirstPix) return cudaErrorInvalidValue;
   dim3 grid((a.R / kFirstPix + 127) / 128, a.R, a.B);
-  k_conv_first<C0, T><<<grid, 128, 0, st>>>(a.R, a.canvas, a.canvas_stride, a.tiles3,
+  k_conv_first<C0, T><<<grid, 128, 0, st>>>(a.R, a.cv, a.tiles3,
                                               a.w.w_f32, a.w.gamma, a.w.beta,
                                               static_cast<T*>(a.y), a.y_cs, a.y_co);
   return cudaGetLastError();
@@ -502,18 +477,6 @@ cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, i
   else
     k_upsample<__nv_bfloat16><<<grid, 128, 0, st>>>(Ri, C, (const __nv_bfloat16*)x, x_cs, x_co,
                                                     (__nv_bfloat16*)y, y_cs, y_co);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gap(int precision, int B, int R, int C, const void* x, int x_cs, int x_co,
-                       float* g, cudaStream_t st) {
-  dim3 grid(B, (C + 31) / 32);
-  if (precision == OMNI_FP32)
-    k_gap<float><<<grid, 256, 0, st>>>(R, C, (const float*)x, x_cs, x_co, g);
-  else if (precision == OMNI_FP16)
-    k_gap<__half><<<grid, 256, 0, st>>>(R, C, (const __half*)x, x_cs, x_co, g);
-  else
-    k_gap<__nv_bfloat16><<<grid, 256, 0, st>>>(R, C, (const __nv_bfloat16*)x, x_cs, x_co, g);
   return cudaGetLastError();
 }
 

@@ -3,10 +3,13 @@
 // 153 parameters of a per-tile, per-class 1x1 head 8 -> 8 -> 8 -> 1, which is
 // applied at every pixel of the pre-head feature h0 = ReLU(Wh y0 + bh).
 //
-// Two kernels: k_controller evaluates theta for every tile of a batch and every
-// class of the scale (the controller weights are read once per batch, not once
-// per pixel block), and k_head runs the pre-head and all heads of the scale
-// over the tile pixels, writing FP32 logits.
+// k_gap_controller reduces the bottleneck of a tile to its channel means and
+// evaluates theta for every class of the scale in the same launch (one CTA per
+// tile); k_head runs the pre-head and all heads of the scale over the tile
+// pixels, writing FP32 logits, where the last decoder conv does not run them
+// in its epilogue.
+#include <algorithm>
+
 #include <cuda_fp16.h>
 
 #include "omni_internal.cuh"
@@ -16,28 +19,6 @@ namespace {
 
 constexpr int kHeadThreads = 128;
 constexpr int kPixPerBlock = 4096;
-constexpr int kCtrlRows = 32;          // controller rows per block
-
-// grid = (ceil(153 / kCtrlRows), tiles); block = 8 warps, one theta row per warp step
-__global__ void __launch_bounds__(256) k_controller(HeadArgs a) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int zdim = a.Cb + a.n_classes + a.n_scales;
-  const int r0 = blockIdx.x * kCtrlRows, b = blockIdx.y;
-  for (int q = warp; q < kCtrlRows; q += 8) {
-    const int row = r0 + q;
-    if (row >= kHeadParams) continue;
-    const float* w = a.wc + (long long)row * zdim;
-    const float* g = a.g + (long long)b * a.Cb;
-    float s = 0.f;
-    for (int k = lane; k < a.Cb; k += 32) s = fmaf(w[k], g[k], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane < a.n_cls_here) {
-      const float th = s + w[a.Cb + a.n_classes + a.scale] + a.bc[row] + w[a.Cb + a.cls_ids[lane]];
-      a.theta[((long long)b * a.n_cls_here + lane) * kHeadParams + row] = th;
-    }
-  }
-}
 
 template <typename T> struct Load8;
 template <> struct Load8<float> {
@@ -71,6 +52,57 @@ template <> struct Load8<__half> {
     }
   }
 };
+
+// One CTA per tile.  GAP: thread t owns the channel octet 8 (t mod octets)
+// .. +7 and the pixels p = phase (mod phases), read as one 16-byte vector per
+// pixel; the phases' partial sums are added in phase order, so the result does
+// not depend on scheduling.  Controller: theta[ci][i] = Wc[i] . g + bc[i] +
+// Wc[i][Cb + n_classes + s] + Wc[i][Cb + class]; warp w takes rows w, w + 16,
+// ..., its lanes stride over the row and a fixed shuffle tree sums them.
+constexpr int kGcThreads = 512;
+template <typename T>
+__global__ void __launch_bounds__(kGcThreads) k_gap_controller(HeadArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const int Cb = a.Cb, octets = Cb / 8;
+  const int phases = max(1, kGcThreads / octets);
+  float* part = sm;                       // [phases][Cb]
+  float* g = sm + phases * Cb;            // [Cb]
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int RR = a.Rb * a.Rb;
+  const int oc = t % octets, ph = t / octets;
+  if (ph < phases) {
+    const T* base = static_cast<const T*>(a.bott) + (long long)b * RR * Cb + 8 * oc;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int p = ph; p < RR; p += phases) {
+      float v[8];
+      Load8<T>::f(base + (long long)p * Cb, v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += v[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) part[ph * Cb + 8 * oc + q] = acc[q];
+  }
+  __syncthreads();
+  for (int c = t; c < Cb; c += kGcThreads) {
+    float s = 0.f;
+    for (int h = 0; h < phases; ++h) s += part[h * Cb + c];
+    g[c] = s / (float)RR;
+    if (a.gap_out) a.gap_out[(long long)b * Cb + c] = g[c];
+  }
+  __syncthreads();
+  const int lane = t & 31, warp = t >> 5, nw = kGcThreads / 32;
+  const int zdim = Cb + a.n_classes + a.n_scales;
+  for (int row = warp; row < kHeadParams; row += nw) {
+    const float* w = a.wc + (long long)row * zdim;
+    float s = 0.f;
+    for (int k = lane; k < Cb; k += 32) s = fmaf(w[k], g[k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float common = s + w[Cb + a.n_classes + a.scale] + a.bc[row];
+    for (int ci = lane; ci < a.n_cls_here; ci += 32)
+      a.theta[((long long)b * a.n_cls_here + ci) * kHeadParams + row] = common + w[Cb + a.cls_ids[ci]];
+  }
+}
 
 // Each thread evaluates kHeadPx pixels (kHeadThreads apart, so a warp's loads
 // cover consecutive pixels) and reuses every weight it reads from shared
@@ -196,10 +228,19 @@ cudaError_t head_t(const HeadArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_controller(const HeadArgs& a, cudaStream_t st) {
-  if (a.n_cls_here < 1 || a.n_cls_here > OMNI_MAX_CLASSES) return cudaErrorInvalidValue;
-  if (a.B < 1) return cudaErrorInvalidValue;
-  k_controller<<<dim3((kHeadParams + kCtrlRows - 1) / kCtrlRows, a.B), 256, 0, st>>>(a);
+cudaError_t launch_gap_controller(const HeadArgs& a, cudaStream_t st) {
+  if (a.n_cls_here < 1 || a.n_cls_here > OMNI_MAX_CLASSES || a.B < 1 || !a.bott || a.Rb < 1) return cudaErrorInvalidValue;
+  if (a.Cb < 8 || a.Cb % 8 || a.Cb / 8 > kGcThreads) return cudaErrorInvalidValue;
+  if (reinterpret_cast<uintptr_t>(a.bott) % 16) return cudaErrorInvalidValue;
+  const int phases = std::max(1, kGcThreads / (a.Cb / 8));
+  const size_t smem = (size_t)(phases + 1) * a.Cb * sizeof(float);
+  if (smem > 48 * 1024) return cudaErrorInvalidValue;
+  if (a.precision == OMNI_FP32)
+    k_gap_controller<float><<<a.B, kGcThreads, smem, st>>>(a);
+  else if (a.precision == OMNI_FP16)
+    k_gap_controller<__half><<<a.B, kGcThreads, smem, st>>>(a);
+  else
+    k_gap_controller<__nv_bfloat16><<<a.B, kGcThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

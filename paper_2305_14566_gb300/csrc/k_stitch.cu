@@ -11,6 +11,10 @@
 // crop is 4-aligned (tile borders fall on multiples of the stride S, S % 4 == 0).
 // With a stitch window the average is weighted: L = sum_p w_p l_p / sum_p w_p,
 // w_p = t(y - y_p) t(x - x_p) from a P-entry table (votes stay unweighted).
+// A launch covers one band of output rows: the slide is stitched band by band
+// as soon as the tile rows covering a band are done, and the tile logits live
+// in a ring of slots (foreground index mod slot_cap) that holds only the tile
+// rows a band still needs.
 #include "omni_internal.cuh"
 
 namespace omni {
@@ -23,8 +27,8 @@ template <bool VEC, bool WIN>
 __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
   constexpr int NV = VEC ? 4 : 1;
   const int ox = (blockIdx.x * 64 + (threadIdx.x & 63)) * NV;
-  const int oy = blockIdx.y * 4 + (threadIdx.x >> 6);
-  if (oy >= a.oh || ox >= a.ow) return;
+  const int oy = a.row0 + blockIdx.y * 4 + (threadIdx.x >> 6);
+  if (oy >= a.row0 + a.nrows || oy >= a.oh || ox >= a.ow) return;
   const int cy = oy + a.oy0, cx = ox + a.ox0;
   const long long PP = (long long)a.P * a.P;
   const int i_lo = max(0, (cy - a.P) / a.S + ((cy - a.P) >= 0 ? 1 : 0));
@@ -51,9 +55,13 @@ __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
     int n = 0;
     for (int i = i_lo; i <= i_hi; ++i) {
       const float wy = WIN ? __ldg(a.window + (cy - i * a.S)) : 1.f;
+      // the covering tiles' loads are independent: unrolled, several are in
+      // flight per thread (the pass is bound by memory latency otherwise)
+#pragma unroll 4
       for (int j = j_lo; j <= j_hi; ++j) {
-        const int slot = a.slot_map[i * a.gw + j];
+        int slot = a.slot_map[i * a.gw + j];
         if (slot < 0) continue;
+        if (a.slot_cap) slot = (slot + a.slot_base) % a.slot_cap;
         ++n;
         const float* base = a.logits + ((long long)slot * a.n_cls + c) * PP +
                             (long long)(cy - i * a.S) * a.P + (cx - j * a.S);
@@ -123,14 +131,15 @@ __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
 
 cudaError_t launch_stitch(const StitchArgs& a, cudaStream_t st) {
   if (a.n_cls < 1 || a.n_cls > OMNI_MAX_CLASSES) return cudaErrorInvalidValue;
-  if (a.oh <= 0 || a.ow <= 0) return cudaSuccess;
+  if (a.oh <= 0 || a.ow <= 0 || a.nrows <= 0) return cudaSuccess;
+  if (a.row0 < 0 || a.slot_cap < 0) return cudaErrorInvalidValue;
   const bool vec = (a.ow % 4 == 0) && (a.ox0 % 4 == 0) && (a.S % 4 == 0) && (a.P % 4 == 0);
   if (vec) {
-    dim3 grid((a.ow / 4 + 63) / 64, (a.oh + 3) / 4);
+    dim3 grid((a.ow / 4 + 63) / 64, (a.nrows + 3) / 4);
     if (a.window) k_stitch<true, true><<<grid, 256, 0, st>>>(a);
     else k_stitch<true, false><<<grid, 256, 0, st>>>(a);
   } else {
-    dim3 grid((a.ow + 63) / 64, (a.oh + 3) / 4);
+    dim3 grid((a.ow + 63) / 64, (a.nrows + 3) / 4);
     if (a.window) k_stitch<false, true><<<grid, 256, 0, st>>>(a);
     else k_stitch<false, false><<<grid, 256, 0, st>>>(a);
   }

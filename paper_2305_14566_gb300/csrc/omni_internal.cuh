@@ -65,15 +65,25 @@ struct ConvLayerW {
 
 enum ResMode { RES_NONE = 0, RES_TENSOR = 1, RES_RGB = 2 };
 
+// Canvases the tiles of one network batch are read from: tile b's origin
+// (tiles3[3 b + 1], tiles3[3 b + 2]) lies in canvas tiles3[3 b] (its slide in
+// a multi-slide call, its scale in a one-slide call).  Every canvas is u8 RGB
+// with its own row stride; rows are its height (for the TMA raw-window maps).
+constexpr int kMaxCanvases = 16;
+struct CanvasTab {
+  const uint8_t* ptr[kMaxCanvases];
+  long long stride[kMaxCanvases];
+  int rows[kMaxCanvases];
+};
+
 struct ConvArgs {
   int B, R, cin, cout;
   const void* x; int x_cs, x_co;          // input NHWC (channel stride / offset)
   const void* r; int r_cs, r_co, cr;      // residual input for RES_TENSOR
   int res_mode;
-  // RES_RGB / first layer: tiles read straight from the uint8 canvas; tile b
-  // has origin (tiles3[3 b + 1], tiles3[3 b + 2]) in canvas pixels
-  const uint8_t* canvas; int64_t canvas_stride; const int32_t* tiles3;
-  int canvas_h;                           // canvas rows (first-layer tensor-core kernel)
+  // RES_RGB / first layer: tiles read straight from the uint8 canvases; tile b
+  // has origin (tiles3[3 b + 1], tiles3[3 b + 2]) in canvas cv.ptr[tiles3[3 b]]
+  CanvasTab cv; const int32_t* tiles3;
   void* y; int y_cs, y_co;                // output NHWC
   ConvLayerW w;                           // device pointers, passed by value
   unsigned* err;
@@ -84,7 +94,7 @@ struct ConvArgs {
   void* y2; int y2_cs;
   int f16;                                // tensor-core operands: 0 BF16, 1 FP16
   // Optional outputs fused into the epilogue of the small-N tensor-core
-  // kernels (TcConfig kinds 1 and 2; see tc_fuses_pool / tc_fuses_head):
+  // kernels (TcConfig kinds 1-4; see tc_fuses_pool / tc_fuses_head):
   // pool = 2x2 max-pool of y, NHWC [B][R/2][R/2] with channel stride pool_cs;
   // head_* = pre-head + dynamic heads of the tile (as launch_head), written as
   // FP32 logits [slot0 + b][head_ncls][R*R]; y may then be null (not stored).
@@ -101,8 +111,6 @@ cudaError_t launch_maxpool(int precision, int B, int R, int C, const void* x, in
                            void* y, int y_cs, int y_co, cudaStream_t st);
 cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, int x_cs,
                             int x_co, void* y, int y_cs, int y_co, cudaStream_t st);
-cudaError_t launch_gap(int precision, int B, int R, int C, const void* x, int x_cs, int x_co,
-                       float* g, cudaStream_t st);
 
 // k_conv_tc.cu (BF16 tcgen05 implicit GEMM)
 struct TcConfig {
@@ -122,7 +130,7 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max);
 // first layer (cin = 3) on the tensor cores: operand rows gathered from the
 // uint8 canvas; weights w.w_bf16 hold FP16 values [cout][32] (K = tap * 3 +
 // channel, zero padded) in every precision; the output is the pipeline's type
-bool conv_first_tc_supported(int R, int cout, const uint8_t* canvas, long long stride);
+bool conv_first_tc_supported(int R, int cout, const CanvasTab& cv);
 cudaError_t launch_conv_first_tc(const ConvArgs& a, cudaStream_t st);
 cudaError_t launch_conv_first_tc_bf16(const ConvArgs& a, cudaStream_t st);
 cudaError_t launch_conv_first_tc_f16(const ConvArgs& a, cudaStream_t st);
@@ -143,9 +151,12 @@ struct HeadArgs {
   int slot0;                               // output slot of tile 0 (tile b -> slot0 + b)
   float* logits;                           // [slot][n_cls_here][P*P]
   float* theta;                            // [B][n_cls_here][153] controller output
+  const void* bott; int Rb;                // bottleneck [B][Rb][Rb][Cb] (fused GAP + controller)
+  float* gap_out;                          // [B][Cb] GAP written by the fused kernel (or null)
 };
-// controller for a batch of tiles: theta[b][ci] = Wc [g_b; onehot; onehot] + bc
-cudaError_t launch_controller(const HeadArgs& a, cudaStream_t st);
+// GAP of the bottleneck and the controller in one launch: per tile the mean of
+// every bottleneck channel, then theta for every class of the scale
+cudaError_t launch_gap_controller(const HeadArgs& a, cudaStream_t st);
 // pre-head + dynamic heads over every pixel, reading theta
 cudaError_t launch_head(const HeadArgs& a, cudaStream_t st);
 
@@ -154,8 +165,11 @@ struct StitchArgs {
   int hs, ws;                 // canvas size at this scale
   int oy0, ox0, oh, ow;       // output crop window in canvas pixels
   int P, S, gh, gw, f;
-  const int32_t* slot_map;    // [gh][gw] logits slot or -1
-  const float* logits;        // [slot][n_cls][P*P]
+  const int32_t* slot_map;    // [gh][gw] index of the tile in the scale's foreground list, or -1
+  const float* logits;        // [slot][n_cls][P*P]; slot = (index + slot_base) mod slot_cap (0: no ring)
+  int slot_cap;
+  int slot_base;              // added to the slot map's index before the ring modulo
+  int row0, nrows;            // output rows row0 .. row0 + nrows - 1 (a band of the crop)
   int n_cls; int cls_ids[OMNI_MAX_CLASSES];
   int mode;                   // OMNI_STITCH_*
   const float* window;        // [P] separable overlap-average weight t(u); null = flat
@@ -183,11 +197,11 @@ struct BwdHeadArgs {
   float *y0, *dh0_pre, *dy0_pre, *dc2;     // pre-head backward outputs
 };
 int loss_blocks();
-cudaError_t launch_loss_partial(const float* L, const uint8_t* gt, long long n, double* partial,
+cudaError_t launch_loss_partial(const float* L, const uint8_t* gt, long long n, float* partial,
                                 cudaStream_t st);
-cudaError_t launch_loss_final(const double* partial, int n_cls, const NPix& npix, double* sums,
+cudaError_t launch_loss_final(const float* partial, int n_cls, const NPix& npix, float* sums,
                               float* loss, cudaStream_t st);
-cudaError_t launch_loss_grad(const float* L, const uint8_t* gt, long long n, const double* sums, double npix,
+cudaError_t launch_loss_grad(const float* L, const uint8_t* gt, long long n, const float* sums, float npix,
                              int n_cls, float* dL, cudaStream_t st);
 cudaError_t launch_affine_relu(const float* c, const float* g, const float* b, int C, long long n, float* a,
                                cudaStream_t st);
@@ -198,12 +212,12 @@ cudaError_t launch_head_bwd(const BwdHeadArgs& a, int C0, cudaStream_t st);
 cudaError_t launch_prehead_bwd(const BwdHeadArgs& a, int C0, long long npx, cudaStream_t st);
 int wgrad_chunks(long long npx);
 cudaError_t launch_wgrad(const float* dY, int O, const float* X, int x_cs, int cin, int taps, int P,
-                         long long npx, float* partial, double* acc, cudaStream_t st);
-cudaError_t launch_colsum(const float* A, const float* B, int C, long long npx, float* partial, double* acc,
+                         long long npx, float* partial, float2* acc, cudaStream_t st);
+cudaError_t launch_colsum(const float* A, const float* B, int C, long long npx, float* partial, float2* acc,
                           cudaStream_t st);
 cudaError_t launch_ctrl_bwd(const float* dtheta_partial, int hblocks, int B, int n_cls, const int* cls_ids_dev,
-                            int n_classes, int n_scales, int scale, const float* g, int Cb, double* dwc,
-                            double* dbc, cudaStream_t st);
-cudaError_t launch_to_f32(const double* a, long long n, float* out, cudaStream_t st);
+                            int n_classes, int n_scales, int scale, const float* g, int Cb, float2* dwc,
+                            float2* dbc, cudaStream_t st);
+cudaError_t launch_to_f32(const float2* a, long long n, float* out, cudaStream_t st);
 
 }  // namespace omni

@@ -30,6 +30,17 @@ struct omni_ctx {
   unsigned* d_err = nullptr;
   float* d_window = nullptr;                        // [P] overlap-average weight t(u), or null (flat)
   int32_t* h_counts = nullptr;                      // pinned
+  uint8_t* h_flags = nullptr;                       // pinned copy of the tile flags (band stitching)
+  size_t h_flags_n = 0;
+  // host-buffer calls: each stitched band's labels go to the host on copy_st
+  // while the network runs on (host_labels[c] non-null for the classes wanted)
+  uint8_t* const* host_labels = nullptr;
+  cudaStream_t copy_st = nullptr;
+  std::vector<cudaEvent_t> band_ev;
+  size_t band_ev_used = 0;
+  // omni_segment_slides: start and per-slide completion events of the last call
+  cudaEvent_t slide_ev[OMNI_MAX_SLIDES + 1] = {};
+  int slide_n = 0;
   // timing
   bool timing = false;
   struct Ev { cudaEvent_t a, b; int kind, tag; double work; };
@@ -56,6 +67,30 @@ namespace {
 omni_status fail(omni_ctx* c, omni_status s, const std::string& m) {
   if (c) c->err = m;
   return s;
+}
+
+// next event of the context's pool (timing disabled), created on demand
+cudaError_t band_event(omni_ctx* c, cudaEvent_t* out) {
+  if (c->band_ev_used == c->band_ev.size()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (r != cudaSuccess) return r;
+    c->band_ev.push_back(e);
+  }
+  *out = c->band_ev[c->band_ev_used++];
+  return cudaSuccess;
+}
+
+// Forget the captured launch chain: its kernel arguments hold device pointers
+// (weights) and kernel choices (fusion, autotuned configurations) of the state
+// it was captured in, so any change to that state must drop it.
+void drop_graph(omni_ctx* c) {
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  c->last_key.clear();
+  c->graph_key.clear();
 }
 
 omni_status cuda_fail(omni_ctx* c, cudaError_t e, const char* where) {
@@ -139,6 +174,7 @@ struct Plan {
   SlideGeom g;
   bool pad;
   int ncls_s[OMNI_MAX_SCALES];
+  int cap[OMNI_MAX_SCALES];   // tile-logit ring slots per scale (a multiple of max_batch)
   // tile stage
   size_t canvas, c20, c10, c5, blk8, grey, blur, hist, otsu, mask, tiles, counts, flags, slot;
   size_t tile_end;
@@ -205,9 +241,20 @@ bool make_plan(const omni_config& c, int H, int W, Plan& p) {
   const size_t e = c.precision == OMNI_FP32 ? 4 : 2;
   const size_t B = (size_t)c.max_batch;
   const size_t PP = (size_t)c.patch * c.patch;
+  // Tile logits live in a ring: an output band of S rows is stitched once the
+  // P/S tile rows covering it are done, so at any time the ring holds at most
+  // P/S tile rows that a band still needs, the row being filled and one batch;
+  // (P/S + 1) rows + a batch, rounded to whole batches so a batch's slots
+  // never wrap.  The logit memory no longer grows with the slide's height.
   size_t lmax = 0;
-  for (int s = 0; s < c.n_scales; ++s)
-    lmax = std::max(lmax, (size_t)g.gh[s] * g.gw[s] * (size_t)p.ncls_s[s]);
+  for (int s = 0; s < c.n_scales; ++s) {
+    const long long rows = (c.patch + g.S[s] - 1) / g.S[s] + 1;
+    long long cap = rows * g.gw[s] + (long long)B;
+    cap = std::min<long long>(cap, (long long)g.gh[s] * g.gw[s] + (long long)B);
+    cap = (cap + (long long)B - 1) / (long long)B * (long long)B;
+    p.cap[s] = (int)cap;
+    lmax = std::max(lmax, (size_t)cap * (size_t)p.ncls_s[s]);
+  }
   p.logits = take(off, lmax * PP * 4);
   const int L = c.levels;
   p.tmp = take(off, B * PP * widths(c, 0) * e);
@@ -316,7 +363,7 @@ omni_status omni_create(const omni_config* cfg, omni_ctx** out) {
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counts, (OMNI_MAX_SCALES + 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counts, OMNI_MAX_SLIDES * (OMNI_MAX_SCALES + 1) * sizeof(int32_t));
   if (e == cudaSuccess && cfg->stitch_window != OMNI_WINDOW_FLAT) {
     // one-dimensional weight of the stitch window, from its definition
     const int P = cfg->patch;
@@ -348,6 +395,11 @@ void omni_destroy(omni_ctx* ctx) {
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->d_window) cudaFree(ctx->d_window);
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
+  if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+  for (cudaEvent_t e : ctx->band_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->slide_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
   for (auto& e : ctx->evs) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -484,6 +536,7 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
     cudaFree(dev);
     return cuda_fail(ctx, e, "cudaMemcpy(weights)");
   }
+  drop_graph(ctx);     // the captured chain still points at the old weights
   if (ctx->wdev) cudaFree(ctx->wdev);
   ctx->wdev = dev;
   uint8_t* d = static_cast<uint8_t*>(dev);
@@ -543,6 +596,18 @@ struct Prep {
   int64_t cs[OMNI_MAX_SCALES];
   int ch[OMNI_MAX_SCALES];      // canvas rows
 };
+
+// canvas table of a one-slide batch: the tiles' first field is their scale s,
+// so every entry is that scale's canvas
+CanvasTab one_canvas(const Prep& pr, int s) {
+  CanvasTab t{};
+  for (int k = 0; k < kMaxCanvases; ++k) {
+    t.ptr[k] = pr.c[s];
+    t.stride[k] = pr.cs[s];
+    t.rows[k] = pr.ch[s];
+  }
+  return t;
+}
 
 // Sec. 2.1 stages on the device; fills `pr` with every scale's canvas.
 omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Plan& p, uint8_t* ws,
@@ -637,10 +702,15 @@ TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, float unfu
   const int n = tc_candidates(a.R, a.cin, a.cout, cr, cands, 16);
   TcConfig best = tc_default(a.R, a.cin, a.cout, cr);
   float best_ms = 1e30f;
+  // a layer that carries the fused head keeps it whenever some variant can
+  // compute it: the dynamic head then never needs a launch of its own
+  bool head_only = false;
+  for (int i = 0; i < n && a.head_theta; ++i) head_only |= tc_fuses_head(cands[i], a.cout, a.head_ncls);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return best;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return best; }
   for (int i = 0; i < n; ++i) {
+    if (head_only && !tc_fuses_head(cands[i], a.cout, a.head_ncls)) continue;
     const ConvArgs ai = fit_fused(a, cands[i]);
     bool ok = launch_conv_tc_cfg(ai, cands[i], st) == cudaSuccess &&
               launch_conv_tc_cfg(ai, cands[i], st) == cudaSuccess;
@@ -701,8 +771,8 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag
 }
 
 // U-Net + heads for `nb` tiles of one scale.
-omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const uint8_t* canvas,
-                      int64_t cstride, int canvas_h, const int32_t* tiles3, int nb, int slot0, int ncls,
+omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const CanvasTab& cv,
+                      const int32_t* tiles3, int nb, int slot0, int ncls,
                       const int* cls, cudaStream_t st, bool stop_before_dec0 = false) {
   const omni_config& c = ctx->cfg;
   const int L = c.levels, prec = c.precision;
@@ -712,9 +782,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   void* bott = ws + p.bott;
   ConvArgs base{};
   base.B = nb;
-  base.canvas = canvas;
-  base.canvas_stride = cstride;
-  base.canvas_h = canvas_h;
+  base.cv = cv;
   base.tiles3 = tiles3;
   base.err = ctx->d_err;
   base.f16 = c.precision == OMNI_FP16 ? 1 : 0;
@@ -729,7 +797,7 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     a.y = tmp; a.y_cs = C(0); a.y_co = 0;
     a.w = ctx->enc1[0];
     Rec r(ctx, st, 0, 0, conv_flops(a));
-    cudaError_t e = prec != OMNI_FP32 && conv_first_tc_supported(a.R, a.cout, canvas, cstride)
+    cudaError_t e = prec != OMNI_FP32 && conv_first_tc_supported(a.R, a.cout, cv)
                         ? launch_conv_first_tc(a, st)
                         : launch_conv_first(a, prec, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "conv_first");
@@ -777,11 +845,6 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
     if (r) return r;
   }
   float* gap = reinterpret_cast<float*>(ws + p.gap);
-  {
-    Rec r(ctx, st, 2, 400);
-    OMNI_CU(launch_gap(prec, nb, c.patch >> (L - 1), C(L - 1), bott, C(L - 1), 0, gap, st), "gap");
-    ctx->launches++;
-  }
   HeadArgs h{};
   h.B = nb; h.P = c.patch; h.C0 = C(0); h.Cb = C(L - 1);
   h.n_classes = c.n_classes; h.n_scales = c.n_scales; h.scale = s;
@@ -792,9 +855,11 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   h.slot0 = slot0;
   h.logits = reinterpret_cast<float*>(ws + p.logits);
   h.theta = reinterpret_cast<float*>(ws + p.theta);
+  h.bott = bott; h.Rb = c.patch >> (L - 1); h.gap_out = gap;
   {
+    // GAP of the bottleneck and the controller of every class of the scale
     Rec r(ctx, st, 2, 401);
-    OMNI_CU(launch_controller(h, st), "controller");
+    OMNI_CU(launch_gap_controller(h, st), "gap + controller");
     ctx->launches++;
   }
   const void* y = bott;
@@ -842,61 +907,197 @@ omni_status run_batch(omni_ctx* ctx, const Plan& p, uint8_t* ws, int s, const ui
   return OMNI_OK;
 }
 
+// Band stitching of one slide at one scale.  Output block row k (canvas rows
+// k S .. k S + S - 1) is covered by tile rows k - P/S + 1 .. k, so it is final
+// once tile rows 0..k are done; advance() takes the number of this slide's
+// tiles (of this scale) done so far and stitches every block row that became
+// final.  A band's labels are also queued for the host when the call has host
+// outputs.
+struct Bands {
+  StitchArgs a;
+  int s = 0, S = 1, nblk = 0, next_blk = 0, row_ptr = 0, gh = 0;
+  const int* row_end = nullptr;
+  const int* cls = nullptr;
+  int ncls = 0;
+
+  omni_status stitch_to(omni_ctx* ctx, int blk_end, cudaStream_t st) {
+    if (blk_end <= next_blk) return OMNI_OK;
+    const int y0 = std::max(0, next_blk * S - a.oy0), y1 = std::min(a.oh, blk_end * S - a.oy0);
+    next_blk = blk_end;
+    if (y1 <= y0) return OMNI_OK;
+    a.row0 = y0;
+    a.nrows = y1 - y0;
+    {
+      Rec rr(ctx, st, 1, 600 + s);
+      OMNI_CU(launch_stitch(a, st), "stitch");
+      ctx->launches++;
+    }
+    if (ctx->host_labels) {
+      // the band is final: its label rows go to the host while the next batches run
+      cudaEvent_t ev;
+      OMNI_CU(band_event(ctx, &ev), "band event");
+      OMNI_CU(cudaEventRecord(ev, st), "band event record");
+      OMNI_CU(cudaStreamWaitEvent(ctx->copy_st, ev, 0), "band wait");
+      for (int k = 0; k < ncls; ++k) {
+        uint8_t* dst = ctx->host_labels[cls[k]];
+        if (!dst || !a.labels[k]) continue;
+        const size_t o0 = (size_t)y0 * a.ow, nb = (size_t)(y1 - y0) * a.ow;
+        OMNI_CU(cudaMemcpyAsync(dst + o0, a.labels[k] + o0, nb, cudaMemcpyDeviceToHost, ctx->copy_st),
+                "download band");
+      }
+    }
+    return OMNI_OK;
+  }
+  omni_status advance(omni_ctx* ctx, int done, cudaStream_t st) {
+    while (row_ptr < gh && row_end[row_ptr] <= done) ++row_ptr;
+    return stitch_to(ctx, row_ptr == gh ? nblk : row_ptr, st);
+  }
+  omni_status finish(omni_ctx* ctx, cudaStream_t st) { return stitch_to(ctx, nblk, st); }
+};
+
+// Stitch state of one slide (plan p, tile stage at ws_prep) at scale s; the
+// slide's tile logits sit in the ring at (index + slot_base) mod cap.
+Bands make_bands(omni_ctx* ctx, const omni_config& c, const Plan& p, const uint8_t* ws_prep, const uint8_t* ws_net,
+                 const Plan& pn, const omni_outputs* out, int H, int W, int s, const int* cls, int ncls, int n_s,
+                 int slot_base, const std::vector<int>& row_end, double& stitch_bytes) {
+  Bands b;
+  const int f = c.factors[s];
+  StitchArgs& a = b.a;
+  a = StitchArgs{};
+  a.hs = p.g.Hp / f; a.ws = p.g.Wp / f;
+  a.oy0 = c.pad_lead / f; a.ox0 = c.pad_lead / f;
+  a.oh = (H + f - 1) / f; a.ow = (W + f - 1) / f;
+  a.window = ctx->d_window; a.P = c.patch; a.S = p.g.S[s]; a.gh = p.g.gh[s]; a.gw = p.g.gw[s]; a.f = f;
+  a.slot_map = reinterpret_cast<const int32_t*>(ws_prep + p.slot) + p.g.grid_off[s];
+  a.slot_cap = pn.cap[s];
+  a.slot_base = slot_base;
+  a.logits = reinterpret_cast<const float*>(ws_net + pn.logits);
+  a.n_cls = ncls;
+  for (int k = 0; k < ncls; ++k) {
+    a.cls_ids[k] = cls[k];
+    a.labels[k] = out->labels[cls[k]];
+    a.out_logits[k] = out->logits[cls[k]];
+  }
+  a.mode = c.stitch_mode;
+  a.tissue = c.tissue_and ? ws_prep + p.mask : nullptr;
+  a.th = p.g.th; a.tw = p.g.tw;
+  a.coverage = out->coverage[s];
+  a.argmax = out->argmax[s];
+  const double px = (double)a.oh * a.ow;
+  stitch_bytes += (double)n_s * ncls * c.patch * c.patch * 4.0;
+  for (int k = 0; k < ncls; ++k) stitch_bytes += px * ((a.labels[k] ? 1 : 0) + (a.out_logits[k] ? 4 : 0));
+  stitch_bytes += px * ((a.coverage ? 2 : 0) + (a.argmax ? 1 : 0));
+  b.s = s;
+  b.S = p.g.S[s];
+  b.nblk = a.hs / b.S;
+  b.gh = p.g.gh[s];
+  b.row_end = row_end.data();
+  b.cls = cls;
+  b.ncls = ncls;
+  return b;
+}
+
+// classes of scale s selected by class_mask
+int classes_at(const omni_config& c, int s, uint32_t class_mask, int* cls) {
+  int n = 0;
+  for (int k = 0; k < c.n_classes; ++k)
+    if (c.class_scale[k] == s && (class_mask >> k & 1u)) cls[n++] = k;
+  return n;
+}
+
+// the caller's stream waits for the last band copy (this also joins the copy
+// stream back into a stream capture)
+omni_status join_copies(omni_ctx* ctx, cudaStream_t st) {
+  if (!ctx->host_labels) return OMNI_OK;
+  cudaEvent_t ev;
+  OMNI_CU(band_event(ctx, &ev), "band event");
+  OMNI_CU(cudaEventRecord(ev, ctx->copy_st), "copy join record");
+  OMNI_CU(cudaStreamWaitEvent(st, ev, 0), "copy join");
+  return OMNI_OK;
+}
+
 // Everything after tiling: every batch of every requested scale, then the
-// stitch + labels of each scale.  Launch-only (no synchronisation), so it can
-// be captured into a CUDA graph.
+// stitch + labels of each scale, band by band.  Launch-only (no
+// synchronisation), so it can be captured into a CUDA graph.
 omni_status run_network(omni_ctx* ctx, const omni_config& c, const Plan& p, uint8_t* ws, const Prep& pr,
                         const omni_outputs* out, int H, int W, uint32_t scale_mask, uint32_t class_mask,
-                        cudaStream_t st, double& stitch_bytes) {
+                        const std::vector<std::vector<int>>& row_end, cudaStream_t st, double& stitch_bytes) {
   omni_status r = OMNI_OK;
   const int32_t* tiles = reinterpret_cast<const int32_t*>(ws + p.tiles);
-  const int32_t* slot = reinterpret_cast<const int32_t*>(ws + p.slot);
   int toff = 0;
   for (int s = 0; s < c.n_scales; ++s) {
     const int n_s = ctx->h_counts[1 + s];
-    int cls[OMNI_MAX_CLASSES], ncls = 0;
-    for (int k = 0; k < c.n_classes; ++k)
-      if (c.class_scale[k] == s && (class_mask >> k & 1u)) cls[ncls++] = k;
-    const bool want = (scale_mask >> s & 1u) && ncls > 0;
-    if (want) {
+    int cls[OMNI_MAX_CLASSES];
+    const int ncls = classes_at(c, s, class_mask, cls);
+    if ((scale_mask >> s & 1u) && ncls > 0) {
+      Bands b = make_bands(ctx, c, p, ws, ws, p, out, H, W, s, cls, ncls, n_s, 0, row_end[s], stitch_bytes);
+      const int cap = p.cap[s];
       for (int start = 0; start < n_s; start += c.max_batch) {
         int nb = std::min(c.max_batch, n_s - start);
-        r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], pr.ch[s], tiles + 3 * (toff + start), nb, start, ncls, cls, st);
+        r = run_batch(ctx, p, ws, s, one_canvas(pr, s), tiles + 3 * (toff + start), nb, start % cap, ncls,
+                      cls, st);
+        if (r) return r;
+        r = b.advance(ctx, start + nb, st);
         if (r) return r;
       }
+      r = b.finish(ctx, st);
+      if (r) return r;
       ctx->tiles_done += n_s;
-      const int f = c.factors[s];
-      StitchArgs a{};
-      a.hs = p.g.Hp / f; a.ws = p.g.Wp / f;
-      a.oy0 = c.pad_lead / f; a.ox0 = c.pad_lead / f;
-      a.oh = (H + f - 1) / f; a.ow = (W + f - 1) / f;
-      a.window = ctx->d_window; a.P = c.patch; a.S = p.g.S[s]; a.gh = p.g.gh[s]; a.gw = p.g.gw[s]; a.f = f;
-      a.slot_map = slot + p.g.grid_off[s];
-      a.logits = reinterpret_cast<const float*>(ws + p.logits);
-      a.n_cls = ncls;
-      for (int k = 0; k < ncls; ++k) {
-        a.cls_ids[k] = cls[k];
-        a.labels[k] = out->labels[cls[k]];
-        a.out_logits[k] = out->logits[cls[k]];
-      }
-      a.mode = c.stitch_mode;
-      a.tissue = c.tissue_and ? ws + p.mask : nullptr;
-      a.th = p.g.th; a.tw = p.g.tw;
-      a.coverage = out->coverage[s];
-      a.argmax = out->argmax[s];
-      double px = (double)a.oh * a.ow;
-      stitch_bytes += (double)n_s * ncls * c.patch * c.patch * 4.0;
-      for (int k = 0; k < ncls; ++k) stitch_bytes += px * ((a.labels[k] ? 1 : 0) + (a.out_logits[k] ? 4 : 0));
-      stitch_bytes += px * ((a.coverage ? 2 : 0) + (a.argmax ? 1 : 0));
-      {
-        Rec rr(ctx, st, 1, 600 + s);
-        OMNI_CU(launch_stitch(a, st), "stitch");
-        ctx->launches++;
-      }
     }
     toff += n_s;
   }
-  return OMNI_OK;
+  return join_copies(ctx, st);
+}
+
+// Runs the launch chain `chain(stitch_bytes)` eagerly, or, with graphs on and
+// a capturable stream, captures it into the context's CUDA graph on the
+// second call with the same key and replays that graph on later calls.
+template <typename F>
+omni_status run_graphed(omni_ctx* ctx, const std::vector<uint64_t>& key, cudaStream_t st, double& stitch_bytes,
+                        F&& chain) {
+  // the legacy default stream cannot be captured: such calls run eagerly
+  const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+  const bool use_graph = ctx->graphs && !ctx->timing && capturable;
+  if (use_graph && ctx->graph_exec && key == ctx->graph_key) {
+    OMNI_CU(cudaGraphLaunch(ctx->graph_exec, st), "graph launch");
+    ctx->launches += ctx->graph_launches;
+    ctx->tiles_done = ctx->graph_tiles;
+    stitch_bytes = ctx->graph_stitch_bytes;
+    return OMNI_OK;
+  }
+  if (use_graph && key == ctx->last_key) {
+    // second call with the same geometry and buffers: capture and replay from now on
+    if (ctx->graph_exec) {
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+    }
+    const int64_t before = ctx->launches;
+    OMNI_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    ctx->capturing = true;
+    omni_status r = chain(stitch_bytes);
+    ctx->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (r) {
+      if (graph) cudaGraphDestroy(graph);
+      return r;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "end capture");
+    const cudaError_t ie = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      ctx->graph_exec = nullptr;
+      return cuda_fail(ctx, ie, "graph instantiate");
+    }
+    ctx->graph_key = key;
+    ctx->graph_launches = ctx->launches - before;
+    ctx->graph_tiles = ctx->tiles_done;
+    ctx->graph_stitch_bytes = stitch_bytes;
+    OMNI_CU(cudaGraphLaunch(ctx->graph_exec, st), "graph launch");
+    return OMNI_OK;
+  }
+  ctx->last_key = key;
+  return chain(stitch_bytes);
 }
 
 omni_status check_ws(omni_ctx* ctx, void* ws, uint64_t bytes, uint64_t need) {
@@ -953,21 +1154,44 @@ omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int
   uint8_t* ws = static_cast<uint8_t*>(ws_);
   ctx->launches = 0;
   ctx->tiles_done = 0;
+  ctx->band_ev_used = 0;
   Prep pr;
   r = run_prep(ctx, rgb, stride, p, ws, st, pr);
   if (r) return r;
   OMNI_CU(cudaMemcpyAsync(ctx->h_counts, ws + p.counts, (size_t)(1 + c.n_scales) * 4, cudaMemcpyDeviceToHost, st),
           "read tile counts");
+  const size_t nflags = (size_t)p.g.grid_off[c.n_scales];
+  if (ctx->h_flags_n < nflags) {
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+    ctx->h_flags = nullptr;
+    ctx->h_flags_n = 0;
+    OMNI_CU(cudaMallocHost(&ctx->h_flags, nflags), "pinned tile flags");
+    ctx->h_flags_n = nflags;
+  }
+  OMNI_CU(cudaMemcpyAsync(ctx->h_flags, ws + p.flags, nflags, cudaMemcpyDeviceToHost, st), "read tile flags");
   OMNI_CU(cudaStreamSynchronize(st), "sync after tiling");
   unsigned herr = 0;
   OMNI_CU(cudaMemcpy(&herr, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
   if (herr) return fail(ctx, OMNI_ETIMEOUT, "a device-side wait gave up in an earlier call");
+  // foreground tiles in rows 0..i of every scale's grid: the band schedule of the stitch
+  std::vector<std::vector<int>> row_end(c.n_scales);
+  for (int s = 0; s < c.n_scales; ++s) {
+    const uint8_t* fl = ctx->h_flags + p.g.grid_off[s];
+    int acc = 0;
+    row_end[s].resize(p.g.gh[s]);
+    for (int i = 0; i < p.g.gh[s]; ++i) {
+      for (int j = 0; j < p.g.gw[s]; ++j) acc += fl[(size_t)i * p.g.gw[s] + j] ? 1 : 0;
+      row_end[s][i] = acc;
+    }
+  }
 
   // ---------------------------------------------------------------- network + stitch
   std::vector<uint64_t> key = {reinterpret_cast<uint64_t>(rgb), (uint64_t)H, (uint64_t)W, (uint64_t)stride,
                                scale_mask, class_mask, reinterpret_cast<uint64_t>(ws_),
                                reinterpret_cast<uint64_t>(st)};
   for (int s = 0; s <= c.n_scales; ++s) key.push_back((uint64_t)ctx->h_counts[s]);
+  for (int s = 0; s < c.n_scales; ++s)
+    for (int v : row_end[s]) key.push_back((uint64_t)v);
   for (int k = 0; k < OMNI_MAX_CLASSES; ++k) {
     key.push_back(reinterpret_cast<uint64_t>(out->labels[k]));
     key.push_back(reinterpret_cast<uint64_t>(out->logits[k]));
@@ -976,49 +1200,13 @@ omni_status omni_segment_slide(omni_ctx* ctx, const uint8_t* rgb, int32_t H, int
     key.push_back(reinterpret_cast<uint64_t>(out->coverage[s]));
     key.push_back(reinterpret_cast<uint64_t>(out->argmax[s]));
   }
+  for (int k = 0; k < OMNI_MAX_CLASSES; ++k)
+    key.push_back(reinterpret_cast<uint64_t>(ctx->host_labels ? ctx->host_labels[k] : nullptr));
   double stitch_bytes = 0;
-  // the legacy default stream cannot be captured: such calls run eagerly
-  const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
-  const bool use_graph = ctx->graphs && !ctx->timing && capturable;
-  if (use_graph && ctx->graph_exec && key == ctx->graph_key) {
-    OMNI_CU(cudaGraphLaunch(ctx->graph_exec, st), "graph launch");
-    ctx->launches += ctx->graph_launches;
-    ctx->tiles_done = ctx->graph_tiles;
-    stitch_bytes = ctx->graph_stitch_bytes;
-  } else if (use_graph && key == ctx->last_key) {
-    // second call with the same geometry and buffers: capture and replay from now on
-    if (ctx->graph_exec) {
-      cudaGraphExecDestroy(ctx->graph_exec);
-      ctx->graph_exec = nullptr;
-    }
-    const int64_t before = ctx->launches;
-    OMNI_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
-    ctx->capturing = true;
-    r = run_network(ctx, c, p, ws, pr, out, H, W, scale_mask, class_mask, st, stitch_bytes);
-    ctx->capturing = false;
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    if (r) {
-      if (graph) cudaGraphDestroy(graph);
-      return r;
-    }
-    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "end capture");
-    const cudaError_t ie = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) {
-      ctx->graph_exec = nullptr;
-      return cuda_fail(ctx, ie, "graph instantiate");
-    }
-    ctx->graph_key = key;
-    ctx->graph_launches = ctx->launches - before;
-    ctx->graph_tiles = ctx->tiles_done;
-    ctx->graph_stitch_bytes = stitch_bytes;
-    OMNI_CU(cudaGraphLaunch(ctx->graph_exec, st), "graph launch");
-  } else {
-    ctx->last_key = key;
-    r = run_network(ctx, c, p, ws, pr, out, H, W, scale_mask, class_mask, st, stitch_bytes);
-    if (r) return r;
-  }
+  r = run_graphed(ctx, key, st, stitch_bytes, [&](double& sb) {
+    return run_network(ctx, c, p, ws, pr, out, H, W, scale_mask, class_mask, row_end, st, sb);
+  });
+  if (r) return r;
   ctx->work[0] += (double)ctx->tiles_done * (double)p.flops_per_tile;
   ctx->work[1] += stitch_bytes;
   return OMNI_OK;
@@ -1039,21 +1227,256 @@ omni_status omni_segment_slide_host(omni_ctx* ctx, const uint8_t* rgb_host, int3
   OMNI_CU(cudaMemcpy2DAsync(ws + p.in, dstride, rgb_host, stride, dstride, H, cudaMemcpyHostToDevice, st),
           "upload slide");
   omni_outputs o{};
+  uint8_t* host[OMNI_MAX_CLASSES] = {};
   for (int k = 0; k < c.n_classes; ++k)
-    if (labels_host[k] && (class_mask >> k & 1u)) o.labels[k] = ws + p.lab[k];
+    if (labels_host[k] && (class_mask >> k & 1u)) {
+      o.labels[k] = ws + p.lab[k];
+      host[k] = labels_host[k];
+    }
+  if (!ctx->copy_st) OMNI_CU(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking), "copy stream");
+  // every label band is downloaded on the copy stream as soon as it is stitched
+  ctx->host_labels = host;
   r = omni_segment_slide(ctx, ws + p.in, H, W, dstride, scale_mask, class_mask, ws_, ws_bytes, &o, stream);
-  if (r) return r;
-  for (int k = 0; k < c.n_classes; ++k) {
-    if (!o.labels[k]) continue;
-    int f = c.factors[c.class_scale[k]];
-    size_t n = (size_t)((H + f - 1) / f) * ((W + f - 1) / f);
-    OMNI_CU(cudaMemcpyAsync(labels_host[k], o.labels[k], n, cudaMemcpyDeviceToHost, st), "download labels");
+  ctx->host_labels = nullptr;
+  if (r) {
+    cudaStreamSynchronize(ctx->copy_st);
+    return r;
   }
   OMNI_CU(cudaStreamSynchronize(st), "sync");
   unsigned herr = 0;
   OMNI_CU(cudaMemcpy(&herr, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
   if (herr) return fail(ctx, OMNI_ETIMEOUT, "a device-side wait gave up");
   return OMNI_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== several slides per call
+namespace {
+
+// Workspace of a multi-slide call: every slide's tile stage (its own plan,
+// laid out from prep_off[i]), the merged tile lists of every scale, then one
+// network stage planned for the largest slide dimensions (its ring holds the
+// widest slide's tile rows).
+struct MultiPlan {
+  int n = 0;
+  Plan sp[OMNI_MAX_SLIDES];
+  size_t prep_off[OMNI_MAX_SLIDES];
+  size_t merged = 0;
+  Plan net;
+  size_t net_base = 0;     // ws + net_base + net.<region> addresses a network region
+  size_t total = 0;
+};
+
+bool make_multi_plan(const omni_config& c, int n, const int32_t* H, const int32_t* W, MultiPlan& m) {
+  if (n < 1 || n > OMNI_MAX_SLIDES) return false;
+  m.n = n;
+  size_t off = 0, ntile = 0;
+  int Hm = 0, Wm = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!make_plan(c, H[i], W[i], m.sp[i])) return false;
+    m.prep_off[i] = off;
+    off += align_up(m.sp[i].tile_end, 256);
+    ntile += (size_t)m.sp[i].g.grid_off[c.n_scales];
+    Hm = std::max(Hm, H[i]);
+    Wm = std::max(Wm, W[i]);
+  }
+  m.merged = off;
+  off = align_up(off + ntile * 3 * 4, 256);
+  if (!make_plan(c, Hm, Wm, m.net)) return false;
+  off = std::max(off, m.net.tile_end);
+  m.net_base = off - m.net.tile_end;
+  m.total = align_up(off + (m.net.net_end - m.net.tile_end), 256);
+  return true;
+}
+
+// merged list entry k = (slide, y, x) of the slide's tile k of one scale
+__global__ void k_merge_tiles(const int32_t* __restrict__ src, int n, int slide, int32_t* __restrict__ dst) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  dst[3 * k] = slide;
+  dst[3 * k + 1] = src[3 * k + 1];
+  dst[3 * k + 2] = src[3 * k + 2];
+}
+
+}  // namespace
+
+extern "C" {
+
+omni_status omni_query_slides(const omni_config* cfg, int32_t n, const int32_t* H, const int32_t* W,
+                              uint64_t* workspace_bytes) {
+  if (!cfg || !H || !W || !workspace_bytes || !validate(*cfg).empty()) return OMNI_EINVAL;
+  MultiPlan m;
+  if (!make_multi_plan(*cfg, n, H, W, m)) return OMNI_EINVAL;
+  *workspace_bytes = m.total;
+  return OMNI_OK;
+}
+
+omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* rgb, const int32_t* H,
+                                const int32_t* W, const int64_t* stride, uint32_t scale_mask,
+                                uint32_t class_mask, void* ws_, uint64_t ws_bytes, const omni_outputs* out,
+                                void* stream) {
+  (void)cudaGetLastError();
+  if (!ctx || !rgb || !H || !W || !stride || !out) return fail(ctx, OMNI_EINVAL, "null argument");
+  if (!ctx->have_weights) return fail(ctx, OMNI_ESTATE, "omni_load_weights has not been called");
+  if (n < 1 || n > OMNI_MAX_SLIDES) return fail(ctx, OMNI_EINVAL, "1..OMNI_MAX_SLIDES slides per call");
+  const omni_config& c = ctx->cfg;
+  for (int i = 0; i < n; ++i) {
+    if (!rgb[i]) return fail(ctx, OMNI_EINVAL, "null slide " + std::to_string(i));
+    if (stride[i] < (int64_t)W[i] * 3) return fail(ctx, OMNI_EINVAL, "row_stride < 3 W for slide " + std::to_string(i));
+  }
+  static thread_local MultiPlan mp;
+  if (!make_multi_plan(c, n, H, W, mp)) return fail(ctx, OMNI_EINVAL, "bad slide size");
+  omni_status r = check_ws(ctx, ws_, ws_bytes, mp.total);
+  if (r) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(ws_);
+  uint8_t* wsn = ws + mp.net_base;
+  ctx->launches = 0;
+  ctx->tiles_done = 0;
+  ctx->band_ev_used = 0;
+  // ---------------------------------------------------------------- every slide's tiling
+  std::vector<Prep> pr(n);
+  size_t nflags = 0;
+  for (int i = 0; i < n; ++i) {
+    r = run_prep(ctx, rgb[i], stride[i], mp.sp[i], ws + mp.prep_off[i], st, pr[i]);
+    if (r) return r;
+    nflags += (size_t)mp.sp[i].g.grid_off[c.n_scales];
+  }
+  if (ctx->h_flags_n < nflags) {
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+    ctx->h_flags = nullptr;
+    ctx->h_flags_n = 0;
+    OMNI_CU(cudaMallocHost(&ctx->h_flags, nflags), "pinned tile flags");
+    ctx->h_flags_n = nflags;
+  }
+  const int ncnt = 1 + c.n_scales;
+  std::vector<size_t> foff(n);
+  for (int i = 0, acc = 0; i < n; ++i) {
+    const Plan& p = mp.sp[i];
+    uint8_t* wp = ws + mp.prep_off[i];
+    foff[i] = (size_t)acc;
+    acc += p.g.grid_off[c.n_scales];
+    OMNI_CU(cudaMemcpyAsync(ctx->h_counts + i * ncnt, wp + p.counts, ncnt * 4, cudaMemcpyDeviceToHost, st),
+            "read tile counts");
+    OMNI_CU(cudaMemcpyAsync(ctx->h_flags + foff[i], wp + p.flags, (size_t)p.g.grid_off[c.n_scales],
+                            cudaMemcpyDeviceToHost, st),
+            "read tile flags");
+  }
+  OMNI_CU(cudaStreamSynchronize(st), "sync after tiling");
+  unsigned herr = 0;
+  OMNI_CU(cudaMemcpy(&herr, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
+  if (herr) return fail(ctx, OMNI_ETIMEOUT, "a device-side wait gave up in an earlier call");
+  // per slide and scale: foreground tiles in grid rows 0..i, and the slide's
+  // offset in the scale's merged list
+  std::vector<std::vector<std::vector<int>>> row_end(n, std::vector<std::vector<int>>(c.n_scales));
+  std::vector<std::array<int, OMNI_MAX_SCALES>> moff(n);
+  std::array<int, OMNI_MAX_SCALES> N{}, soff{};
+  for (int s = 0; s < c.n_scales; ++s) {
+    for (int i = 0; i < n; ++i) {
+      moff[i][s] = N[s];
+      N[s] += ctx->h_counts[i * ncnt + 1 + s];
+      const Plan& p = mp.sp[i];
+      const uint8_t* fl = ctx->h_flags + foff[i] + p.g.grid_off[s];
+      int acc = 0;
+      row_end[i][s].resize(p.g.gh[s]);
+      for (int y = 0; y < p.g.gh[s]; ++y) {
+        for (int x = 0; x < p.g.gw[s]; ++x) acc += fl[(size_t)y * p.g.gw[s] + x] ? 1 : 0;
+        row_end[i][s][y] = acc;
+      }
+    }
+    if (s + 1 < c.n_scales) soff[s + 1] = soff[s] + N[s];
+  }
+  std::vector<uint64_t> key = {0x51u, (uint64_t)n, scale_mask, class_mask, reinterpret_cast<uint64_t>(ws_),
+                               reinterpret_cast<uint64_t>(st)};
+  for (int i = 0; i < n; ++i) {
+    key.insert(key.end(), {reinterpret_cast<uint64_t>(rgb[i]), (uint64_t)H[i], (uint64_t)W[i], (uint64_t)stride[i]});
+    for (int q = 0; q < ncnt; ++q) key.push_back((uint64_t)ctx->h_counts[i * ncnt + q]);
+    for (int s = 0; s < c.n_scales; ++s)
+      for (int v : row_end[i][s]) key.push_back((uint64_t)v);
+    for (int k = 0; k < OMNI_MAX_CLASSES; ++k) {
+      key.push_back(reinterpret_cast<uint64_t>(out[i].labels[k]));
+      key.push_back(reinterpret_cast<uint64_t>(out[i].logits[k]));
+    }
+    for (int s = 0; s < OMNI_MAX_SCALES; ++s) {
+      key.push_back(reinterpret_cast<uint64_t>(out[i].coverage[s]));
+      key.push_back(reinterpret_cast<uint64_t>(out[i].argmax[s]));
+    }
+  }
+  for (int e = 0; e <= n; ++e)
+    if (!ctx->slide_ev[e]) OMNI_CU(cudaEventCreate(&ctx->slide_ev[e]), "slide event");
+  ctx->slide_n = n;
+  int last_scale = -1;
+  for (int s = 0; s < c.n_scales; ++s) {
+    int cls[OMNI_MAX_CLASSES];
+    if ((scale_mask >> s & 1u) && classes_at(c, s, class_mask, cls) > 0) last_scale = s;
+  }
+  int32_t* merged = reinterpret_cast<int32_t*>(ws + mp.merged);
+  // ---------------------------------------------------------------- network over the merged lists
+  auto chain = [&](double& sb) -> omni_status {
+    OMNI_CU(cudaEventRecord(ctx->slide_ev[0], st), "slide event");
+    for (int s = 0; s < c.n_scales; ++s) {
+      int cls[OMNI_MAX_CLASSES];
+      const int ncls = classes_at(c, s, class_mask, cls);
+      if (!(scale_mask >> s & 1u) || ncls == 0) continue;
+      int32_t* ms = merged + 3 * (size_t)soff[s];
+      CanvasTab cv{};
+      std::vector<Bands> bands;
+      for (int i = 0; i < n; ++i) {
+        const Plan& p = mp.sp[i];
+        const int n_is = ctx->h_counts[i * ncnt + 1 + s];
+        cv.ptr[i] = pr[i].c[s];
+        cv.stride[i] = pr[i].cs[s];
+        cv.rows[i] = pr[i].ch[s];
+        if (n_is > 0) {
+          // the slide's list holds its scales in order: scale s starts after the earlier scales' tiles
+          const int32_t* src = reinterpret_cast<const int32_t*>(ws + mp.prep_off[i] + p.tiles);
+          int before = 0;
+          for (int q = 0; q < s; ++q) before += ctx->h_counts[i * ncnt + 1 + q];
+          k_merge_tiles<<<(n_is + 255) / 256, 256, 0, st>>>(src + 3 * (size_t)before, n_is, i, ms + 3 * (size_t)moff[i][s]);
+          OMNI_CU(cudaGetLastError(), "merge tiles");
+          ctx->launches++;
+        }
+        bands.push_back(make_bands(ctx, c, p, ws + mp.prep_off[i], wsn, mp.net, &out[i], H[i], W[i], s, cls, ncls,
+                                   n_is, moff[i][s], row_end[i][s], sb));
+      }
+      const int cap = mp.net.cap[s];
+      for (int start = 0; start < N[s]; start += c.max_batch) {
+        const int nb = std::min(c.max_batch, N[s] - start);
+        omni_status rr = run_batch(ctx, mp.net, wsn, s, cv, ms + 3 * (size_t)start, nb, start % cap, ncls, cls, st);
+        if (rr) return rr;
+        // stitch every band that became final in the slides this batch touched
+        for (int i = 0; i < n; ++i) {
+          const int lo = moff[i][s], n_is = ctx->h_counts[i * ncnt + 1 + s];
+          if (n_is == 0 || lo >= start + nb || lo + n_is <= start) continue;
+          rr = bands[i].advance(ctx, std::min(start + nb - lo, n_is), st);
+          if (rr) return rr;
+        }
+      }
+      for (int i = 0; i < n; ++i) {
+        omni_status rr = bands[i].finish(ctx, st);
+        if (rr) return rr;
+        if (s == last_scale) OMNI_CU(cudaEventRecord(ctx->slide_ev[1 + i], st), "slide event");
+      }
+      ctx->tiles_done += N[s];
+    }
+    return OMNI_OK;
+  };
+  double stitch_bytes = 0;
+  r = run_graphed(ctx, key, st, stitch_bytes, chain);
+  if (r) return r;
+  ctx->work[0] += (double)ctx->tiles_done * (double)mp.net.flops_per_tile;
+  ctx->work[1] += stitch_bytes;
+  return OMNI_OK;
+}
+
+int32_t omni_get_slide_times(omni_ctx* ctx, int32_t max, float* ms) {
+  if (!ctx || !ms || ctx->slide_n < 1) return -1;
+  const int n = std::min<int>(max, ctx->slide_n);
+  if (cudaEventSynchronize(ctx->slide_ev[ctx->slide_n]) != cudaSuccess) return -1;
+  for (int i = 0; i < n; ++i)
+    if (cudaEventElapsedTime(ms + i, ctx->slide_ev[0], ctx->slide_ev[1 + i]) != cudaSuccess) return -1;
+  return n;
 }
 
 omni_status omni_synth_slide(const int64_t* ell, int32_t n_ell, uint64_t seed, int32_t slide_w, int32_t y0,
@@ -1189,26 +1612,21 @@ int64_t omni_last_launch_count(const omni_ctx* ctx) { return ctx ? ctx->launches
 omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled) {
   if (!ctx) return OMNI_EINVAL;
   ctx->autotune = enabled != 0;
+  drop_graph(ctx);
   return OMNI_OK;
 }
 
 omni_status omni_set_graphs(omni_ctx* ctx, int32_t enabled) {
   if (!ctx) return OMNI_EINVAL;
   ctx->graphs = enabled != 0;
-  if (!ctx->graphs && ctx->graph_exec) {
-    cudaGraphExecDestroy(ctx->graph_exec);
-    ctx->graph_exec = nullptr;
-  }
-  ctx->last_key.clear();
-  ctx->graph_key.clear();
+  drop_graph(ctx);
   return OMNI_OK;
 }
 
 omni_status omni_set_fusion(omni_ctx* ctx, int32_t enabled) {
   if (!ctx) return OMNI_EINVAL;
   ctx->fuse = enabled != 0;
-  ctx->last_key.clear();
-  ctx->graph_key.clear();
+  drop_graph(ctx);
   return OMNI_OK;
 }
 
@@ -1278,8 +1696,10 @@ cudaError_t scratch_address(void** out) {
 }
 
 // Thumbnail grey straight from the caller's slide: one warp per 32x32 block of
-// the padded 40x canvas, lane = block row; canvas pixels outside the slide take
-// the 2x2-mean pad colour, so no padded copy of the slide is needed.
+// the padded 40x canvas, lane = column inside the block, the warp walking the
+// block's 32 rows so each row read is 96 contiguous bytes; canvas pixels
+// outside the slide take the 2x2-mean pad colour, so no padded copy of the
+// slide is needed.
 __global__ void k_thumb_direct(const uint8_t* __restrict__ rgb, long long stride, SlideGeom g,
                                uint8_t* __restrict__ grey) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -1291,11 +1711,12 @@ __global__ void k_thumb_direct(const uint8_t* __restrict__ rgb, long long stride
     int s = rgb[c] + rgb[w2 * 3 + c] + rgb[(long long)h2 * stride + c] + rgb[(long long)h2 * stride + w2 * 3 + c];
     pad[c] = (s + 2) >> 2;
   }
-  const int y = ty * kThumb + lane - g.lead;
+  const int x = tx * kThumb + lane - g.lead;
+  const bool xin = x >= 0 && x < g.W;
   int sum[3] = {0, 0, 0};
   for (int q = 0; q < kThumb; ++q) {
-    const int x = tx * kThumb + q - g.lead;
-    if (y >= 0 && y < g.H && x >= 0 && x < g.W) {
+    const int y = ty * kThumb + q - g.lead;
+    if (xin && y >= 0 && y < g.H) {
       const uint8_t* p = rgb + (long long)y * stride + (long long)x * 3;
       sum[0] += p[0]; sum[1] += p[1]; sum[2] += p[2];
     } else {
@@ -1317,6 +1738,7 @@ extern "C" omni_status omni_tile_slide_noalloc(const omni_config* cfg, const uin
                                                void* stream) {
   if (!cfg || !rgb || !out || !out->tiles || !out->counts) return OMNI_EINVAL;
   if (!validate(*cfg).empty() || stride < (int64_t)W * 3) return OMNI_EINVAL;
+  (void)cudaGetLastError();   // a launch error left by an earlier, unrelated call is not this call's
   Plan p;
   if (!make_plan(*cfg, H, W, p)) return OMNI_EINVAL;
   const SlideGeom& g = p.g;
@@ -1381,8 +1803,8 @@ bool make_bwd_plan(const omni_config& c, int H, int W, BwdPlan& b) {
     const int f = c.factors[s];
     b.cov[s] = take(off, (size_t)((H + f - 1) / f) * ((W + f - 1) / f) * 2);
   }
-  b.loss_partial = take(off, (size_t)OMNI_MAX_CLASSES * loss_blocks() * 4 * 8);
-  b.sums = take(off, (size_t)OMNI_MAX_CLASSES * 4 * 8);
+  b.loss_partial = take(off, (size_t)OMNI_MAX_CLASSES * loss_blocks() * 4 * 4);
+  b.sums = take(off, (size_t)OMNI_MAX_CLASSES * 4 * 4);
   b.cls_ids = take(off, OMNI_MAX_CLASSES * 4);
   const size_t npx = (size_t)c.max_batch * c.patch * c.patch;
   const size_t fc = npx * C0 * 4;
@@ -1408,15 +1830,17 @@ bool make_bwd_plan(const omni_config& c, int H, int W, BwdPlan& b) {
   return true;
 }
 
-// [o][tap][c] (FP64 accumulation order) -> [o][c][tap] (blob order), FP32
-__global__ void k_w_to_blob(const double* __restrict__ acc, int O, int cin, int taps, float* __restrict__ out) {
+// [o][tap][c] (accumulation order, compensated (sum, carry) pairs) ->
+// [o][c][tap] (blob order), FP32
+__global__ void k_w_to_blob(const float2* __restrict__ acc, int O, int cin, int taps, float* __restrict__ out) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long n = (long long)O * cin * taps;
   if (i >= n) return;
   const int o = (int)(i / ((long long)cin * taps));
   const int rem = (int)(i % ((long long)cin * taps));
   const int c = rem / taps, t = rem % taps;
-  out[i] = (float)acc[(long long)o * cin * taps + (long long)t * cin + c];
+  const float2 a = acc[(long long)o * cin * taps + (long long)t * cin + c];
+  out[i] = a.x - a.y;
 }
 
 }  // namespace
@@ -1450,7 +1874,7 @@ extern "C" omni_status omni_backward(omni_ctx* ctx, const uint8_t* rgb, int32_t 
   const int L = c.levels, C0 = widths(c, 0), Cb = widths(c, L - 1), P = c.patch;
   const long long PP = (long long)P * P;
   auto F = [&](size_t o) { return reinterpret_cast<float*>(ws + o); };
-  auto D = [&](size_t o) { return reinterpret_cast<double*>(ws + o); };
+  auto D = [&](size_t o) { return reinterpret_cast<float2*>(ws + o); };   // compensated accumulators
 
   // ---------------------------------------------------------------- pass 1: forward
   omni_outputs fo{};
@@ -1465,12 +1889,12 @@ extern "C" omni_status omni_backward(omni_ctx* ctx, const uint8_t* rgb, int32_t 
   for (int k = 0; k < c.n_classes; ++k) {
     const int f = c.factors[c.class_scale[k]];
     npix.n[k] = (long long)((H + f - 1) / f) * ((W + f - 1) / f);
-    OMNI_CU(launch_loss_partial(F(bp.lg[k]), gt_dev[k], npix.n[k], D(bp.loss_partial) + (size_t)k * loss_blocks() * 4, st),
+    OMNI_CU(launch_loss_partial(F(bp.lg[k]), gt_dev[k], npix.n[k], F(bp.loss_partial) + (size_t)k * loss_blocks() * 4, st),
             "loss partial");
   }
-  OMNI_CU(launch_loss_final(D(bp.loss_partial), c.n_classes, npix, D(bp.sums), loss_dev, st), "loss");
+  OMNI_CU(launch_loss_final(F(bp.loss_partial), c.n_classes, npix, F(bp.sums), loss_dev, st), "loss");
   for (int k = 0; k < c.n_classes; ++k)
-    OMNI_CU(launch_loss_grad(F(bp.lg[k]), gt_dev[k], npix.n[k], D(bp.sums) + 4 * k, (double)npix.n[k],
+    OMNI_CU(launch_loss_grad(F(bp.lg[k]), gt_dev[k], npix.n[k], F(bp.sums) + 4 * k, (float)npix.n[k],
                              c.n_classes, F(bp.dl[k]), st),
             "loss grad");
   OMNI_CU(cudaMemsetAsync(ws + bp.acc_wc, 0, bp.total - bp.acc_wc, st), "clear accumulators");
@@ -1496,7 +1920,7 @@ extern "C" omni_status omni_backward(omni_ctx* ctx, const uint8_t* rgb, int32_t 
       const int nb = std::min(c.max_batch, n_s - start);
       const int32_t* t3 = tiles + 3 * (toff + start);
       const long long npx = (long long)nb * PP;
-      r = run_batch(ctx, p, ws, s, pr.c[s], pr.cs[s], pr.ch[s], t3, nb, start, ncls, cls, st, true);
+      r = run_batch(ctx, p, ws, s, one_canvas(pr, s), t3, nb, start, ncls, cls, st, true);
       if (r) return r;
       void* cat0 = ws + p.cat[0];
       ConvArgs a{};
