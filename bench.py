@@ -217,16 +217,21 @@ def run_ragged(args, api, _lib, dev, prec):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         per = []
+        slide_err = None
         with Clocks(0) as clk:
             e0.record()
             for _ in range(args.steps):
                 seg.segment_many(rgbs, outs=outs)
-                per.append(seg.slide_times(len(works)))
+                try:
+                    per.append(seg.slide_times(len(works)))
+                except RuntimeError as exc:      # reported, not fatal to the throughput line
+                    per.append(None)
+                    slide_err = str(exc)
             e1.record()
             torch.cuda.synchronize()
     total_ms = e0.elapsed_time(e1) / args.steps
     mpx = sum(w.H * w.W for w in works) / 1e6
-    lat = np.mean(np.array([p for p in per if p]), axis=0) if any(per) else None
+    lat = np.mean(np.array([p for p in per if p]), axis=0) if any(p for p in per) else None
     print(json.dumps({"metric": "ragged 12-slide segmentation Mpx/s", "value": mpx / (total_ms / 1e3),
                       "unit": "Mpx/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": total_ms, "higher_is_better": True, "dtype": args.precision,
@@ -236,6 +241,7 @@ def run_ragged(args, api, _lib, dev, prec):
                                              "share batches; one CUDA graph after tiling)",
                                  "slides": [[w.H, w.W, round(w.tissue, 3)] for w in works]},
                       "per_slide_done_ms": None if lat is None else [round(float(v), 2) for v in lat],
+                      "per_slide_error": slide_err,
                       "clocks": clk.summary()}))
     seg.close()
 
@@ -431,6 +437,7 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="one slide step after the tuning call, bracketed by cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
+    ap.add_argument("--max-batch", type=int, default=0, help="tiles per network batch (0: the workload's)")
     ap.add_argument("--layer", default=None,
                     help="R,cin,cout,cr,B,repeat: time one fused conv layer instead")
     args = ap.parse_args()
@@ -469,7 +476,7 @@ def main():
     spec = synth.spec_for(work)
     rgb = api.synth_slide(spec, device=dev)
     blob = synth.gen_weights(work)
-    seg = api.Segmenter(work, blob, precision=prec)
+    seg = api.Segmenter(work, blob, precision=prec, max_batch=args.max_batch or None)
     if prec != _lib.FP32 and not args.no_autotune:
         seg.set_autotune(True)          # the first (untimed) call tunes every conv shape
     out = seg.segment(rgb)
@@ -494,27 +501,50 @@ def main():
     for _ in range(args.warmup):
         seg.segment(rgb, out=out)
     barrier()
+    # eager steps with per-launch CUDA events (the library records them on the
+    # launching stream): per-layer breakdown, conv roofline, stitch bandwidth
+    n_inst = max(1, min(args.steps, 3))
     seg.set_timing(True)
-    launches = 0
-    with Clocks(local) as clk:
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        barrier()
-        t0.record()
-        for _ in range(args.steps):
-            seg.segment(rgb, out=out)
-            launches += seg.launch_count()
-        t1.record()
-        barrier()
-    clocks = clk.summary()
+    i0 = torch.cuda.Event(enable_timing=True)
+    i1 = torch.cuda.Event(enable_timing=True)
+    i0.record()
+    for _ in range(n_inst):
+        seg.segment(rgb, out=out)
+    i1.record()
+    barrier()
     conv_ms, conv_n, conv_flops = seg.timing(0)
     st_ms, _, st_bytes = seg.timing(1)
     ms_l, kinds_l, tags_l, work_l = seg.launch_times()
     seg.set_timing(False)
-    ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, device=dev)
+    eager_ms = i0.elapsed_time(i1) / n_inst
     mpx = work.H * work.W / 1e6
+    breakdown = summarize(ms_l, tags_l, work_l, n_inst)
+
+    # the timed steps: tiling, then the network and stitch replayed from the
+    # CUDA graph the library captured on the second call (on a created stream;
+    # the legacy default stream cannot be captured)
+    seg.set_graphs(True)
+    gstream = torch.cuda.Stream()
+    gstream.wait_stream(torch.cuda.current_stream())
+    launches = 0
+    with torch.cuda.stream(gstream):
+        for _ in range(2 + args.warmup):
+            seg.segment(rgb, out=out)      # key, capture, then W warm-up replays
+        barrier()
+        with Clocks(local) as clk:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            barrier()
+            t0.record()
+            for _ in range(args.steps):
+                seg.segment(rgb, out=out)
+                launches += seg.launch_count()
+            t1.record()
+            barrier()
+    seg.set_graphs(False)
+    clocks = clk.summary()
+    ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, device=dev)
     value = whole_job_value(mpx, ms_step, world)
-    breakdown = summarize(ms_l, tags_l, work_l, args.steps)
 
     pk, src = peaks()
     if prec != _lib.FP32:
@@ -526,8 +556,8 @@ def main():
         bound, peak_note = "alu", "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock"
     conv_per_launch_ms = conv_ms / max(conv_n, 1)
     achieved = (conv_flops / max(conv_n, 1)) / (conv_per_launch_ms / 1e3) / 1e12
-    tiles_step = int(round(conv_flops / max(args.steps, 1) / seg.query(work.H, work.W).flops_per_tile))
-    traffic, traffic_step = conv_traffic(prec == _lib.BF16, tiles_step, conv_n / args.steps)
+    tiles_step = int(round(conv_flops / n_inst / seg.query(work.H, work.W).flops_per_tile))
+    traffic, traffic_step = conv_traffic(prec == _lib.BF16, tiles_step, conv_n / n_inst)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": "conv (all U-Net layers)",
             "peak_source": peak_note,
@@ -535,28 +565,12 @@ def main():
                              "2048x8192 slice scaled by foreground tiles" if traffic else
                              "no ncu counters for this conv build / precision"),
             "traffic_per_step": traffic_step,
-            "share_of_step": conv_ms / args.steps / ms_step}
+            "share_of_step": conv_ms / n_inst / eager_ms}
     stitch = {"achieved_gbs": st_bytes / (st_ms / 1e3) / 1e9 if st_ms else None,
-              "peak_gbs": pk["hbm_gbs"], "ms_per_step": st_ms / args.steps}
+              "peak_gbs": pk["hbm_gbs"], "ms_per_step": st_ms / n_inst}
 
-    # the same steps replayed from a captured CUDA graph (library timing off)
-    seg.set_graphs(True)
-    gstream = torch.cuda.Stream()          # the legacy default stream cannot be captured
-    gstream.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(gstream):
-        for _ in range(2):
-            seg.segment(rgb, out=out)      # second call captures
-        barrier()
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        g0.record()
-        for _ in range(args.steps):
-            seg.segment(rgb, out=out)
-        g1.record()
-        barrier()
-    graph = {"value": mpx * world / (g0.elapsed_time(g1) / args.steps / 1e3), "unit": "Mpx/s",
-             "ms_per_step": g0.elapsed_time(g1) / args.steps}
-    seg.set_graphs(False)
+    eager = {"value": mpx * world / (eager_ms / 1e3), "unit": "Mpx/s", "ms_per_step": eager_ms,
+             "steps": n_inst, "note": "eager launches with per-launch events (breakdown, roofline)"}
 
     # the stained 40x product and its 10x resize (Sec. 2.3), one HBM pass
     fac = {c: work.factors[s] for c, s in enumerate(work.class_scale)}
@@ -629,7 +643,7 @@ def main():
                            "parallelism": f"replicas x{world}",
                            "tiles_per_step": tiles_step},
                 "roofline": roof, "stitch": stitch, "stain": stain, "e2e": e2e, "gpu_launches": int(launches),
-                "breakdown": breakdown, "graph_replay": graph,
+                "breakdown": breakdown, "eager": eager,
                 "autotuned": tuned_rows,
                 "clocks": clocks}
         if fp32 is not None:

@@ -271,18 +271,21 @@ omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* 
                                 uint32_t class_mask, void* workspace_dev, uint64_t workspace_bytes,
                                 const omni_outputs* out, void* stream);
 /* Completion time of every slide of the last omni_segment_slides call, in ms
- * after the start of its post-tiling chain (CUDA events recorded on its
- * stream, also inside a replayed graph): writes min(max, n) values and returns
- * that count, or -1.  Synchronises on the last slide's event. */
+ * after the start of its post-tiling chain: the chain writes the device clock
+ * (%globaltimer) at its start and after each slide's last stitch band, also
+ * when replayed from a graph.  Writes min(max, n) values and returns that
+ * count, or -1.  Waits for the chain to finish. */
 int32_t omni_get_slide_times(omni_ctx* ctx, int32_t max, float* ms);
 
 /* Seeded synthetic slide window (input generator, not part of the method):
  * pixel (y, x) of a slide_w-wide slide drawn from `n_ell` rotated ellipses
  * (int64 rows cy, cx, a, b, cos_q14, sin_q14) and SplitMix64 noise seeded
- * with `seed`; writes rows y0..y0+h-1, cols x0..x0+w-1 to out_dev. */
+ * with `seed`; with `structures` != 0 the tissue also holds sharp-edged
+ * discs on a 512-pixel cell grid (needle-biopsy cores); writes rows
+ * y0..y0+h-1, cols x0..x0+w-1 to out_dev. */
 omni_status omni_synth_slide(const int64_t* ellipses_host, int32_t n_ell, uint64_t seed,
-                             int32_t slide_w, int32_t y0, int32_t x0, int32_t h, int32_t w,
-                             uint8_t* out_dev, int64_t row_stride, void* stream);
+                             int32_t structures, int32_t slide_w, int32_t y0, int32_t x0, int32_t h,
+                             int32_t w, uint8_t* out_dev, int64_t row_stride, void* stream);
 
 /* Building block for layer-level checks: one fused residual-U-Net convolution
  * y = ReLU(g * conv3x3(x) + b [+ wp . r]) on B images of R x R pixels, with the

@@ -763,6 +763,55 @@ class DiffProblem:
     def params(self) -> Dict[str, torch.Tensor]:
         return {k: self.p[k].clone() for k in GRAD_PARAMS}
 
+    def loss_and_grads_by_batch(self):
+        """The same loss and gradient as loss_and_grads, one batch of tiles in
+        memory at a time: the chain rule through the overlap average written
+        out.  Pass 1 (no autograd) stitches every class's logits and takes
+        G = dloss/dL; pass 2 recomputes each batch's tile logits l_p with
+        autograd and back-propagates sum_p sum_x G(x) l_p(x) / cov(x), which
+        has the batch's share of the gradient."""
+        work = self.work
+        q = {k: v.clone().requires_grad_(True) for k, v in self.params().items()}
+        Hp, Wp, P = self.prep["Hp"], self.prep["Wp"], work.P
+        acc, cov = {}, {}
+        for c, s in enumerate(work.class_scale):
+            f = work.factors[s]
+            acc[c] = torch.zeros((Hp // f, Wp // f), dtype=F64)
+            cov[c] = torch.zeros((Hp // f, Wp // f), dtype=F64)
+
+        def batch_logits(p, s, cat0, g):
+            h0 = prehead(res_block(cat0, p, "dec0"), p)
+            return {c: dynamic_head(h0, controller(g, c, s, p, work.n_classes, work.n_scales))
+                    for c in [c for c, cs in enumerate(work.class_scale) if cs == s]}
+
+        p = dict(self.p)
+        p.update({k: v.detach() for k, v in q.items()})
+        with torch.no_grad():
+            for (s, chunk, cat0, g) in self.cache:
+                for c, lg in batch_logits(p, s, cat0, g).items():
+                    for bi, (y, x) in enumerate(chunk):
+                        acc[c][y:y + P, x:x + P] += lg[bi]
+                        cov[c][y:y + P, x:x + P] += 1.0
+        Ls = {c: torch.where(cov[c] > 0, acc[c] / torch.clamp(cov[c], min=1.0),
+                             torch.zeros_like(acc[c])).requires_grad_(True) for c in acc}
+        total = torch.zeros((), dtype=F64)
+        for c in range(work.n_classes):
+            H, W = self.gts[c].shape
+            total = total + dice_bce(Ls[c][:H, :W], self.gts[c])
+        total = total / work.n_classes
+        total.backward()
+        G = {c: torch.where(cov[c] > 0, Ls[c].grad / torch.clamp(cov[c], min=1.0), torch.zeros_like(cov[c]))
+             for c in Ls}
+        p = dict(self.p)
+        p.update(q)
+        for (s, chunk, cat0, g) in self.cache:
+            part = torch.zeros((), dtype=F64)
+            for c, lg in batch_logits(p, s, cat0, g).items():
+                for bi, (y, x) in enumerate(chunk):
+                    part = part + (G[c][y:y + P, x:x + P] * lg[bi]).sum()
+            part.backward()
+        return float(total.detach()), {k: v.grad.detach().clone() for k, v in q.items()}
+
     def loss_and_grads(self):
         q = {k: v.clone().requires_grad_(True) for k, v in self.params().items()}
         L = self.loss(q)

@@ -92,7 +92,7 @@ def lib() -> C.CDLL:
                                      C.POINTER(Outputs), vp]),
         "omni_segment_slide_host": (i32, [vp, vp, i32, i32, i64, u32, u32, vp, u64,
                                           C.POINTER(vp), vp]),
-        "omni_synth_slide": (i32, [vp, i32, u64, i32, i32, i32, i32, i32, vp, i64, vp]),
+        "omni_synth_slide": (i32, [vp, i32, u64, i32, i32, i32, i32, i32, i32, vp, i64, vp]),
         "omni_stain": (i32, [vp, i32, i32, i64, i32, C.POINTER(vp), vp, vp, vp, vp, i64, i32, vp,
                              i64, vp]),
         "omni_conv_layer": (i32, [i32, i32, i32, i32, i32, vp, i32, i32, vp, vp, vp, vp, i32,

@@ -204,7 +204,10 @@ class Segmenter:
         """Per-slide completion times (ms) of the last segment_many call."""
         ms = np.zeros(n, np.float32)
         got = self.lib.omni_get_slide_times(self.ctx, n, ms.ctypes.data_as(C.c_void_p))
-        return ms[:got].tolist() if got > 0 else None
+        if got <= 0:
+            raise L.OmniError(L.ECUDA, "omni_get_slide_times returned %d (%s)"
+                              % (got, self.lib.omni_last_error(self.ctx).decode()))
+        return ms[:got].tolist()
 
     def segment_host(self, rgb_host: torch.Tensor, labels_host: Dict[int, torch.Tensor],
                      device="cuda") -> Dict[int, torch.Tensor]:
@@ -423,8 +426,8 @@ def synth_slide(spec, y0: int = 0, x0: int = 0, h: Optional[int] = None,
         out = torch.empty((h, w, 3), dtype=torch.uint8, device=device)
     ell = np.ascontiguousarray(spec.as_int_array(), dtype=np.int64)
     st = L.lib().omni_synth_slide(ell.ctypes.data_as(C.c_void_p), ell.shape[0],
-                                  C.c_uint64(spec.seed & 0xFFFFFFFFFFFFFFFF), spec.W, y0, x0, h, w,
-                                  _ptr(out), out.stride(0), _stream())
+                                  C.c_uint64(spec.seed & 0xFFFFFFFFFFFFFFFF), int(spec.structures), spec.W,
+                                  y0, x0, h, w, _ptr(out), out.stride(0), _stream())
     L.check(st, None, "omni_synth_slide failed")
     return out
 

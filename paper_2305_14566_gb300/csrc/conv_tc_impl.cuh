@@ -199,6 +199,78 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Two / three / four 16-column loads issued back to back before a single
+// completion wait: the TMEM read latency is paid once per group instead of once
+// per load (the epilogues are otherwise bound by those serial waits).
+__device__ __forceinline__ void tmem_ld16x2(uint32_t t0, uint32_t t1, float a[16], float b[16]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(t0), "r"(t1)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[16 + i]);
+  }
+}
+__device__ __forceinline__ void tmem_ld16x3(uint32_t t0, uint32_t t1, uint32_t t2, float a[16], float b[16],
+                                            float c[16]) {
+  uint32_t r[48];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%48];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%49];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%50];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+      : "r"(t0), "r"(t1), "r"(t2)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[16 + i]);
+    c[i] = __uint_as_float(r[32 + i]);
+  }
+}
+__device__ __forceinline__ void tmem_ld16x4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3, float a[16],
+                                            float b[16], float c[16], float d[16]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(t0), "r"(t1), "r"(t2), "r"(t3)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[16 + i]);
+    c[i] = __uint_as_float(r[32 + i]);
+    d[i] = __uint_as_float(r[48 + i]);
+  }
+}
+
 __device__ __forceinline__ float norm_u8(uint8_t u) { return 2.0f * (float)u / 255.0f - 1.0f; }
 
 // Dynamic head of one class on the pre-head feature h0 (already through its
@@ -545,8 +617,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll 1
       for (int c = c_beg; c < c_end; c += 16) {
         float a[16], r[16];
-        tmem_ld16(tb + c, a);
-        if constexpr (RES) tmem_ld16(tb + BN + c, r);
+        if constexpr (RES) tmem_ld16x2(tb + c, tb + BN + c, a, r);
+        else tmem_ld16(tb + c, a);
         uint32_t packed[8];
 #pragma unroll
         for (int j = 0; j < 16; j += 2) {
@@ -872,8 +944,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll 1
       for (int c = c_beg; c < c_end; c += 16) {
         float a[16], r[16], o16[16];
-        tmem_ld16(tb + c, a);
-        if constexpr (RES) tmem_ld16(tb + BN + c, r);
+        if constexpr (RES) tmem_ld16x2(tb + c, tb + BN + c, a, r);
+        else tmem_ld16(tb + c, a);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = c + j;
@@ -1227,10 +1299,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll 1
       for (int c = co_beg; c < co_end; c += 16) {
         float d0[16], d1[16], d2[16], r[16], o16[16];
-        tmem_ld16(tb + c, d0);                   // dx = 0 block
-        tmem_ld16(tb + CO + c, d1);              // dx = 1 block
-        tmem_ld16(tb + 2 * CO + c, d2);          // dx = 2 block
-        if constexpr (RES) tmem_ld16(tb + Cfg::kN + c, r);
+        // dx = 0, 1, 2 blocks (and the projection) in one TMEM read group
+        if constexpr (RES) tmem_ld16x4(tb + c, tb + CO + c, tb + 2 * CO + c, tb + Cfg::kN + c, d0, d1, d2, r);
+        else tmem_ld16x3(tb + c, tb + CO + c, tb + 2 * CO + c, d0, d1, d2);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = c + j;
@@ -1316,8 +1387,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 // pipeline's type.
 //   warps 0-7  builders in two groups of four (group g builds the CTA's
 //              tiles g, g + 2, ...: two tiles in flight), warp 8 MMA issuer +
-//              TMEM owner, warps 9-12 epilogue (lane quarters 1, 2, 3, 0),
-//              warp 13 TMA producer of the raw windows.
+//              TMEM owner, warps 9-16 epilogue in two groups of four taking
+//              alternate tiles (lane quarters 1, 2, 3, 0 in each group),
+//              warp 17 TMA producer of the raw windows.
 __host__ __device__ constexpr uint32_t idesc_f16_ops(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
@@ -1327,8 +1399,9 @@ __device__ __forceinline__ uint32_t pack2_f16(float a, float b) {
 }
 constexpr int kFirstGroups = 2;                           // builder groups, 128 threads each
 constexpr int kFirstBuilders = 128 * kFirstGroups;
-constexpr int kThreadsFirst = kFirstBuilders + 32 + 128 + 32;
-constexpr int kFirstMmaWarp = kFirstBuilders / 32, kFirstProducerWarp = kFirstMmaWarp + 5;
+constexpr int kFirstEpiGroups = 2;                         // epilogue warpgroups, alternate tiles
+constexpr int kThreadsFirst = kFirstBuilders + 32 + 128 * kFirstEpiGroups + 32;
+constexpr int kFirstMmaWarp = kFirstBuilders / 32, kFirstProducerWarp = kFirstMmaWarp + 1 + 4 * kFirstEpiGroups;
 constexpr int kFirstStages = 8;
 static_assert(kFirstStages % kFirstGroups == 0, "builder group g owns the ring slots s = g (mod groups)");
 constexpr int kFirstRowBytes = 64;                        // 32 K values x 2 bytes
@@ -1519,12 +1592,16 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
     }
   } else {
     // ------------------------------------------------------------------ epilogue
+    // two warpgroups take alternate tiles, so one group's TMEM read and stores
+    // overlap the other's; warp w of a group reads lane quarter w % 4
     const int q = warp & 3;
     const int row = q * 32 + lane;
+    const int grp = (warp - kFirstMmaWarp - 1) / 4;
     int tcount = 0;
     TileWalk tw;
     tw.init(p.R / kHTH, p.R / kHTW);
     for (; tw.t < p.n_tiles; tw.next(), ++tcount) {
+      if ((tcount & 1) != grp) continue;
       const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
@@ -1533,17 +1610,22 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
       const long long m = (long long)tw.img * RR + (long long)hh * p.R + ww;
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
 #pragma unroll
-      for (int c = 0; c < CO; c += 16) {
-        float a[16];
-        tmem_ld16(tb + c, a);
-        uint32_t packed[8];
+      for (int c = 0; c < CO; c += 32) {
+        float a2[2][16];
+        tmem_ld16x2(tb + c, tb + c + 16, a2[0], a2[1]);   // 32 columns, one wait
 #pragma unroll
-        for (int j = 0; j < 16; j += 2)
-          packed[j / 2] = pack2(fmaxf(fmaf(sg[c + j], a[j], sb[c + j]), 0.f),
-                                fmaxf(fmaf(sg[c + j + 1], a[j + 1], sb[c + j + 1]), 0.f));
-        uint4* dst = reinterpret_cast<uint4*>(p.y + m * p.y_cs + p.y_co + c);
-        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        for (int h = 0; h < 2; ++h) {
+          const int cc = c + 16 * h;
+          const float* a = a2[h];
+          uint32_t packed[8];
+#pragma unroll
+          for (int j = 0; j < 16; j += 2)
+            packed[j / 2] = pack2(fmaxf(fmaf(sg[cc + j], a[j], sb[cc + j]), 0.f),
+                                  fmaxf(fmaf(sg[cc + j + 1], a[j + 1], sb[cc + j + 1]), 0.f));
+          uint4* dst = reinterpret_cast<uint4*>(p.y + m * p.y_cs + p.y_co + cc);
+          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
       }
       tc_fence_before();
       __syncwarp();

@@ -359,6 +359,8 @@ __global__ void __launch_bounds__(128) k_upsample(int Ri, int C, const T* __rest
     top0[q] = 0.75f * pa[q] + 0.25f * pb[q];
     bot0[q] = 0.25f * pa[q] + 0.75f * pb[q];
   }
+  // unrolled: the next columns' loads issue before this column's stores
+#pragma unroll 4
   for (int l = l_beg; l < l_end; ++l) {
     const int ln = min(l + 1, Ri - 1);
     Vec8<T>::load(xa + (long long)ln * x_cs, ca);

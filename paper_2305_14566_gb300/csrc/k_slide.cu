@@ -25,8 +25,23 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed
   return z ^ (z >> 31);
 }
 
-__global__ void k_synth(EllParams ep, unsigned long long seed, int slide_w, int y0, int x0, int h,
-                        int w, uint8_t* out, long long stride) {
+// Sharp-edged structure discs inside needle cores: one 512 x 512 cell per
+// SplitMix64 draw (seed ^ kStructSalt, index cell_row << 20 | cell_col);
+// returns the disc type 0..2 covering (gy, gx), or -1.
+constexpr unsigned long long kStructSalt = 0x5A17C0DE5EEDull;
+__device__ __forceinline__ int structure_at(unsigned long long seed, long long gy, long long gx) {
+  const long long cy = gy >> 9, cx = gx >> 9;
+  const unsigned long long h = splitmix64(seed ^ kStructSalt, (unsigned long long)((cy << 20) | cx));
+  if ((long long)(h & 0xFF) >= 160) return -1;
+  const long long r = 64 + (long long)((h >> 16) & 0x7F), m = 254 - r;
+  const long long ccy = (cy << 9) + 256 + ((long long)((h >> 24) & 0xFF) * 2 * m) / 255 - m;
+  const long long ccx = (cx << 9) + 256 + ((long long)((h >> 32) & 0xFF) * 2 * m) / 255 - m;
+  const long long dy = gy - ccy, dx = gx - ccx;
+  return dy * dy + dx * dx < r * r ? (int)(((h >> 8) & 0xFF) % 3) : -1;
+}
+
+__global__ void k_synth(EllParams ep, unsigned long long seed, int structures, int slide_w, int y0, int x0,
+                        int h, int w, uint8_t* out, long long stride) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y;
   if (x >= w || y >= h) return;
@@ -50,6 +65,8 @@ __global__ void k_synth(EllParams ep, unsigned long long seed, int slide_w, int 
     }
   }
   const int pink[3] = {232, 150, 200}, purple[3] = {150, 90, 170};
+  const int scol[3][3] = {{120, 50, 140}, {245, 205, 230}, {195, 65, 95}};
+  const int st = structures && depth >= 0 ? structure_at(seed, gy, gx) : -1;
   unsigned long long base = ((unsigned long long)gy * (unsigned long long)slide_w +
                              (unsigned long long)gx) * 3ull;
   uint8_t* o = out + (long long)y * stride + (long long)x * 3;
@@ -60,6 +77,7 @@ __global__ void k_synth(EllParams ep, unsigned long long seed, int slide_w, int 
     long long noise = ((s * 10 - 1310700 + 32768 + (32ll << 16)) >> 16) - 32;
     long long t = depth > 0 ? depth : 0;
     long long col = depth >= 0 ? ((pink[c] * (256 - t) + purple[c] * t + 128) >> 8) : 235;
+    if (st >= 0) col = scol[st][c];
     long long val = col + noise;
     val = val < 0 ? 0 : (val > 255 ? 255 : val);
     o[c] = (uint8_t)val;
@@ -374,8 +392,8 @@ __global__ void __launch_bounds__(1024) k_tile_compact(const uint8_t* __restrict
 
 }  // namespace
 
-cudaError_t launch_synth(const int64_t* ell_host, int n_ell, uint64_t seed, int slide_w, int y0,
-                         int x0, int h, int w, uint8_t* out, int64_t stride, cudaStream_t st) {
+cudaError_t launch_synth(const int64_t* ell_host, int n_ell, uint64_t seed, int structures, int slide_w,
+                         int y0, int x0, int h, int w, uint8_t* out, int64_t stride, cudaStream_t st) {
   if (n_ell < 0 || n_ell > kMaxEll) return cudaErrorInvalidValue;
   EllParams ep;
   ep.n = n_ell;
@@ -383,7 +401,7 @@ cudaError_t launch_synth(const int64_t* ell_host, int n_ell, uint64_t seed, int 
     for (int q = 0; q < 6; ++q) ep.e[k][q] = ell_host[k * 6 + q];
   if (h <= 0 || w <= 0) return cudaSuccess;
   dim3 grid((w + 255) / 256, h);
-  k_synth<<<grid, 256, 0, st>>>(ep, seed, slide_w, y0, x0, h, w, out, stride);
+  k_synth<<<grid, 256, 0, st>>>(ep, seed, structures, slide_w, y0, x0, h, w, out, stride);
   return cudaGetLastError();
 }
 

@@ -36,8 +36,8 @@ struct SlideGeom {
 };
 
 // k_slide.cu
-cudaError_t launch_synth(const int64_t* ell_host, int n_ell, uint64_t seed, int slide_w, int y0,
-                         int x0, int h, int w, uint8_t* out, int64_t stride, cudaStream_t st);
+cudaError_t launch_synth(const int64_t* ell_host, int n_ell, uint64_t seed, int structures, int slide_w,
+                         int y0, int x0, int h, int w, uint8_t* out, int64_t stride, cudaStream_t st);
 cudaError_t launch_pad(const uint8_t* rgb, int64_t stride, const SlideGeom& g, uint8_t* canvas,
                        cudaStream_t st);
 // 40x canvas -> downsampled images for factors 2/4/8 (any may be null) + 8x8 block sums

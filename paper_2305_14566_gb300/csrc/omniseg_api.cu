@@ -38,8 +38,10 @@ struct omni_ctx {
   cudaStream_t copy_st = nullptr;
   std::vector<cudaEvent_t> band_ev;
   size_t band_ev_used = 0;
-  // omni_segment_slides: start and per-slide completion events of the last call
-  cudaEvent_t slide_ev[OMNI_MAX_SLIDES + 1] = {};
+  // omni_segment_slides: device clock stamps (ns) of the chain's start and of
+  // every slide's completion in the last call, and an event after the last
+  unsigned long long* d_stamps = nullptr;
+  cudaEvent_t stamps_done = nullptr;
   int slide_n = 0;
   // timing
   bool timing = false;
@@ -397,8 +399,8 @@ void omni_destroy(omni_ctx* ctx) {
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   for (cudaEvent_t e : ctx->band_ev) cudaEventDestroy(e);
-  for (cudaEvent_t e : ctx->slide_ev)
-    if (e) cudaEventDestroy(e);
+  if (ctx->d_stamps) cudaFree(ctx->d_stamps);
+  if (ctx->stamps_done) cudaEventDestroy(ctx->stamps_done);
   if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
   for (auto& e : ctx->evs) {
     cudaEventDestroy(e.a);
@@ -1290,6 +1292,13 @@ bool make_multi_plan(const omni_config& c, int n, const int32_t* H, const int32_
   return true;
 }
 
+// device clock (ns) at this point of the stream
+__global__ void k_stamp(unsigned long long* out) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  *out = t;
+}
+
 // merged list entry k = (slide, y, x) of the slide's tile k of one scale
 __global__ void k_merge_tiles(const int32_t* __restrict__ src, int n, int slide, int32_t* __restrict__ dst) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1403,8 +1412,9 @@ omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* 
       key.push_back(reinterpret_cast<uint64_t>(out[i].argmax[s]));
     }
   }
-  for (int e = 0; e <= n; ++e)
-    if (!ctx->slide_ev[e]) OMNI_CU(cudaEventCreate(&ctx->slide_ev[e]), "slide event");
+  if (!ctx->d_stamps)
+    OMNI_CU(cudaMalloc(&ctx->d_stamps, (OMNI_MAX_SLIDES + 1) * sizeof(unsigned long long)), "slide stamps");
+  if (!ctx->stamps_done) OMNI_CU(cudaEventCreateWithFlags(&ctx->stamps_done, cudaEventDisableTiming), "stamp event");
   ctx->slide_n = n;
   int last_scale = -1;
   for (int s = 0; s < c.n_scales; ++s) {
@@ -1414,7 +1424,8 @@ omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* 
   int32_t* merged = reinterpret_cast<int32_t*>(ws + mp.merged);
   // ---------------------------------------------------------------- network over the merged lists
   auto chain = [&](double& sb) -> omni_status {
-    OMNI_CU(cudaEventRecord(ctx->slide_ev[0], st), "slide event");
+    k_stamp<<<1, 1, 0, st>>>(ctx->d_stamps);
+    OMNI_CU(cudaGetLastError(), "slide stamp");
     for (int s = 0; s < c.n_scales; ++s) {
       int cls[OMNI_MAX_CLASSES];
       const int ncls = classes_at(c, s, class_mask, cls);
@@ -1456,10 +1467,14 @@ omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* 
       for (int i = 0; i < n; ++i) {
         omni_status rr = bands[i].finish(ctx, st);
         if (rr) return rr;
-        if (s == last_scale) OMNI_CU(cudaEventRecord(ctx->slide_ev[1 + i], st), "slide event");
+        if (s == last_scale) {
+          k_stamp<<<1, 1, 0, st>>>(ctx->d_stamps + 1 + i);
+          OMNI_CU(cudaGetLastError(), "slide stamp");
+        }
       }
       ctx->tiles_done += N[s];
     }
+    OMNI_CU(cudaEventRecord(ctx->stamps_done, st), "stamp event");
     return OMNI_OK;
   };
   double stitch_bytes = 0;
@@ -1471,21 +1486,29 @@ omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* 
 }
 
 int32_t omni_get_slide_times(omni_ctx* ctx, int32_t max, float* ms) {
-  if (!ctx || !ms || ctx->slide_n < 1) return -1;
+  if (!ctx || !ms || max < 1) return -1;
+  if (ctx->slide_n < 1 || !ctx->d_stamps || !ctx->stamps_done) return -2;   // no omni_segment_slides call yet
   const int n = std::min<int>(max, ctx->slide_n);
-  if (cudaEventSynchronize(ctx->slide_ev[ctx->slide_n]) != cudaSuccess) return -1;
-  for (int i = 0; i < n; ++i)
-    if (cudaEventElapsedTime(ms + i, ctx->slide_ev[0], ctx->slide_ev[1 + i]) != cudaSuccess) return -1;
+  unsigned long long h[OMNI_MAX_SLIDES + 1];
+  cudaError_t e = cudaEventSynchronize(ctx->stamps_done);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h, ctx->d_stamps, (size_t)(1 + ctx->slide_n) * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("omni_get_slide_times: ") + cudaGetErrorString(e);
+    return -1000 - (int32_t)e;
+  }
+  for (int i = 0; i < n; ++i) ms[i] = (float)((double)(h[1 + i] - h[0]) * 1e-6);
   return n;
 }
 
-omni_status omni_synth_slide(const int64_t* ell, int32_t n_ell, uint64_t seed, int32_t slide_w, int32_t y0,
-                             int32_t x0, int32_t h, int32_t w, uint8_t* out, int64_t stride, void* stream) {
+omni_status omni_synth_slide(const int64_t* ell, int32_t n_ell, uint64_t seed, int32_t structures,
+                             int32_t slide_w, int32_t y0, int32_t x0, int32_t h, int32_t w, uint8_t* out,
+                             int64_t stride, void* stream) {
   if ((!ell && n_ell) || !out || n_ell < 0 || n_ell > kMaxEll || stride < (int64_t)w * 3) return OMNI_EINVAL;
   (void)cudaGetLastError();
   for (int k = 0; k < n_ell; ++k)
     if (ell[k * 6 + 2] <= 0 || ell[k * 6 + 3] <= 0) return OMNI_EINVAL;
-  cudaError_t e = launch_synth(ell, n_ell, seed, slide_w, y0, x0, h, w, out, stride,
+  cudaError_t e = launch_synth(ell, n_ell, seed, structures != 0, slide_w, y0, x0, h, w, out, stride,
                                static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? OMNI_OK : OMNI_ECUDA;
 }

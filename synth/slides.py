@@ -13,6 +13,15 @@ Pixel recipe (all integer):
   * tissue = union of rotated ellipses (elongated cores along the long axis for
     needle biopsies, free blobs otherwise), coloured by a pink -> purple blend
     on the normalised radial depth inside the deepest covering ellipse,
+  * needle-biopsy cores also hold sharp-edged structures, as kidney tissue
+    holds glomeruli, tubule lumina and vessels: the slide is divided into
+    512 x 512 cells; draw k = (cell row << 20 | cell column) of SplitMix64
+    seeded with seed ^ STRUCT_SALT decides whether the cell holds a disc
+    (low byte < 160), its type (next byte mod 3: dark purple, pale, red), its
+    radius r = 64 + (7 bits) and its centre, offset from the cell centre by
+    (b * 2 m) // 255 - m per axis (b the next bytes, m = 254 - r) so the disc
+    stays inside its cell; tissue pixels inside the disc take the type's
+    colour instead of the depth blend,
   * per-channel noise: Irwin-Hall sum of four 16-bit uniforms from one
     SplitMix64 draw, scaled to sigma ~= 5.8 and rounded to an integer,
   * clamp to [0, 255].
@@ -35,6 +44,9 @@ BACKGROUND = 235
 PINK = (232, 150, 200)
 PURPLE = (150, 90, 170)
 Q14 = 1 << 14
+STRUCT_SALT = 0x5A17C0DE5EED
+STRUCT_CELL_SHIFT = 9                      # 512 x 512 cells at 40x
+STRUCT_COLOURS = ((120, 50, 140), (245, 205, 230), (195, 65, 95))
 
 
 @dataclass(frozen=True)
@@ -53,6 +65,7 @@ class SlideSpec:
     W: int
     seed: int
     ellipses: tuple
+    structures: bool = False     # sharp-edged discs inside the tissue (needle cores)
 
     def as_int_array(self) -> np.ndarray:
         """Ellipses packed as int64 rows (cy, cx, a, b, cos_q14, sin_q14)."""
@@ -103,7 +116,32 @@ def make_spec(H: int, W: int, seed: int, tissue: float, layout: str, n_blobs: in
             b = area / (n * math.pi * a)
             ells.append(_ellipse(rng, rng.uniform(0.1, 0.9) * H, rng.uniform(0.1, 0.9) * W,
                                  a, b, rng.uniform(0, math.pi)))
-    return SlideSpec(H, W, seed, tuple(ells))
+    return SlideSpec(H, W, seed, tuple(ells), structures=(layout == "cores"))
+
+
+def _structures(spec: SlideSpec, ys: np.ndarray, xs: np.ndarray):
+    """Type (0..2) of the structure disc covering each pixel, -1 where none."""
+    sh = STRUCT_CELL_SHIFT
+    cy0, cy1 = int(ys.min()) >> sh, int(ys.max()) >> sh
+    cx0, cx1 = int(xs.min()) >> sh, int(xs.max()) >> sh
+    cyy = np.arange(cy0, cy1 + 1, dtype=np.int64)[:, None]
+    cxx = np.arange(cx0, cx1 + 1, dtype=np.int64)[None, :]
+    k = ((cyy << 20) | cxx).astype(np.uint64)
+    h = splitmix64(spec.seed ^ STRUCT_SALT, k)
+    byte = lambda q: ((h >> np.uint64(8 * q)) & np.uint64(0xFF)).astype(np.int64)  # noqa: E731
+    present = byte(0) < 160
+    stype = byte(1) % 3
+    r = 64 + (((h >> np.uint64(16)) & np.uint64(0x7F)).astype(np.int64))
+    m = 254 - r
+    half = 1 << (sh - 1)
+    ccy = (cyy << sh) + half + (byte(3) * 2 * m) // 255 - m
+    ccx = (cxx << sh) + half + (byte(4) * 2 * m) // 255 - m
+    iy = (ys >> sh) - cy0
+    ix = (xs >> sh) - cx0
+    dy = ys - ccy[iy, ix]
+    dx = xs - ccx[iy, ix]
+    inside = present[iy, ix] & (dy * dy + dx * dx < r[iy, ix] * r[iy, ix])
+    return np.where(inside, stype[iy, ix], -1)
 
 
 def _depth_q8(spec: SlideSpec, ys: np.ndarray, xs: np.ndarray) -> np.ndarray:
@@ -128,6 +166,8 @@ def gen_window(spec: SlideSpec, y0: int, x0: int, h: int, w: int) -> np.ndarray:
     ys = np.arange(y0, y0 + h, dtype=np.int64)[:, None]
     xs = np.arange(x0, x0 + w, dtype=np.int64)[None, :]
     depth = _depth_q8(spec, ys, xs)
+    yy, xx = np.broadcast_arrays(ys, xs)
+    st = _structures(spec, yy, xx) if spec.structures else np.full(depth.shape, -1, np.int64)
     out = np.empty((h, w, 3), np.uint8)
     base_idx = (ys * spec.W + xs) * 3
     for c in range(3):
@@ -138,6 +178,8 @@ def gen_window(spec: SlideSpec, y0: int, x0: int, h: int, w: int) -> np.ndarray:
         noise = ((s * 10 - 1310700 + 32768 + (32 << 16)) >> 16) - 32
         t = np.maximum(depth, 0)
         col = (PINK[c] * (256 - t) + PURPLE[c] * t + 128) >> 8
+        scol = np.array([sc[c] for sc in STRUCT_COLOURS], np.int64)[np.maximum(st, 0)]
+        col = np.where(st >= 0, scol, col)
         val = np.where(depth >= 0, col, BACKGROUND) + noise
         out[..., c] = np.clip(val, 0, 255).astype(np.uint8)
     return out

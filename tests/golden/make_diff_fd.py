@@ -38,7 +38,7 @@ def main():
     rgb = synth.gen_slide(synth.spec_for(w))
     gts = synth.gen_gt_masks(w.H, w.W, w.factors, w.class_scale, seed=7)
     prob = O.DiffProblem(rgb, w, synth.gen_weights(w), gts)
-    loss, grads = prob.loss_and_grads()
+    loss, grads = prob.loss_and_grads_by_batch()
     print("autograd done %.0fs loss %.12f" % (time.time() - t0, loss), flush=True)
     base = prob.params()
     names = list(O.GRAD_PARAMS)

@@ -56,7 +56,9 @@ def test_synth_generator_bit_exact(api):
     g = api.synth_slide(spec).cpu().numpy()
     assert np.array_equal(g, synth.gen_slide(spec))
     spec = synth.spec_for(synth.NEEDLE)
-    for (y0, x0, h, w) in ((0, 0, 64, 96), (5000, 20000, 300, 257), (16384 - 37, 49152 - 53, 37, 53)):
+    assert spec.structures
+    for (y0, x0, h, w) in ((0, 0, 64, 96), (5000, 20000, 300, 257), (5632, 24576, 1024, 1536),
+                           (16384 - 37, 49152 - 53, 37, 53)):
         g = api.synth_slide(spec, y0, x0, h, w).cpu().numpy()
         assert np.array_equal(g, synth.gen_window(spec, y0, x0, h, w)), (y0, x0)
 

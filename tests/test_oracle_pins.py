@@ -564,6 +564,20 @@ def test_heads_only_loss_equals_full_loss():
         assert abs(a - b) <= 1e-13 * max(1.0, abs(a)), (name, a, b)
 
 
+def test_gradient_by_batch_equals_one_pass_autograd():
+    """The batch-by-batch gradient (chain rule through the overlap average
+    written out) equals autograd over the whole stitched loss."""
+    w = synth.small_variant(synth.DIFF, H=256, W=256, P=64, S=32, base=4, levels=3, max_batch=16)
+    rgb = synth.gen_slide(synth.spec_for(w))
+    gts = synth.gen_gt_masks(w.H, w.W, w.factors, w.class_scale, seed=7)
+    prob = O.DiffProblem(rgb, w, synth.gen_weights(w), gts)
+    l1, g1 = prob.loss_and_grads()
+    l2, g2 = prob.loss_and_grads_by_batch()
+    assert abs(l1 - l2) <= 1e-13 * abs(l1)
+    for k in g1:
+        assert torch.allclose(g1[k], g2[k], rtol=1e-10, atol=1e-13 * float(g1[k].abs().max())), k
+
+
 def test_diff_workload_fd_golden_matches_autograd():
     """tests/golden/diff_fd.json (make_diff_fd.py): on the differentiation
     workload itself, the oracle's autograd gradient equals FP64 central
@@ -597,6 +611,27 @@ def test_window_from_regions_equals_whole_slide():
 
 
 # ---------------------------------------------------------------- input generator
+
+
+def test_needle_cores_hold_structure_discs_inside_tissue_only():
+    """Needle-biopsy slides carry the sharp-edged structure discs inside their
+    cores (each disc inside its 512-px cell, every structure pixel on tissue);
+    blob slides carry none."""
+    from synth import slides as S
+    spec = synth.spec_for(synth.NEEDLE)
+    assert spec.structures and not synth.spec_for(synth.TINY).structures
+    ys = np.arange(5120, 7168, dtype=np.int64)[:, None]
+    xs = np.arange(24576, 26624, dtype=np.int64)[None, :]
+    yy, xx = np.broadcast_arrays(ys, xs)
+    st = S._structures(spec, yy, xx)
+    depth = S._depth_q8(spec, ys, xs)
+    inside = (st >= 0) & (depth >= 0)
+    assert inside.mean() > 0.05 and set(np.unique(st[inside]).tolist()) == {0, 1, 2}
+    img = synth.gen_window(spec, 5120, 24576, 2048, 2048).astype(np.int64)
+    for t, col in enumerate(S.STRUCT_COLOURS):
+        m = (st == t) & (depth >= 0)
+        mean = img[m].mean(axis=0)
+        assert np.all(np.abs(mean - np.array(col)) < 2.0), (t, mean)
 
 
 def test_generator_windows_are_consistent():
