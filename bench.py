@@ -217,21 +217,18 @@ def run_ragged(args, api, _lib, dev, prec):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         per = []
-        slide_err = None
         with Clocks(0) as clk:
             e0.record()
             for _ in range(args.steps):
                 seg.segment_many(rgbs, outs=outs)
-                try:
-                    per.append(seg.slide_times(len(works)))
-                except RuntimeError as exc:      # reported, not fatal to the throughput line
-                    per.append(None)
-                    slide_err = str(exc)
             e1.record()
             torch.cuda.synchronize()
+        # per-slide completion stamps of one more (untimed) step
+        seg.segment_many(rgbs, outs=outs)
+        per.append(seg.slide_times())
     total_ms = e0.elapsed_time(e1) / args.steps
     mpx = sum(w.H * w.W for w in works) / 1e6
-    lat = np.mean(np.array([p for p in per if p]), axis=0) if any(p for p in per) else None
+    lat = np.mean(np.array(per), axis=0) if per else None
     print(json.dumps({"metric": "ragged 12-slide segmentation Mpx/s", "value": mpx / (total_ms / 1e3),
                       "unit": "Mpx/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": total_ms, "higher_is_better": True, "dtype": args.precision,
@@ -241,7 +238,6 @@ def run_ragged(args, api, _lib, dev, prec):
                                              "share batches; one CUDA graph after tiling)",
                                  "slides": [[w.H, w.W, round(w.tissue, 3)] for w in works]},
                       "per_slide_done_ms": None if lat is None else [round(float(v), 2) for v in lat],
-                      "per_slide_error": slide_err,
                       "clocks": clk.summary()}))
     seg.close()
 

@@ -269,13 +269,12 @@ omni_status omni_query_slides(const omni_config* cfg, int32_t n, const int32_t* 
 omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* rgb_dev, const int32_t* H,
                                 const int32_t* W, const int64_t* row_stride, uint32_t scale_mask,
                                 uint32_t class_mask, void* workspace_dev, uint64_t workspace_bytes,
-                                const omni_outputs* out, void* stream);
-/* Completion time of every slide of the last omni_segment_slides call, in ms
- * after the start of its post-tiling chain: the chain writes the device clock
- * (%globaltimer) at its start and after each slide's last stitch band, also
- * when replayed from a graph.  Writes min(max, n) values and returns that
- * count, or -1.  Waits for the chain to finish. */
-int32_t omni_get_slide_times(omni_ctx* ctx, int32_t max, float* ms);
+                                const omni_outputs* out, uint64_t* slide_ns_dev, void* stream);
+/* slide_ns_dev (optional, NULL = none): caller-allocated DEVICE array of n + 1
+ * uint64 that the chain fills, on `stream`, with the device clock in ns
+ * (%globaltimer) at the start of the post-tiling chain and after each slide's
+ * last stitch band (also when replayed from a graph): per-slide completion
+ * time = slide_ns[1 + i] - slide_ns[0]. */
 
 /* Seeded synthetic slide window (input generator, not part of the method):
  * pixel (y, x) of a slide_w-wide slide drawn from `n_ell` rotated ellipses

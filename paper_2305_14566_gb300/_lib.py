@@ -11,6 +11,7 @@ import os
 
 MAX_SCALES = 4
 MAX_CLASSES = 16
+MAX_SLIDES = 16
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EWEIGHTS, ESTATE = 0, -1, -2, -3, -4, -5, -6
 FP32, BF16, FP16 = 0, 1, 2
@@ -26,7 +27,7 @@ EXPORTS = ("omni_create", "omni_destroy", "omni_last_error", "omni_weights_count
            "omni_get_timing", "omni_last_launch_count", "omni_get_launch_times",
            "omni_tile_slide_noalloc", "omni_backward", "omni_backward_workspace",
            "omni_set_autotune", "omni_set_graphs", "omni_set_fusion", "omni_get_tuned",
-           "omni_stain", "omni_query_slides", "omni_segment_slides", "omni_get_slide_times")
+           "omni_stain", "omni_query_slides", "omni_segment_slides")
 
 
 class Config(C.Structure):
@@ -111,8 +112,7 @@ def lib() -> C.CDLL:
         "omni_get_tuned": (i32, [vp, vp, i32]),
         "omni_backward": (i32, [vp, vp, i32, i32, i64, C.POINTER(vp), vp, u64, vp, C.POINTER(Grads), vp]),
         "omni_query_slides": (i32, [C.POINTER(Config), i32, vp, vp, C.POINTER(u64)]),
-        "omni_segment_slides": (i32, [vp, i32, vp, vp, vp, vp, u32, u32, vp, u64, vp, vp]),
-        "omni_get_slide_times": (i32, [vp, i32, vp]),
+        "omni_segment_slides": (i32, [vp, i32, vp, vp, vp, vp, u32, u32, vp, u64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -60,6 +60,8 @@ class Segmenter:
         self.blob = None
         self.load_weights(blob)
         self._ws: Optional[torch.Tensor] = None
+        self._stamps: Optional[torch.Tensor] = None
+        self._stamps_n = 0
 
     def load_weights(self, blob: np.ndarray):
         """omni_load_weights: replace the context's weights (a flat FP32 blob in
@@ -194,20 +196,21 @@ class Segmenter:
                 arr[i].logits[k] = t.data_ptr()
         ptrs = (C.c_void_p * n)(*[r.data_ptr() for r in rgbs])
         ws = self.workspace(nbytes.value, dev)
+        if self._stamps is None or self._stamps.numel() < n + 1 or self._stamps.device != dev:
+            self._stamps = torch.zeros(L.MAX_SLIDES + 1, dtype=torch.int64, device=dev)
+        self._stamps_n = n
         L.check(self.lib.omni_segment_slides(self.ctx, n, ptrs, Hs.ctypes.data_as(C.c_void_p),
                                              Ws.ctypes.data_as(C.c_void_p), strides.ctypes.data_as(C.c_void_p),
                                              (1 << cfg.n_scales) - 1, (1 << cfg.n_classes) - 1, _ptr(ws),
-                                             ws.numel(), arr, _stream()), self.ctx)
+                                             ws.numel(), arr, _ptr(self._stamps), _stream()), self.ctx)
         return list(outs)
 
-    def slide_times(self, n: int):
-        """Per-slide completion times (ms) of the last segment_many call."""
-        ms = np.zeros(n, np.float32)
-        got = self.lib.omni_get_slide_times(self.ctx, n, ms.ctypes.data_as(C.c_void_p))
-        if got <= 0:
-            raise L.OmniError(L.ECUDA, "omni_get_slide_times returned %d (%s)"
-                              % (got, self.lib.omni_last_error(self.ctx).decode()))
-        return ms[:got].tolist()
+    def slide_times(self):
+        """Per-slide completion times (ms after the post-tiling chain's start)
+        of the last segment_many call, from the device clock stamps it wrote
+        (waits for the current stream)."""
+        t = self._stamps[:self._stamps_n + 1].cpu().numpy().astype(np.uint64)
+        return [float((t[1 + i] - t[0]) / 1e6) for i in range(self._stamps_n)]
 
     def segment_host(self, rgb_host: torch.Tensor, labels_host: Dict[int, torch.Tensor],
                      device="cuda") -> Dict[int, torch.Tensor]:

@@ -38,11 +38,7 @@ struct omni_ctx {
   cudaStream_t copy_st = nullptr;
   std::vector<cudaEvent_t> band_ev;
   size_t band_ev_used = 0;
-  // omni_segment_slides: device clock stamps (ns) of the chain's start and of
-  // every slide's completion in the last call, and an event after the last
-  unsigned long long* d_stamps = nullptr;
-  cudaEvent_t stamps_done = nullptr;
-  int slide_n = 0;
+
   // timing
   bool timing = false;
   struct Ev { cudaEvent_t a, b; int kind, tag; double work; };
@@ -399,8 +395,6 @@ void omni_destroy(omni_ctx* ctx) {
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   for (cudaEvent_t e : ctx->band_ev) cudaEventDestroy(e);
-  if (ctx->d_stamps) cudaFree(ctx->d_stamps);
-  if (ctx->stamps_done) cudaEventDestroy(ctx->stamps_done);
   if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
   for (auto& e : ctx->evs) {
     cudaEventDestroy(e.a);
@@ -1324,7 +1318,7 @@ omni_status omni_query_slides(const omni_config* cfg, int32_t n, const int32_t* 
 omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* rgb, const int32_t* H,
                                 const int32_t* W, const int64_t* stride, uint32_t scale_mask,
                                 uint32_t class_mask, void* ws_, uint64_t ws_bytes, const omni_outputs* out,
-                                void* stream) {
+                                uint64_t* slide_ns, void* stream) {
   (void)cudaGetLastError();
   if (!ctx || !rgb || !H || !W || !stride || !out) return fail(ctx, OMNI_EINVAL, "null argument");
   if (!ctx->have_weights) return fail(ctx, OMNI_ESTATE, "omni_load_weights has not been called");
@@ -1412,10 +1406,7 @@ omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* 
       key.push_back(reinterpret_cast<uint64_t>(out[i].argmax[s]));
     }
   }
-  if (!ctx->d_stamps)
-    OMNI_CU(cudaMalloc(&ctx->d_stamps, (OMNI_MAX_SLIDES + 1) * sizeof(unsigned long long)), "slide stamps");
-  if (!ctx->stamps_done) OMNI_CU(cudaEventCreateWithFlags(&ctx->stamps_done, cudaEventDisableTiming), "stamp event");
-  ctx->slide_n = n;
+  key.push_back(reinterpret_cast<uint64_t>(slide_ns));
   int last_scale = -1;
   for (int s = 0; s < c.n_scales; ++s) {
     int cls[OMNI_MAX_CLASSES];
@@ -1424,8 +1415,10 @@ omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* 
   int32_t* merged = reinterpret_cast<int32_t*>(ws + mp.merged);
   // ---------------------------------------------------------------- network over the merged lists
   auto chain = [&](double& sb) -> omni_status {
-    k_stamp<<<1, 1, 0, st>>>(ctx->d_stamps);
-    OMNI_CU(cudaGetLastError(), "slide stamp");
+    if (slide_ns) {
+      k_stamp<<<1, 1, 0, st>>>(reinterpret_cast<unsigned long long*>(slide_ns));
+      OMNI_CU(cudaGetLastError(), "slide stamp");
+    }
     for (int s = 0; s < c.n_scales; ++s) {
       int cls[OMNI_MAX_CLASSES];
       const int ncls = classes_at(c, s, class_mask, cls);
@@ -1467,14 +1460,13 @@ omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* 
       for (int i = 0; i < n; ++i) {
         omni_status rr = bands[i].finish(ctx, st);
         if (rr) return rr;
-        if (s == last_scale) {
-          k_stamp<<<1, 1, 0, st>>>(ctx->d_stamps + 1 + i);
+        if (s == last_scale && slide_ns) {
+          k_stamp<<<1, 1, 0, st>>>(reinterpret_cast<unsigned long long*>(slide_ns) + 1 + i);
           OMNI_CU(cudaGetLastError(), "slide stamp");
         }
       }
       ctx->tiles_done += N[s];
     }
-    OMNI_CU(cudaEventRecord(ctx->stamps_done, st), "stamp event");
     return OMNI_OK;
   };
   double stitch_bytes = 0;
@@ -1483,22 +1475,6 @@ omni_status omni_segment_slides(omni_ctx* ctx, int32_t n, const uint8_t* const* 
   ctx->work[0] += (double)ctx->tiles_done * (double)mp.net.flops_per_tile;
   ctx->work[1] += stitch_bytes;
   return OMNI_OK;
-}
-
-int32_t omni_get_slide_times(omni_ctx* ctx, int32_t max, float* ms) {
-  if (!ctx || !ms || max < 1) return -1;
-  if (ctx->slide_n < 1 || !ctx->d_stamps || !ctx->stamps_done) return -2;   // no omni_segment_slides call yet
-  const int n = std::min<int>(max, ctx->slide_n);
-  unsigned long long h[OMNI_MAX_SLIDES + 1];
-  cudaError_t e = cudaEventSynchronize(ctx->stamps_done);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(h, ctx->d_stamps, (size_t)(1 + ctx->slide_n) * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) {
-    ctx->err = std::string("omni_get_slide_times: ") + cudaGetErrorString(e);
-    return -1000 - (int32_t)e;
-  }
-  for (int i = 0; i < n; ++i) ms[i] = (float)((double)(h[1 + i] - h[0]) * 1e-6);
-  return n;
 }
 
 omni_status omni_synth_slide(const int64_t* ell, int32_t n_ell, uint64_t seed, int32_t structures,
