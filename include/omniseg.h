@@ -294,13 +294,24 @@ omni_status omni_synth_slide(const int64_t* ellipses_host, int32_t n_ell, uint64
  * [cout], [cout], [cout][cr]); r may be NULL (no residual).  The layer is
  * launched `repeat` (>= 1) times back to back; if `ms_per_launch` is not NULL
  * it receives the mean device time of one launch (CUDA events on `stream`).
+ * `config` (tensor-core precisions; NULL: the default choice for the shape)
+ * selects one configuration as 4 int32 rows of omni_conv_candidates (the
+ * stages entry may be lowered to 2 or more); a configuration not legal for
+ * the shape returns OMNI_EINVAL.
  * Allocates and frees its own temporary weight buffers; synchronises `stream`. */
 omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin, int32_t cout,
                             const void* x_dev, int32_t x_cs, int32_t x_co,
                             const float* w_host, const float* g_host, const float* b_host,
                             const void* r_dev, int32_t r_cs, int32_t r_co, int32_t cr,
                             const float* wp_host, void* y_dev, int32_t y_cs, int32_t y_co,
-                            int32_t repeat, float* ms_per_launch, void* stream);
+                            const int32_t* config, int32_t repeat, float* ms_per_launch, void* stream);
+
+/* Tensor-core configurations legal for a conv layer shape (R, cin, cout,
+ * projection channels cr): writes 4 int32 per configuration (kind as in
+ * omni_get_tuned, N tile, channel chunk, pipeline stages) to `rows` (host,
+ * up to max_rows) and returns how many it wrote (0: the shape has none). */
+int32_t omni_conv_candidates(int32_t R, int32_t cin, int32_t cout, int32_t cr, int32_t* rows,
+                             int32_t max_rows);
 
 /* Device timing of omni_segment_slide calls with CUDA events recorded on the
  * call's stream around every launch.  omni_set_timing(ctx, 1) enables it and
@@ -325,7 +336,9 @@ int64_t omni_last_launch_count(const omni_ctx* ctx);
  * synchronises the stream, so run one untimed call first.  omni_get_tuned
  * writes 10 int32 per tuned shape: R, cin, cout, cr, residual kind, batch,
  * kind (0 per-tap, 1 small-N, 2 dx-in-N, 3 small-N with two blocks per tile,
- * 4 dx-in-N with two blocks per tile),
+ * 4 dx-in-N with two blocks per tile, 6 kind 3 on pairs of CTAs whose
+ * cta_group::2 MMAs cover 256 pixel rows, 7 kind 4 launched once per 32
+ * output channels),
  * N tile, channel chunk, stages; returns the count. */
 omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled);
 int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows);

@@ -737,6 +737,13 @@ class DiffProblem:
         if not hasattr(self, "_y0"):
             with torch.no_grad():
                 self._y0 = [res_block(cat0, self.p, "dec0") for (_, _, cat0, _) in self.cache]
+        return self.loss_from_y0(q, self._y0)
+
+    def loss_from_y0(self, q: Dict[str, torch.Tensor], y0s) -> torch.Tensor:
+        """loss with the last decoder block's output of every cached batch given
+        (y0s[k] for self.cache[k]) and the controller / pre-head parameters in q
+        (others from the blob)."""
+        assert all(k.startswith("ctrl.") or k.startswith("head.") for k in q)
         work = self.work
         p = dict(self.p)
         p.update(q)
@@ -746,7 +753,7 @@ class DiffProblem:
             f = work.factors[s]
             acc[c] = torch.zeros((Hp // f, Wp // f), dtype=F64)
             cov[c] = torch.zeros((Hp // f, Wp // f), dtype=F64)
-        for (s, chunk, _, g), y0 in zip(self.cache, self._y0):
+        for (s, chunk, _, g), y0 in zip(self.cache, y0s):
             h0 = prehead(y0, p)
             for c in [c for c, cs in enumerate(work.class_scale) if cs == s]:
                 lg = dynamic_head(h0, controller(g, c, s, p, work.n_classes, work.n_scales))

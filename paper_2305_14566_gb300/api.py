@@ -438,18 +438,28 @@ def synth_slide(spec, y0: int = 0, x0: int = 0, h: Optional[int] = None,
 def conv_layer(precision: int, x: torch.Tensor, R: int, cin: int, cout: int, w: np.ndarray,
                g: np.ndarray, b: np.ndarray, y: torch.Tensor, r: Optional[torch.Tensor] = None,
                cr: int = 0, wp: Optional[np.ndarray] = None, x_cs=None, x_co=0, r_cs=None,
-               r_co=0, y_cs=None, y_co=0, repeat: int = 1) -> float:
-    """One fused conv layer through omni_conv_layer; returns ms per launch."""
+               r_co=0, y_cs=None, y_co=0, repeat: int = 1, config=None) -> float:
+    """One fused conv layer through omni_conv_layer; returns ms per launch.
+    config: None (default kernel choice) or a (kind, N tile, chunk, stages)
+    row of conv_candidates."""
     B = x.shape[0]
     w = np.ascontiguousarray(w, np.float32)
     g = np.ascontiguousarray(g, np.float32)
     b = np.ascontiguousarray(b, np.float32)
     wpp = None if wp is None else np.ascontiguousarray(wp, np.float32)
+    cfg = None if config is None else np.ascontiguousarray(config, np.int32)
     ms = C.c_float(0.0)
     st = L.lib().omni_conv_layer(
         precision, B, R, cin, cout, _ptr(x), x_cs or cin, x_co, w.ctypes.data_as(C.c_void_p),
         g.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p), _ptr(r), r_cs or cr, r_co, cr,
         None if wpp is None else wpp.ctypes.data_as(C.c_void_p), _ptr(y), y_cs or cout, y_co,
-        repeat, C.byref(ms), _stream())
+        None if cfg is None else cfg.ctypes.data_as(C.c_void_p), repeat, C.byref(ms), _stream())
     L.check(st, None, "omni_conv_layer failed")
     return ms.value
+
+
+def conv_candidates(R: int, cin: int, cout: int, cr: int = 0):
+    """Legal tensor-core configurations of a conv shape: (kind, N tile, chunk, stages) rows."""
+    rows = np.zeros((16, 4), np.int32)
+    n = L.lib().omni_conv_candidates(R, cin, cout, cr, rows.ctypes.data_as(C.c_void_p), 16)
+    return [tuple(int(v) for v in rows[i]) for i in range(n)]

@@ -127,6 +127,43 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
   }
 }
 
+// ---- CTA pairs (cluster of two; the pair's MMAs are cta_group::2, M = 256)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+// arrive on a barrier of the other CTA of the pair.  Default (CTA-scope)
+// release: a cluster-scope release would first wait until every global store
+// of the thread is visible, which the signals here do not need (TMEM reads are
+// complete after tcgen05.wait::ld and ordered by the before_thread_sync fence;
+// TMA data is tracked by the barrier it completes on).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cl_addr) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+}
+// arrive on this CTA's barrier (CL false) or on the same barrier of CTA 0 of the pair
+template <bool CL>
+__device__ __forceinline__ void mbar_arrive_to(uint32_t bar, bool remote) {
+  if (CL && remote) mbar_arrive_cluster(cluster_addr(bar, 0));
+  else mbar_arrive(bar);
+}
+// waits on barriers that the other CTA of a pair arrives on: the plain bounded
+// wait (the arrivals' ordering is carried by the barrier itself)
+template <bool CL>
+__device__ __forceinline__ bool mbar_wait_t(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                            unsigned* err) {
+  return mbar_wait(bar, parity, abort_flag, err);
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
                                             int c0, int c1, int c2, int c3) {
   asm volatile(
@@ -143,6 +180,20 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
       : "memory");
 }
+// tiled shared -> global store of one box; completion is tracked per thread
+// with bulk groups (commit, then wait until at most N groups still read smem)
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2,
+                                             int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Shared-memory matrix descriptor of a K-major, swizzled operand tile whose
 // rows are SW bytes long (SW = 64 or 128), 8-row groups SW*8 bytes apart.
@@ -157,10 +208,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int sw) {
 }
 
 // Instruction descriptor, kind::f16: BF16 x BF16 (or FP16 x FP16) -> FP32,
-// both operands K-major, M = 128.  Operand format field: 0 = FP16, 1 = BF16.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+// both operands K-major, M = 128 (256 for a CTA pair).  Operand format
+// field: 0 = FP16, 1 = BF16.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, int m = kBM) {
   return (1u << 4) | ((kF16 ? 0u : 1u) << 7) | ((kF16 ? 0u : 1u) << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(kBM >> 4) << 24);
+         ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
@@ -174,6 +226,55 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
+}
+// pair forms: one MMA over 256 rows (128 from each CTA of the pair; B's N
+// columns split N/2 per CTA at the same shared-memory offset), accumulator
+// rows in each CTA's own TMEM; the commit arrives on the barrier at the same
+// offset in both CTAs
+template <bool PAIR>
+__device__ __forceinline__ void mma_t(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                      uint32_t accumulate) {
+  if (!PAIR) {
+    mma_bf16(tmem_d, adesc, bdesc, idesc, accumulate);
+    return;
+  }
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+template <bool PAIR>
+__device__ __forceinline__ void mma_commit_t(uint32_t bar) {
+  if (!PAIR) {
+    mma_commit(bar);
+    return;
+  }
+  const uint16_t both = 3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          bar),
+      "h"(both)
+      : "memory");
+}
+template <bool PAIR>
+__device__ __forceinline__ void tmem_alloc_t(uint32_t slot, uint32_t cols) {
+  if (PAIR) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+}
+template <bool PAIR>
+__device__ __forceinline__ void tmem_dealloc_t(uint32_t base, uint32_t cols) {
+  if (PAIR)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols) : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols) : "memory");
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -272,6 +373,13 @@ __device__ __forceinline__ void tmem_ld16x4(uint32_t t0, uint32_t t1, uint32_t t
 }
 
 __device__ __forceinline__ float norm_u8(uint8_t u) { return 2.0f * (float)u / 255.0f - 1.0f; }
+
+// four consecutive per-channel constants from shared memory in one 16-byte
+// load (the epilogues' gamma / beta / RGB-projection rows are 16-byte aligned)
+__device__ __forceinline__ void lds4(const float* p, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
 
 // Dynamic head of one class on the pre-head feature h0 (already through its
 // ReLU): logit = W3 ReLU(W2 ReLU(W1 h0 + b1) + b2) + b3, with theta laid out
@@ -668,12 +776,23 @@ constexpr int kHBoxPix = (kHTH + 2) * kHTW;   // 160 input pixels per dx box
 // MB = 2: a tile is two vertically adjacent 8 x 16 blocks (16 x 16 pixels);
 // the boxes are 18 rows high and every synchronisation of the pipeline
 // covers twice the MMAs (the per-tile waits dominate at small N).
-template <int BN, int CK, bool RES, int MB>
+//
+// PAIR: the kernel runs as clusters of two CTAs.  Each CTA loads and stores
+// its own tiles (CTA 0 of the pair the even, CTA 1 the odd tiles of the pair's
+// sequence) and holds half of the weights' N rows; one thread of CTA 0 issues
+// cta_group::2 MMAs of M = 256 that cover the same block of both CTAs' tiles,
+// so an instruction does twice the rows for the same issue cost (at N = 32 /
+// 64 an MMA's issue cost, not its math, bounds the layer).  CTA 1's idle MMA
+// warp forwards its loads' completion to CTA 0's stage barriers; the MMA
+// commits arrive on both CTAs' barriers; both epilogues release an
+// accumulator buffer on CTA 0's barrier.
+template <int BN, int CK, bool RES, int MB, bool PAIR = false>
 struct HaloCfg {
   static constexpr int kBoxRows = kHTH * MB + 2;
   static constexpr int kBoxBytes = kBoxRows * kHTW * CK * 2;
   static constexpr int kStageBytes = 3 * kBoxBytes;
-  static constexpr int kWTileBytes = BN * CK * 2;
+  static constexpr int kWRows = PAIR ? BN / 2 : BN;      // weight rows (output channels) held here
+  static constexpr int kWTileBytes = kWRows * CK * 2;
   static constexpr int kBlkCols = RES ? 2 * BN : BN;     // one 128-pixel block: conv | projection
   static constexpr int kBufCols = MB * kBlkCols;
   static constexpr int kBufs = tmem_bufs(kBufCols);
@@ -689,12 +808,12 @@ struct HaloParams {
   int group;                        // slots (one chunk's 3 boxes, or 3 projection chunks) per stage
 };
 
-template <int BN, int CK, bool RES, int MB>
+template <int BN, int CK, bool RES, int MB, bool PAIR>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_conv_tc_halo(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
                    HaloParams hp) {
-  using Cfg = HaloCfg<BN, CK, RES, MB>;
+  using Cfg = HaloCfg<BN, CK, RES, MB, PAIR>;
   const TCParams& p = hp.t;
   const int ST = hp.stages;
   extern __shared__ uint8_t smem_raw[];
@@ -720,6 +839,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool fuse_head = p.theta != nullptr;
+  const bool peer = PAIR && cluster_rank() != 0;          // CTA 1 of a pair
   for (int i = threadIdx.x; i < BN; i += blockDim.x) {
     sg[i] = p.gamma[i];
     sb[i] = p.beta[i];
@@ -734,30 +854,29 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (threadIdx.x < kHeadCh) sbh[threadIdx.x] = p.bh[threadIdx.x];
   }
   if (threadIdx.x == 0) {
+    // pair, CTA 0: the stage and weight barriers also wait for CTA 1's
+    // forwarded completion, the accumulator buffers for both epilogues
+    const uint32_t fwd = PAIR && !peer ? 2 : 1;
     for (int s = 0; s < ST; ++s) {
-      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&full[s]), fwd);
       mbar_init(smem_u32(&empty[s]), 1);
     }
     for (int b = 0; b < Cfg::kBufs; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
       // one block: with the fused head each warpgroup owns the buffers of one parity
-      mbar_init(smem_u32(&tempty[b]), MB == 1 && fuse_head ? kEpiWarps / 2 : kEpiWarps);
+      mbar_init(smem_u32(&tempty[b]), (MB == 1 && fuse_head ? kEpiWarps / 2 : kEpiWarps) * (PAIR ? 2 : 1));
     }
     mbar_init(smem_u32(drain), 1);
-    mbar_init(smem_u32(wbar), 1);
+    mbar_init(smem_u32(wbar), fwd);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(Cfg::kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (PAIR) cluster_sync();                // both CTAs' barriers exist before any remote arrive
+  if (warp == 0) tmem_alloc_t<PAIR>(smem_u32(tmem_slot), Cfg::kTmemCols);
   tc_fence_before();
-  __syncthreads();
+  if (PAIR) cluster_sync();
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int k_total = p.k_main + p.k_res;
@@ -770,10 +889,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       mbar_expect_tx(wb, (uint32_t)(hp.n_wtiles * Cfg::kWTileBytes));
       for (int t = 0; t < 9 * hp.cpt; ++t) {
         const int tap = t / hp.cpt, c = t % hp.cpt;
-        tma_load_2d(smem_u32(sW + (size_t)t * Cfg::kWTileBytes), &mapB, wb, tap * p.cin + c * CK, 0);
+        tma_load_2d(smem_u32(sW + (size_t)t * Cfg::kWTileBytes), &mapB, wb, tap * p.cin + c * CK,
+                    peer ? Cfg::kWRows : 0);
       }
       for (int r = 0; r < hp.res_chunks; ++r)
-        tma_load_2d(smem_u32(sW + (size_t)(9 * hp.cpt + r) * Cfg::kWTileBytes), &mapB2, wb, r * CK, 0);
+        tma_load_2d(smem_u32(sW + (size_t)(9 * hp.cpt + r) * Cfg::kWTileBytes), &mapB2, wb, r * CK,
+                    peer ? Cfg::kWRows : 0);
       int it = 0;
       StageRing ring;
       TileWalk tw;
@@ -784,7 +905,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int h0 = tw.ty * (kHTH * MB), w0 = tw.tx * kHTW;
         for (int k0 = 0; k0 < k_total; k0 += G, ++it, ring.next(ST)) {
           const int s = ring.s;
-          if (ring.lapped && !mbar_wait(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
+          if (ring.lapped && !mbar_wait_t<PAIR>(smem_u32(&empty[s]), ring.ph ^ 1u, abort_flag, p.err)) {
             ok = false;
             break;
           }
@@ -817,19 +938,35 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       for (int q = last - 1; q >= 0 && q >= last - ST; --q) mbar_drain(smem_u32(&full[q % ST]), (q / ST) & 1);
       mbar_drain(wb, 0);
     }
+  } else if (warp == 1 && peer) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- pair: forward CTA 1's loads
+      // (same stage order as CTA 0's MMA issuer) to CTA 0's barriers
+      bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, p.err);
+      if (ok) mbar_arrive_cluster(cluster_addr(smem_u32(wbar), 0));
+      StageRing ring;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x)
+        for (int k0 = 0; k0 < k_total; k0 += G, ring.next(ST)) {
+          if (!mbar_wait(smem_u32(&full[ring.s]), ring.ph, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_cluster(cluster_addr(smem_u32(&full[ring.s]), 0));
+        }
+    }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuer
-      constexpr uint32_t idesc = idesc_bf16(BN);
+      constexpr uint32_t idesc = idesc_bf16(BN, PAIR ? 2 * kBM : kBM);
       const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
       const uint64_t b_desc0 = smem_desc(smem_u32(sW), Cfg::kSW);
       const uint64_t b_tap_step = (uint64_t)(hp.cpt * (Cfg::kWTileBytes >> 4));
-      bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, p.err);
+      bool ok = mbar_wait_t<PAIR>(smem_u32(wbar), 0, abort_flag, p.err);
       int tcount = 0;
       StageRing ring;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
         const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
-        if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
+        if (use >= 1 && !mbar_wait_t<PAIR>(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
           ok = false;
           break;
         }
@@ -839,7 +976,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         for (int k0 = 0; k0 < k_total; k0 += G, ring.next(ST)) {
           const int s = ring.s;
           // TMA-filled stage: the mbarrier's complete_tx orders the copy before the MMAs
-          if (!mbar_wait(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
+          if (!mbar_wait_t<PAIR>(smem_u32(&full[s]), ring.ph, abort_flag, p.err)) {
             ok = false;
             break;
           }
@@ -861,8 +998,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                   const uint64_t bt = bd + (uint64_t)tap * b_tap_step;
 #pragma unroll
                   for (int kk = 0; kk < CK / 16; ++kk)
-                    mma_bf16(acc0 + (uint32_t)(blk * Cfg::kBlkCols), at + (uint64_t)(kk * 2),
-                             bt + (uint64_t)(kk * 2), idesc, (tap > 0 || kk > 0) ? 1u : acc_first);
+                    mma_t<PAIR>(acc0 + (uint32_t)(blk * Cfg::kBlkCols), at + (uint64_t)(kk * 2),
+                                bt + (uint64_t)(kk * 2), idesc, (tap > 0 || kk > 0) ? 1u : acc_first);
                 }
               }
             } else if (RES) {
@@ -875,18 +1012,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                       ad + (uint64_t)((b * Cfg::kBoxBytes + kHTH * blk * kHTW * CK * 2) >> 4);
 #pragma unroll
                   for (int kk = 0; kk < CK / 16; ++kk)
-                    mma_bf16(acc1 + (uint32_t)(blk * Cfg::kBlkCols), ab + (uint64_t)(kk * 2),
-                             bd + (uint64_t)(kk * 2), idesc, (c0 + b > 0 || kk > 0) ? 1u : 0u);
+                    mma_t<PAIR>(acc1 + (uint32_t)(blk * Cfg::kBlkCols), ab + (uint64_t)(kk * 2),
+                                bd + (uint64_t)(kk * 2), idesc, (c0 + b > 0 || kk > 0) ? 1u : 0u);
                 }
               }
             }
           }
-          mma_commit(smem_u32(&empty[s]));
+          mma_commit_t<PAIR>(smem_u32(&empty[s]));
         }
         if (!ok) break;
-        mma_commit(smem_u32(&tfull[buf]));
+        mma_commit_t<PAIR>(smem_u32(&tfull[buf]));
       }
-      mma_commit(smem_u32(drain));
+      mma_commit_t<PAIR>(smem_u32(drain));
       mbar_drain(smem_u32(drain), 0);
     }
   } else {
@@ -923,7 +1060,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           pf.fetch(p.cv, p.tiles3, nx.t, nx.img,
                    nx.ty * (kHTH * MB) + blk * kHTH + row / kHTW, nx.tx * kHTW + row % kHTW);
       }
-      const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
+      const bool ok = mbar_wait_t<PAIR>(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const int img = tw.img;
@@ -947,12 +1084,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         if constexpr (RES) tmem_ld16x2(tb + c, tb + BN + c, a, r);
         else tmem_ld16(tb + c, a);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = c + j;
-          float z = fmaf(sg[n], a[j], sb[n]);
-          if constexpr (RES) z += r[j];
-          if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[BN + n], v2 * swp[2 * BN + n]));
-          o16[j] = fmaxf(z, 0.f);
+        for (int j4 = 0; j4 < 16; j4 += 4) {
+          float g4[4], b4[4], w0[4] = {0.f, 0.f, 0.f, 0.f}, w1[4] = {0.f, 0.f, 0.f, 0.f},
+                                 w2[4] = {0.f, 0.f, 0.f, 0.f};
+          lds4(sg + c + j4, g4);
+          lds4(sb + c + j4, b4);
+          if (rgb) {
+            lds4(swp + c + j4, w0);
+            lds4(swp + BN + c + j4, w1);
+            lds4(swp + 2 * BN + c + j4, w2);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j4 + u;
+            float z = fmaf(g4[u], a[j], b4[u]);
+            if constexpr (RES) z += r[j];
+            if (rgb) z += fmaf(v0, w0[u], fmaf(v1, w1[u], v2 * w2[u]));
+            o16[j] = fmaxf(z, 0.f);
+          }
         }
         if (p.y) {
           uint32_t packed[8];
@@ -980,7 +1129,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+      if (lane == 0) mbar_arrive_to<PAIR>(smem_u32(&tempty[buf]), peer);
       if (fuse_head) {
         // the TMEM buffer is released; the heads run on registers and shared memory
 #pragma unroll
@@ -999,12 +1148,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   }
   __syncwarp();
   tc_fence_before();
-  __syncthreads();
+  // pair: neither CTA leaves while the other's MMAs or arrivals may still touch it
+  if (PAIR) cluster_sync();
+  else __syncthreads();
   tc_fence_after();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(Cfg::kTmemCols)
-                 : "memory");
+  if (warp == 0) tmem_dealloc_t<PAIR>(tmem_base, Cfg::kTmemCols);
 }
 
 // ------------------------------------------------------------------ dx-in-N variant
@@ -1303,15 +1451,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         if constexpr (RES) tmem_ld16x4(tb + c, tb + CO + c, tb + 2 * CO + c, tb + Cfg::kN + c, d0, d1, d2, r);
         else tmem_ld16x3(tb + c, tb + CO + c, tb + 2 * CO + c, d0, d1, d2);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = c + j;
-          // lane-1 holds the left neighbour's dx=0 sum, lane+1 the right's dx=2 sum
-          const float left = __shfl_up_sync(0xffffffffu, d0[j], 1);
-          const float right = __shfl_down_sync(0xffffffffu, d2[j], 1);
-          float z = fmaf(sg[n], left + d1[j] + right, sb[n]);
-          if constexpr (RES) z += r[j];
-          if (p.res_mode == RES_RGB) z += fmaf(v0, swp[n], fmaf(v1, swp[CO + n], v2 * swp[2 * CO + n]));
-          o16[j] = fmaxf(z, 0.f);
+        for (int j4 = 0; j4 < 16; j4 += 4) {
+          float g4[4], b4[4], w0[4] = {0.f, 0.f, 0.f, 0.f}, w1[4] = {0.f, 0.f, 0.f, 0.f},
+                                 w2[4] = {0.f, 0.f, 0.f, 0.f};
+          lds4(sg + c + j4, g4);
+          lds4(sb + c + j4, b4);
+          if (rgb) {
+            lds4(swp + c + j4, w0);
+            lds4(swp + CO + c + j4, w1);
+            lds4(swp + 2 * CO + c + j4, w2);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j4 + u;
+            // lane-1 holds the left neighbour's dx=0 sum, lane+1 the right's dx=2 sum
+            const float left = __shfl_up_sync(0xffffffffu, d0[j], 1);
+            const float right = __shfl_down_sync(0xffffffffu, d2[j], 1);
+            float z = fmaf(g4[u], left + d1[j] + right, b4[u]);
+            if constexpr (RES) z += r[j];
+            if (rgb) z += fmaf(v0, w0[u], fmaf(v1, w1[u], v2 * w2[u]));
+            o16[j] = fmaxf(z, 0.f);
+          }
         }
         if (writes && p.y) {
           uint32_t packed[8];
@@ -1377,14 +1537,19 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 //   1. a TMA load of the tile's raw window, 10 canvas rows x 80 bytes starting
 //      at the 16-byte boundary at or left of the window (the 18-pixel, 54-byte
 //      window sits at byte offset 0..15 of each row; OOB rows read as zero);
-//   2. builder thread r gathers the 27 values v = 2u/255 - 1 of its pixel's
-//      3x3 window from shared memory (zero outside the tile), rounds them to
-//      FP16 (whatever the pipeline's 16-bit type: 8-bit colour values need the
-//      11-bit mantissa) and stores one 64-byte K row (K = 27 padded to 32) in
-//      the 64-byte-swizzled K-major layout the MMA reads (16-byte chunk j of
-//      row r at chunk j ^ ((r >> 1) & 3)).
-// Two FP16 MMAs (K = 16 each) per tile, N = cout; the epilogue writes the
-// pipeline's type.
+//   2. builder thread r reads the nine bytes of each of its pixel's three
+//      window rows as three aligned words (funnel-shifted into place),
+//      normalises them in registers, v = fma(u, 2/255, -1) (for every byte
+//      value this rounds to the same FP16 number as 2u/255 - 1 in exact
+//      arithmetic), zeroes taps outside the tile, rounds to FP16 (whatever the
+//      pipeline's 16-bit type: 8-bit colour values need the 11-bit mantissa)
+//      and stores one 64-byte K row (K = 27 padded to 32) in the
+//      64-byte-swizzled K-major layout the MMA reads (16-byte chunk j of row r
+//      at chunk j ^ ((r >> 1) & 3)).
+// Two FP16 MMAs (K = 16 each) per tile, N = cout.  The epilogue stages each
+// warp's 32 output pixels (two rows of 16) in shared memory, swizzled like the
+// output tensor map, and writes them with one TMA store per warp and tile:
+// whole 128-byte lines instead of 32 scattered 16-byte pieces per store.
 //   warps 0-7  builders in two groups of four (group g builds the CTA's
 //              tiles g, g + 2, ...: two tiles in flight), warp 8 MMA issuer +
 //              TMEM owner, warps 9-16 epilogue in two groups of four taking
@@ -1396,6 +1561,11 @@ __host__ __device__ constexpr uint32_t idesc_f16_ops(int n) {
 __device__ __forceinline__ uint32_t pack2_f16(float a, float b) {
   __half2 h = __floats2half2_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
+}
+constexpr float kNorm = 2.0f / 255.0f;
+// byte i (0..3) of w as an exact float: 2^23 + byte, minus 2^23
+__device__ __forceinline__ float byte_f32(uint32_t w, int i) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | (uint32_t)i)) - 8388608.f;
 }
 constexpr int kFirstGroups = 2;                           // builder groups, 128 threads each
 constexpr int kFirstBuilders = 128 * kFirstGroups;
@@ -1415,8 +1585,10 @@ struct FirstCfg {
   static constexpr int kBufCols = CO;
   static constexpr int kBufs = tmem_bufs(kBufCols);
   static constexpr int kTmemCols = tmem_alloc_cols(kBufs * kBufCols);
+  static constexpr int kOutWarpBytes = 32 * CO * 2;       // one warp's staged pixels (two buffers each)
+  static constexpr int kOutBytes = 4 * kFirstEpiGroups * 2 * kOutWarpBytes;
   static constexpr size_t kSmem =
-      1024 + (size_t)kFirstStages * (kFirstStageBytes + kRawStageBytes) + kWBytes + 2048;
+      1024 + (size_t)kFirstStages * (kFirstStageBytes + kRawStageBytes) + kWBytes + kOutBytes + 2048;
 };
 
 // raw-window tensor maps of the batch's canvases (entry k for canvas cv.ptr[k])
@@ -1427,7 +1599,7 @@ struct CanvasMaps {
 template <int CO>
 __global__ void __launch_bounds__(kThreadsFirst, 1)
     k_conv_tc_first(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CanvasMaps mapsC,
-                    TCParams p) {
+                    const __grid_constant__ CUtensorMap mapY, TCParams p) {
   using Cfg = FirstCfg<CO>;
   constexpr int ST = kFirstStages;
   extern __shared__ uint8_t smem_raw[];
@@ -1435,7 +1607,8 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
   uint8_t* sA = smem;
   uint8_t* sRaw = sA + (size_t)ST * kFirstStageBytes;
   uint8_t* sW = sRaw + (size_t)ST * kRawStageBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sW + Cfg::kWBytes);
+  uint8_t* sOut = sW + Cfg::kWBytes;               // 1024-aligned: the stages and sW are multiples of 1 KB
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sOut + Cfg::kOutBytes);
   uint64_t* full = bars;                           // A stage built (4 builder warps)
   uint64_t* empty = bars + ST;                     // A stage consumed (MMA commit)
   uint64_t* rfull = bars + 2 * ST;                 // raw window landed (TMA)
@@ -1446,8 +1619,7 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
   uint64_t* wbar = drain + 1;
   float* sg = reinterpret_cast<float*>(wbar + 1);
   float* sb = sg + CO;
-  float* snorm = sb + CO;                          // v(u) = 2u/255 - 1 for every byte value
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(snorm + 256);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + CO);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1455,7 +1627,6 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
     sg[i] = p.gamma[i];
     sb[i] = p.beta[i];
   }
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) snorm[i] = norm_u8((uint8_t)i);
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(smem_u32(&full[s]), 4);
@@ -1484,7 +1655,6 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int RR = p.R * p.R;
 
   if (warp == kFirstProducerWarp) {
     if (lane == 0) {
@@ -1525,20 +1695,28 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
       bool ok = !lapped || mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag, p.err);
       ok = ok && mbar_wait(smem_u32(&rfull[s]), ph, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
-      const int off = ((cx0 + tw.tx * kHTW - 1) * 3) & 15;
-      const uint8_t* raw = sRaw + (size_t)s * kRawStageBytes + off;
+      // byte of tap (dy, 0), channel 0 in its raw row: at most 15 + 45, so the
+      // three words read per row end at byte 71 of the 80 loaded
+      const int bb = (((cx0 + tw.tx * kHTW - 1) * 3) & 15) + rw * 3;
+      const uint32_t* wrow = reinterpret_cast<const uint32_t*>(sRaw + (size_t)s * kRawStageBytes) + (bb >> 2);
+      const uint32_t sh = (uint32_t)(bb & 3) * 8u;
       const int h_in = tw.ty * kHTH + rh - 1, w_in = tw.tx * kHTW + rw - 1;   // tile coords of tap (0, 0)
       float v[32];
 #pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
+      for (int dy = 0; dy < 3; ++dy) {
+        const uint32_t* wp = wrow + (rh + dy) * (kRawW / 4);
+        const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
+        const uint32_t by[3] = {__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                                __funnelshift_r(w2, w2, sh)};
+        const int yy = h_in + dy;
+        const bool yin = yy >= 0 && yy < p.R;
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-          const int yy = h_in + dy, xx = w_in + dx;
-          const bool in = yy >= 0 && yy < p.R && xx >= 0 && xx < p.R;
-          const uint8_t* px = raw + (rh + dy) * kRawW + (rw + dx) * 3;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) v[(dy * 3 + dx) * 3 + c] = in ? snorm[px[c]] : 0.f;
+        for (int j = 0; j < 9; ++j) {
+          const int xx = w_in + j / 3;
+          const bool in = yin && xx >= 0 && xx < p.R;
+          v[dy * 9 + j] = in ? fmaf(byte_f32(by[j >> 2], j & 3), kNorm, -1.f) : 0.f;
         }
+      }
 #pragma unroll
       for (int k = 27; k < 32; ++k) v[k] = 0.f;
       __syncwarp();
@@ -1593,11 +1771,17 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
   } else {
     // ------------------------------------------------------------------ epilogue
     // two warpgroups take alternate tiles, so one group's TMEM read and stores
-    // overlap the other's; warp w of a group reads lane quarter w % 4
+    // overlap the other's; warp w of a group reads lane quarter w % 4, i.e.
+    // pixels 32 q .. 32 q + 31 of the tile: tile rows 2q, 2q + 1, which is the
+    // output box {CO channels, 16 columns, 2 rows} with lane = staged row
     const int q = warp & 3;
-    const int row = q * 32 + lane;
-    const int grp = (warp - kFirstMmaWarp - 1) / 4;
-    int tcount = 0;
+    const int ew = warp - kFirstMmaWarp - 1;
+    const int grp = ew / 4;
+    // staged row = lane, swizzled like the output map (64-byte rows: chunk
+    // j ^ ((row >> 1) & 3); 128-byte rows: chunk j ^ (row & 7))
+    const int osw = CO == 32 ? (lane >> 1) & 3 : lane & 7;
+    uint8_t* stg0 = sOut + (size_t)ew * 2 * Cfg::kOutWarpBytes;
+    int tcount = 0, lt = 0;
     TileWalk tw;
     tw.init(p.R / kHTH, p.R / kHTW);
     for (; tw.t < p.n_tiles; tw.next(), ++tcount) {
@@ -1606,8 +1790,10 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const int hh = tw.ty * kHTH + row / kHTW, ww = tw.tx * kHTW + row % kHTW;
-      const long long m = (long long)tw.img * RR + (long long)hh * p.R + ww;
+      // staging buffer lt & 1: the store issued from it two tiles ago has read it
+      if (lane == 0) bulk_wait_read1();
+      __syncwarp();
+      uint8_t* srow = stg0 + (size_t)(lt & 1) * Cfg::kOutWarpBytes + lane * (CO * 2);
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Cfg::kBufCols);
 #pragma unroll
       for (int c = 0; c < CO; c += 32) {
@@ -1622,15 +1808,25 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
           for (int j = 0; j < 16; j += 2)
             packed[j / 2] = pack2(fmaxf(fmaf(sg[cc + j], a[j], sb[cc + j]), 0.f),
                                   fmaxf(fmaf(sg[cc + j + 1], a[j + 1], sb[cc + j + 1]), 0.f));
-          uint4* dst = reinterpret_cast<uint4*>(p.y + m * p.y_cs + p.y_co + cc);
-          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+          const int j0 = cc / 8;
+          *reinterpret_cast<uint4*>(srow + ((j0 ^ osw) << 4)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          *reinterpret_cast<uint4*>(srow + (((j0 + 1) ^ osw) << 4)) =
+              make_uint4(packed[4], packed[5], packed[6], packed[7]);
         }
       }
       tc_fence_before();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&tempty[buf]));
+        tma_store_4d(&mapY, smem_u32(stg0 + (size_t)(lt & 1) * Cfg::kOutWarpBytes), 0, tw.tx * kHTW,
+                     tw.ty * kHTH + 2 * q, tw.img);
+        bulk_commit();
+      }
+      ++lt;
     }
+    // the output must be in global memory before the kernel ends
+    if (lane == 0) bulk_wait_all();
   }
   __syncwarp();
   tc_fence_before();
@@ -1799,16 +1995,16 @@ bool halo_ok(int R, int cout, int cin, int cr) {
   return halo_stages(cin, cout, cr, 32) >= 2;
 }
 
-template <int BN, int CK, bool RES, int MB>
+template <int BN, int CK, bool RES, int MB, bool PAIR = false>
 cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
-  using Cfg = HaloCfg<BN, CK, RES, MB>;
+  using Cfg = HaloCfg<BN, CK, RES, MB, PAIR>;
   CUtensorMap mA, mB, mA2, mB2;
   if (a.R % (kHTH * MB)) return cudaErrorInvalidValue;
   if (!map_act_box(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, kHTW, Cfg::kBoxRows)) return cudaErrorInvalidValue;
-  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, BN, CK)) return cudaErrorInvalidValue;
+  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, Cfg::kWRows, CK)) return cudaErrorInvalidValue;
   if (RES) {
     if (!map_act_box(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK, kHTW, kHTH * MB)) return cudaErrorInvalidValue;
-    if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, BN, CK)) return cudaErrorInvalidValue;
+    if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, Cfg::kWRows, CK)) return cudaErrorInvalidValue;
   } else {
     mA2 = mA;
     mB2 = mB;
@@ -1853,16 +2049,53 @@ cudaError_t launch_halo(const ConvArgs& a, cudaStream_t st, int stages) {
   hp.stages = stages;
   const size_t smem = fixed + (size_t)stages * stage_bytes;
   if (smem > (size_t)kHaloSmemMax) return cudaErrorInvalidValue;
-  auto kern = k_conv_tc_halo<BN, CK, RES, MB>;
+  auto kern = k_conv_tc_halo<BN, CK, RES, MB, PAIR>;
   static bool attr_set = false;
+  static int max_pairs = 0;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloSmemMax);
     if (e != cudaSuccess) return e;
+    if (PAIR) {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(2 * (num_sms() / 2));
+      q.blockDim = dim3(kThreadsTC);
+      q.dynamicSmemBytes = kHaloSmemMax;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      q.attrs = at;
+      q.numAttrs = 1;
+      e = cudaOccupancyMaxActiveClusters(&max_pairs, kern, &q);
+      if (e != cudaSuccess || max_pairs < 1) return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
+    }
     attr_set = true;
   }
-  int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
-  kern<<<grid, kThreadsTC, smem, st>>>(mA, mB, mA2, mB2, hp);
-  return cudaGetLastError();
+  if (!PAIR) {
+    int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
+    kern<<<grid, kThreadsTC, smem, st>>>(mA, mB, mA2, mB2, hp);
+    return cudaGetLastError();
+  }
+  // pairs: CTA 0 of cluster k takes tiles 2k, 2k + grid, ..., CTA 1 the next
+  // ones; both need the same count, so the tile count must be even
+  if (p.n_tiles % 2) return cudaErrorInvalidValue;
+  int pairs = p.n_tiles / 2 < max_pairs ? p.n_tiles / 2 : max_pairs;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * pairs);
+  cfg.blockDim = dim3(kThreadsTC);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mA, mB, mA2, mB2, hp);
+  if (e != cudaSuccess) cudaGetLastError();   // a refused launch leaves no sticky state behind
+  return e;
 }
 
 // dx-in-N variant: resident weights + one 10 x 16 box per stage
@@ -1963,12 +2196,31 @@ bool map_canvas(CUtensorMap* m, const uint8_t* canvas, long long stride, int can
   return r == CUDA_SUCCESS;
 }
 
+// first-layer output as a store target: {CO channels, R, R, B} at channel
+// offset co of rows cs channels long; box {CO, 16 columns, 2 rows, 1 image},
+// swizzled like the epilogue's staging (64-byte rows for CO = 32, 128 for 64)
+bool map_out_first(CUtensorMap* m, void* base, int CO, int cs, int co, int R, int B) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  char* ptr = static_cast<char*>(base) + (size_t)co * 2;
+  cuuint64_t dims[4] = {(cuuint64_t)CO, (cuuint64_t)R, (cuuint64_t)R, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)R * cs * 2, (cuuint64_t)R * R * cs * 2};
+  cuuint32_t box[4] = {(cuuint32_t)CO, (cuuint32_t)kHTW, 2, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, ptr, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CO == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 template <int CO>
 cudaError_t launch_first(const ConvArgs& a, cudaStream_t st) {
   using Cfg = FirstCfg<CO>;
-  CUtensorMap mB;
+  CUtensorMap mB, mY;
   CanvasMaps mC;
   if (!map_w(&mB, a.w.w_bf16, 32, a.cout, CO, 32)) return cudaErrorInvalidValue;
+  if (!map_out_first(&mY, a.y, CO, a.y_cs, a.y_co, a.R, a.B)) return cudaErrorInvalidValue;
   for (int k = 0; k < kMaxCanvases; ++k) {
     if (k > 0 && a.cv.ptr[k] == a.cv.ptr[k - 1] && a.cv.stride[k] == a.cv.stride[k - 1] &&
         a.cv.rows[k] == a.cv.rows[k - 1]) {
@@ -2000,7 +2252,7 @@ cudaError_t launch_first(const ConvArgs& a, cudaStream_t st) {
     attr_set = true;
   }
   int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
-  kern<<<grid, kThreadsFirst, Cfg::kSmem, st>>>(mB, mC, p);
+  kern<<<grid, kThreadsFirst, Cfg::kSmem, st>>>(mB, mC, mY, p);
   return cudaGetLastError();
 }
 
@@ -2054,6 +2306,11 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
     const int stg2 = dxn_stages(cin, cout, cr, 32, 2);
     if (cout == 32 && R % 16 == 0 && stg2 >= 2 && n < max) out[n++] = TcConfig{4, 32, 32, stg2};
   }
+  // kind 4 per 32-output-channel slice (weights of a slice resident)
+  if (cout >= 64 && cout <= 256 && cout % 32 == 0 && R % 16 == 0 && dxn_ok(R, 32, cin, cr)) {
+    const int stg = dxn_stages(cin, 32, cr, 32, 2);
+    if (stg >= 2 && n < max) out[n++] = TcConfig{7, 32, 32, stg};
+  }
   if (halo_ok(R, cout, cin, cr)) {
     for (int ck = 32; ck <= 64; ck *= 2) {
       const int stg = halo_stages(cin, cout, cr, ck);
@@ -2061,6 +2318,7 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
     }
     const int stg2 = halo_stages(cin, cout, cr, 32, 2);
     if (stg2 >= 2 && n < max) out[n++] = TcConfig{3, cout, 32, stg2};
+    if (stg2 >= 2 && n < max) out[n++] = TcConfig{6, cout, 32, stg2};
   }
   for (int bn = 32; bn <= 256; bn *= 2)
     for (int ck = 32; ck <= 64; ck *= 2)
@@ -2068,10 +2326,10 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
   return n;
 }
 
-bool tc_fuses_pool(const TcConfig& c) { return c.kind >= 1 && c.kind <= 4; }
+bool tc_fuses_pool(const TcConfig& c) { return c.kind >= 1 && c.kind <= 6 && c.kind != 5; }
 
 bool tc_fuses_head(const TcConfig& c, int cout, int ncls) {
-  return ((c.kind == 1 || c.kind == 2 || c.kind == 3) && (cout == 32 || cout == 64) ||
+  return ((c.kind == 1 || c.kind == 2 || c.kind == 3 || c.kind == 6) && (cout == 32 || cout == 64) ||
           (c.kind == 4 && cout == 32)) &&
          ncls >= 1 && ncls <= 2;
 }
@@ -2122,6 +2380,28 @@ cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaSt
 #undef OMNI_DXN
     return cudaErrorInvalidValue;
   }
+  if (c.kind == 7) {
+    // one kind-4 launch per 32 output channels: a slice's weight rows, gamma,
+    // beta and projection rows are contiguous; its output starts at channel
+    // y_co + 32 h.  No fused pool / head / RGB projection (they need every
+    // channel of a pixel, or a strided weight layout).
+    if (a.res_mode == RES_RGB || a.pool || a.head_theta || a.cout < 64 || a.cout > 256 || a.cout % 32 ||
+        a.R % 16 || c.bn != 32 || c.ck != 32 || !dxn_ok(a.R, 32, a.cin, cr) || c.stages < 2 ||
+        c.stages > dxn_stages(a.cin, 32, cr, 32, 2))
+      return cudaErrorInvalidValue;
+    for (int h = 0; h < a.cout / 32; ++h) {
+      ConvArgs sl = a;
+      sl.cout = 32;
+      sl.w.w_bf16 = a.w.w_bf16 + (size_t)h * 32 * 9 * a.cin;
+      sl.w.gamma = a.w.gamma + 32 * h;
+      sl.w.beta = a.w.beta + 32 * h;
+      if (res) sl.w.wp_bf16 = a.w.wp_bf16 + (size_t)h * 32 * cr;
+      sl.y_co = a.y_co + 32 * h;
+      cudaError_t e = res ? launch_dxn<32, 32, true, 2>(sl, st, c.stages) : launch_dxn<32, 32, false, 2>(sl, st, c.stages);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   if (c.kind == 4) {
     // two blocks per tile: cout 32 only (TMEM holds two buffers of 2 x (96 + 32) columns)
     if (!dxn_ok(a.R, a.cout, a.cin, cr) || a.cout != 32 || c.bn != 32 || c.ck != 32 || a.R % 16 ||
@@ -2140,10 +2420,15 @@ cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaSt
 #undef OMNI_HALO
     return cudaErrorInvalidValue;
   }
-  if (c.kind == 3) {
+  if (c.kind == 3 || c.kind == 6) {
     if (!halo_ok(a.R, a.cout, a.cin, cr) || c.bn != a.cout || c.ck != 32 || c.stages < 2 ||
         c.stages > halo_stages(a.cin, a.cout, cr, 32, 2))
       return cudaErrorInvalidValue;
+    if (c.kind == 6) {
+      if (c.bn == 32) return res ? launch_halo<32, 32, true, 2, true>(a, st, c.stages) : launch_halo<32, 32, false, 2, true>(a, st, c.stages);
+      if (c.bn == 64) return res ? launch_halo<64, 32, true, 2, true>(a, st, c.stages) : launch_halo<64, 32, false, 2, true>(a, st, c.stages);
+      return cudaErrorInvalidValue;
+    }
     if (c.bn == 32) return res ? launch_halo<32, 32, true, 2>(a, st, c.stages) : launch_halo<32, 32, false, 2>(a, st, c.stages);
     if (c.bn == 64) return res ? launch_halo<64, 32, true, 2>(a, st, c.stages) : launch_halo<64, 32, false, 2>(a, st, c.stages);
     return cudaErrorInvalidValue;

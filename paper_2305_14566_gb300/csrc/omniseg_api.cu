@@ -705,6 +705,21 @@ TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, float unfu
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return best;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return best; }
+  // a variant that cannot fuse a requested 2x2 max-pool pays the separate
+  // pooling launch (the conv's output is pooled afterwards)
+  float pool_ms = 0.f;
+  if (a.pool && a.y) {
+    bool ok = launch_maxpool(ctx->cfg.precision, a.B, a.R, a.cout, a.y, a.y_cs, a.y_co, a.pool, a.pool_cs, 0,
+                             st) == cudaSuccess &&
+              cudaEventRecord(e0, st) == cudaSuccess;
+    for (int r = 0; r < 3 && ok; ++r)
+      ok = launch_maxpool(ctx->cfg.precision, a.B, a.R, a.cout, a.y, a.y_cs, a.y_co, a.pool, a.pool_cs, 0, st) ==
+           cudaSuccess;
+    ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+         cudaEventElapsedTime(&pool_ms, e0, e1) == cudaSuccess;
+    pool_ms = ok ? pool_ms / 3.f : 0.f;
+    ctx->launches += 4;
+  }
   for (int i = 0; i < n; ++i) {
     if (head_only && !tc_fuses_head(cands[i], a.cout, a.head_ncls)) continue;
     const ConvArgs ai = fit_fused(a, cands[i]);
@@ -716,6 +731,7 @@ TcConfig tune_conv(omni_ctx* ctx, const ConvArgs& a, cudaStream_t st, float unfu
     float ms = 0;
     ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
     if (a.head_theta && !ai.head_theta) ms += 3.f * unfused_ms;   // three timed launches
+    if (a.pool && !ai.pool) ms += 3.f * pool_ms;
     if (ok && ms < best_ms) {
       best_ms = ms;
       best = cands[i];
@@ -734,6 +750,7 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag
   Rec r(ctx, st, 0, tag, conv_flops(in));
   ConvArgs a = in;
   cudaError_t e;
+  int nlaunch = 1;
   if (ctx->cfg.precision == OMNI_FP32) {
     a.pool = nullptr;
     a.head_theta = nullptr;
@@ -758,9 +775,10 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag
     }
     a = fit_fused(in, cfg);
     e = launch_conv_tc_cfg(a, cfg, st);
+    if (cfg.kind == 7) nlaunch = a.cout / 32;      // one launch per 32-channel slice
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "conv");
-  ctx->launches++;
+  ctx->launches += nlaunch;
   if (pooled) *pooled = a.pool != nullptr;
   if (headed) *headed = a.head_theta != nullptr;
   return OMNI_OK;
@@ -1493,13 +1511,29 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
                             const void* x, int32_t x_cs, int32_t x_co, const float* w_host,
                             const float* g_host, const float* b_host, const void* r, int32_t r_cs,
                             int32_t r_co, int32_t cr, const float* wp_host, void* y, int32_t y_cs,
-                            int32_t y_co, int32_t repeat, float* ms_per_launch, void* stream) {
+                            int32_t y_co, const int32_t* config, int32_t repeat, float* ms_per_launch,
+                            void* stream) {
   if (repeat < 1) return OMNI_EINVAL;
   if (!x || !y || !w_host || !g_host || !b_host || B <= 0 || R <= 0 || cin <= 0 || cout <= 0) return OMNI_EINVAL;
   if (cin % 8 || cout % 8 || (r && (cr <= 0 || cr % 8 || !wp_host))) return OMNI_EINVAL;
   if (precision != OMNI_FP32 && precision != OMNI_BF16 && precision != OMNI_FP16) return OMNI_EINVAL;
   const bool f16 = precision == OMNI_FP16;
   if (precision != OMNI_FP32 && !conv_tc_supported(R, cin, cout, r ? cr : 0)) return OMNI_EINVAL;
+  TcConfig cfg{};
+  if (precision != OMNI_FP32) {
+    cfg = tc_default(R, cin, cout, r ? cr : 0);
+    if (config) {
+      TcConfig cands[16];
+      const int n = tc_candidates(R, cin, cout, r ? cr : 0, cands, 16);
+      bool found = false;
+      // a candidate's kind, N tile and chunk with at most its pipeline stages
+      for (int i = 0; i < n && !found; ++i)
+        found = cands[i].kind == config[0] && cands[i].bn == config[1] && cands[i].ck == config[2] &&
+                config[3] <= cands[i].stages && (cands[i].stages == 0 ? config[3] == 0 : config[3] >= 2);
+      if (!found) return OMNI_EINVAL;
+      cfg = TcConfig{config[0], config[1], config[2], config[3]};
+    }
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   size_t n9 = (size_t)9 * cin * cout, np = r ? (size_t)cr * cout : 0;
   std::vector<float> w32(n9), wp32(np);
@@ -1559,7 +1593,7 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
       cudaEventRecord(e0, st);
     }
     for (int i = 0; i < repeat && e == cudaSuccess; ++i)
-      e = precision == OMNI_FP32 ? launch_conv_f32(a, st) : launch_conv_tc(a, st);
+      e = precision == OMNI_FP32 ? launch_conv_f32(a, st) : launch_conv_tc_cfg(a, cfg, st);
     if (ms_per_launch) cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (ms_per_launch) {
@@ -1577,6 +1611,21 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
   cudaFree(d);
   cudaFree(derr);
   return rs;
+}
+
+int32_t omni_conv_candidates(int32_t R, int32_t cin, int32_t cout, int32_t cr, int32_t* rows,
+                             int32_t max_rows) {
+  if (!rows || max_rows < 1 || R <= 0 || cin <= 0 || cout <= 0 || cr < 0) return 0;
+  TcConfig cands[16];
+  const int n = tc_candidates(R, cin, cout, cr, cands, 16);
+  int k = 0;
+  for (; k < n && k < max_rows; ++k) {
+    rows[4 * k] = cands[k].kind;
+    rows[4 * k + 1] = cands[k].bn;
+    rows[4 * k + 2] = cands[k].ck;
+    rows[4 * k + 3] = cands[k].stages;
+  }
+  return k;
 }
 
 omni_status omni_set_timing(omni_ctx* ctx, int32_t enabled) {

@@ -4,19 +4,35 @@ needle-biopsy network (synth.NEEDLE, weights seed 11), from the FP64 oracle.
 No trained checkpoint exists, so the network's raw head output carries no
 trained decision threshold: with random weights it is negative everywhere and
 varies smoothly inside tissue.  A class's label decision is well conditioned
-only where few pixels respond near its threshold.  This script therefore
-places class c's threshold at the valley of its raw response:
+only where few pixels respond close to its threshold: a pixel whose raw
+response lies within a small band around the threshold can change label under
+a small perturbation of its logit, a pixel outside it cannot.  This script
+places class c's threshold where that band holds the fewest pixels relative
+to what the label comparison can absorb:
 
   1. calibration tiles: at each scale, vertical strips of tiles across tissue
      cores 0 and 3 of the needle slide (the test crops lie on core 2);
   2. raw response: the oracle's stitched-free tile logits of class c with
      every offset zero, at the tile pixels that the slide's tissue mask marks
      as tissue (the labels are ANDed with that mask);
-  3. threshold t_c: the smallest value of the histogram of those responses,
-     smoothed by a 9-bin moving average over 400 bins spanning their
-     0.5%..99.5% quantiles, among bins between their 5% and 95% quantiles;
-  4. offset_c = -t_c, added to the head's final bias through class c's
-     one-hot input (synth.weights).
+  3. candidates: the responses' quantiles at 400 evenly spaced levels from 1%
+     to 99% (so 1% to 99% of the tissue pixels end up positive) and the
+     midpoints between neighbouring ones;
+  4. for each candidate t: near(t) = share of tissue pixels whose response
+     lies within DELTA = 0.05 of t, pos(t) = share above t, and
+     score(t) = max(near / 0.001, near / (0.01 pos)): near against 0.1% of
+     the tissue and against 1% of the positives (a Dice loss of 0.005 is a
+     flipped share of 1% of the positives);
+  5. threshold t_c: the candidate of least score; offset_c = -t_c, added to
+     the head's final bias through class c's one-hot input (synth.weights).
+
+With this random network the in-tissue responses have no deep interior
+valley: at 10x and 5x they are smooth and unimodal (standard deviation about
+0.5 against 1.7 at 40x), so the least crowded thresholds lie in the low tail
+and label 97-99% of the tissue positive.  Restricted to 5%..95% positive, the
+best 5x thresholds still have 1.3-2.4% of the tissue within 0.05, where
+16-bit storage of the activations (logit noise of a few hundredths) flips
+more than 0.1% of the labels.
 
 Calls only the input generator and the FP64 oracle.  The tissue mask is the
 oracle's (tests/golden/needle_tissue_mask.npz, written by
@@ -60,15 +76,22 @@ def strip_tiles(w, spec, s, core, frac):
     return out
 
 
-def valley(x, bins=400, smooth=9, lo_q=0.05, hi_q=0.95):
-    lo, hi = np.quantile(x, [0.005, 0.995])
-    h, edges = np.histogram(x, bins=bins, range=(lo, hi))
-    hs = np.convolve(h, np.ones(smooth) / smooth, mode="same")
-    centres = 0.5 * (edges[1:] + edges[:-1])
-    a, b = np.quantile(x, [lo_q, hi_q])
-    inside = (centres > a) & (centres < b)
-    i = int(np.argmin(np.where(inside, hs, np.inf)))
-    return float(centres[i]), float(hs[i] / hs.max())
+DELTA = 0.05
+
+
+def least_crowded(x, lo_q=0.01, hi_q=0.99, n=400):
+    """Threshold of least score (see the module docstring) among the quantiles
+    of the responses x; returns (threshold, near share, positive share)."""
+    v = np.sort(np.asarray(x, np.float64))
+    best = None
+    q = np.quantile(v, np.linspace(lo_q, hi_q, n))
+    for t in np.concatenate([q, 0.5 * (q[1:] + q[:-1])]):
+        near = (np.searchsorted(v, t + DELTA, "right") - np.searchsorted(v, t - DELTA, "left")) / v.size
+        pos = 1.0 - np.searchsorted(v, t, "right") / v.size
+        score = max(near / 0.001, near / (0.01 * pos))
+        if best is None or score < best[0]:
+            best = (score, float(t), float(near), float(pos))
+    return best[1], best[2], best[3]
 
 
 def main():
@@ -98,12 +121,12 @@ def main():
                 vals[c].append(lg[k, 0].numpy()[m])
         for c in cls:
             v = np.concatenate(vals[c])
-            t, dens = valley(v)
+            t, near, pos = least_crowded(v)
             offsets[c] = -t
             out["classes"][str(c)] = {"scale": s, "name": synth.CLASS_NAMES[c], "threshold": t,
-                                      "offset": -t, "relative_density_at_threshold": dens,
+                                      "offset": -t, "share_within_delta": near, "delta": DELTA,
                                       "tiles": len(tiles), "tissue_pixels": int(v.size),
-                                      "positive_fraction_in_tissue": float(np.mean(v > t))}
+                                      "positive_fraction_in_tissue": pos}
             print(json.dumps({c: out["classes"][str(c)]}), flush=True)
     out["head_offsets"] = [round(o, 4) for o in offsets]
     with open(os.path.join(HERE, "head_offsets.json"), "w") as fh:

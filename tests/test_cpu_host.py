@@ -157,3 +157,23 @@ def test_stain_rejects_bad_arguments_without_device(L, case):
                             args["alp"].ctypes.data_as(C.c_void_p), args["out40"], args["os"],
                             args["down"], args["outd"], args["ds"], None)
     assert st == L.EINVAL
+
+
+def test_head_calibration_rule_picks_the_emptiest_band():
+    """The needle heads' calibration rule (tests/golden/make_head_offsets.py):
+    on a two-mode response it places the threshold in the empty gap between
+    the modes (no response within 0.05 of it, half the pixels positive); on
+    one Gaussian mode it moves to the low tail, the candidate range's end
+    (99% positive), where the fewest responses crowd the threshold."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "make_head_offsets", os.path.join(os.path.dirname(__file__), "golden", "make_head_offsets.py"))
+    M = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(M)
+    rng = np.random.default_rng(3)
+    two = np.concatenate([rng.normal(-2.0, 0.3, 20000), rng.normal(2.0, 0.3, 20000)])
+    t, near, pos = M.least_crowded(two)
+    assert -0.8 < t < 0.8 and near == 0.0 and abs(pos - 0.5) < 1e-3, (t, near, pos)
+    one = rng.normal(-4.0, 1.0, 40000)
+    t, near, pos = M.least_crowded(one)
+    assert abs(pos - 0.99) < 2e-3 and t < -6.0, (t, near, pos)

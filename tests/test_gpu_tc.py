@@ -54,6 +54,87 @@ def fp16_round(a: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(a, np.float32).astype(np.float16).astype(np.float32)
 
 
+def _layer_case(R, cin, cout, cr, prec, B=2):
+    """Seeded operands of one conv layer (rounded to the 16-bit type) and the
+    oracle's FP64 result on them."""
+    rng = np.random.default_rng(1000 + R + cin + cout + cr)
+    rnd = bf16_round if prec == "bf16" else fp16_round
+    x = rnd(np.abs(rng.standard_normal((B, R, R, cin))))
+    w = rnd(rng.standard_normal((cout, cin, 3, 3)) * np.sqrt(2 / (9 * cin)))
+    g = rng.uniform(0.9, 1.1, cout).astype(np.float32)
+    b = rng.uniform(-0.05, 0.05, cout).astype(np.float32)
+    r = rnd(np.abs(rng.standard_normal((B, R, R, cr)))) if cr else None
+    wp = rnd(rng.standard_normal((cout, cr)) * np.sqrt(1 / cr)) if cr else None
+    xt = torch.from_numpy(x.astype(np.float64)).permute(0, 3, 1, 2)
+    z = O.affine(O.conv3x3(xt, torch.from_numpy(w.astype(np.float64))),
+                 torch.from_numpy(g.astype(np.float64)), torch.from_numpy(b.astype(np.float64)))
+    if cr:
+        z = z + O.conv1x1(torch.from_numpy(r.astype(np.float64)).permute(0, 3, 1, 2),
+                          torch.from_numpy(wp.astype(np.float64)))
+    ref = O.relu(z).permute(0, 2, 3, 1).numpy()
+    return x, w, g, b, r, wp, ref
+
+
+# shapes whose candidates include the small-N kernels (one and two blocks per
+# tile, and the CTA-pair form of the latter) and the dx-in-N kernels
+# (kind 7: the two-block dx-in-N kernel once per 32 output channels)
+VARIANT_SHAPES = [(64, 32, 32, 0), (64, 64, 64, 64), (64, 96, 32, 0), (32, 32, 64, 32), (128, 64, 32, 0),
+                  (64, 192, 64, 0), (32, 64, 128, 64)]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("R,cin,cout,cr", VARIANT_SHAPES)
+def test_every_conv_variant_against_oracle(api, R, cin, cout, cr, prec):
+    """Every legal tensor-core configuration of the shape (omni_conv_candidates)
+    meets the layer bound against the oracle (the 32-channel slices of kind 7
+    included); the CTA-pair form of the two-block small-N kernel (kind 6:
+    cta_group::2 MMAs over both CTAs' tiles) equals its one-CTA form (kind 3)
+    bit for bit: same products, same accumulation order per pixel."""
+    from paper_2305_14566_gb300 import _lib as L
+    B = 2
+    dt = torch.bfloat16 if prec == "bf16" else torch.float16
+    x, w, g, b, r, wp, ref = _layer_case(R, cin, cout, cr, prec, B)
+    xd = torch.from_numpy(x).cuda().to(dt)
+    rd = torch.from_numpy(r).cuda().to(dt) if cr else None
+    cands = api.conv_candidates(R, cin, cout, cr)
+    assert cands, (R, cin, cout, cr)
+    outs = {}
+    ulp = 2.0 ** -8 if prec == "bf16" else 2.0 ** -11
+    bound = ulp * np.abs(ref) + 1e-4 * np.sqrt(9 * cin + cr)
+    for cfg in cands:
+        y = torch.full((B, R, R, cout), float("nan"), dtype=dt, device="cuda")
+        api.conv_layer(L.BF16 if prec == "bf16" else L.FP16, xd, R, cin, cout, w, g, b, y, rd, cr, wp,
+                       config=cfg)
+        got = y.float().cpu().numpy()
+        assert np.isfinite(got).all(), cfg
+        err = np.abs(got - ref)
+        assert (err <= bound).all(), (cfg, float(err.max()), float((err - bound).max()))
+        outs[cfg] = y
+    kinds = {c[0]: c for c in cands}
+    if 3 in kinds:
+        assert 6 in kinds, cands
+        assert torch.equal(outs[kinds[6]], outs[kinds[3]])
+    if cout >= 64:
+        assert 7 in kinds, cands
+
+
+def test_pair_variant_refuses_an_odd_tile_count(api):
+    """The CTA-pair kernel splits tiles between the two CTAs of a pair and
+    needs an even count: one 16 x 16 image is refused with an error (no
+    launch), and the context's next default launch works."""
+    from paper_2305_14566_gb300 import _lib as L
+    x, w, g, b, r, wp, ref = _layer_case(16, 32, 32, 0, "bf16", B=1)
+    xd = torch.from_numpy(x).cuda().to(torch.bfloat16)
+    cfg = [c for c in api.conv_candidates(16, 32, 32, 0) if c[0] == 6]
+    assert cfg
+    y = torch.zeros((1, 16, 16, 32), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(L.OmniError):
+        api.conv_layer(L.BF16, xd, 16, 32, 32, w, g, b, y, config=cfg[0])
+    api.conv_layer(L.BF16, xd, 16, 32, 32, w, g, b, y)
+    err = np.abs(y.float().cpu().numpy() - ref)
+    assert (err <= 2.0 ** -8 * np.abs(ref) + 1e-4 * np.sqrt(9 * 32)).all()
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("R,cin,cout,cr", SHAPES)
 def test_conv_layer_bf16(api, R, cin, cout, cr, prec):
