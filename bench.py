@@ -170,7 +170,9 @@ def run_layer(args):
     from paper_2305_14566_gb300.build import build
     build()
     from paper_2305_14566_gb300 import api, _lib
-    R, cin, cout, cr, B, rep = (int(v) for v in args.layer.split(","))
+    vals = [int(v) for v in args.layer.split(",")]
+    R, cin, cout, cr, B, rep = vals[:6]
+    config = tuple(vals[6:10]) if len(vals) == 10 else None   # kind, N tile, chunk, stages
     rng = np.random.default_rng(0)
     prec = {"bf16": _lib.BF16, "fp16": _lib.FP16, "fp32": _lib.FP32}[args.precision]
     dt = {"bf16": torch.bfloat16, "fp16": torch.float16, "fp32": torch.float32}[args.precision]
@@ -181,12 +183,13 @@ def run_layer(args):
     g = np.ones(cout, np.float32)
     b = np.zeros(cout, np.float32)
     wp = (rng.standard_normal((cout, cr)) * np.sqrt(1 / cr)).astype(np.float32) if cr else None
-    api.conv_layer(prec, x, R, cin, cout, w, g, b, y, r, cr, wp, repeat=1)
-    ms = api.conv_layer(prec, x, R, cin, cout, w, g, b, y, r, cr, wp, repeat=rep)
+    api.conv_layer(prec, x, R, cin, cout, w, g, b, y, r, cr, wp, repeat=1, config=config)
+    ms = api.conv_layer(prec, x, R, cin, cout, w, g, b, y, r, cr, wp, repeat=rep, config=config)
     fl = 2.0 * B * R * R * cout * (9 * cin + cr)
     pk, src = peaks()
     tf = fl / (ms / 1e3) / 1e12
-    print(json.dumps({"layer": {"R": R, "cin": cin, "cout": cout, "cr": cr, "B": B},
+    print(json.dumps({"layer": {"R": R, "cin": cin, "cout": cout, "cr": cr, "B": B,
+                                "config": list(config) if config else "default"},
                       "ms_per_launch": ms, "tflops": tf, "frac_of_bf16_burst": tf / pk["bf16_tflops"],
                       "peak_source": src}))
 
@@ -435,7 +438,8 @@ def main():
                          "(for ncu --profile-from-start off)")
     ap.add_argument("--max-batch", type=int, default=0, help="tiles per network batch (0: the workload's)")
     ap.add_argument("--layer", default=None,
-                    help="R,cin,cout,cr,B,repeat: time one fused conv layer instead")
+                    help="R,cin,cout,cr,B,repeat[,kind,N tile,chunk,stages]: time one fused conv layer "
+                         "instead (optionally one tensor-core configuration of omni_conv_candidates)")
     args = ap.parse_args()
     if args.layer:
         run_layer(args)

@@ -381,48 +381,112 @@ __device__ __forceinline__ void lds4(const float* p, float v[4]) {
   v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
 
-// Dynamic head of one class on the pre-head feature h0 (already through its
-// ReLU): logit = W3 ReLU(W2 ReLU(W1 h0 + b1) + b2) + b3, with theta laid out
-// as W1 (8x8, out-major), W2 (8x8), W3 (8), b1 (8), b2 (8), b3 (1).  theta is
-// a 16-byte aligned shared-memory row (all lanes of a warp read the same
-// tile's row: broadcast 16-byte loads, eight weights per two loads).
-constexpr int kThetaPad = 160;   // theta row stride in the fused heads' shared copies
-__device__ __forceinline__ float dyn_head(const float* th, const float h0[8]) {
+// Dynamic head of one class on the pre-head features h0 of NP pixels (already
+// through their ReLU): logit = W3 ReLU(W2 ReLU(W1 h0 + b1) + b2) + b3, with
+// theta laid out as W1 (8x8, out-major), W2 (8x8), W3 (8), b1 (8), b2 (8),
+// b3 (1).  theta is a 16-byte aligned shared-memory row read with 16-byte
+// loads; every weight loaded serves all NP pixels (a broadcast 16-byte load
+// costs as many shared-memory wavefronts as four 4-byte ones, so the loads,
+// not the FMAs, bound the fused heads).
+constexpr int kThetaPad = 168;   // theta row stride of the fused heads' shared copies: the two
+                                 // classes' rows start 8 banks apart, so lanes reading different
+                                 // classes in one load do not conflict
+template <int NP>
+__device__ __forceinline__ void dyn_head_n(const float* th, const float (*h0)[8], float* out) {
   const float4* t4 = reinterpret_cast<const float4*>(th);
-  float h1[8], h2[8];
+  float h1[NP][8], h2[NP][8];
   const float4 b1a = t4[34], b1b = t4[35], b2a = t4[36], b2b = t4[37];
   const float b1[8] = {b1a.x, b1a.y, b1a.z, b1a.w, b1b.x, b1b.y, b1b.z, b1b.w};
   const float b2[8] = {b2a.x, b2a.y, b2a.z, b2a.w, b2b.x, b2b.y, b2b.z, b2b.w};
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
     const float4 wa = t4[2 * o], wb = t4[2 * o + 1];
-    float s = b1[o];
-    s = fmaf(wa.x, h0[0], s); s = fmaf(wa.y, h0[1], s); s = fmaf(wa.z, h0[2], s); s = fmaf(wa.w, h0[3], s);
-    s = fmaf(wb.x, h0[4], s); s = fmaf(wb.y, h0[5], s); s = fmaf(wb.z, h0[6], s); s = fmaf(wb.w, h0[7], s);
-    h1[o] = fmaxf(s, 0.f);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float* x = h0[q];
+      float s = b1[o];
+      s = fmaf(wa.x, x[0], s); s = fmaf(wa.y, x[1], s); s = fmaf(wa.z, x[2], s); s = fmaf(wa.w, x[3], s);
+      s = fmaf(wb.x, x[4], s); s = fmaf(wb.y, x[5], s); s = fmaf(wb.z, x[6], s); s = fmaf(wb.w, x[7], s);
+      h1[q][o] = fmaxf(s, 0.f);
+    }
   }
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
     const float4 wa = t4[16 + 2 * o], wb = t4[16 + 2 * o + 1];
-    float s = b2[o];
-    s = fmaf(wa.x, h1[0], s); s = fmaf(wa.y, h1[1], s); s = fmaf(wa.z, h1[2], s); s = fmaf(wa.w, h1[3], s);
-    s = fmaf(wb.x, h1[4], s); s = fmaf(wb.y, h1[5], s); s = fmaf(wb.z, h1[6], s); s = fmaf(wb.w, h1[7], s);
-    h2[o] = fmaxf(s, 0.f);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float* x = h1[q];
+      float s = b2[o];
+      s = fmaf(wa.x, x[0], s); s = fmaf(wa.y, x[1], s); s = fmaf(wa.z, x[2], s); s = fmaf(wa.w, x[3], s);
+      s = fmaf(wb.x, x[4], s); s = fmaf(wb.y, x[5], s); s = fmaf(wb.z, x[6], s); s = fmaf(wb.w, x[7], s);
+      h2[q][o] = fmaxf(s, 0.f);
+    }
   }
   const float4 wa = t4[32], wb = t4[33];
-  float s = th[152];
-  s = fmaf(wa.x, h2[0], s); s = fmaf(wa.y, h2[1], s); s = fmaf(wa.z, h2[2], s); s = fmaf(wa.w, h2[3], s);
-  s = fmaf(wb.x, h2[4], s); s = fmaf(wb.y, h2[5], s); s = fmaf(wb.z, h2[6], s); s = fmaf(wb.w, h2[7], s);
-  return s;
+  const float b3 = th[152];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const float* x = h2[q];
+    float s = b3;
+    s = fmaf(wa.x, x[0], s); s = fmaf(wa.y, x[1], s); s = fmaf(wa.z, x[2], s); s = fmaf(wa.w, x[3], s);
+    s = fmaf(wb.x, x[4], s); s = fmaf(wb.y, x[5], s); s = fmaf(wb.z, x[6], s); s = fmaf(wb.w, x[7], s);
+    out[q] = s;
+  }
 }
 
-// h0 += W_h[:, n] v for one channel n: the pre-head weights are stored
-// channel-major (8 outputs of a channel contiguous, 16-byte aligned)
-__device__ __forceinline__ void prehead_acc(const float* swh_t, int n, float v, float h0[8]) {
-  const float4 a = *reinterpret_cast<const float4*>(swh_t + 8 * n);
-  const float4 b = *reinterpret_cast<const float4*>(swh_t + 8 * n + 4);
-  h0[0] = fmaf(a.x, v, h0[0]); h0[1] = fmaf(a.y, v, h0[1]); h0[2] = fmaf(a.z, v, h0[2]); h0[3] = fmaf(a.w, v, h0[3]);
-  h0[4] = fmaf(b.x, v, h0[4]); h0[5] = fmaf(b.y, v, h0[5]); h0[6] = fmaf(b.z, v, h0[6]); h0[7] = fmaf(b.w, v, h0[7]);
+// Fused pre-head on lane pairs.  Lanes 2i and 2i+1 hold horizontally adjacent
+// pixels; lane half h = lane & 1 accumulates pre-head outputs 4h..4h+3 of its
+// own pixel (hs) and of its partner's (hp) from the pre-head weights stored
+// channel-major (the 8 outputs of a channel contiguous, 16-byte aligned), so a
+// lane reads 4 of each channel's 8 weights.  Every output's sum starts from
+// its bias and adds the channels in the order one lane doing all eight would.
+__device__ __forceinline__ void prehead_pair(const float* swh_t, int n, float v, int h, float hs[4],
+                                             float hp[4]) {
+  const float vp = __shfl_xor_sync(0xffffffffu, v, 1);
+  const float4 w = *reinterpret_cast<const float4*>(swh_t + 8 * n + 4 * h);
+  hs[0] = fmaf(w.x, v, hs[0]); hs[1] = fmaf(w.y, v, hs[1]); hs[2] = fmaf(w.z, v, hs[2]); hs[3] = fmaf(w.w, v, hs[3]);
+  hp[0] = fmaf(w.x, vp, hp[0]); hp[1] = fmaf(w.y, vp, hp[1]); hp[2] = fmaf(w.z, vp, hp[2]); hp[3] = fmaf(w.w, vp, hp[3]);
+}
+// ReLU, then one exchange: both lanes of the pair end with all eight pre-head
+// outputs of the even lane's pixel (he) and of the odd lane's (ho)
+__device__ __forceinline__ void prehead_pair_finish(int h, float hs[4], float hp[4], float he[8], float ho[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    hs[k] = fmaxf(hs[k], 0.f);
+    hp[k] = fmaxf(hp[k], 0.f);
+    const float rs = __shfl_xor_sync(0xffffffffu, hs[k], 1);   // partner's pixel, partner's half
+    const float rp = __shfl_xor_sync(0xffffffffu, hp[k], 1);   // this lane's pixel, partner's half
+    he[k] = h ? rs : hs[k];
+    he[4 + k] = h ? hp[k] : rp;
+    ho[k] = h ? rp : hp[k];
+    ho[4 + k] = h ? hs[k] : rs;
+  }
+}
+
+// Dynamic heads of a lane pair's two pixels (he, ho: see prehead_pair_finish)
+// into the batch's logit slots at pixel offsets pe / po of the tile image
+// whose class-0 plane starts at lo.  Two classes: lane half h runs class h for
+// both pixels (one read of its theta row for two pixels); one class: each lane
+// runs it for its own pixel.  A pixel whose write flag is off is not stored.
+__device__ __forceinline__ void heads_pair(const float* sth, int ncls, long long RR, float* lo, int h,
+                                           const float he[8], const float ho[8], long long pe, long long po,
+                                           bool we, bool wo) {
+  if (ncls == 2) {
+    const float x[2][8] = {{he[0], he[1], he[2], he[3], he[4], he[5], he[6], he[7]},
+                           {ho[0], ho[1], ho[2], ho[3], ho[4], ho[5], ho[6], ho[7]}};
+    float l[2];
+    dyn_head_n<2>(sth + h * kThetaPad, x, l);
+    float* L = lo + (long long)h * RR;
+    if (we) L[pe] = l[0];
+    if (wo) L[po] = l[1];
+  } else {
+    float x[1][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[0][k] = h ? ho[k] : he[k];
+    float l[1];
+    dyn_head_n<1>(sth, x, l);
+    if (h ? wo : we) lo[h ? po : pe] = l[0];
+  }
 }
 
 // 2x2 max of a pixel's 16 channel values with the pixels of lanes lane^dxl
@@ -1073,9 +1137,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         v1 = norm_u8((uint8_t)u1);
         v2 = norm_u8((uint8_t)u2);
       }
-      float h0[kHeadCh];
+      // fused head: this lane's half of the pre-head outputs for its pixel and its partner's
+      const int hf = lane & 1;
+      float hs[4], hp[4];
 #pragma unroll
-      for (int o = 0; o < kHeadCh; ++o) h0[o] = fuse_head ? sbh[o] : 0.f;
+      for (int k = 0; k < 4; ++k) hs[k] = hp[k] = fuse_head ? sbh[4 * hf + k] : 0.f;
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) +
                           (uint32_t)(buf * Cfg::kBufCols + blk * Cfg::kBlkCols);
 #pragma unroll 1
@@ -1124,7 +1190,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
         if (fuse_head) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) prehead_acc(swh, c + j, o16[j], h0);
+          for (int j = 0; j < 16; ++j) prehead_pair(swh, c + j, o16[j], hf, hs, hp);
         }
       }
       tc_fence_before();
@@ -1132,8 +1198,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       if (lane == 0) mbar_arrive_to<PAIR>(smem_u32(&tempty[buf]), peer);
       if (fuse_head) {
         // the TMEM buffer is released; the heads run on registers and shared memory
-#pragma unroll
-        for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaxf(h0[o], 0.f);
+        float he[8], ho[8];
+        prehead_pair_finish(hf, hs, hp, he, ho);
         if (img != th_img) {
           __syncwarp();
           const float* src = p.theta + (long long)img * p.ncls * kHeadParams;
@@ -1141,8 +1207,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           __syncwarp();
           th_img = img;
         }
-        float* lo = p.logits + (long long)(p.slot0 + img) * p.ncls * RR + (long long)hh * p.R + ww;
-        for (int ci = 0; ci < p.ncls; ++ci) lo[(long long)ci * RR] = dyn_head(sth + ci * kThetaPad, h0);
+        // the pair's pixels are columns ww and ww ^ 1 of tile row hh
+        const long long pix = (long long)hh * p.R + ww, pix_p = (long long)hh * p.R + (ww ^ 1);
+        heads_pair(sth, p.ncls, RR, p.logits + (long long)(p.slot0 + img) * p.ncls * RR, hf, he, ho,
+                   hf ? pix_p : pix, hf ? pix : pix_p, true, true);
       }
     }
   }
@@ -1441,9 +1509,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       __nv_bfloat16* out = p.y + m * p.y_cs + p.y_co;
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) +
                           (uint32_t)(buf * Cfg::kBufCols + blk * Cfg::kBlkCols);
-      float h0[kHeadCh];
+      // fused head: this lane's half of the pre-head outputs for its pixel and its partner's
+      const int hf = lane & 1;
+      float hs[4], hp[4];
 #pragma unroll
-      for (int o = 0; o < kHeadCh; ++o) h0[o] = fuse_head ? sbh[o] : 0.f;
+      for (int k = 0; k < 4; ++k) hs[k] = hp[k] = fuse_head ? sbh[4 * hf + k] : 0.f;
 #pragma unroll 1
       for (int c = co_beg; c < co_end; c += 16) {
         float d0[16], d1[16], d2[16], r[16], o16[16];
@@ -1495,7 +1565,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
         if (fuse_head) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) prehead_acc(swh, c + j, o16[j], h0);
+          for (int j = 0; j < 16; ++j) prehead_pair(swh, c + j, o16[j], hf, hs, hp);
         }
       }
       tc_fence_before();
@@ -1503,8 +1573,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
       if (fuse_head) {
         // the TMEM buffer is released; the heads run on registers and shared memory
-#pragma unroll
-        for (int o = 0; o < kHeadCh; ++o) h0[o] = fmaxf(h0[o], 0.f);
+        float he[8], ho[8];
+        prehead_pair_finish(hf, hs, hp, he, ho);
         if (img != th_img) {
           __syncwarp();
           const float* src = p.theta + (long long)img * p.ncls * kHeadParams;
@@ -1513,10 +1583,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           __syncwarp();
           th_img = img;
         }
-        if (writes) {
-          float* lo = p.logits + (long long)(p.slot0 + img) * p.ncls * RR + (long long)hh * p.R + ww;
-          for (int ci = 0; ci < p.ncls; ++ci) lo[(long long)ci * RR] = dyn_head(sth + ci * kThetaPad, h0);
-        }
+        // the pair's pixels: this lane's and its partner's (halo lanes and
+        // columns past R write nothing)
+        const long long pix = (long long)hh * p.R + (ww < 0 ? 0 : ww);
+        const long long pix_p = __shfl_xor_sync(0xffffffffu, pix, 1);
+        const bool wr_p = __shfl_xor_sync(0xffffffffu, writes ? 1 : 0, 1) != 0;
+        heads_pair(sth, p.ncls, RR, p.logits + (long long)(p.slot0 + img) * p.ncls * RR, hf, he, ho,
+                   hf ? pix_p : pix, hf ? pix : pix_p, hf ? wr_p : writes, hf ? writes : wr_p);
       }
     }
   }

@@ -357,8 +357,15 @@ def test_graph_replay_is_bit_identical_and_autotune_agrees(api):
     for c in ref["logits"]:
         d = (t_out["logits"][c] - ref["logits"][c]).abs().max().item()
         agree = (t_out["labels"][c] == ref["labels"][c]).float().mean().item()
-        print("autotune class %d max|dL| %.3e agree %.6f" % (c, d, agree))
-        assert d < 0.25 and agree >= 0.999
+        # a label is the sign of its stitched logit (ANDed with the same tissue
+        # mask), so the two runs' labels can differ only where the default
+        # run's logit lies within d of the threshold
+        decided = ref["logits"][c].abs() > d
+        same = (t_out["labels"][c] == ref["labels"][c])
+        print("autotune class %d max|dL| %.3e agree %.6f undecided %.5f" %
+              (c, d, agree, 1.0 - decided.float().mean().item()))
+        assert d < 0.25
+        assert bool(same[decided].all()), c
     tuned.close()
 
 
