@@ -291,6 +291,8 @@ def run_large(args, api, _lib, dev, prec):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if achieved else None, "traffic": None,
                          "kernel": "conv (all U-Net layers)", "peak_source": f"bf16 dense sustained ({src})"},
+            "memory": {"workspace_bytes": int(seg.query(works[0].H, works[0].W).workspace_bytes),
+                       "max_batch": int(works[0].max_batch)},
             "clocks": clk.summary()}
     if args.compare_fp32 and prec != _lib.FP32:
         keep = {c: t.clone() for c, t in outs[0]["labels"].items()}
@@ -643,6 +645,11 @@ def main():
                            "parallelism": f"replicas x{world}",
                            "tiles_per_step": tiles_step},
                 "roofline": roof, "stitch": stitch, "stain": stain, "e2e": e2e, "gpu_launches": int(launches),
+                "memory": {"workspace_bytes": int(seg.query(work.H, work.W).workspace_bytes),
+                           "max_batch": int(args.max_batch or work.max_batch),
+                           "note": "device workspace of one slide call (batch activations, tile-logit ring "
+                                   "of the banded stitch, pyramid, tiling); the slide and outputs are the "
+                                   "caller's"},
                 "breakdown": breakdown, "eager": eager,
                 "autotuned": tuned_rows,
                 "clocks": clocks}

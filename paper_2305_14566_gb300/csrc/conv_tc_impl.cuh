@@ -1774,6 +1774,8 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
       const uint32_t* wrow = reinterpret_cast<const uint32_t*>(sRaw + (size_t)s * kRawStageBytes) + (bb >> 2);
       const uint32_t sh = (uint32_t)(bb & 3) * 8u;
       const int h_in = tw.ty * kHTH + rh - 1, w_in = tw.tx * kHTW + rw - 1;   // tile coords of tap (0, 0)
+      // blocks whose 10 x 18 window lies inside the tile need no zero padding
+      const bool inner = tw.ty > 0 && (tw.ty + 1) * kHTH < p.R && tw.tx > 0 && (tw.tx + 1) * kHTW < p.R;
       float v[32];
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy) {
@@ -1781,13 +1783,18 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
         const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
         const uint32_t by[3] = {__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
                                 __funnelshift_r(w2, w2, sh)};
-        const int yy = h_in + dy;
-        const bool yin = yy >= 0 && yy < p.R;
+        if (inner) {
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
-          const int xx = w_in + j / 3;
-          const bool in = yin && xx >= 0 && xx < p.R;
-          v[dy * 9 + j] = in ? fmaf(byte_f32(by[j >> 2], j & 3), kNorm, -1.f) : 0.f;
+          for (int j = 0; j < 9; ++j) v[dy * 9 + j] = fmaf(byte_f32(by[j >> 2], j & 3), kNorm, -1.f);
+        } else {
+          const int yy = h_in + dy;
+          const bool yin = yy >= 0 && yy < p.R;
+#pragma unroll
+          for (int j = 0; j < 9; ++j) {
+            const int xx = w_in + j / 3;
+            const bool in = yin && xx >= 0 && xx < p.R;
+            v[dy * 9 + j] = in ? fmaf(byte_f32(by[j >> 2], j & 3), kNorm, -1.f) : 0.f;
+          }
         }
       }
 #pragma unroll

