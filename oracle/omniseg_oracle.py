@@ -194,6 +194,43 @@ def tissue_mask(canvas: np.ndarray, k: int):
     return b.astype(np.int64) <= t, t, b, hst
 
 
+def area_filter(mask: np.ndarray, min_area: int) -> np.ndarray:
+    """[reading] Sec. 2.1's contour step on the tissue mask: a tissue region is
+    a set of mask pixels connected through their 8 neighbours (a region's
+    outer contour encloses exactly such a set once its holes are counted as
+    part of it; only the region's own pixels are kept, holes stay background),
+    and regions with fewer than ``min_area`` pixels are removed.  The paper
+    names no area; 0 keeps every region (the mask unchanged).
+
+    Written as the definition: a breadth-first flood fill from every unvisited
+    tissue pixel collects one region, whose size decides whether it stays."""
+    if min_area <= 0:
+        return mask.copy()
+    h, w = mask.shape
+    seen = np.zeros((h, w), dtype=bool)
+    out = np.zeros((h, w), dtype=bool)
+    ys, xs = np.nonzero(mask)
+    for y0, x0 in zip(ys.tolist(), xs.tolist()):
+        if seen[y0, x0]:
+            continue
+        seen[y0, x0] = True
+        region = [(y0, x0)]
+        k = 0
+        while k < len(region):
+            y, x = region[k]
+            k += 1
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    yy, xx = y + dy, x + dx
+                    if 0 <= yy < h and 0 <= xx < w and mask[yy, xx] and not seen[yy, xx]:
+                        seen[yy, xx] = True
+                        region.append((yy, xx))
+        if len(region) >= min_area:
+            for (y, x) in region:
+                out[y, x] = True
+    return out
+
+
 # ----------------------------------------------------------------------------
 # Sec. 2.2: overlapping tile grid and foreground selection
 # ----------------------------------------------------------------------------
@@ -541,6 +578,7 @@ def prepare(rgb: np.ndarray, work):
     Hp, Wp, lead = padded_dims(work, rgb.shape[0], rgb.shape[1])
     pyr = pyramid(canvas, work.factors)
     mask, t, blurred, hst = tissue_mask(canvas, work.median_k)
+    mask = area_filter(mask, getattr(work, "min_tissue_area", 0))
     tiles, flags = tile_list(work, mask, Hp, Wp)
     return dict(canvas=canvas, Hp=Hp, Wp=Wp, lead=lead, pyr=pyr, mask=mask, otsu=t,
                 blurred=blurred, hist=hst, tiles=tiles, flags=flags)

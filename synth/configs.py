@@ -55,6 +55,7 @@ class Workload:
     head_offsets: Tuple[float, ...] = ()   # per-class addition to b3 through the class one-hot
     strides: Tuple[int, ...] = ()  # per-scale tile stride; () or 0 = S (Sec. 3.2: 256, 64, 64)
     stitch_window: int = WINDOW_FLAT
+    min_tissue_area: int = 0       # drop 8-connected tissue regions under this many thumbnail px
 
     @property
     def n_classes(self) -> int:

@@ -693,3 +693,27 @@ def test_resize_down_rounding_edges_and_pyramid():
     assert np.array_equal(O.resize_down(c, 8), c[::8, ::8])
     e = rng(24).integers(0, 256, (16, 24, 3)).astype(np.uint8)
     assert np.array_equal(O.resize_down(e, 2), O.half(e))
+
+
+def test_area_filter_pins():
+    """Sec. 2.1's contour step as read here (8-connected tissue regions under
+    min_area pixels removed): hand cases fix the connectivity and the hole
+    handling; on random masks the kept pixels equal scipy's 8-connected
+    labelling with its region sizes (an independent library routine)."""
+    ndi = pytest.importorskip("scipy.ndimage")
+    m = np.zeros((6, 6), bool)
+    m[1, 1] = m[2, 2] = True                       # diagonal contact: one region of 2
+    assert O.area_filter(m, 2).sum() == 2 and O.area_filter(m, 3).sum() == 0
+    ring = np.zeros((5, 5), bool)
+    ring[1:4, 1:4] = True
+    ring[2, 2] = False                             # 8 pixels around a hole: one region of 8
+    assert np.array_equal(O.area_filter(ring, 8), ring) and not O.area_filter(ring, 9).any()
+    assert np.array_equal(O.area_filter(ring, 0), ring)
+    rng = np.random.default_rng(5)
+    for trial in range(6):
+        mask = rng.random((40, 57)) < 0.35 + 0.05 * trial
+        lab, n = ndi.label(mask, structure=np.ones((3, 3), int))
+        sizes = np.bincount(lab.ravel())
+        for a in (1, 3, 7, 20):
+            want = mask & (sizes[lab] >= a)
+            assert np.array_equal(O.area_filter(mask, a), want), (trial, a)
