@@ -97,6 +97,11 @@ typedef struct omni_config {
                            canvas is padded to a multiple of lcm_s(f_s * S_s).        */
   int32_t stitch_window;/* OMNI_WINDOW_*: overlap-average weight (omni_backward needs
                            OMNI_WINDOW_FLAT)                                             */
+  int32_t min_tissue_area; /* Sec. 2.1 contour step: tissue regions (8-connected pixels of
+                           the thumbnail mask) with fewer pixels than this are removed
+                           before tiling and label masking; 0 = keep every region (the
+                           paper gives no area).  Not supported by
+                           omni_tile_slide_noalloc (OMNI_EINVAL when > 0).               */
 } omni_config;
 
 /* Sizes derived from a configuration and a slide size (omni_query). */

@@ -38,7 +38,7 @@ class Config(C.Structure):
                 ("stitch_mode", C.c_int32), ("tissue_filter", C.c_int32),
                 ("tissue_and", C.c_int32), ("pad_lead", C.c_int32), ("median_k", C.c_int32),
                 ("max_batch", C.c_int32), ("scale_stride", C.c_int32 * MAX_SCALES),
-                ("stitch_window", C.c_int32)]
+                ("stitch_window", C.c_int32), ("min_tissue_area", C.c_int32)]
 
 
 class Sizes(C.Structure):

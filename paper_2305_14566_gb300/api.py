@@ -43,6 +43,7 @@ def make_config(work, precision: int = L.FP32, max_batch: Optional[int] = None) 
     for i in range(c.n_scales):
         c.scale_stride[i] = work.stride(i)
     c.stitch_window = work.stitch_window
+    c.min_tissue_area = getattr(work, "min_tissue_area", 0)
     return c
 
 

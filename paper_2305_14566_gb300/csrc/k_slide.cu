@@ -420,6 +420,101 @@ cudaError_t launch_pyramid(const uint8_t* c40, int64_t stride40, int Hp, int Wp,
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ area filter
+// Sec. 2.1 contour step: tissue regions are the 8-connected components of the
+// thumbnail mask; regions of fewer than min_area pixels are cleared.  The
+// components come from a concurrent union-find over the mask: a label points
+// to a smaller pixel index until the root (the region's smallest index);
+// every tissue pixel unites with its tissue neighbours to the west,
+// north-west, north and north-east (the other four directions are those
+// pixels' own unions).  A union relinks the larger root below the smaller
+// with atomicMin and retries with whatever the larger root had become, so
+// labels only decrease and every loop ends; each loop also stops after n
+// steps with an error bit (it cannot need more).
+__device__ __forceinline__ int ccl_find(const volatile int32_t* L, int x, int n, bool& ok) {
+  for (int k = 0; k < n; ++k) {
+    const int y = L[x];
+    if (y == x) return x;
+    x = y;
+  }
+  ok = false;
+  return x;
+}
+
+__device__ __forceinline__ bool ccl_unite(int32_t* L, int a, int b, int n) {
+  bool ok = true;
+  for (int k = 0; k < n && ok; ++k) {
+    a = ccl_find(L, a, n, ok);
+    b = ccl_find(L, b, n, ok);
+    if (!ok || a == b) return ok;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicMin(&L[b], a);
+    if (old == b) return true;      // b was a root and now hangs below a
+    b = old;                        // b had been relinked meanwhile: join a with its new parent
+  }
+  return false;
+}
+
+__global__ void k_ccl_init(const uint8_t* __restrict__ mask, int n, int32_t* __restrict__ L,
+                           int32_t* __restrict__ area) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  L[i] = mask[i] ? i : -1;
+  area[i] = 0;
+}
+
+__global__ void k_ccl_union(const uint8_t* __restrict__ mask, int th, int tw, int32_t* L, unsigned* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = th * tw;
+  if (i >= n || !mask[i]) return;
+  const int y = i / tw, x = i - y * tw;
+  bool ok = true;
+  if (x > 0 && mask[i - 1]) ok &= ccl_unite(L, i, i - 1, n);
+  if (y > 0) {
+    const int up = i - tw;
+    if (x > 0 && mask[up - 1]) ok &= ccl_unite(L, i, up - 1, n);
+    if (mask[up]) ok &= ccl_unite(L, i, up, n);
+    if (x + 1 < tw && mask[up + 1]) ok &= ccl_unite(L, i, up + 1, n);
+  }
+  if (!ok) atomicOr(err, kErrTimeout);
+}
+
+// every tissue pixel's label becomes its region's root; the root counts it
+__global__ void k_ccl_count(const uint8_t* __restrict__ mask, int n, int32_t* L, int32_t* area,
+                            unsigned* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !mask[i]) return;
+  bool ok = true;
+  const int r = ccl_find(L, i, n, ok);
+  if (!ok) atomicOr(err, kErrTimeout);
+  L[i] = r;
+  atomicAdd(&area[r], 1);
+}
+
+__global__ void k_ccl_apply(uint8_t* __restrict__ mask, int n, const int32_t* __restrict__ L,
+                            const int32_t* __restrict__ area, int min_area) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !mask[i]) return;
+  if (area[L[i]] < min_area) mask[i] = 0;
+}
+
+cudaError_t launch_area_filter(uint8_t* mask, int th, int tw, int min_area, int32_t* region, int32_t* area,
+                               unsigned* err, cudaStream_t st) {
+  if (min_area <= 0) return cudaSuccess;
+  if (th <= 0 || tw <= 0 || (long long)th * tw > (1LL << 30)) return cudaErrorInvalidValue;
+  const int n = th * tw;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  k_ccl_init<<<blocks, 256, 0, st>>>(mask, n, region, area);
+  k_ccl_union<<<blocks, 256, 0, st>>>(mask, th, tw, region, err);
+  k_ccl_count<<<blocks, 256, 0, st>>>(mask, n, region, area, err);
+  k_ccl_apply<<<blocks, 256, 0, st>>>(mask, n, region, area, min_area);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tissue(const uint16_t* blk8, const SlideGeom& g, int median_k, uint8_t* grey,
                           uint8_t* blurred, int32_t* hist, int32_t* otsu, uint8_t* mask,
                           cudaStream_t st) {

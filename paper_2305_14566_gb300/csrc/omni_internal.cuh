@@ -47,6 +47,11 @@ cudaError_t launch_tissue(const uint16_t* blk8, const SlideGeom& g, int median_k
                           uint8_t* blurred, int32_t* hist, int32_t* otsu, uint8_t* mask,
                           cudaStream_t st);
 // median blur, histogram, Otsu and mask from an existing thumbnail grey image
+// Sec. 2.1 contour step: clears tissue regions (8-connected mask pixels) of
+// fewer than min_area pixels.  region / area: th * tw int32 scratch each; err
+// gets kErrTimeout if a union or find loop exceeds its bound.
+cudaError_t launch_area_filter(uint8_t* mask, int th, int tw, int min_area, int32_t* region, int32_t* area,
+                               unsigned* err, cudaStream_t st);
 cudaError_t launch_tissue_grey(const uint8_t* grey, const SlideGeom& g, int median_k, uint8_t* blurred,
                                int32_t* hist, int32_t* otsu, uint8_t* mask, cudaStream_t st);
 cudaError_t launch_tiles(const uint8_t* mask, const SlideGeom& g, int filter, int32_t* tiles,

@@ -156,6 +156,7 @@ std::string validate(const omni_config& c) {
   if (c.stitch_mode != OMNI_STITCH_AVG && c.stitch_mode != OMNI_STITCH_VOTE) return "bad stitch_mode";
   if (c.stitch_window < OMNI_WINDOW_FLAT || c.stitch_window > OMNI_WINDOW_HANN) return "bad stitch_window";
   if (c.median_k < 1 || c.median_k % 2 == 0 || c.median_k > 255) return "median_k must be odd, 1..255";
+  if (c.min_tissue_area < 0) return "min_tissue_area must be >= 0";
   if (c.max_batch < 1 || c.max_batch > 4096) return "max_batch must be 1..4096";
   if (c.pad_lead < 0 || c.pad_lead % fmax) return "pad_lead must be a non-negative multiple of the largest factor";
   if (widths(c, c.levels - 1) > 1024) return "bottleneck wider than 1024 channels";
@@ -175,6 +176,7 @@ struct Plan {
   int cap[OMNI_MAX_SCALES];   // tile-logit ring slots per scale (a multiple of max_batch)
   // tile stage
   size_t canvas, c20, c10, c5, blk8, grey, blur, hist, otsu, mask, tiles, counts, flags, slot;
+  size_t region, area;               // tissue-region labels and sizes (area filter)
   size_t tile_end;
   // network stage
   size_t logits, tmp, pooled, pooled2, cat[kMaxLevels], bott, ydec[kMaxLevels], gap, theta;
@@ -229,6 +231,8 @@ bool make_plan(const omni_config& c, int H, int W, Plan& p) {
   p.mask = take(off, tn);
   p.hist = take(off, 256 * 4);
   p.otsu = take(off, 4);
+  p.region = c.min_tissue_area > 0 ? take(off, tn * 4) : kNone;
+  p.area = c.min_tissue_area > 0 ? take(off, tn * 4) : kNone;
   int ntile = g.grid_off[c.n_scales];
   p.tiles = take(off, (size_t)ntile * 3 * 4);
   p.counts = take(off, (OMNI_MAX_SCALES + 1) * 4);
@@ -642,6 +646,12 @@ omni_status run_prep(omni_ctx* ctx, const uint8_t* rgb, int64_t stride, const Pl
                           (int32_t*)(ws + p.hist), (int32_t*)(ws + p.otsu), ws + p.mask, st),
             "tissue");
     ctx->launches += 5;
+    if (c.min_tissue_area > 0) {
+      OMNI_CU(launch_area_filter(ws + p.mask, g.th, g.tw, c.min_tissue_area, (int32_t*)(ws + p.region),
+                                 (int32_t*)(ws + p.area), ctx->d_err, st),
+              "area filter");
+      ctx->launches += 4;
+    }
   }
   {
     Rec r(ctx, st, 3, 703);
@@ -1786,6 +1796,7 @@ extern "C" omni_status omni_tile_slide_noalloc(const omni_config* cfg, const uin
                                                void* stream) {
   if (!cfg || !rgb || !out || !out->tiles || !out->counts) return OMNI_EINVAL;
   if (!validate(*cfg).empty() || stride < (int64_t)W * 3) return OMNI_EINVAL;
+  if (cfg->min_tissue_area > 0) return OMNI_EINVAL;     // the fixed scratch has no room for the area filter
   (void)cudaGetLastError();   // a launch error left by an earlier, unrelated call is not this call's
   Plan p;
   if (!make_plan(*cfg, H, W, p)) return OMNI_EINVAL;

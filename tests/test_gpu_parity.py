@@ -97,6 +97,35 @@ def test_tile_slide_ragged_with_filter_and_padding(api):
     assert 0 < len(prep["tiles"]) < sum(int(np.prod(f.shape)) for f in prep["flags"])
 
 
+def _specks_slide():
+    """Glass with one large dark tissue region and small dark specks of 2 x 2
+    to 6 x 6 thumbnail cells (64..192 px at 40x), some touching diagonally."""
+    rng = np.random.default_rng(9)
+    rgb = np.full((3072, 4096, 3), 232, np.uint8)
+    rgb += rng.integers(0, 12, rgb.shape, dtype=np.uint8)
+    rgb[640:2432, 512:2560] = (150, 80, 140)                       # the biopsy core
+    for k, (cy, cx, r) in enumerate([(300, 3000, 2), (900, 3300, 3), (2000, 3500, 4), (2700, 3000, 6),
+                                     (2800, 300, 3), (200, 200, 2)]):
+        rgb[cy:cy + 32 * r, cx:cx + 32 * r] = (140, 70, 130)
+    rgb[1500:1564, 3700:3764] = (140, 70, 130)                     # two 2 x 2 specks touching at a corner
+    rgb[1564:1628, 3764:3828] = (140, 70, 130)
+    return rgb
+
+
+@pytest.mark.parametrize("min_area", [0, 5, 12, 30])
+def test_tile_slide_area_filter_matches_oracle(api, min_area):
+    """Sec. 2.1 contour step: 8-connected tissue regions of the thumbnail mask
+    under min_area pixels are removed before tiling; mask, flags and tile list
+    bit-exact against the oracle, with specks on both sides of each area."""
+    w = synth.NEEDLE.with_(H=3072, W=4096, median_k=3, max_batch=2, min_tissue_area=min_area)
+    prep = _tile_compare(api, w, _specks_slide())
+    base = O.prepare(_specks_slide(), w.with_(min_tissue_area=0))
+    if min_area:
+        assert prep["mask"].sum() < base["mask"].sum()
+    else:
+        assert np.array_equal(prep["mask"], base["mask"])
+
+
 def test_tile_slide_constant_slide_has_no_tiles(api):
     w = synth.NEEDLE.with_(H=2048, W=2048, median_k=3, max_batch=2)
     rgb = np.full((2048, 2048, 3), 235, np.uint8)
