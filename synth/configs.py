@@ -96,7 +96,7 @@ NEEDLE_HEAD_OFFSETS = (6.8456, 7.3584, 6.974, 6.0431, 7.3029, 6.2199)
 NEEDLE = Workload(
     name="needle", H=16384, W=49152, seed=1, tissue=0.40, layout="cores", n_blobs=4,
     factors=(1, 4, 8), P=512, S=256, base=32, levels=5,
-    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=128,
+    class_scale=(0, 0, 1, 1, 2, 2), weights_seed=11, max_batch=256,
     head_offsets=NEEDLE_HEAD_OFFSETS)
 
 DIFF = Workload(
