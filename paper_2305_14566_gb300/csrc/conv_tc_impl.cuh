@@ -372,7 +372,10 @@ __device__ __forceinline__ void tmem_ld16x4(uint32_t t0, uint32_t t1, uint32_t t
   }
 }
 
-__device__ __forceinline__ float norm_u8(uint8_t u) { return 2.0f * (float)u / 255.0f - 1.0f; }
+// v = 2u/255 - 1 for the epilogues' RGB projection: one FMA with the FP32
+// constant 2/255, absolute error below 2^-22 like the rounded division it
+// replaces (no division sequence per pixel)
+__device__ __forceinline__ float norm_u8(uint8_t u) { return fmaf((float)u, 2.0f / 255.0f, -1.0f); }
 
 // four consecutive per-channel constants from shared memory in one 16-byte
 // load (the epilogues' gamma / beta / RGB-projection rows are 16-byte aligned)
@@ -466,8 +469,11 @@ __device__ __forceinline__ void prehead_pair_finish(int h, float hs[4], float hp
 // Dynamic heads of a lane pair's two pixels (he, ho: see prehead_pair_finish)
 // into the batch's logit slots at pixel offsets pe / po of the tile image
 // whose class-0 plane starts at lo.  Two classes: lane half h runs class h for
-// both pixels (one read of its theta row for two pixels); one class: each lane
-// runs it for its own pixel.  A pixel whose write flag is off is not stored.
+// both pixels (one read of its theta row for two pixels), then the pair swaps
+// one value so each lane holds both classes of its own pixel and every store
+// instruction writes one class plane at the warp's 32 consecutive-row pixels;
+// one class: each lane runs it for its own pixel.  A pixel whose write flag is
+// off is not stored.
 __device__ __forceinline__ void heads_pair(const float* sth, int ncls, long long RR, float* lo, int h,
                                            const float he[8], const float ho[8], long long pe, long long po,
                                            bool we, bool wo) {
@@ -476,9 +482,15 @@ __device__ __forceinline__ void heads_pair(const float* sth, int ncls, long long
                            {ho[0], ho[1], ho[2], ho[3], ho[4], ho[5], ho[6], ho[7]}};
     float l[2];
     dyn_head_n<2>(sth + h * kThetaPad, x, l);
-    float* L = lo + (long long)h * RR;
-    if (we) L[pe] = l[0];
-    if (wo) L[po] = l[1];
+    // lane 0 of the pair keeps class 0 of the even pixel and receives its class 1;
+    // lane 1 keeps class 1 of the odd pixel and receives its class 0
+    const float other = __shfl_xor_sync(0xffffffffu, h ? l[0] : l[1], 1);
+    const float own = h ? l[1] : l[0];
+    const long long pix = h ? po : pe;
+    if (h ? wo : we) {
+      lo[pix] = h ? other : own;
+      lo[RR + pix] = h ? own : other;
+    }
   } else {
     float x[1][8];
 #pragma unroll
