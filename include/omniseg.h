@@ -348,6 +348,14 @@ int64_t omni_last_launch_count(const omni_ctx* ctx);
 omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled);
 int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows);
 
+/* Kernel choice for checks (tensor-core contexts): kind >= 0 (as in
+ * omni_get_tuned) makes every conv layer whose shape has a configuration of
+ * that kind run the first such configuration of omni_conv_candidates,
+ * overriding the autotuner; other layers keep the default choice.  -1
+ * restores the default / autotuned choice.  omni_get_tuned then also lists the
+ * configuration each layer shape ran with.  OMNI_EINVAL outside -1..7. */
+omni_status omni_set_conv_kind(omni_ctx* ctx, int32_t kind);
+
 /* CUDA graphs.  When enabled, omni_segment_slide captures its post-tiling
  * launch chain (every network batch and the stitches) into a CUDA graph on
  * the second call that sees the same slide pointer, size, scale/class masks,

@@ -27,7 +27,7 @@ EXPORTS = ("omni_create", "omni_destroy", "omni_last_error", "omni_weights_count
            "omni_get_timing", "omni_last_launch_count", "omni_get_launch_times",
            "omni_tile_slide_noalloc", "omni_backward", "omni_backward_workspace",
            "omni_set_autotune", "omni_set_graphs", "omni_set_fusion", "omni_get_tuned",
-           "omni_stain", "omni_query_slides", "omni_segment_slides", "omni_conv_candidates")
+           "omni_stain", "omni_query_slides", "omni_segment_slides", "omni_conv_candidates", "omni_set_conv_kind")
 
 
 class Config(C.Structure):
@@ -99,6 +99,7 @@ def lib() -> C.CDLL:
         "omni_conv_layer": (i32, [i32, i32, i32, i32, i32, vp, i32, i32, vp, vp, vp, vp, i32,
                                   i32, i32, vp, vp, i32, i32, vp, i32, vp, vp]),
         "omni_conv_candidates": (i32, [i32, i32, i32, i32, vp, i32]),
+        "omni_set_conv_kind": (i32, [vp, i32]),
         "omni_set_timing": (i32, [vp, i32]),
         "omni_get_timing": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64),
                                   C.POINTER(C.c_double)]),

@@ -287,6 +287,10 @@ class Segmenter:
     def set_autotune(self, on: bool = True):
         L.check(self.lib.omni_set_autotune(self.ctx, int(on)), self.ctx)
 
+    def set_conv_kind(self, kind: int = -1):
+        """Force one tensor-core kernel kind on every layer that has it (-1: default)."""
+        L.check(self.lib.omni_set_conv_kind(self.ctx, int(kind)), self.ctx)
+
     def set_graphs(self, on: bool = True):
         L.check(self.lib.omni_set_graphs(self.ctx, int(on)), self.ctx)
 

@@ -49,6 +49,7 @@ struct omni_ctx {
   int64_t tiles_done = 0;
   // conv autotuner: layer shape -> fastest tensor-core configuration
   bool autotune = false;
+  int force_kind = -1;         // >= 0: every layer with a candidate of this kind runs it
   std::map<std::array<int, 6>, TcConfig> tuned;
   // CUDA graph of the post-tiling launch chain (network + stitch)
   bool graphs = false;
@@ -771,7 +772,19 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag
                                         " cin=" + std::to_string(a.cin) + " cout=" + std::to_string(a.cout));
     const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
     TcConfig cfg = tc_default(a.R, a.cin, a.cout, cr);
-    if (ctx->autotune) {
+    if (ctx->force_kind >= 0) {
+      // the first candidate of the forced kind (its largest chunk first), if the
+      // shape has one and it can take this layer's fused head
+      TcConfig cands[16];
+      const int n = tc_candidates(a.R, a.cin, a.cout, cr, cands, 16);
+      for (int i = 0; i < n; ++i)
+        if (cands[i].kind == ctx->force_kind &&
+            (!a.head_theta || tc_fuses_head(cands[i], a.cout, a.head_ncls) || !tc_fuses_head(cfg, a.cout, a.head_ncls))) {
+          cfg = cands[i];
+          break;
+        }
+      ctx->tuned[std::array<int, 6>{a.R, a.cin, a.cout, cr, a.res_mode, a.B}] = cfg;   // reported by omni_get_tuned
+    } else if (ctx->autotune) {
       const std::array<int, 6> key{a.R, a.cin, a.cout, cr, a.res_mode, a.B};
       auto it = ctx->tuned.find(key);
       if (it != ctx->tuned.end()) {
@@ -1670,6 +1683,14 @@ int64_t omni_last_launch_count(const omni_ctx* ctx) { return ctx ? ctx->launches
 omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled) {
   if (!ctx) return OMNI_EINVAL;
   ctx->autotune = enabled != 0;
+  drop_graph(ctx);
+  return OMNI_OK;
+}
+
+omni_status omni_set_conv_kind(omni_ctx* ctx, int32_t kind) {
+  if (!ctx || kind < -1 || kind > 7) return OMNI_EINVAL;
+  ctx->force_kind = kind;
+  ctx->tuned.clear();          // forced choices are recorded there; the autotuner starts afresh
   drop_graph(ctx);
   return OMNI_OK;
 }

@@ -370,6 +370,32 @@ def test_graph_replay_is_bit_identical_and_autotune_agrees(api):
     tuned.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_forced_pair_kernel_equals_one_cta_kernel_through_the_slide(api, prec):
+    """The whole path with every small-N layer forced onto CTA pairs (kind 6,
+    including the encoder layers with the fused max-pool and RGB projection
+    and the last decoder layer with the fused pre-head and heads) gives the
+    same logits and labels, bit for bit, as the same layers forced onto the
+    one-CTA two-block kernel (kind 3)."""
+    from paper_2305_14566_gb300 import _lib as L
+    w = synth.NEEDLE.with_(H=2048, W=4096, P=256, S=128, median_k=5, max_batch=16)
+    rgb = api.synth_slide(synth.make_spec(2048, 4096, 44, 0.5, "cores", 3))
+    blob = synth.gen_weights(w)
+    outs, kinds = {}, {}
+    for k in (3, 6):
+        seg = api.Segmenter(w, blob, precision=L.BF16 if prec == "bf16" else L.FP16)
+        seg.set_conv_kind(k)
+        o = seg.segment(rgb, logits=True)
+        torch.cuda.synchronize()
+        outs[k] = {n: {c: t.clone() for c, t in d.items()} for n, d in o.items() if n in ("labels", "logits")}
+        kinds[k] = [int(r[6]) for r in seg.tuned()]
+        seg.close()
+    assert kinds[6].count(6) >= 3 and 6 not in kinds[3], kinds
+    for c in outs[3]["logits"]:
+        assert torch.equal(outs[6]["logits"][c], outs[3]["logits"][c]), c
+        assert torch.equal(outs[6]["labels"][c], outs[3]["labels"][c]), c
+
+
 def test_graph_is_dropped_when_weights_are_reloaded(api):
     """A captured launch chain holds the weight pointers of the state it was
     captured in: reloading weights (as a fine-tuning loop does) must make the
