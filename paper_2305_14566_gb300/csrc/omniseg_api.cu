@@ -777,8 +777,10 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag
       // shape has one and it can take this layer's fused head
       TcConfig cands[16];
       const int n = tc_candidates(a.R, a.cin, a.cout, cr, cands, 16);
+      // (the CTA-pair kernel needs an even count of 16 x 16 tiles)
+      const bool pair_ok = ((long long)a.B * (a.R / 16) * (a.R / 16)) % 2 == 0;
       for (int i = 0; i < n; ++i)
-        if (cands[i].kind == ctx->force_kind &&
+        if (cands[i].kind == ctx->force_kind && (cands[i].kind != 6 || pair_ok) &&
             (!a.head_theta || tc_fuses_head(cands[i], a.cout, a.head_ncls) || !tc_fuses_head(cfg, a.cout, a.head_ncls))) {
           cfg = cands[i];
           break;
