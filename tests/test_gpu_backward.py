@@ -136,3 +136,41 @@ def test_omniseg_loss_autograd_matches_backward_and_tracks_params(api):
     with pytest.raises(ValueError):
         api.OmniSegLoss.apply(seg, rgb, gts, *bad)
     seg.close()
+
+
+def test_finetuning_loop_lowers_the_stitched_loss(api):
+    """A fine-tuning loop over the differentiated sub-chain (controller,
+    pre-head, last decoder block): torch.optim.Adam on the OmniSegLoss
+    parameters, one forward + backward + step per iteration on the
+    differentiation workload's slide and masks.  The stitched soft-Dice + BCE
+    loss falls over the iterations, and the last value equals the oracle's
+    loss at the updated weights."""
+    from paper_2305_14566_gb300 import _lib as L
+    w = synth.DIFF.with_(base=8, levels=3)
+    rgb_np = synth.gen_slide(synth.spec_for(w))
+    gts_np = synth.gen_gt_masks(w.H, w.W, w.factors, w.class_scale, seed=7)
+    blob = synth.gen_weights(w)
+    rgb = torch.from_numpy(rgb_np).cuda()
+    gts = [torch.from_numpy(g).cuda() for g in gts_np]
+    seg = api.Segmenter(w, blob, max_batch=16)
+    offs, shapes = seg.grad_offsets(), seg.grad_shapes()
+    params = [torch.from_numpy(blob[offs[k]:offs[k] + int(np.prod(shapes[k]))].reshape(shapes[k]).copy())
+              .cuda().requires_grad_(True) for k in L.GRAD_FIELDS]
+    opt = torch.optim.Adam(params, lr=1e-3)
+    losses = []
+    for it in range(8):
+        opt.zero_grad()
+        loss = api.OmniSegLoss.apply(seg, rgb, gts, *params)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss))
+    final = float(api.OmniSegLoss.apply(seg, rgb, gts, *params))
+    torch.cuda.synchronize()
+    print("fine-tuning losses", ["%.5f" % v for v in losses], "final %.5f" % final)
+    assert final < losses[0] and losses[-1] < losses[0], losses
+    blob2 = blob.copy()
+    for k, p in zip(L.GRAD_FIELDS, params):
+        blob2[offs[k]:offs[k] + p.numel()] = p.detach().cpu().numpy().ravel()
+    ol = float(O.DiffProblem(rgb_np, w, blob2, gts_np).loss({}))
+    assert abs(final - ol) <= 1e-5 * abs(ol), (final, ol)
+    seg.close()
