@@ -1628,13 +1628,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 //      value this rounds to the same FP16 number as 2u/255 - 1 in exact
 //      arithmetic), zeroes taps outside the tile, rounds to FP16 (whatever the
 //      pipeline's 16-bit type: 8-bit colour values need the 11-bit mantissa)
-//      and stores one 64-byte K row (K = 27 padded to 32) in the
-//      64-byte-swizzled K-major layout the MMA reads (16-byte chunk j of row r
-//      at chunk j ^ ((r >> 1) & 3)).
-// Two FP16 MMAs (K = 16 each) per tile, N = cout.  The epilogue stages each
-// warp's 32 output pixels (two rows of 16) in shared memory, swizzled like the
-// output tensor map, and writes them with one TMA store per warp and tile:
-// whole 128-byte lines instead of 32 scattered 16-byte pieces per store.
+//      and stores one 64-byte K row (the 27 values, a constant 1, zeros to
+//      32) in the 64-byte-swizzled K-major layout the MMA reads (16-byte
+//      chunk j of row r at chunk j ^ ((r >> 1) & 3)).
+// Two FP16 MMAs (K = 16 each) per tile, N = cout.  The layer's norm rides in
+// the weights: the host stores g[o] * w in K entries 0..26 and b[o] in entry
+// 27, whose operand is the constant 1, so the accumulator already holds
+// g * conv + b and the epilogue applies only the ReLU.  The epilogue stages
+// each warp's 32 output pixels (two rows of 16) in shared memory, swizzled
+// like the output tensor map, and writes them with one TMA store per warp and
+// tile: whole 128-byte lines instead of 32 scattered 16-byte pieces per store.
 //   warps 0-7  builders in two groups of four (group g builds the CTA's
 //              tiles g, g + 2, ...: two tiles in flight), warp 8 MMA issuer +
 //              TMEM owner, warps 9-16 epilogue in two groups of four taking
@@ -1702,16 +1705,10 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
   uint64_t* tempty = bars + 4 * ST + kMaxTmemBufs;
   uint64_t* drain = bars + 4 * ST + 2 * kMaxTmemBufs;
   uint64_t* wbar = drain + 1;
-  float* sg = reinterpret_cast<float*>(wbar + 1);
-  float* sb = sg + CO;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + CO);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < CO; i += blockDim.x) {
-    sg[i] = p.gamma[i];
-    sb[i] = p.beta[i];
-  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(smem_u32(&full[s]), 4);
@@ -1809,8 +1806,9 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
           }
         }
       }
+      v[27] = 1.f;                                   // operand of the norm shift b (weight row entry 27)
 #pragma unroll
-      for (int k = 27; k < 32; ++k) v[k] = 0.f;
+      for (int k = 28; k < 32; ++k) v[k] = 0.f;
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&rempty[s]));
       uint8_t* row = sA + (size_t)s * kFirstStageBytes + r * kFirstRowBytes;
@@ -1897,9 +1895,7 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
           const float* a = a2[h];
           uint32_t packed[8];
 #pragma unroll
-          for (int j = 0; j < 16; j += 2)
-            packed[j / 2] = pack2(fmaxf(fmaf(sg[cc + j], a[j], sb[cc + j]), 0.f),
-                                  fmaxf(fmaf(sg[cc + j + 1], a[j + 1], sb[cc + j + 1]), 0.f));
+          for (int j = 0; j < 16; j += 2) packed[j / 2] = pack2(fmaxf(a[j], 0.f), fmaxf(a[j + 1], 0.f));
           const int j0 = cc / 8;
           *reinterpret_cast<uint4*>(srow + ((j0 ^ osw) << 4)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
           *reinterpret_cast<uint4*>(srow + (((j0 + 1) ^ osw) << 4)) =

@@ -449,8 +449,11 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
     // blob: w1-style [cout][cin][3][3], g, b ; projection handled by caller
     Pending q{};
     q.cin = cin; q.cout = cout; q.cproj = cproj_used;
-    // 16-bit weights: [cout][9 cin] (tap-major K); the first layer's rows are
-    // FP16 in every precision and padded to K = 32 for its tensor-core kernel
+    // 16-bit weights: [cout][9 cin] (tap-major K).  The first layer's rows are
+    // FP16 in every precision, padded to K = 32 for its tensor-core kernel,
+    // and carry the layer's norm: K entries 0..26 hold g[o] * w, entry 27
+    // holds b[o] (its operand is the constant 1), so the MMA yields g * conv + b
+    // (one FP16 rounding of each product instead of one of each weight)
     const size_t kdim = cin == 3 ? 32 : (size_t)9 * cin;
     q.w32 = alloc((size_t)9 * cin * cout * 4);
     q.w16 = alloc(kdim * cout * 2);
@@ -458,13 +461,17 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
     q.b = alloc((size_t)cout * 4);
     float* w32 = reinterpret_cast<float*>(host.data() + q.w32);
     uint16_t* w16 = reinterpret_cast<uint16_t*>(host.data() + q.w16);
-    for (int o = 0; o < cout; ++o)
+    const float* gsrc = src + (size_t)cout * cin * 9;     // the layer's norm scale and shift
+    const float* bsrc = gsrc + cout;
+    for (int o = 0; o < cout; ++o) {
       for (int ci = 0; ci < cin; ++ci)
         for (int tap = 0; tap < 9; ++tap) {
           float v = src[((size_t)o * cin + ci) * 9 + tap];
           w32[((size_t)tap * cin + ci) * cout + o] = v;
-          w16[(size_t)o * kdim + (size_t)tap * cin + ci] = to_lp(v, f16 || cin == 3);
+          w16[(size_t)o * kdim + (size_t)tap * cin + ci] = cin == 3 ? to_lp(gsrc[o] * v, true) : to_lp(v, f16);
         }
+      if (cin == 3) w16[(size_t)o * kdim + 27] = to_lp(bsrc[o], true);
+    }
     src += (size_t)cout * cin * 9;
     memcpy(host.data() + q.g, src, cout * 4);
     src += cout;
