@@ -343,7 +343,7 @@ int64_t omni_last_launch_count(const omni_ctx* ctx);
  * kind (0 per-tap, 1 small-N, 2 dx-in-N, 3 small-N with two blocks per tile,
  * 4 dx-in-N with two blocks per tile, 6 kind 3 on pairs of CTAs whose
  * cta_group::2 MMAs cover 256 pixel rows, 7 kind 4 launched once per 32
- * output channels),
+ * output channels, 8 kind 0 on pairs of CTAs),
  * N tile, channel chunk, stages; returns the count. */
 omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled);
 int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows);
@@ -353,7 +353,7 @@ int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows);
  * that kind run the first such configuration of omni_conv_candidates,
  * overriding the autotuner; other layers keep the default choice.  -1
  * restores the default / autotuned choice.  omni_get_tuned then also lists the
- * configuration each layer shape ran with.  OMNI_EINVAL outside -1..7. */
+ * configuration each layer shape ran with.  OMNI_EINVAL outside -1..8. */
 omni_status omni_set_conv_kind(omni_ctx* ctx, int32_t kind);
 
 /* CUDA graphs.  When enabled, omni_segment_slide captures its post-tiling

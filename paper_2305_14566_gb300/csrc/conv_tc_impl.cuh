@@ -598,10 +598,15 @@ struct TileWalk {
   }
 };
 
-template <int BN, int CK, bool RES>
+// PAIR: clusters of two CTAs take adjacent M tiles of one N tile; one thread
+// of CTA 0 issues cta_group::2 MMAs (M = 256) and each CTA holds half of the
+// B tile's rows, so a K step moves a quarter less operand data per SM
+// (the wide layers here are bound by that traffic, not by the MMA rate)
+template <int BN, int CK, bool RES, bool PAIR = false>
 struct TCCfg {
   static constexpr int kABytes = kBM * CK * 2;
-  static constexpr int kBBytes = BN * CK * 2;
+  static constexpr int kBRows = PAIR ? BN / 2 : BN;       // B rows (output channels) held here
+  static constexpr int kBBytes = kBRows * CK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStages0 = (kSmemBudget - 2048) / kStageBytes;
   static constexpr int kStages = kStages0 > 16 ? 16 : kStages0;       // (A, B) slots
@@ -617,12 +622,12 @@ struct TCCfg {
                                   2 * 512 * 4 /*gamma, beta*/;
 };
 
-template <int BN, int CK, bool RES>
+template <int BN, int CK, bool RES, bool PAIR>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
               TCParams p) {
-  using Cfg = TCCfg<BN, CK, RES>;
+  using Cfg = TCCfg<BN, CK, RES, PAIR>;
   constexpr int ST = Cfg::kStages;     // (A, B) slots
   constexpr int G = Cfg::kGroup;       // slots per stage
   constexpr int RING = Cfg::kRing;     // stages
@@ -642,33 +647,40 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   float* sb = sg + 512;                                                                // beta[cout]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int crank = PAIR ? (int)cluster_rank() : 0;
+  const bool peer = crank != 0;                          // CTA 1 of a pair
+  // work items: (M tile, N tile); a pair takes M tiles 2 a and 2 a + 1 of one N tile
+  const int t_beg = PAIR ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
+  const int t_step = PAIR ? (int)gridDim.x >> 1 : (int)gridDim.x;
+  const int t_end = PAIR ? p.n_tiles >> 1 : p.n_tiles;
+  auto tile_mn = [&](int t, int& mt, int& nt) {
+    const int a = t / p.n_tiles_n;
+    nt = t - a * p.n_tiles_n;
+    mt = PAIR ? 2 * a + crank : a;
+  };
   for (int i = threadIdx.x; i < p.cout; i += blockDim.x) {
     sg[i] = p.gamma[i];
     sb[i] = p.beta[i];
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
-      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&full[s]), PAIR && !peer ? 2 : 1);   // pair: plus CTA 1's forwarded loads
       mbar_init(smem_u32(&empty[s]), 1);
     }
     for (int b = 0; b < Cfg::kBufs; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
-      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+      mbar_init(smem_u32(&tempty[b]), kEpiWarps * (PAIR ? 2 : 1));
     }
     mbar_init(smem_u32(drain), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(Cfg::kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (PAIR) cluster_sync();                // both CTAs' barriers exist before any remote arrive
+  if (warp == 0) tmem_alloc_t<PAIR>(smem_u32(tmem_slot), Cfg::kTmemCols);
   tc_fence_before();
-  __syncthreads();
+  if (PAIR) cluster_sync();
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int k_total = p.k_main + p.k_res;
@@ -681,8 +693,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       StageRing ring;
       bool ok = true;
       const int cpt = p.cin / CK;
-      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-        const int mt = tile / p.n_tiles_n, nt = tile % p.n_tiles_n;
+      for (int tile = t_beg; tile < t_end && ok; tile += t_step) {
+        int mt, nt;
+        tile_mn(tile, mt, nt);
         const int m0 = mt * kBM;
         const int img = m0 / RR, rem = m0 % RR;
         const int h0 = rem / p.R, w0 = rem % p.R;
@@ -703,7 +716,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             if (k < p.k_main) {
               const int c0 = cc * CK;
               tma_load_4d(da, &mapA, fb, c0, w0 + tdx - 1, h0 + tdy - 1, img);
-              tma_load_2d(db, &mapB, fb, (tdy * 3 + tdx) * p.cin + c0, nt * BN);
+              tma_load_2d(db, &mapB, fb, (tdy * 3 + tdx) * p.cin + c0, nt * BN + crank * Cfg::kBRows);
               if (++cc == cpt) {
                 cc = 0;
                 if (++tdx == 3) {
@@ -714,7 +727,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             } else {
               const int c0 = (k - p.k_main) * CK;
               tma_load_4d(da, &mapA2, fb, c0, w0, h0, img);
-              tma_load_2d(db, &mapB2, fb, c0, nt * BN);
+              tma_load_2d(db, &mapB2, fb, c0, nt * BN + crank * Cfg::kBRows);
             }
           }
         }
@@ -723,16 +736,31 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       const int last = it;
       for (int q = last - 1; q >= 0 && q >= last - RING; --q) mbar_drain(smem_u32(&full[q % RING]), (q / RING) & 1);
     }
+  } else if (warp == 1 && peer) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- pair: forward CTA 1's loads
+      // (same stage order as CTA 0's MMA issuer) to CTA 0's stage barriers
+      StageRing ring;
+      bool ok = true;
+      for (int tile = t_beg; tile < t_end && ok; tile += t_step)
+        for (int k0 = 0; k0 < k_total; k0 += G, ring.next(RING)) {
+          if (!mbar_wait(smem_u32(&full[ring.s]), ring.ph, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_cluster(cluster_addr(smem_u32(&full[ring.s]), 0));
+        }
+    }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuer
-      constexpr uint32_t idesc = idesc_bf16(BN);
+      constexpr uint32_t idesc = idesc_bf16(BN, PAIR ? 2 * kBM : kBM);
       const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
       const uint64_t b_desc0 = smem_desc(smem_u32(sB), Cfg::kSW);
       int tcount = 0;
       StageRing ring;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x, ++tcount) {
+      for (int tile = t_beg; tile < t_end && ok; tile += t_step, ++tcount) {
         const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
         if (use >= 1 && !mbar_wait(smem_u32(&tempty[buf]), (use - 1) & 1, abort_flag, p.err)) {
           ok = false;
@@ -758,16 +786,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int kfirst = second ? p.k_main : 0;
 #pragma unroll
             for (int kk = 0; kk < CK / 16; ++kk)
-              mma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                       (k > kfirst || kk > 0) ? 1u : 0u);
+              mma_t<PAIR>(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                          (k > kfirst || kk > 0) ? 1u : 0u);
           }
-          mma_commit(smem_u32(&empty[s]));
+          mma_commit_t<PAIR>(smem_u32(&empty[s]));
         }
         if (!ok) break;
-        mma_commit(smem_u32(&tfull[buf]));
+        mma_commit_t<PAIR>(smem_u32(&tfull[buf]));
       }
       // all MMAs issued by this thread complete before TMEM is released
-      mma_commit(smem_u32(drain));
+      mma_commit_t<PAIR>(smem_u32(drain));
       mbar_drain(smem_u32(drain), 0);
     }
   } else {
@@ -776,13 +804,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int row = q * 32 + lane;
     const int c_beg = ((warp - 2) >> 2) * (BN / 2), c_end = c_beg + BN / 2;
     int tcount = 0;
-    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++tcount) {
+    for (int tile = t_beg; tile < t_end; tile += t_step, ++tcount) {
       const int buf = tcount % Cfg::kBufs, use = tcount / Cfg::kBufs;
       // every lane waits; the vote keeps the warp converged for tcgen05.ld
       const bool ok = mbar_wait(smem_u32(&tfull[buf]), use & 1, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const int mt = tile / p.n_tiles_n, nt = tile % p.n_tiles_n;
+      int mt, nt;
+      tile_mn(tile, mt, nt);
       const long long m = (long long)mt * kBM + row;
       const int n0 = nt * BN;
       float v0 = 0.f, v1 = 0.f, v2 = 0.f;
@@ -825,17 +854,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+      if (lane == 0) mbar_arrive_to<PAIR>(smem_u32(&tempty[buf]), peer);
     }
   }
   __syncwarp();
   tc_fence_before();
-  __syncthreads();
+  // pair: neither CTA leaves while the other's MMAs or arrivals may still touch it
+  if (PAIR) cluster_sync();
+  else __syncthreads();
   tc_fence_after();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(Cfg::kTmemCols)
-                 : "memory");
+  if (warp == 0) tmem_dealloc_t<PAIR>(tmem_base, Cfg::kTmemCols);
 }
 
 // ------------------------------------------------------------------ small-N variant
@@ -2007,15 +2035,15 @@ int num_sms() {
   return n;
 }
 
-template <int BN, int CK, bool RES>
+template <int BN, int CK, bool RES, bool PAIR = false>
 cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
-  using Cfg = TCCfg<BN, CK, RES>;
+  using Cfg = TCCfg<BN, CK, RES, PAIR>;
   CUtensorMap mA, mB, mA2, mB2;
   if (!map_act(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK)) return cudaErrorInvalidValue;
-  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, BN, CK)) return cudaErrorInvalidValue;
+  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, Cfg::kBRows, CK)) return cudaErrorInvalidValue;
   if (RES) {
     if (!map_act(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK)) return cudaErrorInvalidValue;
-    if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, BN, CK)) return cudaErrorInvalidValue;
+    if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, Cfg::kBRows, CK)) return cudaErrorInvalidValue;
   } else {
     mA2 = mA;
     mB2 = mB;
@@ -2038,16 +2066,52 @@ cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
   p.y_co = a.y_co;
   p.err = a.err;
   if (a.pool || a.head_theta || !a.y) return cudaErrorInvalidValue;   // no fused outputs here
-  auto kern = k_conv_tc<BN, CK, RES>;
+  auto kern = k_conv_tc<BN, CK, RES, PAIR>;
   static bool attr_set = false;
+  static int max_pairs = 0;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
     if (e != cudaSuccess) return e;
+    if (PAIR) {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(2 * (num_sms() / 2));
+      q.blockDim = dim3(kThreadsTC);
+      q.dynamicSmemBytes = Cfg::kSmem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      q.attrs = at;
+      q.numAttrs = 1;
+      e = cudaOccupancyMaxActiveClusters(&max_pairs, kern, &q);
+      if (e != cudaSuccess || max_pairs < 1) return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
+    }
     attr_set = true;
   }
-  int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
-  kern<<<grid, kThreadsTC, Cfg::kSmem, st>>>(mA, mB, mA2, mB2, p);
-  return cudaGetLastError();
+  if (!PAIR) {
+    int grid = p.n_tiles < num_sms() ? p.n_tiles : num_sms();
+    kern<<<grid, kThreadsTC, Cfg::kSmem, st>>>(mA, mB, mA2, mB2, p);
+    return cudaGetLastError();
+  }
+  // pairs take M tiles 2 a, 2 a + 1 of one N tile: the M tile count must be even
+  if (p.n_tiles_m % 2) return cudaErrorInvalidValue;
+  const int pairs = p.n_tiles / 2 < max_pairs ? p.n_tiles / 2 : max_pairs;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * pairs);
+  cfg.blockDim = dim3(kThreadsTC);
+  cfg.dynamicSmemBytes = Cfg::kSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mA, mB, mA2, mB2, p);
+  if (e != cudaSuccess) cudaGetLastError();   // a refused launch leaves no sticky state behind
+  return e;
 }
 
 constexpr int kHaloSmemMax = 227 * 1024;
@@ -2411,6 +2475,10 @@ int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max) {
   for (int bn = 32; bn <= 256; bn *= 2)
     for (int ck = 32; ck <= 64; ck *= 2)
       if (pertap_ok(R, cin, cout, cr, bn, ck) && n < max) out[n++] = TcConfig{0, bn, ck, 0};
+  // per-tap on CTA pairs, for the wide N tiles whose B traffic it halves
+  for (int bn = 128; bn <= 256; bn *= 2)
+    if (pertap_ok(R, cin, cout, cr, bn, 64) && (long long)R * R % (2 * kBM) == 0 && n < max)
+      out[n++] = TcConfig{8, bn, 64, 0};
   return n;
 }
 
@@ -2522,6 +2590,12 @@ cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaSt
     return cudaErrorInvalidValue;
   }
   if (!pertap_ok(a.R, a.cin, a.cout, cr, c.bn, c.ck)) return cudaErrorInvalidValue;
+  if (c.kind == 8) {
+    if (c.ck != 64) return cudaErrorInvalidValue;
+    if (c.bn == 128) return res ? launch_t<128, 64, true, true>(a, st) : launch_t<128, 64, false, true>(a, st);
+    if (c.bn == 256 && !res) return launch_t<256, 64, false, true>(a, st);
+    return cudaErrorInvalidValue;
+  }
 #define OMNI_TC(BN_, CK_, RES_) \
   if (c.bn == BN_ && c.ck == CK_ && res == RES_) return launch_t<BN_, CK_, RES_>(a, st);
   OMNI_TC(32, 32, false) OMNI_TC(32, 32, true) OMNI_TC(32, 64, false) OMNI_TC(32, 64, true)

@@ -124,7 +124,8 @@ struct TcConfig {
                 // 3: small-N variant with two 8x16 blocks per tile (32-channel chunks),
                 // 4: dx-in-N variant with two blocks per tile (cout 32),
                 // 6: kind 3 on CTA pairs (cta_group::2 MMAs, M = 256),
-                // 7: kind 4 once per 32-output-channel slice (cout 64..256)
+                // 7: kind 4 once per 32-output-channel slice (cout 64..256),
+                // 8: kind 0 on CTA pairs (N tile 128 / 256, 64-channel chunks)
   int bn;       // N tile
   int ck;       // channel chunk (32 -> 64-byte swizzle, 64 -> 128-byte swizzle)
   int stages;   // pipeline stages (small-N variant; per-tap derives its own)

@@ -1697,7 +1697,7 @@ omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled) {
 }
 
 omni_status omni_set_conv_kind(omni_ctx* ctx, int32_t kind) {
-  if (!ctx || kind < -1 || kind > 7) return OMNI_EINVAL;
+  if (!ctx || kind < -1 || kind > 8) return OMNI_EINVAL;
   ctx->force_kind = kind;
   ctx->tuned.clear();          // forced choices are recorded there; the autotuner starts afresh
   drop_graph(ctx);

@@ -78,8 +78,9 @@ def _layer_case(R, cin, cout, cr, prec, B=2):
 # shapes whose candidates include the small-N kernels (one and two blocks per
 # tile, and the CTA-pair form of the latter) and the dx-in-N kernels
 # (kind 7: the two-block dx-in-N kernel once per 32 output channels)
+# (kind 8: the per-tap kernel on CTA pairs, N tiles 128 and 256)
 VARIANT_SHAPES = [(64, 32, 32, 0), (64, 64, 64, 64), (64, 96, 32, 0), (32, 32, 64, 32), (128, 64, 32, 0),
-                  (64, 192, 64, 0), (32, 64, 128, 64)]
+                  (64, 192, 64, 0), (32, 64, 128, 64), (32, 128, 256, 0), (16, 256, 256, 128)]
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
@@ -89,7 +90,9 @@ def test_every_conv_variant_against_oracle(api, R, cin, cout, cr, prec):
     meets the layer bound against the oracle (the 32-channel slices of kind 7
     included); the CTA-pair form of the two-block small-N kernel (kind 6:
     cta_group::2 MMAs over both CTAs' tiles) equals its one-CTA form (kind 3)
-    bit for bit: same products, same accumulation order per pixel."""
+    bit for bit: same products, same accumulation order per pixel, and so does
+    the pair form of the per-tap kernel (kind 8) against kind 0 with the same
+    N tile and chunk."""
     from paper_2305_14566_gb300 import _lib as L
     B = 2
     dt = torch.bfloat16 if prec == "bf16" else torch.float16
@@ -114,6 +117,9 @@ def test_every_conv_variant_against_oracle(api, R, cin, cout, cr, prec):
     if 3 in kinds:
         assert 6 in kinds, cands
         assert torch.equal(outs[kinds[6]], outs[kinds[3]])
+    for c in cands:
+        if c[0] == 8:   # per-tap on CTA pairs: the same sums as the one-CTA per-tap kernel
+            assert torch.equal(outs[c], outs[(0, c[1], c[2], 0)]), c
     if cout >= 64:
         assert 7 in kinds, cands
 
