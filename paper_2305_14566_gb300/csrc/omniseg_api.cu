@@ -1270,8 +1270,12 @@ omni_status omni_segment_slide_host(omni_ctx* ctx, const uint8_t* rgb_host, int3
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t* ws = static_cast<uint8_t*>(ws_);
   const int64_t dstride = (int64_t)W * 3;
-  OMNI_CU(cudaMemcpy2DAsync(ws + p.in, dstride, rgb_host, stride, dstride, H, cudaMemcpyHostToDevice, st),
-          "upload slide");
+  // packed rows go up as one linear copy; padded rows as a pitched copy
+  if (stride == dstride)
+    OMNI_CU(cudaMemcpyAsync(ws + p.in, rgb_host, (size_t)dstride * H, cudaMemcpyHostToDevice, st), "upload slide");
+  else
+    OMNI_CU(cudaMemcpy2DAsync(ws + p.in, dstride, rgb_host, stride, dstride, H, cudaMemcpyHostToDevice, st),
+            "upload slide");
   omni_outputs o{};
   uint8_t* host[OMNI_MAX_CLASSES] = {};
   for (int k = 0; k < c.n_classes; ++k)
