@@ -1651,17 +1651,21 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 //      at the 16-byte boundary at or left of the window (the 18-pixel, 54-byte
 //      window sits at byte offset 0..15 of each row; OOB rows read as zero);
 //   2. builder thread r reads the nine bytes of each of its pixel's three
-//      window rows as three aligned words (funnel-shifted into place),
-//      normalises them in registers, v = fma(u, 2/255, -1) (for every byte
-//      value this rounds to the same FP16 number as 2u/255 - 1 in exact
-//      arithmetic), zeroes taps outside the tile, rounds to FP16 (whatever the
-//      pipeline's 16-bit type: 8-bit colour values need the 11-bit mantissa)
-//      and stores one 64-byte K row (the 27 values, a constant 1, zeros to
-//      32) in the 64-byte-swizzled K-major layout the MMA reads (16-byte
-//      chunk j of row r at chunk j ^ ((r >> 1) & 3)).
-// Two FP16 MMAs (K = 16 each) per tile, N = cout.  The layer's norm rides in
-// the weights: the host stores g[o] * w in K entries 0..26 and b[o] in entry
-// 27, whose operand is the constant 1, so the accumulator already holds
+//      window rows as three aligned words (funnel-shifted into place) and
+//      writes each byte u as the FP16 number 512 + u, whose bits are
+//      0x6000 | 2u (FP16 spacing is 1/2 on [512, 1024)): two bytes become a
+//      pair of halves with one byte permute and one multiply-add.  A tap
+//      outside the tile takes 639.5 = 512 + 127.5 (bits 0x60FF), the value
+//      at which the normalisation v = 2u/255 - 1 is zero.  The 64-byte K row
+//      (the 27 operands, two constant 1s, zeros to 32; FP16 in every precision,
+//      exact for 8-bit colour) is stored in the 64-byte-swizzled K-major
+//      layout the MMA reads (16-byte chunk j of row r at chunk j ^ ((r >> 1) & 3)).
+// Two FP16 MMAs (K = 16 each) per tile, N = cout.  The normalisation and the
+// layer's norm ride in the weights: with A = 512 + u, v = (A - 639.5) 2/255,
+// so g (w . v) + b = sum_k W_k A_k + B for W = g w 2/255 (entries 0..26,
+// rounded to FP16) and B = b - 639.5 sum_k W_k over the rounded W (exact, so
+// only the weight rounding remains), carried as an FP16 pair hi + lo in
+// entries 27 and 28, whose operands are 1.  The accumulator already holds
 // g * conv + b and the epilogue applies only the ReLU.  The epilogue stages
 // each warp's 32 output pixels (two rows of 16) in shared memory, swizzled
 // like the output tensor map, and writes them with one TMA store per warp and
@@ -1674,15 +1678,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 __host__ __device__ constexpr uint32_t idesc_f16_ops(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
-__device__ __forceinline__ uint32_t pack2_f16(float a, float b) {
-  __half2 h = __floats2half2_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&h);
-}
-constexpr float kNorm = 2.0f / 255.0f;
-// byte i (0..3) of w as an exact float: 2^23 + byte, minus 2^23
-__device__ __forceinline__ float byte_f32(uint32_t w, int i) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | (uint32_t)i)) - 8388608.f;
-}
+// first-layer operand bits: FP16 512 + u for byte u, and 639.5 (v = 0) for a padding tap
+constexpr uint32_t kFirstOp = 0x6000u, kFirstPad = 0x60FFu, kFirstOne = 0x3C00u;
 constexpr int kFirstGroups = 2;                           // builder groups, 128 threads each
 constexpr int kFirstBuilders = 128 * kFirstGroups;
 constexpr int kFirstEpiGroups = 2;                         // epilogue warpgroups, alternate tiles
@@ -1813,39 +1810,62 @@ __global__ void __launch_bounds__(kThreadsFirst, 1)
       const int h_in = tw.ty * kHTH + rh - 1, w_in = tw.tx * kHTW + rw - 1;   // tile coords of tap (0, 0)
       // blocks whose 10 x 18 window lies inside the tile need no zero padding
       const bool inner = tw.ty > 0 && (tw.ty + 1) * kHTH < p.R && tw.tx > 0 && (tw.tx + 1) * kHTW < p.R;
-      float v[32];
+      uint32_t wd[3][3];                             // bytes 0..8 of the three window rows
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy) {
         const uint32_t* wp = wrow + (rh + dy) * (kRawW / 4);
         const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
-        const uint32_t by[3] = {__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
-                                __funnelshift_r(w2, w2, sh)};
-        if (inner) {
+        wd[dy][0] = __funnelshift_r(w0, w1, sh);
+        wd[dy][1] = __funnelshift_r(w1, w2, sh);
+        wd[dy][2] = __funnelshift_r(w2, w2, sh);
+      }
+      // K entry k = 9 dy + 3 dx + c is byte k % 9 of row k / 9; word i of the
+      // row holds entries 2i and 2i + 1 (entry 27 and 28 are the constant 1s)
+      uint32_t a16[16];
 #pragma unroll
-          for (int j = 0; j < 9; ++j) v[dy * 9 + j] = fmaf(byte_f32(by[j >> 2], j & 3), kNorm, -1.f);
+      for (int i = 0; i < 14; ++i) {
+        const int k0 = 2 * i, k1 = 2 * i + 1;
+        const uint32_t x0 = wd[k0 / 9][(k0 % 9) >> 2];
+        const uint32_t b0 = (uint32_t)((k0 % 9) & 3);
+        uint32_t pr;
+        if (k1 == 27) {
+          pr = __byte_perm(x0, 0u, b0 | 0x4440u);                      // [u0, 0, 0, 0]
+        } else if (k0 / 9 == k1 / 9 && (k0 % 9) >> 2 == (k1 % 9) >> 2) {
+          const uint32_t b1 = (uint32_t)((k1 % 9) & 3);
+          pr = __byte_perm(x0, 0u, b0 | 0x4040u | (b1 << 8));          // [u0, 0, u1, 0]
         } else {
-          const int yy = h_in + dy;
-          const bool yin = yy >= 0 && yy < p.R;
+          const uint32_t b1 = (uint32_t)((k1 % 9) & 3) + 4u;
+          pr = __byte_perm(x0, wd[k1 / 9][(k1 % 9) >> 2], b0 | (b1 << 8)) & 0x00FF00FFu;
+        }
+        uint32_t h = pr * 2u + (kFirstOp | kFirstOp << 16);            // halves 512 + u
+        if (k1 == 27) h = (h & 0xFFFFu) | kFirstOne << 16;
+        a16[i] = h;
+      }
+      if (!inner) {
+        // zero padding: taps outside the tile take the operand of v = 0
+        bool yin[3], xin[3];
 #pragma unroll
-          for (int j = 0; j < 9; ++j) {
-            const int xx = w_in + j / 3;
-            const bool in = yin && xx >= 0 && xx < p.R;
-            v[dy * 9 + j] = in ? fmaf(byte_f32(by[j >> 2], j & 3), kNorm, -1.f) : 0.f;
-          }
+        for (int d = 0; d < 3; ++d) {
+          yin[d] = h_in + d >= 0 && h_in + d < p.R;
+          xin[d] = w_in + d >= 0 && w_in + d < p.R;
+        }
+#pragma unroll
+        for (int i = 0; i < 14; ++i) {
+          const int k0 = 2 * i, k1 = 2 * i + 1;
+          uint32_t m = yin[k0 / 9] && xin[(k0 % 9) / 3] ? 0u : 0xFFFFu;
+          if (k1 != 27) m |= yin[k1 / 9] && xin[(k1 % 9) / 3] ? 0u : 0xFFFF0000u;
+          a16[i] = (a16[i] & ~m) | ((kFirstPad | kFirstPad << 16) & m);
         }
       }
-      v[27] = 1.f;                                   // operand of the norm shift b (weight row entry 27)
-#pragma unroll
-      for (int k = 28; k < 32; ++k) v[k] = 0.f;
+      a16[14] = kFirstOne;                           // entry 28 = 1 (operand of the shift's low half)
+      a16[15] = 0u;
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&rempty[s]));
       uint8_t* row = sA + (size_t)s * kFirstStageBytes + r * kFirstRowBytes;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        uint4 q = make_uint4(pack2_f16(v[8 * j], v[8 * j + 1]), pack2_f16(v[8 * j + 2], v[8 * j + 3]),
-                             pack2_f16(v[8 * j + 4], v[8 * j + 5]), pack2_f16(v[8 * j + 6], v[8 * j + 7]));
-        *reinterpret_cast<uint4*>(row + ((j ^ swz) << 4)) = q;
-      }
+      for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<uint4*>(row + ((j ^ swz) << 4)) =
+            make_uint4(a16[4 * j], a16[4 * j + 1], a16[4 * j + 2], a16[4 * j + 3]);
       // make this thread's generic-proxy stores visible to the tensor core's reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();

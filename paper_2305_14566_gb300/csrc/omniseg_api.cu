@@ -316,6 +316,12 @@ uint16_t to_fp16(float f) {
   return u;
 }
 
+float fp16_value(uint16_t u) {
+  __half h;
+  memcpy(&h, &u, 2);
+  return __half2float(h);
+}
+
 // 16-bit operand bits of the tensor-core path (BF16 or FP16)
 uint16_t to_lp(float f, bool f16) { return f16 ? to_fp16(f) : to_bf16(f); }
 
@@ -451,9 +457,12 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
     q.cin = cin; q.cout = cout; q.cproj = cproj_used;
     // 16-bit weights: [cout][9 cin] (tap-major K).  The first layer's rows are
     // FP16 in every precision, padded to K = 32 for its tensor-core kernel,
-    // and carry the layer's norm: K entries 0..26 hold g[o] * w, entry 27
-    // holds b[o] (its operand is the constant 1), so the MMA yields g * conv + b
-    // (one FP16 rounding of each product instead of one of each weight)
+    // and carry the input normalisation and the layer's norm: its operands are
+    // A = 512 + u per colour byte u (639.5 at a padding tap), and v = 2u/255 - 1
+    // = (A - 639.5) 2/255, so K entries 0..26 hold W = g[o] w 2/255 (rounded)
+    // and entries 27, 28 (operands 1) the FP16 pair hi + lo of
+    // B = b[o] - 639.5 sum_k W_k, summed over the rounded W: the MMA yields
+    // g * conv(v) + b with only the weights' rounding
     const size_t kdim = cin == 3 ? 32 : (size_t)9 * cin;
     q.w32 = alloc((size_t)9 * cin * cout * 4);
     q.w16 = alloc(kdim * cout * 2);
@@ -464,13 +473,27 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
     const float* gsrc = src + (size_t)cout * cin * 9;     // the layer's norm scale and shift
     const float* bsrc = gsrc + cout;
     for (int o = 0; o < cout; ++o) {
+      double wsum = 0.0;                                 // first layer: sum of the stored W
       for (int ci = 0; ci < cin; ++ci)
         for (int tap = 0; tap < 9; ++tap) {
           float v = src[((size_t)o * cin + ci) * 9 + tap];
           w32[((size_t)tap * cin + ci) * cout + o] = v;
-          w16[(size_t)o * kdim + (size_t)tap * cin + ci] = cin == 3 ? to_lp(gsrc[o] * v, true) : to_lp(v, f16);
+          uint16_t h;
+          if (cin == 3) {
+            h = to_fp16((float)((double)gsrc[o] * v * (2.0 / 255.0)));
+            wsum += (double)fp16_value(h);
+          } else {
+            h = to_lp(v, f16);
+          }
+          w16[(size_t)o * kdim + (size_t)tap * cin + ci] = h;
         }
-      if (cin == 3) w16[(size_t)o * kdim + 27] = to_lp(bsrc[o], true);
+      if (cin == 3) {
+        const double shift = (double)bsrc[o] - 639.5 * wsum;
+        const uint16_t hi = to_fp16((float)shift);
+        w16[(size_t)o * kdim + 27] = hi;
+        w16[(size_t)o * kdim + 28] = to_fp16((float)(shift - (double)fp16_value(hi)));
+        for (int k = 29; k < 32; ++k) w16[(size_t)o * kdim + k] = 0;
+      }
     }
     src += (size_t)cout * cin * 9;
     memcpy(host.data() + q.g, src, cout * 4);
