@@ -90,9 +90,9 @@ def test_every_conv_variant_against_oracle(api, R, cin, cout, cr, prec):
     meets the layer bound against the oracle (the 32-channel slices of kind 7
     included); the CTA-pair form of the two-block small-N kernel (kind 6:
     cta_group::2 MMAs over both CTAs' tiles) equals its one-CTA form (kind 3)
-    bit for bit: same products, same accumulation order per pixel, and so does
-    the pair form of the per-tap kernel (kind 8) against kind 0 with the same
-    N tile and chunk."""
+    bit for bit: same products, same accumulation order per pixel; so do all
+    per-tap configurations, one CTA (kind 0) or CTA pairs (kind 8), whatever
+    their N tile and channel chunk."""
     from paper_2305_14566_gb300 import _lib as L
     B = 2
     dt = torch.bfloat16 if prec == "bf16" else torch.float16
@@ -117,9 +117,11 @@ def test_every_conv_variant_against_oracle(api, R, cin, cout, cr, prec):
     if 3 in kinds:
         assert 6 in kinds, cands
         assert torch.equal(outs[kinds[6]], outs[kinds[3]])
-    for c in cands:
-        if c[0] == 8:   # per-tap on CTA pairs: the same sums as the one-CTA per-tap kernel
-            assert torch.equal(outs[c], outs[(0, c[1], c[2], 0)]), c
+    # per-tap, one CTA or CTA pairs, any N tile or chunk: every output sums the
+    # same K = 16 products in the same order (tap, then channel)
+    pertap = [c for c in cands if c[0] in (0, 8)]
+    for c in pertap[1:]:
+        assert torch.equal(outs[c], outs[pertap[0]]), (c, pertap[0])
     if cout >= 64:
         assert 7 in kinds, cands
 
@@ -400,6 +402,32 @@ def test_forced_pair_kernel_equals_one_cta_kernel_through_the_slide(api, prec):
     for c in outs[3]["logits"]:
         assert torch.equal(outs[6]["logits"][c], outs[3]["logits"][c]), c
         assert torch.equal(outs[6]["labels"][c], outs[3]["labels"][c]), c
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_forced_pair_per_tap_kernel_equals_default_through_the_slide(api, prec):
+    """The whole path with every layer that has a per-tap CTA-pair candidate
+    (cout >= 128: levels 2 to 4 of encoder and decoder) forced onto it (kind 8)
+    gives the same logits and labels, bit for bit, as the default choices
+    (the one-CTA per-tap kernel at those layers, the same kernels elsewhere)."""
+    from paper_2305_14566_gb300 import _lib as L
+    w = synth.NEEDLE.with_(H=2048, W=4096, P=256, S=128, median_k=5, max_batch=16)
+    rgb = api.synth_slide(synth.make_spec(2048, 4096, 44, 0.5, "cores", 3))
+    blob = synth.gen_weights(w)
+    outs, kinds = {}, {}
+    for k in (-1, 8):
+        seg = api.Segmenter(w, blob, precision=L.BF16 if prec == "bf16" else L.FP16)
+        seg.set_conv_kind(k)
+        o = seg.segment(rgb, logits=True)
+        torch.cuda.synchronize()
+        outs[k] = {n: {c: t.clone() for c, t in d.items()} for n, d in o.items() if n in ("labels", "logits")}
+        kinds[k] = [int(r[6]) for r in seg.tuned()]
+        seg.close()
+    # 10 layer shapes with cout >= 128, each at every batch size of the call
+    assert kinds[8].count(8) >= 10, kinds
+    for c in outs[-1]["logits"]:
+        assert torch.equal(outs[8]["logits"][c], outs[-1]["logits"][c]), c
+        assert torch.equal(outs[8]["labels"][c], outs[-1]["labels"][c]), c
 
 
 def test_graph_is_dropped_when_weights_are_reloaded(api):
