@@ -372,7 +372,9 @@ omni_status omni_set_graphs(omni_ctx* ctx, int32_t enabled);
  * of the tile's classes (Sec. 2.2; at most two classes per scale) in its
  * epilogue, writing the FP32 tile logits directly; its 16-bit output is then
  * not stored.  Pooling fuses into the small-N and dx-in-N variants (kinds
- * 1-4), the head into all of them for 32 or 64 output channels; the
+ * 1-4 and 6), the head into kinds 1-3 and 6 for 32 or 64 output channels and
+ * kind 4 for 32 (the per-tap kinds 0 and 8 and the sliced kind 7 fuse
+ * neither; the pool then runs as its own launch); the
  * autotuner then considers only variants that fuse the head, so the dynamic
  * head needs no launch of its own.  The GAP of the bottleneck and the
  * controller always run as one launch per batch.  With the head fused, the
