@@ -14,6 +14,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -43,15 +44,24 @@ WORKLOAD = describe(WORK)
 METRIC = "segmented slide Mpx/s (6 classes x 3 scales)"
 
 
+def code_digest(path):
+    """SHA-256 of a C++ source with its comments and runs of white space
+    removed: the counters depend on the code, not on how it is commented."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()
+
+
 def conv_traffic(bf16, tiles_per_step, conv_launches_per_step):
     """DRAM bytes of the conv kernels from the committed ncu counters (per
-    foreground tile), valid only while the conv source is the one captured."""
+    foreground tile), valid only while the conv code is the one captured."""
     p = os.path.join(ROOT, "profiles", "conv_traffic_needle_bf16.json")
     src = os.path.join(ROOT, "paper_2305_14566_gb300", "csrc", "conv_tc_impl.cuh")
     if not bf16 or not os.path.exists(p) or conv_launches_per_step <= 0:
         return None, None
     d = json.load(open(p))
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != d.get("conv_source_sha256"):
+    if code_digest(src) != d.get("conv_code_sha256"):
         return None, None
     per_step = d["bytes_per_tile"] * tiles_per_step
     return per_step / conv_launches_per_step, per_step

@@ -600,8 +600,9 @@ struct TileWalk {
 
 // PAIR: clusters of two CTAs take adjacent M tiles of one N tile; one thread
 // of CTA 0 issues cta_group::2 MMAs (M = 256) and each CTA holds half of the
-// B tile's rows, so a K step moves a quarter less operand data per SM
-// (the wide layers here are bound by that traffic, not by the MMA rate)
+// B tile's rows, so a K step moves a quarter (N = 128) to a third (N = 256)
+// less operand data per SM (the wide layers here are bound by that traffic,
+// not by the MMA rate)
 template <int BN, int CK, bool RES, bool PAIR = false>
 struct TCCfg {
   static constexpr int kABytes = kBM * CK * 2;
