@@ -184,8 +184,9 @@ def run_layer(args):
     R, cin, cout, cr, B, rep = vals[:6]
     config = tuple(vals[6:10]) if len(vals) == 10 else None   # kind, N tile, chunk, stages
     rng = np.random.default_rng(0)
-    prec = {"bf16": _lib.BF16, "fp16": _lib.FP16, "fp32": _lib.FP32}[args.precision]
-    dt = {"bf16": torch.bfloat16, "fp16": torch.float16, "fp32": torch.float32}[args.precision]
+    prec = {"bf16": _lib.BF16, "fp16": _lib.FP16, "fp32": _lib.FP32, "e4m3": _lib.E4M3}[args.precision]
+    dt = {"bf16": torch.bfloat16, "fp16": torch.float16, "fp32": torch.float32,
+          "e4m3": torch.bfloat16}[args.precision]      # E4M3: BF16 activations in and out
     x = torch.rand((B, R, R, cin), device="cuda").to(dt)
     r = torch.rand((B, R, R, cr), device="cuda").to(dt) if cr else None
     y = torch.empty((B, R, R, cout), device="cuda", dtype=dt)
@@ -198,10 +199,14 @@ def run_layer(args):
     fl = 2.0 * B * R * R * cout * (9 * cin + cr)
     pk, src = peaks()
     tf = fl / (ms / 1e3) / 1e12
-    print(json.dumps({"layer": {"R": R, "cin": cin, "cout": cout, "cr": cr, "B": B,
-                                "config": list(config) if config else "default"},
-                      "ms_per_launch": ms, "tflops": tf, "frac_of_bf16_burst": tf / pk["bf16_tflops"],
-                      "peak_source": src}))
+    line = {"layer": {"R": R, "cin": cin, "cout": cout, "cr": cr, "B": B,
+                      "config": list(config) if config else "default"},
+            "precision": args.precision, "ms_per_launch": ms, "tflops": tf,
+            "frac_of_bf16_burst": tf / pk["bf16_tflops"], "peak_source": src}
+    if prec == _lib.E4M3:
+        # E4M3 peak: the measured BF16 burst times the nominal 4.5 / 2.25 ratio
+        line["frac_of_e4m3_burst"] = tf / (2.0 * pk["bf16_tflops"])
+    print(json.dumps(line))
 
 
 def run_ragged(args, api, _lib, dev, prec):
@@ -431,7 +436,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32", "e4m3"],
+                    help="e4m3: the 8-bit experiment, --layer only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true",
                     help="skip the step of the plain FP32 path that the line reports as fp32_plain")
@@ -476,6 +482,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    if args.precision == "e4m3":
+        raise SystemExit("--precision e4m3 is the layer experiment: use it with --layer")
     prec = {"bf16": _lib.BF16, "fp16": _lib.FP16, "fp32": _lib.FP32}[args.precision]
 
     if args.ragged:

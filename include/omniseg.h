@@ -54,6 +54,9 @@ typedef int omni_status;
 #define OMNI_BF16 1  /* BF16 operands, FP32 accumulation in TMEM (tcgen05.mma)    */
 #define OMNI_FP16 2  /* FP16 operands and activations, FP32 accumulation in TMEM;
                         same tensor-core rate as BF16, 3 more mantissa bits      */
+#define OMNI_E4M3 3  /* omni_conv_layer only (experiment): E4M3 operands with one
+                        activation scale and per-output-channel weight scales,
+                        FP32 accumulation in TMEM, BF16 activations in and out */
 
 /* Overlap aggregation (Sec. 2.2, Sec. 3.2). */
 #define OMNI_STITCH_AVG 0   /* label = mean logit of covering tiles > 0            */
@@ -303,6 +306,15 @@ omni_status omni_synth_slide(const int64_t* ellipses_host, int32_t n_ell, uint64
  * selects one configuration as 4 int32 rows of omni_conv_candidates (the
  * stages entry may be lowered to 2 or more); a configuration not legal for
  * the shape returns OMNI_EINVAL.
+ * OMNI_E4M3 (the 8-bit experiment of the network's convolutions): x and y are
+ * bfloat16, x contiguous (x_cs = cin, x_co = 0), no residual, cin a multiple
+ * of 128.  The call quantises x to E4M3 with one scale s_x = max|x| / 448 and
+ * weight row o with s_w[o] = max_k |w[o][k]| / 448 (round to nearest even,
+ * saturating), then runs the per-tap kernel on the E4M3 operands (kind::f8f6f4,
+ * FP32 accumulation) with g[o] s_x s_w[o] as the epilogue scale; only those
+ * launches are timed.  `config`: kind 0 or 8 (CTA pairs; R * R a multiple of
+ * 256), N tile 128 or 256, chunk 128, stages 0; NULL picks kind 8 with the
+ * widest N tile that divides cout.
  * Allocates and frees its own temporary weight buffers; synchronises `stream`. */
 omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin, int32_t cout,
                             const void* x_dev, int32_t x_cs, int32_t x_co,

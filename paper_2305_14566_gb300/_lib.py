@@ -15,6 +15,7 @@ MAX_SLIDES = 16
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EWEIGHTS, ESTATE = 0, -1, -2, -3, -4, -5, -6
 FP32, BF16, FP16 = 0, 1, 2
+E4M3 = 3          # omni_conv_layer only: the 8-bit experiment
 STITCH_AVG, STITCH_VOTE = 0, 1
 NOALLOC_MAX_THUMB_PX = 4 << 20
 NOALLOC_MAX_TILES = 1 << 16

@@ -215,6 +215,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int n, int m = kBM) {
          ((uint32_t)(m >> 4) << 24);
 }
 
+// kind::f8f6f4 with E4M3 x E4M3 -> FP32 (operand format code 0 = E4M3), K-major,
+// K = 32 per instruction: the same 32 bytes of each operand row as kind::f16
+__host__ __device__ constexpr uint32_t idesc_e4m3(int n, int m = kBM) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(
@@ -231,9 +237,24 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 // columns split N/2 per CTA at the same shared-memory offset), accumulator
 // rows in each CTA's own TMEM; the commit arrives on the barrier at the same
 // offset in both CTAs
-template <bool PAIR>
+template <bool PAIR, bool F8 = false>
 __device__ __forceinline__ void mma_t(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                       uint32_t accumulate) {
+  if constexpr (F8) {
+    if constexpr (PAIR)
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+          : "memory");
+    return;
+  }
   if (!PAIR) {
     mma_bf16(tmem_d, adesc, bdesc, idesc, accumulate);
     return;
@@ -603,11 +624,15 @@ struct TileWalk {
 // B tile's rows, so a K step moves a quarter (N = 128) to a third (N = 256)
 // less operand data per SM (the wide layers here are bound by that traffic,
 // not by the MMA rate)
-template <int BN, int CK, bool RES, bool PAIR = false>
+// F8: E4M3 operands (1 byte per element, K = 32 per MMA); a chunk of CK = 128
+// channels is the same 128-byte row as a 64-channel 16-bit chunk
+template <int BN, int CK, bool RES, bool PAIR = false, bool F8 = false>
 struct TCCfg {
-  static constexpr int kABytes = kBM * CK * 2;
+  static constexpr int kEB = F8 ? 1 : 2;                  // operand bytes per element
+  static constexpr int kABytes = kBM * CK * kEB;
   static constexpr int kBRows = PAIR ? BN / 2 : BN;       // B rows (output channels) held here
-  static constexpr int kBBytes = kBRows * CK * 2;
+  static constexpr int kBBytes = kBRows * CK * kEB;
+  static constexpr int kKSteps = CK * kEB / 32;           // MMAs per K step (32 bytes of K each)
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStages0 = (kSmemBudget - 2048) / kStageBytes;
   static constexpr int kStages = kStages0 > 16 ? 16 : kStages0;       // (A, B) slots
@@ -618,17 +643,18 @@ struct TCCfg {
   static constexpr int kBufCols = RES ? 2 * BN : BN;     // TMEM columns per accumulator buffer
   static constexpr int kBufs = tmem_bufs(kBufCols);       // accumulator ring depth
   static constexpr int kTmemCols = tmem_alloc_cols(kBufs * kBufCols);
-  static constexpr int kSW = CK * 2;                      // row bytes = swizzle span
+  static constexpr int kSW = CK * kEB;                    // row bytes = swizzle span
   static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*align*/ +
                                   2 * 512 * 4 /*gamma, beta*/;
+  static_assert(!F8 || !RES, "E4M3 operands: no projection accumulator");
 };
 
-template <int BN, int CK, bool RES, bool PAIR>
+template <int BN, int CK, bool RES, bool PAIR, bool F8 = false>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
               TCParams p) {
-  using Cfg = TCCfg<BN, CK, RES, PAIR>;
+  using Cfg = TCCfg<BN, CK, RES, PAIR, F8>;
   constexpr int ST = Cfg::kStages;     // (A, B) slots
   constexpr int G = Cfg::kGroup;       // slots per stage
   constexpr int RING = Cfg::kRing;     // stages
@@ -755,7 +781,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuer
-      constexpr uint32_t idesc = idesc_bf16(BN, PAIR ? 2 * kBM : kBM);
+      constexpr uint32_t idesc = F8 ? idesc_e4m3(BN, PAIR ? 2 * kBM : kBM) : idesc_bf16(BN, PAIR ? 2 * kBM : kBM);
       const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::kSW);
       const uint64_t b_desc0 = smem_desc(smem_u32(sB), Cfg::kSW);
       int tcount = 0;
@@ -786,9 +812,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const uint32_t d = second ? acc1 : acc0;
             const int kfirst = second ? p.k_main : 0;
 #pragma unroll
-            for (int kk = 0; kk < CK / 16; ++kk)
-              mma_t<PAIR>(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                          (k > kfirst || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < Cfg::kKSteps; ++kk)
+              mma_t<PAIR, F8>(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                              (k > kfirst || kk > 0) ? 1u : 0u);
           }
           mma_commit_t<PAIR>(smem_u32(&empty[s]));
         }
@@ -1996,19 +2022,21 @@ EncodeFn encoder() {
   return fn;
 }
 
-// NHWC activation box: {CK channels, bw pixels, bh rows, 1 image}
-bool map_act(CUtensorMap* m, const void* base, int channels, int cs, int co, int R, int B, int CK) {
+// NHWC activation box: {CK channels, bw pixels, bh rows, 1 image}; eb bytes
+// per element (2: BF16 / FP16, 1: E4M3 bytes)
+bool map_act(CUtensorMap* m, const void* base, int channels, int cs, int co, int R, int B, int CK,
+             int eb = 2) {
   EncodeFn enc = encoder();
   if (!enc) return false;
-  const char* ptr = static_cast<const char*>(base) + (size_t)co * 2;
+  const char* ptr = static_cast<const char*>(base) + (size_t)co * eb;
   cuuint64_t dims[4] = {(cuuint64_t)channels, (cuuint64_t)R, (cuuint64_t)R, (cuuint64_t)B};
-  cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)R * cs * 2, (cuuint64_t)R * R * cs * 2};
+  cuuint64_t strides[3] = {(cuuint64_t)cs * eb, (cuuint64_t)R * cs * eb, (cuuint64_t)R * R * cs * eb};
   const int bw = R < kBM ? R : kBM;
   cuuint32_t box[4] = {(cuuint32_t)CK, (cuuint32_t)bw, (cuuint32_t)(kBM / bw), 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<char*>(ptr), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+  CUresult r = enc(m, eb == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                   const_cast<char*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CK * eb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -2030,17 +2058,17 @@ bool map_act_box(CUtensorMap* m, const void* base, int channels, int cs, int co,
   return r == CUDA_SUCCESS;
 }
 
-// K-major weights [rows = cout][K]: box {CK, BN}
-bool map_w(CUtensorMap* m, const void* base, int K, int cout, int BN, int CK) {
+// K-major weights [rows = cout][K]: box {CK, BN}; eb bytes per element
+bool map_w(CUtensorMap* m, const void* base, int K, int cout, int BN, int CK, int eb = 2) {
   EncodeFn enc = encoder();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cout};
-  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)K * eb};
   cuuint32_t box[2] = {(cuuint32_t)CK, (cuuint32_t)BN};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+  CUresult r = enc(m, eb == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CK * eb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -2056,12 +2084,12 @@ int num_sms() {
   return n;
 }
 
-template <int BN, int CK, bool RES, bool PAIR = false>
+template <int BN, int CK, bool RES, bool PAIR = false, bool F8 = false>
 cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
-  using Cfg = TCCfg<BN, CK, RES, PAIR>;
+  using Cfg = TCCfg<BN, CK, RES, PAIR, F8>;
   CUtensorMap mA, mB, mA2, mB2;
-  if (!map_act(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK)) return cudaErrorInvalidValue;
-  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, Cfg::kBRows, CK)) return cudaErrorInvalidValue;
+  if (!map_act(&mA, a.x, a.cin, a.x_cs, a.x_co, a.R, a.B, CK, Cfg::kEB)) return cudaErrorInvalidValue;
+  if (!map_w(&mB, a.w.w_bf16, 9 * a.cin, a.cout, Cfg::kBRows, CK, Cfg::kEB)) return cudaErrorInvalidValue;
   if (RES) {
     if (!map_act(&mA2, a.r, a.cr, a.r_cs, a.r_co, a.R, a.B, CK)) return cudaErrorInvalidValue;
     if (!map_w(&mB2, a.w.wp_bf16, a.cr, a.cout, Cfg::kBRows, CK)) return cudaErrorInvalidValue;
@@ -2087,7 +2115,7 @@ cudaError_t launch_t(const ConvArgs& a, cudaStream_t st) {
   p.y_co = a.y_co;
   p.err = a.err;
   if (a.pool || a.head_theta || !a.y) return cudaErrorInvalidValue;   // no fused outputs here
-  auto kern = k_conv_tc<BN, CK, RES, PAIR>;
+  auto kern = k_conv_tc<BN, CK, RES, PAIR, F8>;
   static bool attr_set = false;
   static int max_pairs = 0;
   if (!attr_set) {
@@ -2657,6 +2685,22 @@ cudaError_t launch_conv_first_tc(const ConvArgs& a, cudaStream_t st) {
 
 cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_t st) {
   return a.f16 ? launch_conv_tc_cfg_f16(a, c, st) : launch_conv_tc_cfg_bf16(a, c, st);
+}
+
+cudaError_t launch_conv_tc_e4m3(const ConvArgs& a, const TcConfig& c, cudaStream_t st) {
+  // x and the weights hold E4M3 bytes; per-tap kernel, one CTA (kind 0) or CTA
+  // pairs (kind 8), 128-channel chunks, no projection or fused outputs
+  if (a.res_mode != RES_NONE || a.pool || a.head_theta || !a.y || c.ck != 128) return cudaErrorInvalidValue;
+  if (!pertap_ok(a.R, a.cin, a.cout, 0, c.bn, 128) || (c.bn != 128 && c.bn != 256)) return cudaErrorInvalidValue;
+  if ((a.x_co % 16) || (a.x_cs % 16) || (a.y_co % 8) || (a.y_cs % 8) ||
+      (reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.y) |
+       reinterpret_cast<uintptr_t>(a.w.w_bf16)) % 16)
+    return cudaErrorInvalidValue;
+  if (c.kind == 0)
+    return c.bn == 128 ? launch_t<128, 128, false, false, true>(a, st) : launch_t<256, 128, false, false, true>(a, st);
+  if (c.kind == 8 && (long long)a.R * a.R % (2 * kBM) == 0)
+    return c.bn == 128 ? launch_t<128, 128, false, true, true>(a, st) : launch_t<256, 128, false, true, true>(a, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st) {

@@ -8,6 +8,7 @@
 // The SIMT implicit GEMM below computes one such convolution with the norm,
 // the 1x1 residual projection and the ReLU fused into its epilogue.
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "omni_internal.cuh"
 
@@ -479,6 +480,36 @@ cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, i
   else
     k_upsample<__nv_bfloat16><<<grid, 128, 0, st>>>(Ri, C, (const __nv_bfloat16*)x, x_cs, x_co,
                                                     (__nv_bfloat16*)y, y_cs, y_co);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- E4M3 experiment
+namespace {
+// max |x| over n BF16 values, as the bits of a non-negative float (ordered
+// like the floats themselves, so atomicMax on the bits is a float max)
+__global__ void k_absmax_bf16(const __nv_bfloat16* __restrict__ x, long long n, unsigned* out) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(__bfloat162float(x[i])));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// q = E4M3(x * inv_scale), round to nearest even, saturating at +-448
+__global__ void k_quant_e4m3(const __nv_bfloat16* __restrict__ x, long long n, float inv_scale,
+                             uint8_t* __restrict__ q) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    q[i] = __nv_cvt_float_to_fp8(__bfloat162float(x[i]) * inv_scale, __NV_SATFINITE, __NV_E4M3);
+}
+}  // namespace
+
+cudaError_t launch_absmax_bf16(const void* x, long long n, unsigned* out_bits, cudaStream_t st) {
+  k_absmax_bf16<<<1024, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(x), n, out_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant_e4m3(const void* x, long long n, float inv_scale, uint8_t* q, cudaStream_t st) {
+  k_quant_e4m3<<<1024, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(x), n, inv_scale, q);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,10 @@ cudaError_t launch_conv_first(const ConvArgs& a, int precision, cudaStream_t st)
 cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st);
 cudaError_t launch_maxpool(int precision, int B, int R, int C, const void* x, int x_cs, int x_co,
                            void* y, int y_cs, int y_co, cudaStream_t st);
+// E4M3 experiment: max |x| of n BF16 values (float bits, atomicMax into a
+// zeroed word) and x quantised to E4M3 bytes with one scale
+cudaError_t launch_absmax_bf16(const void* x, long long n, unsigned* out_bits, cudaStream_t st);
+cudaError_t launch_quant_e4m3(const void* x, long long n, float inv_scale, uint8_t* q, cudaStream_t st);
 cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, int x_cs,
                             int x_co, void* y, int y_cs, int y_co, cudaStream_t st);
 
@@ -132,6 +136,10 @@ struct TcConfig {
 };
 cudaError_t launch_conv_tc(const ConvArgs& a, cudaStream_t st);
 cudaError_t launch_conv_tc_cfg(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
+// E4M3 experiment: per-tap conv (TcConfig kind 0 or 8, N tile 128 / 256, chunk
+// 128) on E4M3 activations (x) and weights (w.w_bf16 holding bytes), FP32
+// accumulation, BF16 output; the dequantisation scales ride in w.gamma
+cudaError_t launch_conv_tc_e4m3(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
 cudaError_t launch_conv_tc_cfg_bf16(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
 cudaError_t launch_conv_tc_cfg_f16(const ConvArgs& a, const TcConfig& c, cudaStream_t st);
 int tc_candidates(int R, int cin, int cout, int cr, TcConfig* out, int max);

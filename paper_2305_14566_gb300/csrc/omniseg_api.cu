@@ -2,6 +2,8 @@
 // workspace planning and the orchestration of the three stages of the
 // whole-slide pipeline (Sec. 2.1 tiling, Sec. 2.2 segmentation, Sec. 2.3
 // aggregation).
+#include <cuda_fp8.h>
+
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -1566,6 +1568,103 @@ omni_status omni_synth_slide(const int64_t* ell, int32_t n_ell, uint64_t seed, i
   return e == cudaSuccess ? OMNI_OK : OMNI_ECUDA;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The E4M3 experiment of omni_conv_layer: activation scale s_x = max|x| / 448
+// and weight scales s_w[o] = max_k |w[o][k]| / 448 (448 = the largest finite
+// E4M3 value), so the quantised operands use the whole E4M3 range; the
+// product of the two scales and g rides in the epilogue's per-channel scale.
+omni_status conv_layer_e4m3(int32_t B, int32_t R, int32_t cin, int32_t cout, const void* x, int32_t x_cs,
+                            int32_t x_co, const float* w_host, const float* g_host, const float* b_host,
+                            void* y, int32_t y_cs, int32_t y_co, const int32_t* config, int32_t repeat,
+                            float* ms_per_launch, cudaStream_t st) {
+  if (x_cs != cin || x_co != 0 || cin % 128 || cout % 128 || cout > 512) return OMNI_EINVAL;
+  if (!(R == 16 || R == 32 || R == 64 || (R >= 128 && R % 128 == 0))) return OMNI_EINVAL;
+  TcConfig cfg{(long long)R * R % 256 == 0 ? 8 : 0, cout % 256 == 0 ? 256 : 128, 128, 0};
+  if (config) {
+    if (!((config[0] == 0 || config[0] == 8) && (config[1] == 128 || config[1] == 256) && config[2] == 128 &&
+          config[3] == 0))
+      return OMNI_EINVAL;
+    cfg = TcConfig{config[0], config[1], config[2], 0};
+  }
+  const size_t K = (size_t)9 * cin;
+  const long long n = (long long)B * R * R * cin;
+  size_t off = 0;
+  const size_t o_w = take(off, (size_t)cout * K), o_g = take(off, (size_t)cout * 4), o_b = take(off, (size_t)cout * 4),
+               o_amax = take(off, 4), o_err = take(off, 4), o_x = take(off, (size_t)n);
+  uint8_t* d = nullptr;
+  if (cudaMalloc(&d, align_up(off, 256)) != cudaSuccess) return OMNI_ECUDA;
+  omni_status rs = OMNI_OK;
+  unsigned amax_bits = 0;
+  cudaError_t e = cudaMemsetAsync(d + o_amax, 0, 4, st);      // max |x|
+  if (e == cudaSuccess) e = cudaMemsetAsync(d + o_err, 0, 4, st);   // the kernels' status word
+  if (e == cudaSuccess) e = launch_absmax_bf16(x, n, reinterpret_cast<unsigned*>(d + o_amax), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&amax_bits, d + o_amax, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float amax = 0.f;
+  memcpy(&amax, &amax_bits, 4);
+  const double s_x = amax > 0.f ? (double)amax / 448.0 : 1.0;
+  if (e == cudaSuccess) e = launch_quant_e4m3(x, n, (float)(1.0 / s_x), d + o_x, st);
+  // weight rows [cout][9 cin] (tap-major K, as the 16-bit paths) in E4M3
+  std::vector<uint8_t> wq((size_t)cout * K);
+  std::vector<float> gs(cout);
+  for (int o = 0; o < cout; ++o) {
+    float m = 0.f;
+    for (size_t k = 0; k < K; ++k) m = std::max(m, std::fabs(w_host[(size_t)o * K + k]));
+    const double s_w = m > 0.f ? (double)m / 448.0 : 1.0;
+    for (int ci = 0; ci < cin; ++ci)
+      for (int tap = 0; tap < 9; ++tap)
+        wq[(size_t)o * K + (size_t)tap * cin + ci] = __nv_cvt_float_to_fp8(
+            (float)(w_host[((size_t)o * cin + ci) * 9 + tap] / s_w), __NV_SATFINITE, __NV_E4M3);
+    gs[o] = (float)(g_host[o] * s_x * s_w);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + o_w, wq.data(), wq.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + o_g, gs.data(), (size_t)cout * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + o_b, b_host, (size_t)cout * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    ConvArgs a{};
+    a.B = B; a.R = R; a.cin = cin; a.cout = cout;
+    a.x = d + o_x; a.x_cs = cin; a.x_co = 0;
+    a.res_mode = RES_NONE;
+    a.y = y; a.y_cs = y_cs; a.y_co = y_co;
+    a.w.cin = cin; a.w.cout = cout;
+    a.w.w_bf16 = reinterpret_cast<__nv_bfloat16*>(d + o_w);     // E4M3 bytes
+    a.w.gamma = reinterpret_cast<float*>(d + o_g);
+    a.w.beta = reinterpret_cast<float*>(d + o_b);
+    a.err = reinterpret_cast<unsigned*>(d + o_err);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms_per_launch) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, st);
+    }
+    for (int i = 0; i < repeat && e == cudaSuccess; ++i) e = launch_conv_tc_e4m3(a, cfg, st);
+    if (ms_per_launch) cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (ms_per_launch) {
+      float t = 0;
+      if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+      *ms_per_launch = t / repeat;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+    unsigned herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, d + o_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && herr) rs = OMNI_ETIMEOUT;
+  }
+  if (e == cudaErrorInvalidValue) rs = OMNI_EINVAL;
+  else if (e != cudaSuccess) rs = OMNI_ECUDA;
+  cudaFree(d);
+  return rs;
+}
+
+}  // namespace
+
+extern "C" {
+
 omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin, int32_t cout,
                             const void* x, int32_t x_cs, int32_t x_co, const float* w_host,
                             const float* g_host, const float* b_host, const void* r, int32_t r_cs,
@@ -1573,6 +1672,12 @@ omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin
                             int32_t y_co, const int32_t* config, int32_t repeat, float* ms_per_launch,
                             void* stream) {
   if (repeat < 1) return OMNI_EINVAL;
+  if (precision == OMNI_E4M3) {
+    if (!x || !y || !w_host || !g_host || !b_host || B <= 0 || R <= 0 || cin <= 0 || cout <= 0 || r)
+      return OMNI_EINVAL;
+    return conv_layer_e4m3(B, R, cin, cout, x, x_cs, x_co, w_host, g_host, b_host, y, y_cs, y_co, config,
+                           repeat, ms_per_launch, static_cast<cudaStream_t>(stream));
+  }
   if (!x || !y || !w_host || !g_host || !b_host || B <= 0 || R <= 0 || cin <= 0 || cout <= 0) return OMNI_EINVAL;
   if (cin % 8 || cout % 8 || (r && (cr <= 0 || cr % 8 || !wp_host))) return OMNI_EINVAL;
   if (precision != OMNI_FP32 && precision != OMNI_BF16 && precision != OMNI_FP16) return OMNI_EINVAL;
