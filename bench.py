@@ -271,6 +271,8 @@ def run_large(args, api, _lib, dev, prec):
     seg = api.Segmenter(works[0], blob, precision=prec)
     if prec != _lib.FP32 and not args.no_autotune:
         seg.set_autotune(True)
+    if args.e4m3:
+        seg.set_e4m3(True)
     seg.workspace(seg.query(works[0].H, works[0].W).workspace_bytes, dev)
     rgbs = [api.synth_slide(synth.spec_for(w), device=dev) for w in works]
     outs = [seg.segment(r) for r in rgbs]
@@ -309,6 +311,9 @@ def run_large(args, api, _lib, dev, prec):
             "memory": {"workspace_bytes": int(seg.query(works[0].H, works[0].W).workspace_bytes),
                        "max_batch": int(works[0].max_batch)},
             "clocks": clk.summary()}
+    if args.e4m3:
+        line["e4m3"] = ("experiment: enc3.1, enc4.1, dec2.1 and dec3.1 on E4M3 operands (per-call "
+                        "activation scale, per-channel weight scales), the rest BF16")
     if args.compare_fp32 and prec != _lib.FP32:
         keep = {c: t.clone() for c, t in outs[0]["labels"].items()}
         seg.close()
@@ -441,6 +446,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true",
                     help="skip the step of the plain FP32 path that the line reports as fp32_plain")
+    ap.add_argument("--e4m3", action="store_true",
+                    help="with --large: the E4M3 experiment (the deeper levels' first convs on 8-bit operands)")
     ap.add_argument("--compare-fp32", action="store_true",
                     help="--large: also segment the first slide with the FP32 path and compare labels")
     ap.add_argument("--ragged", action="store_true",

@@ -368,6 +368,17 @@ int32_t omni_get_tuned(const omni_ctx* ctx, int32_t* rows, int32_t max_rows);
  * configuration each layer shape ran with.  OMNI_EINVAL outside -1..8. */
 omni_status omni_set_conv_kind(omni_ctx* ctx, int32_t kind);
 
+/* E4M3 experiment of the network (BF16 contexts; off by default).  When
+ * enabled, every conv without a residual projection, fused pool or fused head
+ * whose cin and cout are multiples of 128 (the first conv of the deeper
+ * encoder and decoder levels) runs as the E4M3 layer of omni_conv_layer: the
+ * call's activation is quantised with its own scale max|x| / 448 (computed on
+ * the device), the weights with the per-row scales prepared at
+ * omni_load_weights, and the output stays BF16.  Everything else runs as in
+ * BF16.  Graph capture is skipped while it is on.  OMNI_EINVAL on a context
+ * that is not BF16. */
+omni_status omni_set_e4m3(omni_ctx* ctx, int32_t enabled);
+
 /* CUDA graphs.  When enabled, omni_segment_slide captures its post-tiling
  * launch chain (every network batch and the stitches) into a CUDA graph on
  * the second call that sees the same slide pointer, size, scale/class masks,

@@ -27,7 +27,7 @@ EXPORTS = ("omni_create", "omni_destroy", "omni_last_error", "omni_weights_count
            "omni_segment_slide_host", "omni_synth_slide", "omni_conv_layer", "omni_set_timing",
            "omni_get_timing", "omni_last_launch_count", "omni_get_launch_times",
            "omni_tile_slide_noalloc", "omni_backward", "omni_backward_workspace",
-           "omni_set_autotune", "omni_set_graphs", "omni_set_fusion", "omni_get_tuned",
+           "omni_set_autotune", "omni_set_e4m3", "omni_set_graphs", "omni_set_fusion", "omni_get_tuned",
            "omni_stain", "omni_query_slides", "omni_segment_slides", "omni_conv_candidates", "omni_set_conv_kind")
 
 
@@ -110,6 +110,7 @@ def lib() -> C.CDLL:
                                           C.POINTER(TileList), vp]),
         "omni_backward_workspace": (u64, [C.POINTER(Config), i32, i32]),
         "omni_set_autotune": (i32, [vp, i32]),
+        "omni_set_e4m3": (i32, [vp, i32]),
         "omni_set_graphs": (i32, [vp, i32]),
         "omni_set_fusion": (i32, [vp, i32]),
         "omni_get_tuned": (i32, [vp, vp, i32]),

@@ -287,6 +287,11 @@ class Segmenter:
     def set_autotune(self, on: bool = True):
         L.check(self.lib.omni_set_autotune(self.ctx, int(on)), self.ctx)
 
+    def set_e4m3(self, on: bool = True):
+        """E4M3 experiment: the first convs of the deeper levels (cin, cout
+        multiples of 128) run on E4M3 operands (BF16 segmenters only)."""
+        L.check(self.lib.omni_set_e4m3(self.ctx, int(on)), self.ctx)
+
     def set_conv_kind(self, kind: int = -1):
         """Force one tensor-core kernel kind on every layer that has it (-1: default)."""
         L.check(self.lib.omni_set_conv_kind(self.ctx, int(kind)), self.ctx)

@@ -501,7 +501,50 @@ __global__ void k_quant_e4m3(const __nv_bfloat16* __restrict__ x, long long n, f
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     q[i] = __nv_cvt_float_to_fp8(__bfloat162float(x[i]) * inv_scale, __NV_SATFINITE, __NV_E4M3);
 }
+__device__ __forceinline__ float e4m3_amax(const unsigned* amax_bits) {
+  const float m = __uint_as_float(*amax_bits);
+  return m > 0.f ? m : 448.f;        // an all-zero input keeps scale 1
+}
+
+__global__ void k_absmax_strided(const __nv_bfloat16* __restrict__ x, long long npix, int cin, int x_cs,
+                                 int x_co, unsigned* out) {
+  float m = 0.f;
+  const long long n = npix * cin;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long pix = i / cin;
+    m = fmaxf(m, fabsf(__bfloat162float(x[pix * x_cs + x_co + (i - pix * cin)])));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+__global__ void k_quant_strided(const __nv_bfloat16* __restrict__ x, long long npix, int cin, int x_cs, int x_co,
+                                const unsigned* amax_bits, uint8_t* __restrict__ q) {
+  const float inv = 448.f / e4m3_amax(amax_bits);
+  const long long n = npix * cin;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long pix = i / cin;
+    q[i] = __nv_cvt_float_to_fp8(__bfloat162float(x[pix * x_cs + x_co + (i - pix * cin)]) * inv, __NV_SATFINITE,
+                                 __NV_E4M3);
+  }
+}
+
+__global__ void k_e4m3_gamma(const float* __restrict__ gamma, const float* __restrict__ s_w, int cout,
+                             const unsigned* amax_bits, float* __restrict__ out) {
+  const float s_x = e4m3_amax(amax_bits) / 448.f;
+  for (int o = threadIdx.x; o < cout; o += blockDim.x) out[o] = gamma[o] * s_w[o] * s_x;
+}
 }  // namespace
+
+cudaError_t launch_e4m3_activation(const void* x, long long npix, int cin, int x_cs, int x_co,
+                                   unsigned* amax_bits, uint8_t* q, const float* gamma, const float* s_w,
+                                   int cout, float* gamma_out, cudaStream_t st) {
+  const __nv_bfloat16* xb = static_cast<const __nv_bfloat16*>(x);
+  k_absmax_strided<<<1216, 256, 0, st>>>(xb, npix, cin, x_cs, x_co, amax_bits);
+  k_quant_strided<<<1216, 256, 0, st>>>(xb, npix, cin, x_cs, x_co, amax_bits, q);
+  k_e4m3_gamma<<<1, 512, 0, st>>>(gamma, s_w, cout, amax_bits, gamma_out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_absmax_bf16(const void* x, long long n, unsigned* out_bits, cudaStream_t st) {
   k_absmax_bf16<<<1024, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(x), n, out_bits);

@@ -66,6 +66,10 @@ struct ConvLayerW {
   __nv_bfloat16* wp_bf16;        // [cout][cproj]
   float* gamma;                  // [cout]
   float* beta;                   // [cout]
+  // E4M3 experiment (cin, cout multiples of 128): rows [cout][9*cin] of
+  // E4M3(w / s_w[o]) with s_w[o] = max |w[o]| / 448; null where not prepared
+  uint8_t* w_e4m3;
+  float* s_w;
 };
 
 enum ResMode { RES_NONE = 0, RES_TENSOR = 1, RES_RGB = 2 };
@@ -118,6 +122,13 @@ cudaError_t launch_maxpool(int precision, int B, int R, int C, const void* x, in
 // zeroed word) and x quantised to E4M3 bytes with one scale
 cudaError_t launch_absmax_bf16(const void* x, long long n, unsigned* out_bits, cudaStream_t st);
 cudaError_t launch_quant_e4m3(const void* x, long long n, float inv_scale, uint8_t* q, cudaStream_t st);
+// the same inside the network, scale on the device: amax_bits (zeroed by the
+// caller) receives max |x| over npix pixels of cin channels (channel stride
+// x_cs, offset x_co), q the contiguous E4M3(x * 448 / max|x|), and
+// gamma_out[o] = gamma[o] * s_w[o] * max|x| / 448
+cudaError_t launch_e4m3_activation(const void* x, long long npix, int cin, int x_cs, int x_co,
+                                   unsigned* amax_bits, uint8_t* q, const float* gamma, const float* s_w,
+                                   int cout, float* gamma_out, cudaStream_t st);
 cudaError_t launch_upsample(int precision, int B, int R, int C, const void* x, int x_cs,
                             int x_co, void* y, int y_cs, int y_co, cudaStream_t st);
 

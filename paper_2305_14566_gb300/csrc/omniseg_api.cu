@@ -52,6 +52,11 @@ struct omni_ctx {
   // conv autotuner: layer shape -> fastest tensor-core configuration
   bool autotune = false;
   int force_kind = -1;         // >= 0: every layer with a candidate of this kind runs it
+  // E4M3 experiment: eligible convs run on E4M3 operands (omni_set_e4m3);
+  // e8 is their scratch (quantised activation, max |x|, scaled gamma)
+  bool e4m3 = false;
+  uint8_t* e8 = nullptr;
+  size_t e8_bytes = 0;
   std::map<std::array<int, 6>, TcConfig> tuned;
   // CUDA graph of the post-tiling launch chain (network + stitch)
   bool graphs = false;
@@ -405,6 +410,7 @@ void omni_destroy(omni_ctx* ctx) {
   if (ctx->wdev) cudaFree(ctx->wdev);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->d_window) cudaFree(ctx->d_window);
+  if (ctx->e8) cudaFree(ctx->e8);
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   for (cudaEvent_t e : ctx->band_ev) cudaEventDestroy(e);
@@ -450,7 +456,7 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
     if (host.size() < off) host.resize(off + (1 << 20));
     return o;
   };
-  struct Pending { size_t w32, wp32, w16, wp16, g, b; int cin, cout, cproj; };
+  struct Pending { size_t w32, wp32, w16, wp16, g, b, w8, s8; int cin, cout, cproj; bool has8; };
   std::vector<Pending> pend;
   const float* src = blob;
   auto conv = [&](int cin, int cout, int cproj_blob, int cproj_used) {
@@ -495,6 +501,24 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
         w16[(size_t)o * kdim + 27] = hi;
         w16[(size_t)o * kdim + 28] = to_fp16((float)(shift - (double)fp16_value(hi)));
         for (int k = 29; k < 32; ++k) w16[(size_t)o * kdim + k] = 0;
+      }
+    }
+    if (cin % 128 == 0 && cout % 128 == 0) {
+      // E4M3 rows for the experiment: per-row scale s_w = max |w[o]| / 448
+      q.has8 = true;
+      q.w8 = alloc(kdim * cout);
+      q.s8 = alloc((size_t)cout * 4);
+      uint8_t* w8 = host.data() + q.w8;
+      float* s8 = reinterpret_cast<float*>(host.data() + q.s8);
+      for (int o = 0; o < cout; ++o) {
+        float m = 0.f;
+        for (size_t k = 0; k < kdim; ++k) m = std::max(m, std::fabs(src[(size_t)o * kdim + k]));
+        const double sw = m > 0.f ? (double)m / 448.0 : 1.0;
+        for (int ci = 0; ci < cin; ++ci)
+          for (int tap = 0; tap < 9; ++tap)
+            w8[(size_t)o * kdim + (size_t)tap * cin + ci] = __nv_cvt_float_to_fp8(
+                (float)(src[((size_t)o * cin + ci) * 9 + tap] / sw), __NV_SATFINITE, __NV_E4M3);
+        s8[o] = (float)sw;
       }
     }
     src += (size_t)cout * cin * 9;
@@ -583,6 +607,10 @@ omni_status omni_load_weights(omni_ctx* ctx, const float* blob, int64_t n_floats
     if (q.cproj) {
       w.wp_f32 = reinterpret_cast<float*>(d + q.wp32);
       w.wp_bf16 = reinterpret_cast<__nv_bfloat16*>(d + q.wp16);
+    }
+    if (q.has8) {
+      w.w_e4m3 = d + q.w8;
+      w.s_w = reinterpret_cast<float*>(d + q.s8);
     }
     return w;
   };
@@ -803,6 +831,36 @@ omni_status run_conv(omni_ctx* ctx, const ConvArgs& in, cudaStream_t st, int tag
       return fail(ctx, OMNI_EINVAL, "BF16 tensor-core conv does not support R=" + std::to_string(a.R) +
                                         " cin=" + std::to_string(a.cin) + " cout=" + std::to_string(a.cout));
     const int cr = a.res_mode == RES_TENSOR ? a.cr : 0;
+    if (ctx->e4m3 && a.res_mode == RES_NONE && !a.pool && !a.head_theta && a.y && a.w.w_e4m3 &&
+        a.cout <= 512 && (a.R == 16 || a.R == 32 || a.R == 64 || a.R % 128 == 0)) {
+      // E4M3 experiment: quantise this call's activation with its own scale
+      const long long npix = (long long)a.B * a.R * a.R;
+      const size_t need = (size_t)npix * a.cin + 4096;
+      if (ctx->e8_bytes < need) {
+        if (ctx->e8) cudaFree(ctx->e8);
+        ctx->e8 = nullptr;
+        ctx->e8_bytes = 0;
+        OMNI_CU(cudaMalloc(&ctx->e8, need), "E4M3 scratch");
+        ctx->e8_bytes = need;
+      }
+      unsigned* amax = reinterpret_cast<unsigned*>(ctx->e8);
+      float* gq = reinterpret_cast<float*>(ctx->e8 + 256);
+      uint8_t* q = ctx->e8 + 4096;
+      OMNI_CU(cudaMemsetAsync(amax, 0, 4, st), "E4M3 max");
+      OMNI_CU(launch_e4m3_activation(a.x, npix, a.cin, a.x_cs, a.x_co, amax, q, a.w.gamma, a.w.s_w, a.cout, gq, st),
+              "E4M3 activation");
+      ConvArgs a8 = a;
+      a8.x = q; a8.x_cs = a.cin; a8.x_co = 0;
+      a8.w.w_bf16 = reinterpret_cast<__nv_bfloat16*>(a.w.w_e4m3);
+      a8.w.gamma = gq;
+      const TcConfig c8{(long long)a.R * a.R % 256 == 0 ? 8 : 0, a.cout % 256 == 0 ? 256 : 128, 128, 0};
+      e = launch_conv_tc_e4m3(a8, c8, st);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "conv (E4M3)");
+      ctx->launches += 4;
+      if (pooled) *pooled = false;
+      if (headed) *headed = false;
+      return OMNI_OK;
+    }
     TcConfig cfg = tc_default(a.R, a.cin, a.cout, cr);
     if (ctx->force_kind >= 0) {
       // the first candidate of the forced kind (its largest chunk first), if the
@@ -1128,7 +1186,8 @@ omni_status run_graphed(omni_ctx* ctx, const std::vector<uint64_t>& key, cudaStr
                         F&& chain) {
   // the legacy default stream cannot be captured: such calls run eagerly
   const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
-  const bool use_graph = ctx->graphs && !ctx->timing && capturable;
+  // (the E4M3 experiment may allocate its scratch mid-chain: no capture)
+  const bool use_graph = ctx->graphs && !ctx->timing && capturable && !ctx->e4m3;
   if (use_graph && ctx->graph_exec && key == ctx->graph_key) {
     OMNI_CU(cudaGraphLaunch(ctx->graph_exec, st), "graph launch");
     ctx->launches += ctx->graph_launches;
@@ -1824,6 +1883,14 @@ int64_t omni_last_launch_count(const omni_ctx* ctx) { return ctx ? ctx->launches
 omni_status omni_set_autotune(omni_ctx* ctx, int32_t enabled) {
   if (!ctx) return OMNI_EINVAL;
   ctx->autotune = enabled != 0;
+  drop_graph(ctx);
+  return OMNI_OK;
+}
+
+omni_status omni_set_e4m3(omni_ctx* ctx, int32_t enabled) {
+  if (!ctx) return OMNI_EINVAL;
+  if (enabled && ctx->cfg.precision != OMNI_BF16) return fail(ctx, OMNI_EINVAL, "the E4M3 experiment needs a BF16 context");
+  ctx->e4m3 = enabled != 0;
   drop_graph(ctx);
   return OMNI_OK;
 }

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import synth
 from oracle import omniseg_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -109,3 +110,54 @@ def test_e4m3_layer_refuses_unsupported_shapes(api):
     # the context still works
     y2 = _run(api, L, xb, 32, 128, 256, w, g, b, None)
     assert torch.isfinite(y2.float()).all()
+
+
+def _agree_dice(a, b):
+    a = a > 0
+    b = b > 0
+    den = int(a.sum() + b.sum())
+    return float((a == b).mean()), (1.0 if den == 0 else 2.0 * float((a & b).sum()) / den)
+
+
+def test_e4m3_network_against_fp32(api):
+    """The network with the E4M3 experiment on (the first convs of the deeper
+    levels, cin and cout multiples of 128, on 8-bit operands) against the FP32
+    path: labels are reported (the 16-bit bar does not apply) and must agree on
+    most pixels; the logits differ from the BF16 run's, and switching the
+    experiment off gives the BF16 run's bits back.  A non-BF16 segmenter
+    refuses it."""
+    from paper_2305_14566_gb300 import _lib as L
+    w = synth.NEEDLE.with_(H=2048, W=4096, P=256, S=128, median_k=5, max_batch=16)
+    rgb = api.synth_slide(synth.make_spec(2048, 4096, 44, 0.5, "cores", 3))
+    blob = synth.gen_weights(w)
+    seg = api.Segmenter(w, blob, precision=L.BF16)
+
+    def run():
+        o = seg.segment(rgb, logits=True)
+        torch.cuda.synchronize()
+        return {n: {c: t.clone() for c, t in d.items()} for n, d in o.items() if n in ("labels", "logits")}
+
+    ob = run()
+    seg.set_e4m3(True)
+    o8 = run()
+    seg.set_e4m3(False)
+    ob2 = run()
+    seg.close()
+    seg32 = api.Segmenter(w, blob, precision=L.FP32)
+    o = seg32.segment(rgb, logits=True)
+    torch.cuda.synchronize()
+    l32 = {c: t.cpu().numpy() for c, t in o["labels"].items()}
+    seg32.close()
+    for c in ob["logits"]:
+        assert torch.equal(ob2["logits"][c], ob["logits"][c]), c
+        assert not torch.equal(o8["logits"][c], ob["logits"][c]), c
+        ag8, dc8 = _agree_dice(o8["labels"][c].cpu().numpy(), l32[c])
+        agb, dcb = _agree_dice(ob["labels"][c].cpu().numpy(), l32[c])
+        d = (o8["logits"][c] - ob["logits"][c]).abs()
+        print("e4m3 network class %d vs fp32: agree %.6f dice %.5f (bf16: %.6f / %.5f), max|dL| vs bf16 %.3f" %
+              (c, ag8, dc8, agb, dcb, float(d.max())))
+        assert ag8 >= 0.9, (c, ag8)
+    s16 = api.Segmenter(w, blob, precision=L.FP16)
+    with pytest.raises(RuntimeError):
+        s16.set_e4m3(True)
+    s16.close()
