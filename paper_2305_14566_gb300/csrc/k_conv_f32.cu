@@ -506,13 +506,31 @@ __device__ __forceinline__ float e4m3_amax(const unsigned* amax_bits) {
   return m > 0.f ? m : 448.f;        // an all-zero input keeps scale 1
 }
 
+// pixel p's channels c .. c+7 (cin, x_cs, x_co multiples of 8): one 16-byte load
+__device__ __forceinline__ void load8_bf16(const __nv_bfloat16* x, long long v, int c8n, int x_cs, int x_co,
+                                           float f[8]) {
+  const long long pix = v / c8n;
+  const int c = (int)(v - pix * c8n) * 8;
+  const uint4 u = *reinterpret_cast<const uint4*>(x + pix * x_cs + x_co + c);
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 t = __bfloat1622float2(h[k]);
+    f[2 * k] = t.x;
+    f[2 * k + 1] = t.y;
+  }
+}
+
 __global__ void k_absmax_strided(const __nv_bfloat16* __restrict__ x, long long npix, int cin, int x_cs,
                                  int x_co, unsigned* out) {
   float m = 0.f;
-  const long long n = npix * cin;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long pix = i / cin;
-    m = fmaxf(m, fabsf(__bfloat162float(x[pix * x_cs + x_co + (i - pix * cin)])));
+  const int c8n = cin / 8;
+  const long long nv = npix * c8n;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+    float f[8];
+    load8_bf16(x, v, c8n, x_cs, x_co, f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m = fmaxf(m, fabsf(f[k]));
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
@@ -521,11 +539,16 @@ __global__ void k_absmax_strided(const __nv_bfloat16* __restrict__ x, long long 
 __global__ void k_quant_strided(const __nv_bfloat16* __restrict__ x, long long npix, int cin, int x_cs, int x_co,
                                 const unsigned* amax_bits, uint8_t* __restrict__ q) {
   const float inv = 448.f / e4m3_amax(amax_bits);
-  const long long n = npix * cin;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long pix = i / cin;
-    q[i] = __nv_cvt_float_to_fp8(__bfloat162float(x[pix * x_cs + x_co + (i - pix * cin)]) * inv, __NV_SATFINITE,
-                                 __NV_E4M3);
+  const int c8n = cin / 8;
+  const long long nv = npix * c8n;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+    float f[8];
+    load8_bf16(x, v, c8n, x_cs, x_co, f);
+    uint32_t w[2] = {0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)   // channel c + k goes to byte k (little-endian words)
+      w[k >> 2] |= (uint32_t)__nv_cvt_float_to_fp8(f[k] * inv, __NV_SATFINITE, __NV_E4M3) << (8 * (k & 3));
+    *reinterpret_cast<uint2*>(q + v * 8) = make_uint2(w[0], w[1]);     // q is contiguous [npix][cin]
   }
 }
 
@@ -539,6 +562,8 @@ __global__ void k_e4m3_gamma(const float* __restrict__ gamma, const float* __res
 cudaError_t launch_e4m3_activation(const void* x, long long npix, int cin, int x_cs, int x_co,
                                    unsigned* amax_bits, uint8_t* q, const float* gamma, const float* s_w,
                                    int cout, float* gamma_out, cudaStream_t st) {
+  if (cin % 8 || x_cs % 8 || x_co % 8 || reinterpret_cast<uintptr_t>(x) % 16 || reinterpret_cast<uintptr_t>(q) % 8)
+    return cudaErrorInvalidValue;
   const __nv_bfloat16* xb = static_cast<const __nv_bfloat16*>(x);
   k_absmax_strided<<<1216, 256, 0, st>>>(xb, npix, cin, x_cs, x_co, amax_bits);
   k_quant_strided<<<1216, 256, 0, st>>>(xb, npix, cin, x_cs, x_co, amax_bits, q);
