@@ -313,8 +313,9 @@ omni_status omni_synth_slide(const int64_t* ellipses_host, int32_t n_ell, uint64
  * saturating), then runs the per-tap kernel on the E4M3 operands (kind::f8f6f4,
  * FP32 accumulation) with g[o] s_x s_w[o] as the epilogue scale; only those
  * launches are timed.  `config`: kind 0 or 8 (CTA pairs; R * R a multiple of
- * 256), N tile 128 or 256, chunk 128, stages 0; NULL picks kind 8 with the
- * widest N tile that divides cout.
+ * 256), N tile 128 or 256, chunk 128, stages 0; NULL picks kind 8 (kind 0
+ * where R * R is not a multiple of 256) with the widest N tile that divides
+ * cout.
  * Allocates and frees its own temporary weight buffers; synchronises `stream`. */
 omni_status omni_conv_layer(int32_t precision, int32_t B, int32_t R, int32_t cin, int32_t cout,
                             const void* x_dev, int32_t x_cs, int32_t x_co,

@@ -451,7 +451,8 @@ def conv_layer(precision: int, x: torch.Tensor, R: int, cin: int, cout: int, w: 
                r_co=0, y_cs=None, y_co=0, repeat: int = 1, config=None) -> float:
     """One fused conv layer through omni_conv_layer; returns ms per launch.
     config: None (default kernel choice) or a (kind, N tile, chunk, stages)
-    row of conv_candidates."""
+    row of conv_candidates.  precision E4M3 (the 8-bit experiment): x and y
+    BF16, no residual, config (0 or 8, 128 or 256, 128, 0)."""
     B = x.shape[0]
     w = np.ascontiguousarray(w, np.float32)
     g = np.ascontiguousarray(g, np.float32)
